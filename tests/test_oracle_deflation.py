@@ -1,0 +1,88 @@
+"""Pins for oracle.deflation against dense matrices (Algorithms 1 and 2)."""
+import numpy as np
+import pytest
+
+from oracle import deflation, dense, multigrid
+from paper_1909_12234_gb300 import synth
+
+
+@pytest.fixture(scope="module")
+def setup():
+    dims = (4, 4, 2, 2)
+    U = synth.random_su3_links(dims, 0.3, 8)  # kappa(A) ~ 160: restarted GCR converges
+    m0 = -0.4
+    H = multigrid.setup(U, m0, dims, [(2, 2, 2, 2)], [6], seed=3, null_maxit=50)
+    A = H.levels[0].matrix.toarray()
+    Ainv = dense.inverse(A)
+    G5 = dense.gamma5_matrix(64)
+    return dict(H=H, A=A, Ainv=Ainv, G5=G5)
+
+
+def _dense_P(alg, setup):
+    W = alg.T.matrix().toarray()
+    g5c = np.diag(alg.g5)
+    return setup["A"] @ W @ alg.U @ np.diag(1.0 / alg.lam) @ alg.U.conj().T @ g5c @ W.conj().T
+
+
+def test_alg2_projector_identities(setup):
+    H = setup["H"]
+    alg = deflation.Alg2(H.transfers[0], H.matrices[0], 10)
+    P = _dense_P(alg, setup)
+    assert np.abs(P @ P - P).max() < 1e-10 * np.abs(P).max()
+    B = setup["Ainv"] @ (np.eye(P.shape[0]) - P)
+    G5 = setup["G5"]
+    assert np.abs(G5 @ B @ G5 - B.conj().T).max() < 1e-10 * np.abs(B).max()
+    # trace split of Sec. 2.1: t0 + tr(A^{-1}(I - P)) = tr A^{-1}
+    assert abs(alg.t0 + np.trace(B) - np.trace(setup["Ainv"])) < 1e-9 * abs(np.trace(setup["Ainv"]))
+    # t0 equals tr(A^{-1} P) computed densely
+    assert abs(alg.t0 - np.trace(setup["Ainv"] @ P)) < 1e-9 * abs(alg.t0)
+
+
+def test_alg2_vector_and_scalar_forms(setup):
+    H = setup["H"]
+    alg = deflation.Alg2(H.transfers[0], H.matrices[0], 10)
+    rng = np.random.default_rng(4)
+    Z = np.sign(rng.standard_normal((setup["A"].shape[0], 3))) + 0j
+    Ainv = setup["Ainv"]
+    vec = np.einsum("ij,ij->j", Z.conj(), Ainv @ alg.project(H.levels[0].matvec, Z))
+    ZhV, UhKZ = alg.coeffs(Z)
+    scal = np.einsum("ij,ij->j", Z.conj(), Ainv @ Z) - alg.correction(ZhV, UhKZ, alg.k)
+    assert np.allclose(vec, scal, rtol=1e-10)
+    # rank sweep from the stored k x s matrices equals rebuilding at that rank
+    for r in (3, 7):
+        t0r = alg.t0_rank(r)
+        corr = alg.correction(ZhV, UhKZ, r)
+        alg.set_rank(r)
+        assert abs(t0r - alg.t0) < 1e-10 * abs(alg.t0)
+        v = np.einsum("ij,ij->j", Z.conj(), Ainv @ alg.project(H.levels[0].matvec, Z))
+        s = np.einsum("ij,ij->j", Z.conj(), Ainv @ Z) - corr
+        assert np.allclose(v, s, rtol=1e-10)
+    alg.set_rank(alg.k)
+
+
+def test_alg2_smallest_eigvecs(setup):
+    H = setup["H"]
+    alg = deflation.Alg2(H.transfers[0], H.matrices[0], 10)
+    Hd = H.matrices[0].toarray() * alg.g5[None, :]
+    mu_all = np.linalg.eigvalsh(0.5 * (Hd + Hd.conj().T))
+    want = np.sort(np.abs(mu_all))[:10]
+    assert np.allclose(np.abs(alg.mu), want, rtol=1e-10)
+    assert np.allclose(alg.Ubar.conj().T @ alg.Ubar, np.eye(10), atol=1e-12)
+
+
+def test_alg1_identities(setup):
+    A, Ainv, G5 = setup["A"], setup["Ainv"], setup["G5"]
+    mu, Ue = deflation.fine_eigvecs_dense(A, G5, 12)
+    # exact eigenvectors: u^H A^{-1} u = u^H gamma5 u / mu
+    direct = np.sum(np.einsum("ni,nn,ni->i", Ue.conj(), G5, Ue) / mu)
+    xi = 1e-11
+    a1 = deflation.Alg1(Ue, setup["H"].levels[0].matvec, xi)
+    # each solve is within kappa * xi of the exact one (k = 12 solves)
+    bound = 12 * np.linalg.cond(A) * xi * np.max(np.abs(1.0 / mu))
+    assert abs(a1.t0 - direct) < 10 * bound
+    Pp = np.eye(A.shape[0]) - Ue @ Ue.conj().T
+    assert abs(a1.t0 + np.trace(Ainv @ Pp) - np.trace(Ainv)) < 10 * bound
+    # deflating the smallest |mu| lowers the exact variance
+    v0 = dense.exact_variance_real_rademacher(Ainv)
+    v1 = dense.exact_variance_real_rademacher(Ainv @ Pp)
+    assert v1 < v0

@@ -1,0 +1,349 @@
+/*
+ * qdtrace.h -- C ABI of libqdtrace, a single-GPU (sm_103a) library for the
+ * deflated Hutchinson estimator of tr(A^{-1}) for the 4-D Wilson-Dirac
+ * operator A, following "Multigrid deflation for Lattice QCD" (Romero,
+ * Stathopoulos, Orginos, arXiv:1909.12234).
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions (all entry points)
+ * ---------------------------------------------------------------------------
+ * Status:    every function returns QD_OK (0) or a negative qd_status code.
+ *            qd_last_error() returns a message for the last failure on the
+ *            calling host thread.  No C++ exception crosses this ABI.
+ * Streams:   every device computation is issued on the stream given to
+ *            qd_ctx_create().  Functions that return host results
+ *            (statistics, solve stats, eigenvalues) synchronise that stream;
+ *            the others are asynchronous unless stated.
+ * Ownership: pointers passed in are owned by the caller and never freed by
+ *            the library.  Device buffers must stay valid until the stream
+ *            has finished the call.  Opaque handles (qd_ctx, qd_gauge, qd_mg,
+ *            qd_defl) are owned by the library and freed by *_destroy.
+ *            The library allocates its own device work space on first use.
+ * Numbers:   complex numbers are two doubles (re, im), FP64.
+ *
+ * Lattice:   dims = {Lx, Ly, Lz, Lt}, periodic; Lx must be even.
+ *            lexicographic site  lex = x + Lx*(y + Ly*(z + Lz*t));
+ *            parity p = (x+y+z+t) mod 2;
+ *            even-odd site       eo  = p * V/2 + lex/2   (V = Lx Ly Lz Lt).
+ *            Direction mu = 0..3 is x, y, z, t.
+ *
+ * Field layout ("qd layout"), used by every device field argument:
+ *   fine level   : element (eo site i, a, r) at complex offset
+ *                  (i * 12 + a) * nrhs + r,  a = 3*spin + colour,
+ *                  r = right-hand side 0..nrhs-1 (innermost);
+ *   coarse level l>=1: element (coarse lex site i, d, r) at
+ *                  (i * dc + d) * nrhs + r,  dc = 2*nv[l-1]; coarse sites are
+ *                  lexicographic on the coarse lattice dims / block;
+ *                  d < nv is chirality +1, d >= nv chirality -1.
+ * Spin basis: chiral, gamma5 = diag(1, 1, -1, -1).
+ *
+ * The operator (no paper passage writes it out; the paper uses the Wilson
+ * operator and its gamma5-Hermiticity, Sec. 2.1 and Sec. 3):
+ *   (A x)(n) = (4 + m0) x(n)
+ *              - 1/2 sum_mu [(1 - gamma_mu) U_mu(n) x(n+mu)
+ *                            + (1 + gamma_mu) U_mu(n-mu)^H x(n-mu)]
+ *              + i tau gamma5 x(n)          (tau: shift of Sec. 3.2)
+ */
+#ifndef QDTRACE_H
+#define QDTRACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QD_ABI_VERSION 1
+#define QD_MAX_LEVELS 4 /* fine level + up to 3 coarse levels */
+
+typedef enum {
+  QD_OK = 0,
+  QD_ERR_INVALID = -1,       /* bad argument, size or layout */
+  QD_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  QD_ERR_OOM = -3,           /* device allocation failed */
+  QD_ERR_NOT_CONVERGED = -4, /* solver hit maxit; stats are still filled */
+  QD_ERR_NONFINITE = -5,     /* NaN/Inf met in an input or a reduction */
+  QD_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+  QD_ERR_INTERNAL = -7
+} qd_status;
+
+typedef struct qd_ctx qd_ctx;
+typedef struct qd_gauge qd_gauge;
+typedef struct qd_mg qd_mg;
+typedef struct qd_defl qd_defl;
+
+/* ------------------------------------------------------------------------ */
+/* Context and errors                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* ABI version of the loaded library (QD_ABI_VERSION it was built with). */
+int qd_abi_version(void);
+
+/* Message of the last failure on this host thread ("" if none). */
+const char* qd_last_error(void);
+
+/* Create a context on CUDA device `device`, issuing work on `stream`
+ * (a cudaStream_t; NULL = legacy default stream). */
+int qd_ctx_create(qd_ctx** ctx, int device, void* stream);
+int qd_ctx_destroy(qd_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Geometry (Sec. 1 red-black partitioning; even-odd layout)                 */
+/* ------------------------------------------------------------------------ */
+
+/* Host-only: eo_of_lex[lex] = even-odd index of every site (V entries,
+ * caller-allocated host array).  QD_ERR_INVALID for odd Lx or dims < 1. */
+int qd_eo_index(const int dims[4], int64_t* eo_of_lex);
+
+/* ------------------------------------------------------------------------ */
+/* Gauge field                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Upload links.  links_host: host array [V][4][3][3] complex, lexicographic
+ * sites, U_mu(n)[row][col] on the link n -> n + mu.  Copied; the caller may
+ * free it on return.  Synchronous. */
+int qd_gauge_create(qd_ctx* ctx, const int dims[4], const double* links_host,
+                    qd_gauge** gauge);
+int qd_gauge_destroy(qd_gauge* gauge);
+
+/* Reorder fields between the canonical host order [r][V lex][12] (each
+ * right-hand side a contiguous lexicographic vector) and the qd layout.
+ * to_qd != 0: canon -> qd; 0: qd -> canon.  Both are device buffers of
+ * 12 V nrhs complex numbers and must not overlap. */
+int qd_field_reorder(qd_ctx* ctx, const qd_gauge* gauge, int nrhs, int to_qd,
+                     const double* in, double* out);
+
+/* ------------------------------------------------------------------------ */
+/* a1: Rademacher noise (Sec. 1, Eq. 1: x_j with entries +-1)                */
+/* ------------------------------------------------------------------------ */
+
+/* out (qd layout, nrhs columns): real +-1 noise for global samples
+ * sample_offset .. sample_offset+nrhs-1.  Dof i = 12*lex + a of sample j is
+ * bit (i mod 128) of Philox4x32-10(counter = (i/128, j, 0, 0),
+ * key = (seed & 0xffffffff, seed >> 32)) (word (i mod 128)/32, bit i mod 32);
+ * bit 0 -> +1, bit 1 -> -1; imaginary part 0.  Bit-exact on any device. */
+int qd_rademacher(qd_ctx* ctx, const qd_gauge* gauge, uint64_t seed,
+                  int64_t sample_offset, int nrhs, double* out);
+
+/* ------------------------------------------------------------------------ */
+/* a2: Wilson-Dirac operator (Sec. 2 two-grid method acts with A; Sec. 3.2   */
+/* shift i tau gamma5)                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* out = A in (dagger = 0) or A^H in (dagger != 0), nrhs columns, qd layout.
+ * in and out must not overlap.  Asynchronous. */
+int qd_dirac_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau,
+                   int dagger, int nrhs, const double* in, double* out);
+
+/* ------------------------------------------------------------------------ */
+/* a10: adaptive multigrid setup (Sec. 2 "adaptive setup" and "blocking";    */
+/* Sec. 4 tolerance 1e-2 / 200 iterations; Algorithm 2 step 1)              */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int nlevels;                  /* coarse levels to build, 1..QD_MAX_LEVELS-1 */
+  int block[QD_MAX_LEVELS][4];  /* block[l] = aggregate shape on level l */
+  int nv[QD_MAX_LEVELS];        /* null vectors on level l (coarse dof 2 nv) */
+  double null_tol;              /* relative residual of A y = 0 (1e-2) */
+  int null_maxit;               /* minimal-residual steps cap (200) */
+  uint64_t seed;                /* level l uses seed + l for its starts */
+  int smoother_steps;           /* minimal-residual post-smoothing steps */
+  double coarse_tol;            /* relative tolerance of coarse GCR */
+  int coarse_maxit;             /* iteration cap of coarse GCR */
+  int coarse_restart;           /* restart length of coarse GCR */
+} qd_mg_params;
+
+/* Fill `p` with this library's defaults (1 level, 2^4 blocks, nv 12,
+ * 1e-2 / 200, 4 smoothing steps, coarse GCR to 0.1 / 256 / 16). */
+void qd_mg_params_default(qd_mg_params* p);
+
+/* Build the hierarchy for A(m0, tau).  Null-vector starts are complex
+ * +-1 +-i signs: re from bit 2(i mod 64), im from bit 2(i mod 64)+1 of
+ * Philox(counter = (i/64, v, 1, 0), key = seed + level) with i the dof index
+ * lex_site * dof + d of that level.  injected_null (nullable): device array
+ * of the level-0 null vectors in qd layout with nrhs = nv[0]; when given the
+ * level-0 iteration is skipped (used to compare implementations).
+ * Synchronous. */
+int qd_mg_setup(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau,
+                const qd_mg_params* params, const double* injected_null,
+                qd_mg** mg);
+int qd_mg_destroy(qd_mg* mg);
+
+/* Sizes of level l (0 = fine): dims[4], dofs per site and number of sites.
+ * Also the minimal-residual steps each level-l null vector took (host array
+ * of nv[l] ints, nullable; zeros for injected vectors). */
+int qd_mg_level_info(const qd_mg* mg, int level, int dims[4], int* dof,
+                     int64_t* nsites, int* null_steps);
+
+/* ------------------------------------------------------------------------ */
+/* a3: prolongation W c and restriction W^H x (Sec. 2 two-grid step 1)       */
+/* ------------------------------------------------------------------------ */
+
+/* fine (level l, qd layout) = W_l coarse (level l+1).  Asynchronous. */
+int qd_prolongate(qd_mg* mg, int level, int nrhs, const double* coarse,
+                  double* fine);
+/* coarse (level l+1) = W_l^H fine (level l).  Asynchronous. */
+int qd_restrict(qd_mg* mg, int level, int nrhs, const double* fine,
+                double* coarse);
+
+/* ------------------------------------------------------------------------ */
+/* a4: coarse operator C_l = W^H A W (Sec. 2, "V^H A V")                     */
+/* ------------------------------------------------------------------------ */
+
+/* out = C_level in, level >= 1, 9-point block stencil.  Asynchronous. */
+int qd_coarse_apply(qd_mg* mg, int level, int nrhs, const double* in,
+                    double* out);
+
+/* ------------------------------------------------------------------------ */
+/* a5/a6: solves A x = b to ||b - A x|| <= tol ||b|| (Sec. 1, inexact solve; */
+/* Sec. 2 multigrid preconditioning, GCR)                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int iterations;                /* max outer iterations over the columns */
+  int converged;                 /* columns whose TRUE residual met tol */
+  double max_true_rel_residual;  /* max over columns of ||b-Ax||/||b|| */
+  int* iters_per_rhs;            /* optional host [nrhs] */
+  double* true_rel_residual;     /* optional host [nrhs] */
+} qd_solve_stats;
+
+/* Flexible restarted GCR on A(m0, tau), right-preconditioned by the V-cycle
+ * of `mg` (nullable: unpreconditioned).  With mg the operator is mg's.
+ * x is overwritten (zero initial guess).  Returns QD_ERR_NOT_CONVERGED if a
+ * column missed tol within maxit (stats filled).  Synchronous. */
+int qd_solve(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, double m0,
+             double tau, int nrhs, const double* b, double* x, double tol,
+             int maxit, int restart, qd_solve_stats* stats);
+
+/* ------------------------------------------------------------------------ */
+/* a7: deflation space (Algorithm 1 step 1; Algorithm 2 steps 1-4)           */
+/* ------------------------------------------------------------------------ */
+
+enum {
+  QD_DEFL_EIG_ORTHO = 1,  /* Algorithm 1: k eigenvectors of A gamma5 */
+  QD_DEFL_MG_OBLIQUE = 2  /* Algorithm 2: k eigenvectors of C gamma5^W */
+};
+
+typedef struct {
+  int kind;          /* QD_DEFL_* */
+  int k;             /* rank of the deflation space */
+  int guard;         /* extra subspace-iteration vectors (>= 0) */
+  double eig_tol;    /* stop when ||H u - mu u|| <= eig_tol |mu| for all k */
+  double solve_tol;  /* xi of the inner solves H^{-1} */
+  int maxit;         /* subspace iterations cap */
+  uint64_t seed;     /* starting block: Philox random starts, this key */
+} qd_defl_params;
+
+void qd_defl_params_default(qd_defl_params* p);
+
+/* Build a deflation space for A(m0, tau) (tau taken from mg for kind 2).
+ * kind 1 needs mg only as the solver's preconditioner (nullable); kind 2
+ * needs mg (level 1 is used).  injected_basis (nullable device array):
+ * kind 2: U_bar in level-1 qd layout with nrhs = k; kind 1: U in level-0 qd
+ * layout with nrhs = k (orthonormal columns); skips the eigensolver.
+ * Synchronous. */
+int qd_defl_create(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, double m0,
+                   double tau, const qd_defl_params* params,
+                   const double* injected_basis, qd_defl** defl);
+int qd_defl_destroy(qd_defl* defl);
+
+/* Set the active rank r <= k (Algorithm 2 step 3 on the leading r columns;
+ * Algorithm 1 keeps the first r vectors) and return t0 (complex, 2 doubles).
+ * Synchronous. */
+int qd_defl_set_rank(qd_defl* defl, int rank, double* t0);
+
+/* Host copies: eigenvalues mu of the eigensolve (k, nullable), Lambda of
+ * the active rank (rank, nullable), iterations taken (nullable). */
+int qd_defl_info(const qd_defl* defl, double* mu, double* lambda,
+                 int* iterations);
+
+/* ------------------------------------------------------------------------ */
+/* a8: deflation projection (Algorithm 1 step 3, Algorithm 2 step 5,         */
+/* Sec. 2.2 a-posteriori filtering)                                          */
+/* ------------------------------------------------------------------------ */
+
+/* out = (I - P) z on the fine level, nrhs columns, qd layout:
+ *   kind 2: P = A W U Lambda^{-1} U^H gamma5^W W^H (K = gamma5 projector);
+ *   kind 1: P = U U^H.
+ * Uses the active rank.  Asynchronous. */
+int qd_deflate_project(qd_defl* defl, int nrhs, const double* z, double* out);
+
+/* Sec. 2.2 matrices for an a-posteriori rank sweep (kind 2 only), host
+ * outputs, row-major complex: ZhV [nrhs][k] = Z^H W U_bar and
+ * UhKZ [k][nrhs] = U_bar^H gamma5^W W^H Z.  Synchronous. */
+int qd_deflate_coeffs(qd_defl* defl, int nrhs, const double* z, double* ZhV,
+                      double* UhKZ);
+
+/* ------------------------------------------------------------------------ */
+/* a9: deflated Hutchinson estimator (Eq. 1; Algorithms 1 and 2)             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  uint64_t seed;          /* noise key */
+  int64_t sample_offset;  /* first global sample index */
+  int nsamples;           /* s, solved together as one multi-RHS batch */
+  double tol;             /* xi */
+  int maxit;              /* outer GCR iteration cap */
+  int restart;            /* outer GCR restart length */
+} qd_trace_params;
+
+typedef struct {
+  double t0[2];            /* deterministic part (0 without deflation) */
+  double mean[2];          /* (1/s) sum_j t_j */
+  double estimate[2];      /* t0 + mean */
+  double var;              /* (1/(s-1)) sum |t_j - mean|^2 */
+  double var_re;           /* same for Re t_j */
+  double stderr_mean;      /* sqrt(var / s) */
+  double var_jackknife_err;/* delete-one jackknife error of var */
+  int nsamples;
+  int iterations;          /* outer GCR iterations (max over samples) */
+  double max_true_rel_residual;
+  double* t_samples;       /* optional host [nsamples][2]: t_j */
+  double* ZhV;             /* optional host [nsamples][k][2] (kind 2) */
+  double* UhKZ;            /* optional host [k][nsamples][2] (kind 2) */
+} qd_trace_result;
+
+/* One batch of the deflated estimator: z_j = Rademacher(seed, offset + j),
+ * b_j = (I - P) z_j (defl nullable: P = 0), x_j = A^{-1}_xi b_j by qd_solve
+ * with mg (nullable), t_j = z_j^H x_j; statistics accumulated on the device
+ * with compensated FP64 sums in a fixed order.  Synchronous.  Returns
+ * QD_ERR_NOT_CONVERGED (result filled) if any solve missed tol. */
+int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg,
+                        qd_defl* defl, double m0, double tau,
+                        const qd_trace_params* params,
+                        qd_trace_result* result);
+
+/* ------------------------------------------------------------------------ */
+/* Kernel timing (measurement support; the paper has no counterpart)         */
+/* ------------------------------------------------------------------------ */
+
+/* Kernel kinds: operator x precision. */
+enum {
+  QD_PROF_WILSON_F64 = 0,   /* a2 stencil, FP64 */
+  QD_PROF_WILSON_F32 = 1,   /* a2 stencil, FP32 */
+  QD_PROF_COARSE_F64 = 2,   /* a4 coarse stencil, FP64 */
+  QD_PROF_COARSE_F32 = 3,   /* a4 coarse stencil, FP32 */
+  QD_PROF_PROLONG_F64 = 4,  /* a3 W c, FP64 */
+  QD_PROF_PROLONG_F32 = 5,
+  QD_PROF_RESTRICT_F64 = 6, /* a3 W^H x, FP64 */
+  QD_PROF_RESTRICT_F32 = 7,
+  QD_PROF_NKINDS = 8
+};
+
+/* enable != 0: record a CUDA event pair on the context stream around every
+ * launch of the kinds above, with the launch's algorithmic flops and bytes;
+ * enable == 0: stop recording.  Recording adds host work per launch. */
+int qd_prof_enable(qd_ctx* ctx, int enable);
+
+/* Totals for one kind since the last reset: launches, summed device time
+ * (ms) of those launches, algorithmic flops and bytes.  Synchronises the
+ * stream.  reset != 0 clears the totals of that kind afterwards. */
+int qd_prof_read(qd_ctx* ctx, int kind, int64_t* launches, double* ms,
+                 double* flops, double* bytes, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDTRACE_H */

@@ -1,0 +1,231 @@
+// Batched level-1 kernels on multi-RHS fields (RHS innermost).  Every
+// right-hand side is an independent vector: reductions return one value per
+// column.  Reductions are deterministic: a fixed grid writes per-block
+// partial sums (fixed tree order inside a block) and a second kernel adds the
+// partials in block order.
+#pragma once
+
+#include "qd_internal.cuh"
+
+namespace qd {
+namespace blas {
+
+constexpr int kThreads = 256;
+constexpr int kDotK = 8;  // dot products per reduction launch
+
+// Thread tile for an (n rows) x (nrhs columns) sweep: RT lanes along the
+// columns (coalesced), RY = 256 / RT rows per block.
+struct Sweep {
+  int RT, RY;
+  dim3 block, grid;
+};
+
+inline Sweep sweep(int64_t n, int nrhs, int max_row_blocks = 4 * kNumSMs) {
+  Sweep s;
+  int rt = 1;
+  while (rt < nrhs && rt < 32) rt <<= 1;
+  s.RT = rt;
+  s.RY = kThreads / rt;
+  int gy = div_up(nrhs, rt);
+  int64_t want = (n + s.RY - 1) / s.RY;
+  int cap = max_row_blocks / gy;
+  if (cap < 1) cap = 1;
+  int gx = (int)(want < cap ? want : cap);
+  if (gx < 1) gx = 1;
+  s.block = dim3(s.RT, s.RY);
+  s.grid = dim3(gx, gy);
+  return s;
+}
+
+// partials[(blk*K + k)*nrhs + r] = sum over this block's rows of conj(X_k) Y_k
+template <class C>
+__global__ void k_dots(int K, int64_t n, int nrhs, const C* __restrict__ X, int64_t xs,
+                       const C* __restrict__ Y, int64_t ys, cplx* __restrict__ partials) {
+  typedef typename CTraits<C>::R R;
+  __shared__ cplx sm[kDotK][kThreads];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r = blockIdx.y * blockDim.x + tx;
+  C acc[kDotK];
+#pragma unroll
+  for (int k = 0; k < kDotK; ++k) acc[k] = mk<C>((R)0, (R)0);
+  if (r < nrhs) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.y + ty; i < n; i += (int64_t)gridDim.x * blockDim.y) {
+      const int64_t e = i * nrhs + r;
+      if (ys == 0) {
+        const C y = Y[e];
+#pragma unroll
+        for (int k = 0; k < kDotK; ++k)
+          if (k < K) cfmac(acc[k], X[k * xs + e], y);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kDotK; ++k)
+          if (k < K) cfmac(acc[k], X[k * xs + e], Y[k * ys + e]);
+      }
+    }
+  }
+  const int t = ty * blockDim.x + tx;
+#pragma unroll
+  for (int k = 0; k < kDotK; ++k) sm[k][t] = mkc((double)acc[k].x, (double)acc[k].y);
+  __syncthreads();
+  for (int h = blockDim.y / 2; h > 0; h >>= 1) {
+    if (ty < h) {
+#pragma unroll
+      for (int k = 0; k < kDotK; ++k)
+        if (k < K) sm[k][t] = cadd(sm[k][t], sm[k][t + h * blockDim.x]);
+    }
+    __syncthreads();
+  }
+  if (ty == 0 && r < nrhs) {
+    for (int k = 0; k < K; ++k) partials[((int64_t)blockIdx.x * K + k) * nrhs + r] = sm[k][tx];
+  }
+}
+
+// out[k*nrhs + r] = sum_b partials[b][k][r] in block order
+static __global__ void k_dots_final(int K, int nrhs, int nblk, const cplx* __restrict__ partials,
+                             cplx* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= K * nrhs) return;
+  const int k = idx / nrhs, r = idx - k * nrhs;
+  cplx s = mkc(0.0, 0.0);
+  for (int b = 0; b < nblk; ++b) s = cadd(s, partials[((int64_t)b * K + k) * nrhs + r]);
+  out[idx] = s;
+}
+
+// out[k][r] = <X_k, Y_k>_r for k < K (any K), X_k = X + k*xs, Y_k = Y + k*ys
+// (strides in complex elements; ys may be 0).  out: device cplx [K][nrhs].
+template <class C>
+void dots(qd_ctx& ctx, int K, int64_t n, int nrhs, const C* X, int64_t xs, const C* Y, int64_t ys,
+          cplx* out) {
+  if (K <= 0) return;
+  for (int k0 = 0; k0 < K; k0 += kDotK) {
+    const int kk = (K - k0) < kDotK ? (K - k0) : kDotK;
+    Sweep s = sweep(n, nrhs);
+    const size_t need = (size_t)s.grid.x * kk * nrhs * sizeof(cplx);
+    ctx.red_partials.resize(need);
+    k_dots<C><<<s.grid, s.block, 0, ctx.stream>>>(kk, n, nrhs, X + k0 * xs, xs, Y + k0 * ys, ys,
+                                                   ctx.red_partials.as<cplx>());
+    QD_LAUNCH_CHECK();
+    const int tot = kk * nrhs;
+    k_dots_final<<<div_up(tot, 128), 128, 0, ctx.stream>>>(kk, nrhs, s.grid.x,
+                                                            ctx.red_partials.as<cplx>(),
+                                                            out + (int64_t)k0 * nrhs);
+    QD_LAUNCH_CHECK();
+  }
+}
+
+// Y_j[i,r] -= sum_k coef[k][r] X_k[i,r] for (Y, X) and, when Y2 != null,
+// (Y2, X2) with the same coefficients; columns with active[r] == 0 untouched.
+template <class C>
+__global__ void k_multi_axpy(int K, int64_t n, int nrhs, const cplx* __restrict__ coef,
+                             const int* __restrict__ active, const C* __restrict__ X, int64_t xs,
+                             C* __restrict__ Y, const C* __restrict__ X2, C* __restrict__ Y2) {
+  typedef typename CTraits<C>::R R;
+  const int64_t tot = n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % nrhs);
+    if (active && !active[r]) continue;
+    C y = Y[e];
+    C y2 = Y2 ? Y2[e] : mk<C>((R)0, (R)0);
+    for (int k = 0; k < K; ++k) {
+      const cplx cd = coef[(int64_t)k * nrhs + r];
+      const C c = mk<C>((R)(-cd.x), (R)(-cd.y));
+      cfma(y, c, X[k * xs + e]);
+      if (Y2) cfma(y2, c, X2[k * xs + e]);
+    }
+    Y[e] = y;
+    if (Y2) Y2[e] = y2;
+  }
+}
+
+inline int grid_1d(int64_t tot, int threads = kThreads) {
+  int64_t b = (tot + threads - 1) / threads;
+  const int64_t cap = 32LL * kNumSMs;
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+template <class C>
+void multi_axpy(qd_ctx& ctx, int K, int64_t n, int nrhs, const cplx* coef, const int* active,
+                const C* X, int64_t xs, C* Y, const C* X2 = nullptr, C* Y2 = nullptr) {
+  if (K <= 0) return;
+  k_multi_axpy<C><<<grid_1d(n * nrhs), kThreads, 0, ctx.stream>>>(K, n, nrhs, coef, active, X, xs, Y,
+                                                                 X2, Y2);
+  QD_LAUNCH_CHECK();
+}
+
+// y = a x + b y with per-column complex a, b (device arrays; nullptr a -> 1,
+// nullptr b -> 0).  Columns with active[r] == 0 untouched.
+template <class C>
+__global__ void k_axpby(int64_t n, int nrhs, const cplx* __restrict__ a, const C* __restrict__ x,
+                        const cplx* __restrict__ b, C* __restrict__ y, const int* __restrict__ active) {
+  typedef typename CTraits<C>::R R;
+  const int64_t tot = n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % nrhs);
+    if (active && !active[r]) continue;
+    C v = x[e];
+    if (a) v = cmul(mk<C>((R)a[r].x, (R)a[r].y), v);
+    if (b) cfma(v, mk<C>((R)b[r].x, (R)b[r].y), y[e]);
+    y[e] = v;
+  }
+}
+
+template <class C>
+void axpby(qd_ctx& ctx, int64_t n, int nrhs, const cplx* a, const C* x, const cplx* b, C* y,
+           const int* active = nullptr) {
+  k_axpby<C><<<grid_1d(n * nrhs), kThreads, 0, ctx.stream>>>(n, nrhs, a, x, b, y, active);
+  QD_LAUNCH_CHECK();
+}
+
+// z = x - y (elementwise, all columns)
+template <class C>
+__global__ void k_sub(int64_t tot, const C* x, const C* y, C* z) {  // z may alias x or y
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x)
+    z[e] = csub(x[e], y[e]);
+}
+template <class C> void sub(qd_ctx& ctx, int64_t tot, const C* x, const C* y, C* z) {
+  k_sub<C><<<grid_1d(tot), kThreads, 0, ctx.stream>>>(tot, x, y, z);
+  QD_LAUNCH_CHECK();
+}
+
+// y += x (elementwise)
+template <class C>
+__global__ void k_add(int64_t tot, const C* __restrict__ x, C* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = cadd(y[e], x[e]);
+}
+template <class C> void add(qd_ctx& ctx, int64_t tot, const C* x, C* y) {
+  k_add<C><<<grid_1d(tot), kThreads, 0, ctx.stream>>>(tot, x, y);
+  QD_LAUNCH_CHECK();
+}
+
+// gamma5 on a field with `dof` per site: negate the second half of each site.
+template <class C>
+__global__ void k_gamma5(int64_t nsites, int dof, int nrhs, const C* __restrict__ x, C* __restrict__ y) {
+  const int64_t tot = nsites * dof * nrhs;
+  const int half = dof / 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int d = (int)((e / nrhs) % dof);
+    C v = x[e];
+    if (d >= half) { v.x = -v.x; v.y = -v.y; }
+    y[e] = v;
+  }
+}
+template <class C> void gamma5(qd_ctx& ctx, int64_t nsites, int dof, int nrhs, const C* x, C* y) {
+  k_gamma5<C><<<grid_1d(nsites * dof * nrhs), kThreads, 0, ctx.stream>>>(nsites, dof, nrhs, x, y);
+  QD_LAUNCH_CHECK();
+}
+
+template <class C> void copy(qd_ctx& ctx, int64_t tot, const C* x, C* y) {
+  QD_CUDA(cudaMemcpyAsync(y, x, tot * sizeof(C), cudaMemcpyDeviceToDevice, ctx.stream));
+}
+template <class C> void zero(qd_ctx& ctx, int64_t tot, C* y) {
+  QD_CUDA(cudaMemsetAsync(y, 0, tot * sizeof(C), ctx.stream));
+}
+
+}  // namespace blas
+}  // namespace qd

@@ -1,0 +1,479 @@
+// extern "C" entry points of libqdtrace (declared in include/qdtrace.h).
+// Every function catches internal errors and returns a qd_status code; the
+// message is kept per host thread for qd_last_error().
+#include <cmath>
+
+#include "blas.cuh"
+#include "defl.cuh"
+
+
+static thread_local std::string g_last_error;
+
+template <class F> static int guarded(F&& f) {
+  try {
+    g_last_error.clear();
+    f();
+    return QD_OK;
+  } catch (const qd::Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return QD_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return QD_ERR_INTERNAL;
+  } catch (...) {
+    g_last_error = "unknown error";
+    return QD_ERR_INTERNAL;
+  }
+}
+
+#define NONNULL(p) QD_REQUIRE((p) != nullptr, #p " must not be NULL")
+
+static void set_device(const qd_ctx* c) { QD_CUDA(cudaSetDevice(c->device)); }
+
+extern "C" {
+
+int qd_abi_version(void) { return QD_ABI_VERSION; }
+
+const char* qd_last_error(void) { return g_last_error.c_str(); }
+
+int qd_ctx_create(qd_ctx** ctx, int device, void* stream) {
+  return guarded([&] {
+    NONNULL(ctx);
+    int ndev = 0;
+    QD_CUDA(cudaGetDeviceCount(&ndev));
+    QD_REQUIRE(device >= 0 && device < ndev, "no such CUDA device");
+    QD_CUDA(cudaSetDevice(device));
+    std::unique_ptr<qd_ctx> c(new qd_ctx());
+    c->device = device;
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    QD_CUDA(cudaMallocHost(&c->host_pinned, 64 * sizeof(int)));
+    *ctx = c.release();
+  });
+}
+
+int qd_ctx_destroy(qd_ctx* ctx) {
+  return guarded([&] {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    for (auto& p : ctx->prof_pending) {
+      cudaEventDestroy(p.e0);
+      cudaEventDestroy(p.e1);
+    }
+    for (auto e : ctx->prof_pool) cudaEventDestroy(e);
+    delete ctx;
+  });
+}
+
+int qd_eo_index(const int dims[4], int64_t* eo_of_lex) {
+  return guarded([&] {
+    NONNULL(dims);
+    NONNULL(eo_of_lex);
+    int64_t V = 1;
+    for (int m = 0; m < 4; ++m) {
+      QD_REQUIRE(dims[m] >= 1, "lattice extents must be >= 1");
+      V *= dims[m];
+    }
+    QD_REQUIRE(dims[0] % 2 == 0, "even-odd ordering needs an even Lx");
+    for (int64_t l = 0; l < V; ++l) {
+      const int64_t x = l % dims[0], y = (l / dims[0]) % dims[1];
+      const int64_t z = (l / ((int64_t)dims[0] * dims[1])) % dims[2];
+      const int64_t t = l / ((int64_t)dims[0] * dims[1] * dims[2]);
+      eo_of_lex[l] = ((x + y + z + t) & 1) * (V / 2) + l / 2;
+    }
+  });
+}
+
+int qd_gauge_create(qd_ctx* ctx, const int dims[4], const double* links_host, qd_gauge** gauge) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(dims);
+    NONNULL(links_host);
+    NONNULL(gauge);
+    set_device(ctx);
+    std::unique_ptr<qd_gauge> g(new qd_gauge());
+    g->ctx = ctx;
+    g->geo.build(dims, true);
+    qd::gauge_import(*ctx, *g, links_host);
+    *gauge = g.release();
+  });
+}
+
+int qd_gauge_destroy(qd_gauge* gauge) {
+  return guarded([&] {
+    if (!gauge) return;
+    cudaStreamSynchronize(gauge->ctx->stream);
+    delete gauge;
+  });
+}
+
+int qd_field_reorder(qd_ctx* ctx, const qd_gauge* gauge, int nrhs, int to_qd, const double* in, double* out) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    set_device(ctx);
+    qd::field_reorder(*ctx, gauge->geo, nrhs, to_qd != 0, reinterpret_cast<const qd::cplx*>(in),
+                      reinterpret_cast<qd::cplx*>(out));
+  });
+}
+
+int qd_rademacher(qd_ctx* ctx, const qd_gauge* gauge, uint64_t seed, int64_t sample_offset, int nrhs, double* out) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    set_device(ctx);
+    qd::rademacher_fill(*ctx, gauge->geo, seed, sample_offset, nrhs, reinterpret_cast<qd::cplx*>(out));
+  });
+}
+
+int qd_dirac_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau, int dagger, int nrhs,
+                   const double* in, double* out) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    QD_REQUIRE(std::isfinite(m0) && std::isfinite(tau), "m0 and tau must be finite");
+    set_device(ctx);
+    qd::wilson_apply<qd::cplx>(*ctx, gauge->geo, gauge->links.as<qd::cplx>(), m0, tau, dagger != 0,
+                               reinterpret_cast<const qd::cplx*>(in), reinterpret_cast<qd::cplx*>(out), nrhs);
+  });
+}
+
+void qd_mg_params_default(qd_mg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nlevels = 1;
+  for (int l = 0; l < QD_MAX_LEVELS; ++l) {
+    for (int m = 0; m < 4; ++m) p->block[l][m] = 2;
+    p->nv[l] = 12;
+  }
+  p->null_tol = 1e-2;
+  p->null_maxit = 200;
+  p->seed = 7;
+  p->smoother_steps = 4;
+  p->coarse_tol = 0.1;
+  p->coarse_maxit = 256;
+  p->coarse_restart = 16;
+}
+
+int qd_mg_setup(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau, const qd_mg_params* params,
+                const double* injected_null, qd_mg** mg) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(params);
+    NONNULL(mg);
+    set_device(ctx);
+    std::unique_ptr<qd_mg> h(new qd_mg());
+    h->ctx = ctx;
+    h->gauge = gauge;
+    h->m0 = m0;
+    h->tau = tau;
+    h->p = *params;
+    QD_REQUIRE(params->coarse_restart >= 1 && params->coarse_maxit >= 1, "coarse GCR parameters must be >= 1");
+    QD_REQUIRE(params->smoother_steps >= 0 && params->null_maxit >= 0, "step counts must be >= 0");
+    qd::mg_build(*h, injected_null);
+    *mg = h.release();
+  });
+}
+
+int qd_mg_destroy(qd_mg* mg) {
+  return guarded([&] {
+    if (!mg) return;
+    cudaStreamSynchronize(mg->ctx->stream);
+    delete mg;
+  });
+}
+
+int qd_mg_level_info(const qd_mg* mg, int level, int dims[4], int* dof, int64_t* nsites, int* null_steps) {
+  return guarded([&] {
+    NONNULL(mg);
+    QD_REQUIRE(level >= 0 && level <= mg->nlevels, "level out of range");
+    const qd::LevelGeom& g = mg->geom(level);
+    if (dims)
+      for (int m = 0; m < 4; ++m) dims[m] = g.dims[m];
+    if (dof) *dof = mg->dof(level);
+    if (nsites) *nsites = g.nsites;
+    if (null_steps && level < mg->nlevels)
+      for (int v = 0; v < mg->T[level]->nv; ++v) null_steps[v] = mg->T[level]->null_steps[v];
+  });
+}
+
+int qd_prolongate(qd_mg* mg, int level, int nrhs, const double* coarse, double* fine) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(coarse);
+    NONNULL(fine);
+    QD_REQUIRE(level >= 0 && level < mg->nlevels, "level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    set_device(mg->ctx);
+    const qd::Transfer& T = *mg->T[level];
+    qd::prolongate<qd::cplx>(*mg->ctx, T, T.W.as<qd::cplx>(), reinterpret_cast<const qd::cplx*>(coarse),
+                             reinterpret_cast<qd::cplx*>(fine), nrhs);
+  });
+}
+
+int qd_restrict(qd_mg* mg, int level, int nrhs, const double* fine, double* coarse) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(coarse);
+    NONNULL(fine);
+    QD_REQUIRE(level >= 0 && level < mg->nlevels, "level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    set_device(mg->ctx);
+    const qd::Transfer& T = *mg->T[level];
+    qd::restrict_<qd::cplx>(*mg->ctx, T, T.W.as<qd::cplx>(), reinterpret_cast<const qd::cplx*>(fine),
+                            reinterpret_cast<qd::cplx*>(coarse), nrhs);
+  });
+}
+
+int qd_coarse_apply(qd_mg* mg, int level, int nrhs, const double* in, double* out) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(level >= 1 && level <= mg->nlevels, "coarse level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    set_device(mg->ctx);
+    const qd::CoarseLevel& lv = *mg->L[level - 1];
+    qd::coarse_apply<qd::cplx>(*mg->ctx, lv, lv.Cm.as<qd::cplx>(), reinterpret_cast<const qd::cplx*>(in),
+                               reinterpret_cast<qd::cplx*>(out), nrhs);
+  });
+}
+
+int qd_solve(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, double m0, double tau, int nrhs, const double* b,
+             double* x, double tol, int maxit, int restart, qd_solve_stats* stats) {
+  int not_conv = 0;
+  int rc = guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(b);
+    NONNULL(x);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(tol > 0.0 && maxit >= 1, "tol must be > 0 and maxit >= 1");
+    set_device(ctx);
+    qd::SolveInfo info;
+    qd::solve(*ctx, *gauge, mg, m0, tau, nrhs, reinterpret_cast<const qd::cplx*>(b), reinterpret_cast<qd::cplx*>(x),
+              tol, maxit, restart, info);
+    if (stats) {
+      stats->iterations = info.iterations;
+      stats->converged = info.converged;
+      stats->max_true_rel_residual = info.max_rel;
+      if (stats->iters_per_rhs)
+        for (int c = 0; c < nrhs; ++c) stats->iters_per_rhs[c] = info.iters[c];
+      if (stats->true_rel_residual)
+        for (int c = 0; c < nrhs; ++c) stats->true_rel_residual[c] = info.true_rel[c];
+    }
+    not_conv = info.converged < nrhs;
+  });
+  if (rc == QD_OK && not_conv) {
+    g_last_error = "solve did not reach the tolerance within maxit";
+    return QD_ERR_NOT_CONVERGED;
+  }
+  return rc;
+}
+
+void qd_defl_params_default(qd_defl_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->kind = QD_DEFL_MG_OBLIQUE;
+  p->k = 24;
+  p->guard = 16;
+  p->eig_tol = 1e-6;
+  p->solve_tol = 1e-10;
+  p->maxit = 50;
+  p->seed = 12345;
+}
+
+int qd_defl_create(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, double m0, double tau, const qd_defl_params* params,
+                   const double* injected_basis, qd_defl** defl) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(params);
+    NONNULL(defl);
+    set_device(ctx);
+    if (mg) QD_REQUIRE(mg->gauge == gauge && mg->m0 == m0 && mg->tau == tau, "mg built for another operator");
+    std::unique_ptr<qd_defl> d(new qd_defl());
+    d->ctx = ctx;
+    d->gauge = gauge;
+    d->mg = mg;
+    d->m0 = m0;
+    d->tau = tau;
+    d->p = *params;
+    d->kind = params->kind;
+    qd::defl_build(*d, injected_basis);
+    *defl = d.release();
+  });
+}
+
+int qd_defl_destroy(qd_defl* defl) {
+  return guarded([&] {
+    if (!defl) return;
+    cudaStreamSynchronize(defl->ctx->stream);
+    delete defl;
+  });
+}
+
+int qd_defl_set_rank(qd_defl* defl, int rank, double* t0) {
+  return guarded([&] {
+    NONNULL(defl);
+    set_device(defl->ctx);
+    qd::defl_set_rank(*defl, rank);
+    if (t0) {
+      t0[0] = defl->t0[0];
+      t0[1] = defl->t0[1];
+    }
+  });
+}
+
+int qd_defl_info(const qd_defl* defl, double* mu, double* lambda, int* iterations) {
+  return guarded([&] {
+    NONNULL(defl);
+    if (mu)
+      for (int i = 0; i < defl->p.k; ++i) mu[i] = defl->mu[i];
+    if (lambda && defl->kind == QD_DEFL_MG_OBLIQUE) {
+      QD_CUDA(cudaMemcpy(lambda, defl->lam.as<double>(), defl->rank * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if (iterations) *iterations = defl->iterations;
+  });
+}
+
+int qd_deflate_project(qd_defl* defl, int nrhs, const double* z, double* out) {
+  return guarded([&] {
+    NONNULL(defl);
+    NONNULL(z);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(z != out, "z and out must not overlap");
+    set_device(defl->ctx);
+    qd::defl_project(*defl, nrhs, reinterpret_cast<const qd::cplx*>(z), reinterpret_cast<qd::cplx*>(out));
+  });
+}
+
+int qd_deflate_coeffs(qd_defl* defl, int nrhs, const double* z, double* ZhV, double* UhKZ) {
+  return guarded([&] {
+    NONNULL(defl);
+    NONNULL(z);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    set_device(defl->ctx);
+    const int k = defl->p.k;
+    qd::DevBuf m1((size_t)k * nrhs * sizeof(qd::cplx)), m2((size_t)k * nrhs * sizeof(qd::cplx));
+    qd::defl_coeffs(*defl, nrhs, reinterpret_cast<const qd::cplx*>(z), m1.as<qd::cplx>(), m2.as<qd::cplx>());
+    std::vector<qd::cplx> h1((size_t)k * nrhs), h2((size_t)k * nrhs);
+    QD_CUDA(cudaMemcpyAsync(h1.data(), m1.as<qd::cplx>(), h1.size() * sizeof(qd::cplx), cudaMemcpyDeviceToHost,
+                            defl->ctx->stream));
+    QD_CUDA(cudaMemcpyAsync(h2.data(), m2.as<qd::cplx>(), h2.size() * sizeof(qd::cplx), cudaMemcpyDeviceToHost,
+                            defl->ctx->stream));
+    QD_CUDA(cudaStreamSynchronize(defl->ctx->stream));
+    // ZhV[j][i] = conj((U_bar^H W^H Z)[i][j]); UhKZ[i][j] as computed
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < nrhs; ++j) {
+        const qd::cplx a = h1[(size_t)i * nrhs + j], b = h2[(size_t)i * nrhs + j];
+        if (ZhV) {
+          ZhV[2 * ((size_t)j * k + i)] = a.x;
+          ZhV[2 * ((size_t)j * k + i) + 1] = -a.y;
+        }
+        if (UhKZ) {
+          UhKZ[2 * ((size_t)i * nrhs + j)] = b.x;
+          UhKZ[2 * ((size_t)i * nrhs + j) + 1] = b.y;
+        }
+      }
+  });
+}
+
+int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, qd_defl* defl, double m0, double tau,
+                        const qd_trace_params* params, qd_trace_result* result) {
+  int not_conv = 0;
+  int rc = guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(params);
+    NONNULL(result);
+    QD_REQUIRE(params->tol > 0.0 && params->maxit >= 1 && params->restart >= 1, "bad solver parameters");
+    set_device(ctx);
+    qd::TraceOut out;
+    std::vector<qd::cplx> M1, M2;
+    const bool coeffs = defl && defl->kind == QD_DEFL_MG_OBLIQUE && (result->ZhV || result->UhKZ);
+    qd::hutchinson(*ctx, *gauge, mg, defl, m0, tau, *params, coeffs, out, &M1, &M2);
+    const int s = params->nsamples;
+    result->t0[0] = defl ? defl->t0[0] : 0.0;
+    result->t0[1] = defl ? defl->t0[1] : 0.0;
+    result->mean[0] = out.stats[0];
+    result->mean[1] = out.stats[1];
+    result->estimate[0] = result->t0[0] + out.stats[0];
+    result->estimate[1] = result->t0[1] + out.stats[1];
+    result->var = out.stats[2];
+    result->var_re = out.stats[3];
+    result->stderr_mean = out.stats[4];
+    result->var_jackknife_err = out.stats[5];
+    result->nsamples = s;
+    result->iterations = out.info.iterations;
+    result->max_true_rel_residual = out.info.max_rel;
+    if (result->t_samples)
+      for (int j = 0; j < s; ++j) {
+        result->t_samples[2 * j] = out.t[j].x;
+        result->t_samples[2 * j + 1] = out.t[j].y;
+      }
+    if (coeffs) {
+      const int k = defl->p.k;
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < s; ++j) {
+          const qd::cplx a = M1[(size_t)i * s + j], b = M2[(size_t)i * s + j];
+          if (result->ZhV) {
+            result->ZhV[2 * ((size_t)j * k + i)] = a.x;
+            result->ZhV[2 * ((size_t)j * k + i) + 1] = -a.y;
+          }
+          if (result->UhKZ) {
+            result->UhKZ[2 * ((size_t)i * s + j)] = b.x;
+            result->UhKZ[2 * ((size_t)i * s + j) + 1] = b.y;
+          }
+        }
+    }
+    not_conv = out.info.converged < s;
+  });
+  if (rc == QD_OK && not_conv) {
+    g_last_error = "a solve did not reach the tolerance within maxit";
+    return QD_ERR_NOT_CONVERGED;
+  }
+  return rc;
+}
+
+int qd_prof_enable(qd_ctx* ctx, int enable) {
+  return guarded([&] {
+    NONNULL(ctx);
+    if (!enable && ctx->prof) qd::prof_flush(*ctx);
+    ctx->prof = enable != 0;
+  });
+}
+
+int qd_prof_read(qd_ctx* ctx, int kind, int64_t* launches, double* ms, double* flops, double* bytes, int reset) {
+  return guarded([&] {
+    NONNULL(ctx);
+    QD_REQUIRE(kind >= 0 && kind < QD_PROF_NKINDS, "unknown kernel kind");
+    set_device(ctx);
+    qd::prof_flush(*ctx);
+    const qd::ProfTotals& t = ctx->prof_tot[kind];
+    if (launches) *launches = t.launches;
+    if (ms) *ms = t.ms;
+    if (flops) *flops = t.flops;
+    if (bytes) *bytes = t.bytes;
+    if (reset) ctx->prof_tot[kind] = qd::ProfTotals();
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,349 @@
+// Deflation spaces, projection and the Hutchinson estimator.
+//
+// Algorithm 1: U = k eigenvectors of gamma5 (A + i tau gamma5)^{-1} of
+//   largest magnitude (= eigenvectors of the Hermitian A gamma5 with smallest
+//   |eigenvalue| at tau = 0); t0 = sum_i u_i^H A^{-1}_xi u_i; P = U U^H.
+// Algorithm 2: U_bar = k eigenvectors of gamma5^W C^{-1} of largest
+//   magnitude (= of the Hermitian C gamma5^W with smallest |mu|);
+//   U_hat Lambda U_hat^H = U_bar^H gamma5^W C U_bar; U = U_bar U_hat;
+//   t0 = sum_i u_i^H gamma5^W u_i / lambda_i;
+//   P = A W U Lambda^{-1} U^H gamma5^W W^H (the K = gamma5 projector of
+//   Sec. 2.1 with V = W U).
+// Both eigenproblems are solved by block inverse subspace iteration with
+// Rayleigh-Ritz ("eigs" on the inverse with largest magnitude, Sec. 3.1):
+//   Y = H^{-1} X (inexact GCR solves to solve_tol), Q = orth(Y) by Cholesky
+//   QR applied twice, T = Q^H H Q, T S = S Theta, X = Q S.
+// Sec. 2.2: the a-posteriori matrices Z^H W U_bar and U_bar^H gamma5^W W^H Z.
+#include "blas.cuh"
+#include "defl.cuh"
+#include "dense.cuh"
+
+namespace qd {
+
+SolverCache& cache(qd_ctx& ctx) {
+  if (!ctx.cache) ctx.cache = std::make_shared<SolverCache>();
+  return *static_cast<SolverCache*>(ctx.cache.get());
+}
+
+// Q <- Y R^{-1} with Y = Q R, twice (Cholesky QR 2).  Y: n x m (ld m).
+static void cholqr2(qd_ctx& ctx, int64_t n, int m, cplx* Y, cplx* tmp, DevBuf& small) {
+  small.resize((size_t)(2 * m * m) * sizeof(cplx) + 16);
+  cplx* G = small.as<cplx>();
+  cplx* Ri = G + (size_t)m * m;
+  DevBuf flag(sizeof(int));
+  QD_CUDA(cudaMemsetAsync(flag.as<int>(), 0, sizeof(int), ctx.stream));
+  for (int pass = 0; pass < 2; ++pass) {
+    blockdot(ctx, n, Y, m, m, Y, m, m, G);
+    hermitize(ctx, m, G);
+    cholesky_inverse(ctx, m, G, Ri, flag.as<int>());
+    blockmul(ctx, n, Y, m, m, Ri, m, m, tmp, m, 1.0, 0.0);
+    blas::copy(ctx, n * m, tmp, Y);
+  }
+  int h = 0;
+  QD_CUDA(cudaMemcpyAsync(&h, flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  if (h) fail(QD_ERR_NONFINITE, "Cholesky QR: block is numerically rank deficient");
+}
+
+// Block inverse subspace iteration for the m eigenpairs of the Hermitian
+// H = Op gamma5 closest to 0.  X (n x m, ld m) out; theta (host, m) out.
+static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, Precond<cplx>* M, const LevelGeom& geo, int m, int k,
+                         double eig_tol, double solve_tol, int maxit, uint64_t seed, cplx* X,
+                         std::vector<double>& theta, int& iters_out) {
+  const int64_t n = A.n();
+  const int dof = A.dof();
+  const size_t blk = (size_t)n * m * sizeof(cplx);
+  DevBuf Yb(blk), Zb(blk), Tb(blk), small, eig((size_t)(3 * m * m + 4) * sizeof(cplx) + 4 * m * sizeof(double)),
+      resid(m * sizeof(cplx)), iv((m + 8) * sizeof(int));
+  cplx* Y = Yb.as<cplx>();
+  cplx* Z = Zb.as<cplx>();
+  cplx* Tm = Tb.as<cplx>();
+  cplx* Tmat = eig.as<cplx>();
+  cplx* S = Tmat + (size_t)m * m;
+  cplx* Ss = S + (size_t)m * m;
+  double* w = reinterpret_cast<double*>(Ss + (size_t)m * m);
+  double* ws = w + m;
+  random_starts_fill(ctx, geo, dof, seed, m, X);
+  cholqr2(ctx, n, m, X, Tm, small);
+  GCR<cplx> solver;
+  theta.assign(m, 0.0);
+  int it = 0;
+  for (; it < maxit; ++it) {
+    // Y = H^{-1} X = gamma5 Op^{-1} X
+    SolveInfo info;
+    solver.solve(ctx, A, M, X, Tm, m, solve_tol, 100000, 32, &info);
+    blas::gamma5(ctx, geo.nsites, dof, m, Tm, Y);
+    cholqr2(ctx, n, m, Y, Tm, small);
+    // Z = H Y = Op gamma5 Y
+    blas::gamma5(ctx, geo.nsites, dof, m, Y, Tm);
+    A.apply(ctx, Tm, Z, m);
+    blockdot(ctx, n, Y, m, m, Z, m, m, Tmat);
+    hermitize(ctx, m, Tmat);
+    jacobi_eigh(ctx, m, Tmat, S, w, nullptr);
+    sort_by_abs(ctx, m, w, S, ws, Ss, iv.as<int>());
+    blockmul(ctx, n, Y, m, m, Ss, m, m, X, m, 1.0, 0.0);   // X = Q S
+    blockmul(ctx, n, Z, m, m, Ss, m, m, Tm, m, 1.0, 0.0);  // HX = Z S
+    eig_residuals(ctx, n, m, Tm, X, ws, resid.as<cplx>());
+    std::vector<cplx> hr(m);
+    QD_CUDA(cudaMemcpyAsync(hr.data(), resid.as<cplx>(), m * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaMemcpyAsync(theta.data(), ws, m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaStreamSynchronize(ctx.stream));
+    double worst = 0.0;
+    for (int i = 0; i < k; ++i) {
+      const double rel = std::sqrt(hr[i].x) / (std::fabs(theta[i]) > 0 ? std::fabs(theta[i]) : 1.0);
+      if (!(rel <= worst)) worst = rel;
+    }
+    if (worst <= eig_tol) {
+      ++it;
+      break;
+    }
+  }
+  iters_out = it;
+}
+
+// ---------------------------------------------------------------------------
+void defl_build(qd_defl& d, const double* injected) {
+  qd_ctx& ctx = *d.ctx;
+  const int k = d.p.k;
+  QD_REQUIRE(k >= 1, "deflation rank k must be >= 1");
+  if (d.kind == QD_DEFL_MG_OBLIQUE) {
+    QD_REQUIRE(d.mg != nullptr, "Algorithm 2 deflation needs a multigrid hierarchy");
+    d.level = 1;
+  } else {
+    QD_REQUIRE(d.kind == QD_DEFL_EIG_ORTHO, "unknown deflation kind");
+    d.level = 0;
+  }
+  const LevelGeom& geo = d.level == 0 ? d.gauge->geo : d.mg->geom(1);
+  const int dof = d.level == 0 ? 12 : d.mg->dof(1);
+  d.nb = geo.nsites * (int64_t)dof;
+  QD_REQUIRE(k <= d.nb, "deflation rank exceeds the dimension");
+  d.Ubar.resize((size_t)d.nb * k * sizeof(cplx));
+  std::unique_ptr<Op<cplx>> op;
+  if (d.level == 1)
+    op = d.mg->op<cplx>(1);
+  else
+    op.reset(new WilsonOp<cplx>(d.gauge, d.gauge->links.as<cplx>(), d.m0, d.tau, false));
+  d.mu.assign(k, 0.0);
+  d.iterations = 0;
+  if (injected) {
+    QD_CUDA(cudaMemcpyAsync(d.Ubar.as<cplx>(), injected, (size_t)d.nb * k * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                            ctx.stream));
+  } else {
+    int m = k + (d.p.guard > 0 ? d.p.guard : 0);
+    if (m > d.nb) m = (int)d.nb;
+    DevBuf X((size_t)d.nb * m * sizeof(cplx));
+    Precond<cplx>* M = nullptr;
+    std::unique_ptr<MGPrecond<cplx>> pre;
+    if (d.level == 1 && d.mg->nlevels >= 2) {
+      pre.reset(new MGPrecond<cplx>(d.mg, 1));
+      M = pre.get();
+    } else if (d.level == 0 && d.mg) {
+      M = d.mg->pre64.get();
+    }
+    std::vector<double> theta;
+    subspace_eig(ctx, *op, M, geo, m, k, d.p.eig_tol, d.p.solve_tol, d.p.maxit, d.p.seed, X.as<cplx>(), theta,
+                 d.iterations);
+    for (int i = 0; i < k; ++i) d.mu[i] = theta[i];
+    // U_bar = first k columns of X (ld m -> ld k)
+    blockmul_identity_cols(ctx, d.nb, X.as<cplx>(), m, k, d.Ubar.as<cplx>());
+  }
+  if (d.kind == QD_DEFL_MG_OBLIQUE) {
+    // G = U_bar^H gamma5^W C U_bar
+    DevBuf t1((size_t)d.nb * k * sizeof(cplx)), t2((size_t)d.nb * k * sizeof(cplx));
+    op->apply(ctx, d.Ubar.as<cplx>(), t1.as<cplx>(), k);
+    blas::gamma5(ctx, geo.nsites, dof, k, t1.as<cplx>(), t2.as<cplx>());
+    d.G.resize((size_t)k * k * sizeof(cplx));
+    blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, t2.as<cplx>(), k, k, d.G.as<cplx>());
+    hermitize(ctx, k, d.G.as<cplx>());
+  } else {
+    // Y = A^{-1}_xi U for t0 = sum u_i^H A^{-1}_xi u_i (Algorithm 1, step 2)
+    d.AinvU.resize((size_t)d.nb * k * sizeof(cplx));
+    GCR<cplx> solver;
+    SolveInfo info;
+    solver.solve(ctx, *op, d.mg ? d.mg->pre64.get() : nullptr, d.Ubar.as<cplx>(), d.AinvU.as<cplx>(), k,
+                 d.p.solve_tol, 100000, 32, &info);
+  }
+  defl_set_rank(d, k);
+}
+
+void defl_set_rank(qd_defl& d, int r) {
+  qd_ctx& ctx = *d.ctx;
+  QD_REQUIRE(r >= 1 && r <= d.p.k, "rank must be in [1, k]");
+  const int k = d.p.k;
+  d.rank = r;
+  const LevelGeom& geo = d.level == 0 ? d.gauge->geo : d.mg->geom(1);
+  const int dof = d.level == 0 ? 12 : d.mg->dof(1);
+  DevBuf dv(r * sizeof(cplx));
+  if (d.kind == QD_DEFL_MG_OBLIQUE) {
+    // step 3 on the leading r columns: G_r = U_hat Lambda U_hat^H
+    DevBuf Gr((size_t)r * r * sizeof(cplx)), E((size_t)r * r * sizeof(cplx));
+    copy_leading_block(ctx, k, r, d.G.as<cplx>(), Gr.as<cplx>());
+    d.lam.resize(r * sizeof(double));
+    jacobi_eigh(ctx, r, Gr.as<cplx>(), E.as<cplx>(), d.lam.as<double>(), nullptr);
+    d.U.resize((size_t)d.nb * r * sizeof(cplx));
+    blockmul(ctx, d.nb, d.Ubar.as<cplx>(), k, r, E.as<cplx>(), r, r, d.U.as<cplx>(), r, 1.0, 0.0);
+    // step 4: t0 = sum_i u_i^H gamma5^W u_i / lambda_i
+    DevBuf g((size_t)d.nb * r * sizeof(cplx));
+    blas::gamma5(ctx, geo.nsites, dof, r, d.U.as<cplx>(), g.as<cplx>());
+    blas::dots(ctx, 1, d.nb, r, d.U.as<cplx>(), 0, g.as<cplx>(), 0, dv.as<cplx>());
+    sum_over_lambda(ctx, r, dv.as<cplx>(), d.lam.as<double>(), d.t0_dev());
+  } else {
+    // t0 = sum_{i<r} u_i^H (A^{-1}_xi u_i): column dots on the leading r columns
+    DevBuf Ur((size_t)d.nb * r * sizeof(cplx)), Yr((size_t)d.nb * r * sizeof(cplx));
+    blockmul_identity_cols(ctx, d.nb, d.Ubar.as<cplx>(), k, r, Ur.as<cplx>());
+    blockmul_identity_cols(ctx, d.nb, d.AinvU.as<cplx>(), k, r, Yr.as<cplx>());
+    blas::dots(ctx, 1, d.nb, r, Ur.as<cplx>(), 0, Yr.as<cplx>(), 0, dv.as<cplx>());
+    sum_over_lambda(ctx, r, dv.as<cplx>(), nullptr, d.t0_dev());
+    d.U.resize((size_t)d.nb * r * sizeof(cplx));
+    QD_CUDA(cudaMemcpyAsync(d.U.as<cplx>(), Ur.as<cplx>(), (size_t)d.nb * r * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                            ctx.stream));
+  }
+  QD_CUDA(cudaMemcpyAsync(d.t0, d.t0_dev(), sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+}
+
+// out = (I - P) z, s columns
+void defl_project(qd_defl& d, int s, const cplx* z, cplx* out) {
+  qd_ctx& ctx = *d.ctx;
+  const int r = d.rank;
+  const int64_t nf = d.gauge->geo.nsites * 12;
+  DevBuf a((size_t)r * s * sizeof(cplx));
+  if (d.kind == QD_DEFL_MG_OBLIQUE) {
+    const Transfer& T = *d.mg->T[0];
+    const LevelGeom& cg = d.mg->geom(1);
+    DevBuf c((size_t)d.nb * s * sizeof(cplx)), gc((size_t)d.nb * s * sizeof(cplx)), f((size_t)nf * s * sizeof(cplx));
+    restrict_<cplx>(ctx, T, T.W.as<cplx>(), z, c.as<cplx>(), s);
+    blas::gamma5(ctx, cg.nsites, T.Dc, s, c.as<cplx>(), gc.as<cplx>());
+    blockdot(ctx, d.nb, d.U.as<cplx>(), r, r, gc.as<cplx>(), s, s, a.as<cplx>());  // U^H g5 W^H z
+    scale_rows_inv(ctx, r, s, d.lam.as<double>(), a.as<cplx>());                  // Lambda^{-1}
+    blockmul(ctx, d.nb, d.U.as<cplx>(), r, r, a.as<cplx>(), s, s, c.as<cplx>(), s, 1.0, 0.0);  // U (.)
+    prolongate<cplx>(ctx, T, T.W.as<cplx>(), c.as<cplx>(), f.as<cplx>(), s);       // W (.)
+    wilson_apply<cplx>(ctx, d.gauge->geo, d.gauge->links.as<cplx>(), d.m0, d.tau, false, f.as<cplx>(), out, s);
+    blas::sub(ctx, nf * s, z, out, out);  // out = z - A W U Lambda^{-1} U^H g5 W^H z
+  } else {
+    blockdot(ctx, nf, d.U.as<cplx>(), r, r, z, s, s, a.as<cplx>());  // U^H z
+    blas::copy(ctx, nf * s, z, out);
+    blockmul(ctx, nf, d.U.as<cplx>(), r, r, a.as<cplx>(), s, s, out, s, -1.0, 1.0);
+  }
+}
+
+// Sec. 2.2 matrices (kind 2): M1 = U_bar^H W^H Z (k x s), M2 = U_bar^H g5 W^H Z.
+void defl_coeffs(qd_defl& d, int s, const cplx* z, cplx* M1, cplx* M2) {
+  qd_ctx& ctx = *d.ctx;
+  QD_REQUIRE(d.kind == QD_DEFL_MG_OBLIQUE, "a-posteriori coefficients are defined for Algorithm 2");
+  const int k = d.p.k;
+  const Transfer& T = *d.mg->T[0];
+  const LevelGeom& cg = d.mg->geom(1);
+  DevBuf c((size_t)d.nb * s * sizeof(cplx)), gc((size_t)d.nb * s * sizeof(cplx));
+  restrict_<cplx>(ctx, T, T.W.as<cplx>(), z, c.as<cplx>(), s);
+  blas::gamma5(ctx, cg.nsites, T.Dc, s, c.as<cplx>(), gc.as<cplx>());
+  blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, c.as<cplx>(), s, s, M1);
+  blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, gc.as<cplx>(), s, s, M2);
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------
+__global__ void k_copy_cols(int64_t n, const cplx* __restrict__ X, int ldx, int r, cplx* __restrict__ Y) {
+  const int64_t tot = n * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % r);
+    const int64_t i = e / r;
+    Y[e] = X[i * ldx + c];
+  }
+}
+void blockmul_identity_cols(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int r, cplx* Y) {
+  int blocks = div_up(n * r, 256);
+  if (blocks > 32 * kNumSMs) blocks = 32 * kNumSMs;
+  k_copy_cols<<<blocks, 256, 0, ctx.stream>>>(n, X, ldx, r, Y);
+  QD_LAUNCH_CHECK();
+}
+void copy_leading_block(qd_ctx& ctx, int k, int r, const cplx* G, cplx* Gr) {
+  blockmul_identity_cols(ctx, r, G, k, r, Gr);
+}
+
+// out = sum_i d_i / lam_i (lam nullable -> 1), Neumaier-compensated, in order
+__global__ void k_sum_over_lambda(int r, const cplx* __restrict__ dv, const double* __restrict__ lam,
+                                  cplx* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double sr = 0, cr = 0, si = 0, ci = 0;
+  for (int i = 0; i < r; ++i) {
+    const double l = lam ? lam[i] : 1.0;
+    const double xr = dv[i].x / l, xi = dv[i].y / l;
+    double t = sr + xr;
+    cr += (fabs(sr) >= fabs(xr)) ? (sr - t) + xr : (xr - t) + sr;
+    sr = t;
+    t = si + xi;
+    ci += (fabs(si) >= fabs(xi)) ? (si - t) + xi : (xi - t) + si;
+    si = t;
+  }
+  *out = mkc(sr + cr, si + ci);
+}
+void sum_over_lambda(qd_ctx& ctx, int r, const cplx* dv, const double* lam, cplx* out) {
+  k_sum_over_lambda<<<1, 32, 0, ctx.stream>>>(r, dv, lam, out);
+  QD_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// Estimator statistics on the device (a9): Neumaier sums in sample order.
+// out: [0] mean re, [1] mean im, [2] var, [3] var_re, [4] stderr, [5] jk err
+// ---------------------------------------------------------------------------
+__device__ void neu_add(double& s, double& c, double x) {
+  const double t = s + x;
+  c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+
+__global__ void k_trace_stats(int s, const cplx* __restrict__ t, double* __restrict__ out, double* __restrict__ loo) {
+  // delete-one variances, one sample per thread
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double mr = 0, cmr = 0, mi = 0, cmi = 0;
+    for (int j = 0; j < s; ++j) {
+      if (j == i) continue;
+      neu_add(mr, cmr, t[j].x);
+      neu_add(mi, cmi, t[j].y);
+    }
+    const double m_r = (mr + cmr) / (s - 1), m_i = (mi + cmi) / (s - 1);
+    double v = 0, cv = 0;
+    for (int j = 0; j < s; ++j) {
+      if (j == i) continue;
+      const double dr = t[j].x - m_r, di = t[j].y - m_i;
+      neu_add(v, cv, dr * dr + di * di);
+    }
+    loo[i] = s > 2 ? (v + cv) / (s - 2) : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double sr = 0, cr = 0, si = 0, ci = 0;
+  for (int j = 0; j < s; ++j) {
+    neu_add(sr, cr, t[j].x);
+    neu_add(si, ci, t[j].y);
+  }
+  const double mr = (sr + cr) / s, mi = (si + ci) / s;
+  double v = 0, cv = 0, vr = 0, cvr = 0;
+  for (int j = 0; j < s; ++j) {
+    const double dr = t[j].x - mr, di = t[j].y - mi;
+    neu_add(v, cv, dr * dr + di * di);
+    neu_add(vr, cvr, dr * dr);
+  }
+  const double var = s > 1 ? (v + cv) / (s - 1) : 0.0;
+  const double var_re = s > 1 ? (vr + cvr) / (s - 1) : 0.0;
+  double lm = 0, clm = 0;
+  for (int j = 0; j < s; ++j) neu_add(lm, clm, loo[j]);
+  const double lmean = (lm + clm) / s;
+  double q = 0, cq = 0;
+  for (int j = 0; j < s; ++j) neu_add(q, cq, (loo[j] - lmean) * (loo[j] - lmean));
+  out[0] = mr;
+  out[1] = mi;
+  out[2] = var;
+  out[3] = var_re;
+  out[4] = s > 0 ? sqrt(var / s) : 0.0;
+  out[5] = s > 2 ? sqrt((double)(s - 1) / s * (q + cq)) : 0.0;
+}
+
+void trace_stats(qd_ctx& ctx, int s, const cplx* t, double* out_dev, double* loo_dev) {
+  k_trace_stats<<<1, 256, 0, ctx.stream>>>(s, t, out_dev, loo_dev);
+  QD_LAUNCH_CHECK();
+}
+
+}  // namespace qd

@@ -1,0 +1,96 @@
+// Solvers and the multigrid hierarchy object (Sec. 2 two-grid method and
+// adaptive setup; Sec. 1 inexact solves).
+#pragma once
+
+#include "qd_internal.cuh"
+
+namespace qd {
+
+struct SolveInfo {
+  int iterations = 0;
+  int converged = 0;
+  double max_rel = 0.0;
+  std::vector<int> iters;
+  std::vector<double> true_rel;
+};
+
+// Flexible restarted GCR, batched over independent right-hand sides.
+template <class C> class GCR {
+ public:
+  // x = A^{-1} b to ||b - A x|| <= tol ||b|| per column (x overwritten,
+  // zero initial guess).  M (nullable) is a right preconditioner that may
+  // change between calls.  `quiet` skips per-column statistics.
+  void solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x, int nrhs, double tol,
+             int maxit, int restart, SolveInfo* info);
+
+ private:
+  void ensure(int64_t n, int nrhs, int m);
+  DevBuf P_, Q_, r_, t_;
+  DevBuf sc_;   // cplx per-RHS scalars
+  DevBuf act_;  // int [nrhs + 1]: active flags, then the count of active
+  int64_t cap_n_ = -1;
+  int cap_rhs_ = -1, cap_m_ = -1;
+};
+
+// Minimal-residual steps on A x = b, batched.  Fixed number of steps with
+// x0 = 0 (smoother), or until ||r|| <= tol ||r0|| per column (null vectors,
+// x0 given).  steps (device int[nrhs], nullable) counts steps per column.
+template <class C>
+void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int nrhs, int nsteps,
+              double tol, C* rbuf, C* qbuf, int* steps_dev, DevBuf& scratch);
+
+}  // namespace qd
+
+struct qd_mg;
+
+namespace qd {
+
+// V-cycle preconditioner for level `level` of a hierarchy (Sec. 2 two-grid
+// method: coarse-grid correction, then smoothing; deeper levels precondition
+// the coarse GCR with the next V-cycle; no recursion below the coarsest).
+template <class C> class MGPrecond : public Precond<C> {
+ public:
+  MGPrecond(qd_mg* mg, int level);
+  void apply(qd_ctx& ctx, const C* r, C* z, int nrhs) override;
+
+ private:
+  qd_mg* mg_;
+  int level_;
+  std::unique_ptr<MGPrecond<C>> next_;
+  GCR<C> coarse_;
+  DevBuf rc_, ec_, t_, res_, q_, d_, scratch_;
+  int cap_ = -1;
+};
+
+// FP32 V-cycle used as the preconditioner of an FP64 outer solve: converts
+// the residual to FP32, runs the FP32 V-cycle, converts back.
+class MixedPrecond : public Precond<cplx> {
+ public:
+  MixedPrecond(qd_mg* mg);
+  void apply(qd_ctx& ctx, const cplx* r, cplx* z, int nrhs) override;
+
+ private:
+  qd_mg* mg_;
+  MGPrecond<cplxf> inner_;
+  DevBuf rf_, zf_;
+};
+
+}  // namespace qd
+
+struct qd_mg {
+  qd_ctx* ctx = nullptr;
+  const qd_gauge* gauge = nullptr;
+  double m0 = 0.0, tau = 0.0;
+  qd_mg_params p{};
+  int nlevels = 0;  // coarse levels
+  std::vector<std::unique_ptr<qd::Transfer>> T;     // T[l]: level l -> l+1
+  std::vector<std::unique_ptr<qd::CoarseLevel>> L;  // L[l-1]: level l >= 1
+  std::unique_ptr<qd::MGPrecond<qd::cplx>> pre64;
+  std::unique_ptr<qd::MixedPrecond> pre_mixed;
+
+  const qd::LevelGeom& geom(int level) const { return level == 0 ? gauge->geo : L[level - 1]->geo; }
+  int dof(int level) const { return level == 0 ? 12 : L[level - 1]->D; }
+  // Operator of a level in precision C (caller owns the returned object).
+  template <class C> std::unique_ptr<qd::Op<C>> op(int level);
+  template <class C> const C* W(int level);
+};

@@ -1,0 +1,390 @@
+// Krylov solvers and multigrid: flexible GCR (Sec. 1 inexact solves A^{-1}_xi
+// with the true-residual stopping rule; Sec. 2 and Sec. 3 use GCR on every
+// level), minimal-residual smoothing and null vectors, the V-cycle of the
+// two-grid method (Sec. 2) and the adaptive setup (Sec. 2, Sec. 4
+// tolerance 1e-2 / 200 iterations).
+#include "blas.cuh"
+#include "mg.cuh"
+
+namespace qd {
+
+// ---------------------------------------------------------------------------
+// Fused update kernels with a per-column |r|^2 reduction (deterministic).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rows_reduce(double v, cplx* partials, int nrhs) {
+  __shared__ double sm[blas::kThreads];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int t = ty * blockDim.x + tx;
+  sm[t] = v;
+  __syncthreads();
+  for (int h = blockDim.y / 2; h > 0; h >>= 1) {
+    if (ty < h) sm[t] += sm[t + h * blockDim.x];
+    __syncthreads();
+  }
+  const int r = blockIdx.y * blockDim.x + tx;
+  if (ty == 0 && r < nrhs) partials[(int64_t)blockIdx.x * nrhs + r] = mkc(sm[tx], 0.0);
+}
+
+// GCR step for active columns, with s2[0][r] = <q,q>, s2[1][r] = <q,r>:
+//   a = <q,r>/<q,q>;  x += a p;  r -= a q;  q, p scaled to ||q|| = 1.
+template <class C>
+__global__ void k_gcr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
+                             const int* __restrict__ active, C* __restrict__ q, C* __restrict__ p,
+                             C* __restrict__ x, C* __restrict__ r, cplx* __restrict__ partials) {
+  typedef typename CTraits<C>::R R;
+  const int col = blockIdx.y * blockDim.x + threadIdx.x;
+  R acc = 0;
+  if (col < nrhs && active[col]) {
+    const double qq = s2[col].x;
+    const cplx qr = s2[nrhs + col];
+    const double inv = qq > 0.0 ? 1.0 / sqrt(qq) : 0.0;
+    const double ar = qq > 0.0 ? qr.x / qq : 0.0, ai = qq > 0.0 ? qr.y / qq : 0.0;
+    const C a = mk<C>((R)ar, (R)ai), na = mk<C>((R)(-ar), (R)(-ai));
+    const R ri = (R)inv;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < n;
+         i += (int64_t)gridDim.x * blockDim.y) {
+      const int64_t e = i * nrhs + col;
+      const C qv = q[e], pv = p[e];
+      C xv = x[e], rv = r[e];
+      cfma(xv, a, pv);
+      cfma(rv, na, qv);
+      x[e] = xv;
+      r[e] = rv;
+      q[e] = cscale(ri, qv);
+      p[e] = cscale(ri, pv);
+      acc += cnorm2(rv);
+    }
+  }
+  rows_reduce((double)acc, partials, nrhs);
+}
+
+// Minimal-residual step: a = <q,r>/<q,q>; x += a r; r -= a q.
+template <class C>
+__global__ void k_mr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
+                            const int* __restrict__ active, C* __restrict__ q, C* __restrict__ x,
+                            C* __restrict__ r, cplx* __restrict__ partials) {
+  typedef typename CTraits<C>::R R;
+  const int col = blockIdx.y * blockDim.x + threadIdx.x;
+  R acc = 0;
+  if (col < nrhs && (!active || active[col])) {
+    const double qq = s2[col].x;
+    const cplx qr = s2[nrhs + col];
+    const double ar = qq > 0.0 ? qr.x / qq : 0.0, ai = qq > 0.0 ? qr.y / qq : 0.0;
+    const C a = mk<C>((R)ar, (R)ai), na = mk<C>((R)(-ar), (R)(-ai));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < n;
+         i += (int64_t)gridDim.x * blockDim.y) {
+      const int64_t e = i * nrhs + col;
+      const C qv = q[e];
+      C xv = x[e], rv = r[e];
+      cfma(xv, a, rv);
+      cfma(rv, na, qv);
+      x[e] = xv;
+      r[e] = rv;
+      acc += cnorm2(rv);
+    }
+  }
+  if (partials) rows_reduce((double)acc, partials, nrhs);
+}
+
+// rn2[c] = sum of partials; active columns stay active while
+// rn2 > tol2 * ref2; counts active columns and non-finite norms.
+__global__ void k_resid_final(int nrhs, int nblk, const cplx* __restrict__ partials, cplx* __restrict__ rn2,
+                              const cplx* __restrict__ ref2, double tol2, int* __restrict__ active,
+                              int* __restrict__ count, int* __restrict__ nonfin, int* __restrict__ iters) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrhs) return;
+  if (!active[c]) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partials[(int64_t)b * nrhs + c].x;
+  rn2[c] = mkc(s, 0.0);
+  if (iters) iters[c] += 1;
+  if (!isfinite(s)) {
+    atomicAdd(nonfin, 1);
+    active[c] = 0;
+    return;
+  }
+  if (s > tol2 * ref2[c].x) {
+    atomicAdd(count, 1);
+  } else {
+    active[c] = 0;
+  }
+}
+
+// active[c] = (rn2 > tol2 * ref2), counting active and non-finite columns.
+__global__ void k_set_active(int nrhs, const cplx* __restrict__ rn2, const cplx* __restrict__ ref2, double tol2,
+                             int* __restrict__ active, int* __restrict__ count, int* __restrict__ nonfin) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrhs) return;
+  const double s = rn2[c].x;
+  if (!isfinite(s) || !isfinite(ref2[c].x)) {
+    atomicAdd(nonfin, 1);
+    active[c] = 0;
+    return;
+  }
+  const int a = s > tol2 * ref2[c].x ? 1 : 0;
+  active[c] = a;
+  if (a) atomicAdd(count, 1);
+}
+
+static void read_flags(qd_ctx& ctx, const int* dev, int n, int* host) {
+  QD_CUDA(cudaMemcpyAsync(ctx.host_pinned, dev, n * sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  for (int i = 0; i < n; ++i) host[i] = ctx.host_pinned[i];
+}
+
+// ---------------------------------------------------------------------------
+// GCR
+// ---------------------------------------------------------------------------
+template <class C> void GCR<C>::ensure(int64_t n, int nrhs, int m) {
+  if (n == cap_n_ && nrhs <= cap_rhs_ && m <= cap_m_) return;
+  const size_t vec = (size_t)n * nrhs * sizeof(C);
+  P_.release();
+  Q_.release();
+  P_.resize(vec * m);
+  Q_.resize(vec * m);
+  r_.resize(vec);
+  t_.resize(vec);
+  sc_.resize((size_t)(4 + m) * nrhs * sizeof(cplx));
+  act_.resize((size_t)(2 * nrhs + 4) * sizeof(int));
+  cap_n_ = n;
+  cap_rhs_ = nrhs;
+  cap_m_ = m;
+}
+
+template <class C>
+void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x, int nrhs, double tol,
+                   int maxit, int restart, SolveInfo* info) {
+  QD_REQUIRE(restart >= 1 && restart <= 256, "GCR restart length must be in [1, 256]");
+  QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+  const int64_t n = A.n();
+  const int64_t tot = n * nrhs;
+  ensure(n, nrhs, restart);
+  C* P = P_.as<C>();
+  C* Q = Q_.as<C>();
+  C* r = r_.as<C>();
+  C* t = t_.as<C>();
+  cplx* bn2 = sc_.as<cplx>();
+  cplx* rn2 = bn2 + nrhs;
+  cplx* s2 = bn2 + 2 * nrhs;
+  cplx* beta = bn2 + 4 * nrhs;
+  int* act = act_.as<int>();
+  int* iters = act + nrhs;
+  int* flags = act + 2 * nrhs;  // [0] count, [1] non-finite
+  const double tol2 = tol * tol;
+  blas::zero(ctx, tot, x);
+  blas::copy(ctx, tot, b, r);
+  blas::dots(ctx, 1, n, nrhs, b, 0, b, 0, bn2);
+  QD_CUDA(cudaMemcpyAsync(rn2, bn2, nrhs * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx.stream));
+  QD_CUDA(cudaMemsetAsync(iters, 0, nrhs * sizeof(int), ctx.stream));
+  const blas::Sweep sw = blas::sweep(n, nrhs);
+  ctx.red_partials.resize((size_t)sw.grid.x * nrhs * sizeof(cplx));
+  int its = 0;
+  int hflags[2];
+  while (true) {
+    QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
+    k_set_active<<<div_up(nrhs, 128), 128, 0, ctx.stream>>>(nrhs, rn2, bn2, tol2, act, flags, flags + 1);
+    QD_LAUNCH_CHECK();
+    read_flags(ctx, flags, 2, hflags);
+    if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
+    if (hflags[0] == 0 || its >= maxit) break;
+    for (int i = 0; i < restart; ++i) {
+      C* Pi = P + i * tot;
+      C* Qi = Q + i * tot;
+      if (M)
+        M->apply(ctx, r, Pi, nrhs);
+      else
+        blas::copy(ctx, tot, r, Pi);
+      A.apply(ctx, Pi, Qi, nrhs);
+      for (int pass = 0; pass < 2 && i > 0; ++pass) {
+        blas::dots(ctx, i, n, nrhs, Q, tot, Qi, 0, beta);
+        blas::multi_axpy(ctx, i, n, nrhs, beta, act, Q, tot, Qi, P, Pi);
+      }
+      blas::dots(ctx, 1, n, nrhs, Qi, 0, Qi, 0, s2);
+      blas::dots(ctx, 1, n, nrhs, Qi, 0, r, 0, s2 + nrhs);
+      ctx.red_partials.resize((size_t)sw.grid.x * nrhs * sizeof(cplx));
+      k_gcr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, act, Qi, Pi, x, r,
+                                                            ctx.red_partials.as<cplx>());
+      QD_LAUNCH_CHECK();
+      QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
+      k_resid_final<<<div_up(nrhs, 128), 128, 0, ctx.stream>>>(nrhs, sw.grid.x, ctx.red_partials.as<cplx>(),
+                                                              rn2, bn2, tol2, act, flags, flags + 1, iters);
+      QD_LAUNCH_CHECK();
+      ++its;
+      read_flags(ctx, flags, 2, hflags);
+      if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
+      if (hflags[0] == 0 || its >= maxit) break;
+    }
+    // true residual r = b - A x
+    A.apply(ctx, x, t, nrhs);
+    blas::sub(ctx, tot, b, t, r);
+    blas::dots(ctx, 1, n, nrhs, r, 0, r, 0, rn2);
+  }
+  if (info) {
+    std::vector<cplx> hb(nrhs), hr(nrhs);
+    info->iters.assign(nrhs, 0);
+    QD_CUDA(cudaMemcpyAsync(hb.data(), bn2, nrhs * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaMemcpyAsync(hr.data(), rn2, nrhs * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaMemcpyAsync(info->iters.data(), iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaStreamSynchronize(ctx.stream));
+    info->iterations = its;
+    info->true_rel.assign(nrhs, 0.0);
+    info->converged = 0;
+    info->max_rel = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+      const double rel = hb[c].x > 0.0 ? std::sqrt(hr[c].x / hb[c].x) : 0.0;
+      info->true_rel[c] = rel;
+      if (rel <= tol) info->converged++;
+      if (rel > info->max_rel || rel != rel) info->max_rel = rel;
+    }
+  }
+}
+
+template class GCR<cplx>;
+template class GCR<cplxf>;
+
+// ---------------------------------------------------------------------------
+// Minimal-residual steps
+// ---------------------------------------------------------------------------
+template <class C>
+void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int nrhs, int nsteps,
+              double tol, C* r, C* q, int* steps_dev, DevBuf& scratch) {
+  const int64_t n = A.n(), tot = n * nrhs;
+  scratch.resize((size_t)4 * nrhs * sizeof(cplx) + (size_t)(nrhs + 4) * sizeof(int));
+  cplx* s2 = scratch.as<cplx>();
+  cplx* r0n2 = s2 + 2 * nrhs;
+  cplx* rn2 = s2 + 3 * nrhs;
+  int* act = reinterpret_cast<int*>(s2 + 4 * nrhs);
+  int* flags = act + nrhs;
+  if (x_is_zero) {
+    blas::zero(ctx, tot, x);
+    blas::copy(ctx, tot, b, r);
+  } else {
+    A.apply(ctx, x, q, nrhs);
+    blas::sub(ctx, tot, b, q, r);
+  }
+  const bool check = tol > 0.0;
+  const blas::Sweep sw = blas::sweep(n, nrhs);
+  int hflags[2];
+  if (check) {
+    blas::dots(ctx, 1, n, nrhs, r, 0, r, 0, r0n2);
+    QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
+    k_set_active<<<div_up(nrhs, 128), 128, 0, ctx.stream>>>(nrhs, r0n2, r0n2, 0.0, act, flags, flags + 1);
+    QD_LAUNCH_CHECK();
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    A.apply(ctx, r, q, nrhs);
+    blas::dots(ctx, 1, n, nrhs, q, 0, q, 0, s2);
+    blas::dots(ctx, 1, n, nrhs, q, 0, r, 0, s2 + nrhs);
+    ctx.red_partials.resize((size_t)sw.grid.x * nrhs * sizeof(cplx));
+    k_mr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, check ? act : nullptr, q, x, r,
+                                                         check ? ctx.red_partials.as<cplx>() : nullptr);
+    QD_LAUNCH_CHECK();
+    if (check) {
+      QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
+      k_resid_final<<<div_up(nrhs, 128), 128, 0, ctx.stream>>>(nrhs, sw.grid.x, ctx.red_partials.as<cplx>(),
+                                                              rn2, r0n2, tol * tol, act, flags, flags + 1,
+                                                              steps_dev);
+      QD_LAUNCH_CHECK();
+      read_flags(ctx, flags, 2, hflags);
+      if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in minimal-residual iteration");
+      if (hflags[0] == 0) break;
+    }
+  }
+}
+
+template void mr_steps<cplx>(qd_ctx&, const Op<cplx>&, const cplx*, cplx*, bool, int, int, double, cplx*,
+                             cplx*, int*, DevBuf&);
+template void mr_steps<cplxf>(qd_ctx&, const Op<cplxf>&, const cplxf*, cplxf*, bool, int, int, double,
+                              cplxf*, cplxf*, int*, DevBuf&);
+
+// ---------------------------------------------------------------------------
+// V-cycle
+// ---------------------------------------------------------------------------
+template <class C>
+MGPrecond<C>::MGPrecond(qd_mg* mg, int level) : mg_(mg), level_(level) {
+  if (level + 1 < mg->nlevels) next_.reset(new MGPrecond<C>(mg, level + 1));
+}
+
+template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int nrhs) {
+  const Transfer& T = *mg_->T[level_];
+  const int64_t nf = mg_->geom(level_).nsites * (int64_t)mg_->dof(level_);
+  const int64_t nc = mg_->geom(level_ + 1).nsites * (int64_t)mg_->dof(level_ + 1);
+  if (nrhs > cap_) {
+    rc_.resize(nc * nrhs * sizeof(C));
+    ec_.resize(nc * nrhs * sizeof(C));
+    t_.resize(nf * nrhs * sizeof(C));
+    res_.resize(nf * nrhs * sizeof(C));
+    q_.resize(nf * nrhs * sizeof(C));
+    d_.resize(nf * nrhs * sizeof(C));
+    cap_ = nrhs;
+  }
+  const C* W = mg_->W<C>(level_);
+  // coarse-grid correction: z = W C^{-1} W^H r
+  restrict_<C>(ctx, T, W, r, rc_.as<C>(), nrhs);
+  auto Ac = mg_->op<C>(level_ + 1);
+  coarse_.solve(ctx, *Ac, next_.get(), rc_.as<C>(), ec_.as<C>(), nrhs, mg_->p.coarse_tol,
+                mg_->p.coarse_maxit, mg_->p.coarse_restart, nullptr);
+  prolongate<C>(ctx, T, W, ec_.as<C>(), z, nrhs);
+  // smoothing: z += M^{-1} (r - A z), M^{-1} = minimal-residual steps from 0
+  const int nu = mg_->p.smoother_steps;
+  if (nu > 0) {
+    auto Af = mg_->op<C>(level_);
+    Af->apply(ctx, z, t_.as<C>(), nrhs);
+    blas::sub(ctx, nf * nrhs, r, t_.as<C>(), res_.as<C>());
+    mr_steps<C>(ctx, *Af, res_.as<C>(), d_.as<C>(), true, nrhs, nu, 0.0, t_.as<C>(), q_.as<C>(), nullptr,
+                scratch_);
+    blas::add(ctx, nf * nrhs, d_.as<C>(), z);
+  }
+}
+
+template class MGPrecond<cplx>;
+template class MGPrecond<cplxf>;
+
+MixedPrecond::MixedPrecond(qd_mg* mg) : mg_(mg), inner_(mg, 0) {}
+
+void MixedPrecond::apply(qd_ctx& ctx, const cplx* r, cplx* z, int nrhs) {
+  const int64_t tot = mg_->geom(0).nsites * 12 * (int64_t)nrhs;
+  rf_.resize(tot * sizeof(cplxf));
+  zf_.resize(tot * sizeof(cplxf));
+  to_f32(ctx, r, rf_.as<cplxf>(), tot);
+  inner_.apply(ctx, rf_.as<cplxf>(), zf_.as<cplxf>(), nrhs);
+  to_f64(ctx, zf_.as<cplxf>(), z, tot);
+}
+
+}  // namespace qd
+
+// ---------------------------------------------------------------------------
+// qd_mg helpers
+// ---------------------------------------------------------------------------
+template <>
+std::unique_ptr<qd::Op<qd::cplx>> qd_mg::op<qd::cplx>(int level) {
+  if (level == 0)
+    return std::unique_ptr<qd::Op<qd::cplx>>(
+        new qd::WilsonOp<qd::cplx>(gauge, gauge->links.as<qd::cplx>(), m0, tau, false));
+  return std::unique_ptr<qd::Op<qd::cplx>>(new qd::CoarseOp<qd::cplx>(L[level - 1].get(), L[level - 1]->Cm.as<qd::cplx>()));
+}
+
+template <>
+std::unique_ptr<qd::Op<qd::cplxf>> qd_mg::op<qd::cplxf>(int level) {
+  if (level == 0)
+    return std::unique_ptr<qd::Op<qd::cplxf>>(
+        new qd::WilsonOp<qd::cplxf>(gauge, const_cast<qd_gauge*>(gauge)->links_f32(), m0, tau, false));
+  qd::CoarseLevel& lv = *L[level - 1];
+  if (lv.Cmf.bytes() == 0) {
+    const int64_t n = lv.geo.nsites * 9 * (int64_t)lv.D * lv.D;
+    lv.Cmf.resize(n * sizeof(qd::cplxf));
+    qd::to_f32(*ctx, lv.Cm.as<qd::cplx>(), lv.Cmf.as<qd::cplxf>(), n);
+  }
+  return std::unique_ptr<qd::Op<qd::cplxf>>(new qd::CoarseOp<qd::cplxf>(&lv, lv.Cmf.as<qd::cplxf>()));
+}
+
+template <> const qd::cplx* qd_mg::W<qd::cplx>(int level) { return T[level]->W.as<qd::cplx>(); }
+template <> const qd::cplxf* qd_mg::W<qd::cplxf>(int level) {
+  qd::Transfer& t = *T[level];
+  if (t.Wf.bytes() == 0) {
+    const int64_t n = t.nfine * t.Df * (int64_t)t.nv;
+    t.Wf.resize(n * sizeof(qd::cplxf));
+    qd::to_f32(*ctx, t.W.as<qd::cplx>(), t.Wf.as<qd::cplxf>(), n);
+  }
+  return t.Wf.as<qd::cplxf>();
+}

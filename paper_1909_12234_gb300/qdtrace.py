@@ -1,0 +1,449 @@
+"""Python binding of libqdtrace (C ABI in include/qdtrace.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the stream.  Importing this
+module loads ``libqdtrace.so`` from the package directory and raises
+:class:`QDError` if it is missing (build it with
+``python -m paper_1909_12234_gb300.build``); there is no fallback.
+
+Device fields are ``torch.complex128`` CUDA tensors in the library's "qd
+layout": fine level shape ``(V, 12, nrhs)`` with sites in even-odd order,
+coarse level ``(Vc, dc, nrhs)`` with lexicographic coarse sites.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqdtrace.so")
+
+QD_OK = 0
+QD_ERR_INVALID = -1
+QD_ERR_CUDA = -2
+QD_ERR_OOM = -3
+QD_ERR_NOT_CONVERGED = -4
+QD_ERR_NONFINITE = -5
+QD_ERR_TIMEOUT = -6
+QD_ERR_INTERNAL = -7
+QD_MAX_LEVELS = 4
+QD_DEFL_EIG_ORTHO = 1
+QD_DEFL_MG_OBLIQUE = 2
+
+_STATUS = {0: "QD_OK", -1: "QD_ERR_INVALID", -2: "QD_ERR_CUDA", -3: "QD_ERR_OOM",
+           -4: "QD_ERR_NOT_CONVERGED", -5: "QD_ERR_NONFINITE", -6: "QD_ERR_TIMEOUT",
+           -7: "QD_ERR_INTERNAL"}
+
+
+class QDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MGParams(ctypes.Structure):
+    _fields_ = [("nlevels", ctypes.c_int),
+                ("block", (ctypes.c_int * 4) * QD_MAX_LEVELS),
+                ("nv", ctypes.c_int * QD_MAX_LEVELS),
+                ("null_tol", ctypes.c_double),
+                ("null_maxit", ctypes.c_int),
+                ("seed", ctypes.c_uint64),
+                ("smoother_steps", ctypes.c_int),
+                ("coarse_tol", ctypes.c_double),
+                ("coarse_maxit", ctypes.c_int),
+                ("coarse_restart", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int),
+                ("converged", ctypes.c_int),
+                ("max_true_rel_residual", ctypes.c_double),
+                ("iters_per_rhs", ctypes.POINTER(ctypes.c_int)),
+                ("true_rel_residual", ctypes.POINTER(ctypes.c_double))]
+
+
+class DeflParams(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int),
+                ("k", ctypes.c_int),
+                ("guard", ctypes.c_int),
+                ("eig_tol", ctypes.c_double),
+                ("solve_tol", ctypes.c_double),
+                ("maxit", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+class TraceParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64),
+                ("sample_offset", ctypes.c_int64),
+                ("nsamples", ctypes.c_int),
+                ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int),
+                ("restart", ctypes.c_int)]
+
+
+class TraceResult(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_double * 2),
+                ("mean", ctypes.c_double * 2),
+                ("estimate", ctypes.c_double * 2),
+                ("var", ctypes.c_double),
+                ("var_re", ctypes.c_double),
+                ("stderr_mean", ctypes.c_double),
+                ("var_jackknife_err", ctypes.c_double),
+                ("nsamples", ctypes.c_int),
+                ("iterations", ctypes.c_int),
+                ("max_true_rel_residual", ctypes.c_double),
+                ("t_samples", ctypes.POINTER(ctypes.c_double)),
+                ("ZhV", ctypes.POINTER(ctypes.c_double)),
+                ("UhKZ", ctypes.POINTER(ctypes.c_double))]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_IPTR = ctypes.POINTER(ctypes.c_int)
+_DPTR = ctypes.POINTER(ctypes.c_double)
+_I64PTR = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes); the ABI's exported symbols
+SIGNATURES = {
+    "qd_abi_version": (_I, []),
+    "qd_last_error": (ctypes.c_char_p, []),
+    "qd_ctx_create": (_I, [_PP, _I, _P]),
+    "qd_ctx_destroy": (_I, [_P]),
+    "qd_eo_index": (_I, [_IPTR, _I64PTR]),
+    "qd_gauge_create": (_I, [_P, _IPTR, _P, _PP]),
+    "qd_gauge_destroy": (_I, [_P]),
+    "qd_field_reorder": (_I, [_P, _P, _I, _I, _P, _P]),
+    "qd_rademacher": (_I, [_P, _P, ctypes.c_uint64, ctypes.c_int64, _I, _P]),
+    "qd_dirac_apply": (_I, [_P, _P, _D, _D, _I, _I, _P, _P]),
+    "qd_mg_params_default": (None, [ctypes.POINTER(MGParams)]),
+    "qd_mg_setup": (_I, [_P, _P, _D, _D, ctypes.POINTER(MGParams), _P, _PP]),
+    "qd_mg_destroy": (_I, [_P]),
+    "qd_mg_level_info": (_I, [_P, _I, _IPTR, _IPTR, _I64PTR, _IPTR]),
+    "qd_prolongate": (_I, [_P, _I, _I, _P, _P]),
+    "qd_restrict": (_I, [_P, _I, _I, _P, _P]),
+    "qd_coarse_apply": (_I, [_P, _I, _I, _P, _P]),
+    "qd_solve": (_I, [_P, _P, _P, _D, _D, _I, _P, _P, _D, _I, _I, ctypes.POINTER(SolveStats)]),
+    "qd_defl_params_default": (None, [ctypes.POINTER(DeflParams)]),
+    "qd_defl_create": (_I, [_P, _P, _P, _D, _D, ctypes.POINTER(DeflParams), _P, _PP]),
+    "qd_defl_destroy": (_I, [_P]),
+    "qd_defl_set_rank": (_I, [_P, _I, _DPTR]),
+    "qd_defl_info": (_I, [_P, _DPTR, _DPTR, _IPTR]),
+    "qd_deflate_project": (_I, [_P, _I, _P, _P]),
+    "qd_deflate_coeffs": (_I, [_P, _I, _P, _DPTR, _DPTR]),
+    "qd_hutchinson_trace": (_I, [_P, _P, _P, _P, _D, _D, ctypes.POINTER(TraceParams),
+                                 ctypes.POINTER(TraceResult)]),
+    "qd_prof_enable": (_I, [_P, _I]),
+    "qd_prof_read": (_I, [_P, _I, _I64PTR, _DPTR, _DPTR, _DPTR, _I]),
+}
+
+PROF_KINDS = {"wilson_f64": 0, "wilson_f32": 1, "coarse_f64": 2, "coarse_f32": 3, "prolong_f64": 4,
+              "prolong_f32": 5, "restrict_f64": 6, "restrict_f32": 7}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libqdtrace.so (once) and declare every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise QDError(QD_ERR_INTERNAL, f"{path} not found: build it with "
+                      "`python -m paper_1909_12234_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, allow=()):
+    if rc != QD_OK and rc not in allow:
+        raise QDError(rc, load().qd_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    """Device pointer of a contiguous complex128 CUDA tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise QDError(QD_ERR_INVALID, "expected a CUDA tensor")
+    if t.dtype != torch.complex128 or not t.is_contiguous():
+        raise QDError(QD_ERR_INVALID, "expected a contiguous torch.complex128 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dims(dims):
+    return (ctypes.c_int * 4)(*[int(d) for d in dims])
+
+
+def eo_index(dims):
+    """eo_index(dims)[lex] from the library (host-side index arithmetic)."""
+    V = int(np.prod(dims))
+    out = np.empty(V, dtype=np.int64)
+    _check(load().qd_eo_index(_dims(dims), out.ctypes.data_as(_I64PTR)))
+    return out
+
+
+class Context:
+    """qd_ctx on one device, issuing work on a torch CUDA stream."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check(load().qd_ctx_create(ctypes.byref(h), self.device, ctypes.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().qd_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Gauge:
+    """qd_gauge: links (4, V, 3, 3) complex128 numpy array (U[mu, lex])."""
+
+    def __init__(self, ctx, dims, links):
+        self.ctx = ctx
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        canon = np.ascontiguousarray(np.transpose(np.asarray(links, dtype=np.complex128), (1, 0, 2, 3)))
+        if canon.shape != (self.V, 4, 3, 3):
+            raise QDError(QD_ERR_INVALID, "links must have shape (4, V, 3, 3)")
+        h = ctypes.c_void_p()
+        _check(load().qd_gauge_create(ctx.h, _dims(self.dims), canon.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().qd_gauge_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def field_reorder(ctx, gauge, nrhs, to_qd, inp, out):
+    _check(load().qd_field_reorder(ctx.h, gauge.h, int(nrhs), 1 if to_qd else 0, _ptr(inp), _ptr(out)))
+
+
+def to_qd(ctx, gauge, x):
+    """Host field (V, 4, 3, s) numpy, lexicographic -> device qd layout (V, 12, s)."""
+    import torch
+    x = np.asarray(x, dtype=np.complex128)
+    s = x.shape[3]
+    canon = torch.from_numpy(np.ascontiguousarray(np.transpose(x.reshape(gauge.V, 12, s), (2, 0, 1))))
+    canon = canon.to(f"cuda:{ctx.device}")
+    out = torch.empty((gauge.V, 12, s), dtype=torch.complex128, device=f"cuda:{ctx.device}")
+    field_reorder(ctx, gauge, s, True, canon, out)
+    return out
+
+
+def from_qd(ctx, gauge, y):
+    """Device qd-layout field (V, 12, s) -> host (V, 4, 3, s) numpy, lexicographic."""
+    import torch
+    s = y.shape[2]
+    canon = torch.empty((s, gauge.V, 12), dtype=torch.complex128, device=y.device)
+    field_reorder(ctx, gauge, s, False, y, canon)
+    torch.cuda.synchronize(y.device)
+    return np.transpose(canon.cpu().numpy(), (1, 2, 0)).reshape(gauge.V, 4, 3, s)
+
+
+def rademacher(ctx, gauge, seed, sample_offset, nrhs, out):
+    _check(load().qd_rademacher(ctx.h, gauge.h, int(seed), int(sample_offset), int(nrhs), _ptr(out)))
+
+
+def dirac_apply(ctx, gauge, m0, tau, dagger, nrhs, inp, out):
+    _check(load().qd_dirac_apply(ctx.h, gauge.h, float(m0), float(tau), 1 if dagger else 0, int(nrhs),
+                                 _ptr(inp), _ptr(out)))
+
+
+def mg_params(nlevels=1, blocks=((2, 2, 2, 2),), nvs=(12,), **kw):
+    p = MGParams()
+    load().qd_mg_params_default(ctypes.byref(p))
+    p.nlevels = int(nlevels)
+    for l in range(nlevels):
+        for m in range(4):
+            p.block[l][m] = int(blocks[l][m])
+        p.nv[l] = int(nvs[l])
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Multigrid:
+    """qd_mg handle (adaptive setup)."""
+
+    def __init__(self, ctx, gauge, m0, tau, params, injected_null=None):
+        self.ctx, self.gauge, self.m0, self.tau = ctx, gauge, float(m0), float(tau)
+        self.params = params
+        h = ctypes.c_void_p()
+        inj = _ptr(injected_null) if injected_null is not None else None
+        _check(load().qd_mg_setup(ctx.h, gauge.h, self.m0, self.tau, ctypes.byref(params), inj, ctypes.byref(h)))
+        self.h = h
+
+    def level_info(self, level):
+        dims = (ctypes.c_int * 4)()
+        dof = ctypes.c_int()
+        ns = ctypes.c_int64()
+        nv = self.params.nv[level] if level < self.params.nlevels else 0
+        steps = (ctypes.c_int * max(nv, 1))()
+        _check(load().qd_mg_level_info(self.h, int(level), dims, ctypes.byref(dof), ctypes.byref(ns), steps))
+        return tuple(dims), dof.value, ns.value, list(steps)[:nv]
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().qd_mg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prolongate(mg, level, nrhs, coarse, fine):
+    _check(load().qd_prolongate(mg.h, int(level), int(nrhs), _ptr(coarse), _ptr(fine)))
+
+
+def restrict(mg, level, nrhs, fine, coarse):
+    _check(load().qd_restrict(mg.h, int(level), int(nrhs), _ptr(fine), _ptr(coarse)))
+
+
+def coarse_apply(mg, level, nrhs, inp, out):
+    _check(load().qd_coarse_apply(mg.h, int(level), int(nrhs), _ptr(inp), _ptr(out)))
+
+
+def solve(ctx, gauge, mg, m0, tau, nrhs, b, x, tol, maxit=10000, restart=16, allow_not_converged=False):
+    """Returns (status, iterations, per-column iterations, per-column true residual)."""
+    it = (ctypes.c_int * nrhs)()
+    rel = (ctypes.c_double * nrhs)()
+    st = SolveStats(0, 0, 0.0, it, rel)
+    rc = load().qd_solve(ctx.h, gauge.h, mg.h if mg is not None else None, float(m0), float(tau), int(nrhs),
+                         _ptr(b), _ptr(x), float(tol), int(maxit), int(restart), ctypes.byref(st))
+    _check(rc, allow=(QD_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return rc, st.iterations, list(it), list(rel)
+
+
+def defl_params(kind=QD_DEFL_MG_OBLIQUE, k=24, **kw):
+    p = DeflParams()
+    load().qd_defl_params_default(ctypes.byref(p))
+    p.kind = int(kind)
+    p.k = int(k)
+    for key, v in kw.items():
+        setattr(p, key, v)
+    return p
+
+
+class Deflation:
+    """qd_defl handle (Algorithm 1 or 2 deflation space)."""
+
+    def __init__(self, ctx, gauge, mg, m0, tau, params, injected_basis=None):
+        self.ctx, self.gauge, self.mg, self.params = ctx, gauge, mg, params
+        h = ctypes.c_void_p()
+        inj = _ptr(injected_basis) if injected_basis is not None else None
+        _check(load().qd_defl_create(ctx.h, gauge.h, mg.h if mg is not None else None, float(m0), float(tau),
+                                     ctypes.byref(params), inj, ctypes.byref(h)))
+        self.h = h
+        self.rank = params.k
+
+    def set_rank(self, r):
+        t0 = (ctypes.c_double * 2)()
+        _check(load().qd_defl_set_rank(self.h, int(r), t0))
+        self.rank = int(r)
+        return complex(t0[0], t0[1])
+
+    def info(self):
+        k = self.params.k
+        mu = (ctypes.c_double * k)()
+        lam = (ctypes.c_double * k)()
+        its = ctypes.c_int()
+        _check(load().qd_defl_info(self.h, mu, lam, ctypes.byref(its)))
+        return np.array(mu[:]), np.array(lam[:self.rank]), its.value
+
+    def project(self, nrhs, z, out):
+        _check(load().qd_deflate_project(self.h, int(nrhs), _ptr(z), _ptr(out)))
+
+    def coeffs(self, nrhs, z):
+        k = self.params.k
+        zhv = np.zeros((nrhs, k, 2))
+        uhkz = np.zeros((k, nrhs, 2))
+        _check(load().qd_deflate_coeffs(self.h, int(nrhs), _ptr(z), zhv.ctypes.data_as(_DPTR),
+                                        uhkz.ctypes.data_as(_DPTR)))
+        return zhv[..., 0] + 1j * zhv[..., 1], uhkz[..., 0] + 1j * uhkz[..., 1]
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().qd_defl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prof_enable(ctx, on):
+    _check(load().qd_prof_enable(ctx.h, 1 if on else 0))
+
+
+def prof_read(ctx, kind, reset=False):
+    """Totals of one kernel kind: dict(launches, ms, flops, bytes)."""
+    n = ctypes.c_int64()
+    ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    k = PROF_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(load().qd_prof_read(ctx.h, k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by),
+                               1 if reset else 0))
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
+
+
+def hutchinson_trace(ctx, gauge, mg, defl, m0, tau, seed, sample_offset, nsamples, tol, maxit=10000,
+                     restart=16, want_samples=True, want_coeffs=False, allow_not_converged=False):
+    """One multi-RHS batch of the deflated estimator; returns a dict."""
+    p = TraceParams(int(seed), int(sample_offset), int(nsamples), float(tol), int(maxit), int(restart))
+    r = TraceResult()
+    ts = np.zeros((nsamples, 2)) if want_samples else None
+    k = defl.params.k if defl is not None else 0
+    zhv = np.zeros((nsamples, k, 2)) if want_coeffs and k else None
+    uhkz = np.zeros((k, nsamples, 2)) if want_coeffs and k else None
+    r.t_samples = ts.ctypes.data_as(_DPTR) if ts is not None else None
+    r.ZhV = zhv.ctypes.data_as(_DPTR) if zhv is not None else None
+    r.UhKZ = uhkz.ctypes.data_as(_DPTR) if uhkz is not None else None
+    rc = load().qd_hutchinson_trace(ctx.h, gauge.h, mg.h if mg is not None else None,
+                                    defl.h if defl is not None else None, float(m0), float(tau),
+                                    ctypes.byref(p), ctypes.byref(r))
+    _check(rc, allow=(QD_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    out = {
+        "status": rc,
+        "t0": complex(r.t0[0], r.t0[1]),
+        "mean": complex(r.mean[0], r.mean[1]),
+        "estimate": complex(r.estimate[0], r.estimate[1]),
+        "var": r.var, "var_re": r.var_re, "stderr": r.stderr_mean,
+        "var_jackknife_err": r.var_jackknife_err, "iterations": r.iterations,
+        "max_true_rel_residual": r.max_true_rel_residual, "s": r.nsamples,
+    }
+    if ts is not None:
+        out["t"] = ts[:, 0] + 1j * ts[:, 1]
+    if zhv is not None:
+        out["ZhV"] = zhv[..., 0] + 1j * zhv[..., 1]
+        out["UhKZ"] = uhkz[..., 0] + 1j * uhkz[..., 1]
+    return out

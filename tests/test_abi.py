@@ -1,0 +1,88 @@
+"""The C-ABI library: it loads, exports every symbol include/qdtrace.h
+declares, its struct layouts match the binding's, and the host-side
+even-odd map is bit-exact against the oracle.  No GPU needed."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import lattice
+from paper_1909_12234_gb300 import build as qbuild
+from paper_1909_12234_gb300 import qdtrace as qd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qdtrace.h")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def library():
+    if not os.path.exists(qd.LIB_PATH):
+        qbuild.build()
+    return qd.load()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qd_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(library):
+    names = _declared()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(library, n), f"{n} missing from libqdtrace.so"
+    assert set(names) == set(qd.SIGNATURES), "binding and header disagree"
+
+
+def test_abi_version(library):
+    assert library.qd_abi_version() == 1
+
+
+def test_struct_layouts_match_c(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "qdtrace.h"
+int main(void) {
+  printf("%zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol), offsetof(qd_mg_params, coarse_restart));
+  printf("%zu %zu\n", sizeof(qd_solve_stats), offsetof(qd_solve_stats, true_rel_residual));
+  printf("%zu %zu\n", sizeof(qd_defl_params), offsetof(qd_defl_params, seed));
+  printf("%zu %zu\n", sizeof(qd_trace_params), offsetof(qd_trace_params, restart));
+  printf("%zu %zu %zu\n", sizeof(qd_trace_result), offsetof(qd_trace_result, nsamples), offsetof(qd_trace_result, UhKZ));
+  return 0;
+}''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [list(map(int, l.split())) for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines()]
+    want = [
+        [ctypes.sizeof(qd.MGParams), qd.MGParams.null_tol.offset, qd.MGParams.coarse_restart.offset],
+        [ctypes.sizeof(qd.SolveStats), qd.SolveStats.true_rel_residual.offset],
+        [ctypes.sizeof(qd.DeflParams), qd.DeflParams.seed.offset],
+        [ctypes.sizeof(qd.TraceParams), qd.TraceParams.restart.offset],
+        [ctypes.sizeof(qd.TraceResult), qd.TraceResult.nsamples.offset, qd.TraceResult.UhKZ.offset],
+    ]
+    assert got == want
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 2, 2, 2), (8, 4, 6, 2), (6, 6, 6, 6), (4, 3, 5, 2)])
+def test_eo_index_bit_exact(dims):
+    assert np.array_equal(qd.eo_index(dims), lattice.eo_index(dims))
+
+
+def test_eo_index_rejects_odd_lx():
+    with pytest.raises(qd.QDError) as e:
+        qd.eo_index((3, 4, 4, 4))
+    assert e.value.code == qd.QD_ERR_INVALID
+
+
+def test_defaults(library):
+    p = qd.mg_params()
+    assert p.null_tol == 1e-2 and p.null_maxit == 200 and p.nv[0] == 12
+    assert tuple(p.block[0]) == (2, 2, 2, 2)
+    d = qd.defl_params()
+    assert d.kind == qd.QD_DEFL_MG_OBLIQUE and d.k == 24

@@ -1,0 +1,127 @@
+"""GPU parity: reorder, Rademacher noise (bit-exact) and the FP64 Wilson
+stencil (1e-12 relative) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import lattice, philox, wilson
+from paper_1909_12234_gb300 import synth
+
+from gpu_util import dev, host, need_gpu, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qd():
+    need_gpu()
+    from paper_1909_12234_gb300 import qdtrace
+    qdtrace.load()
+    return qdtrace
+
+
+@pytest.fixture(scope="module")
+def ctx(qd):
+    return qd.Context(0)
+
+
+DIMS = [(4, 4, 4, 4), (2, 2, 2, 2), (8, 4, 6, 2), (4, 2, 2, 6), (6, 6, 6, 6)]
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_reorder_places_sites_by_even_odd_index(qd, ctx, dims):
+    U = synth.random_su3_links(dims, 0.3, 1)
+    g = qd.Gauge(ctx, dims, U)
+    V = g.V
+    s = 3
+    x = synth.random_field(dims, s, 2)
+    y = qd.to_qd(ctx, g, x)
+    eo = lattice.eo_index(dims)
+    want = np.empty((V, 12, s), dtype=complex)
+    want[eo] = x.reshape(V, 12, s)
+    assert np.array_equal(host(y), want)
+    assert np.array_equal(qd.from_qd(ctx, g, y), x)
+
+
+@pytest.mark.parametrize("dims,seed,offset,s", [((4, 4, 4, 4), 101, 0, 32), ((8, 4, 6, 2), 7, 5, 3),
+                                                ((2, 2, 2, 2), 2**40 + 3, 1000, 1), ((6, 6, 6, 6), 9, 0, 70)])
+def test_rademacher_bit_exact(qd, ctx, dims, seed, offset, s):
+    U = synth.random_su3_links(dims, 0.0, 0, unit=True)
+    g = qd.Gauge(ctx, dims, U)
+    out = torch.empty((g.V, 12, s), dtype=torch.complex128, device="cuda:0")
+    qd.rademacher(ctx, g, seed, offset, s, out)
+    got = qd.from_qd(ctx, g, out).reshape(12 * g.V, s)
+    want = philox.rademacher(12 * g.V, seed, range(offset, offset + s))
+    assert np.array_equal(got.real, want) and np.all(got.imag == 0)
+
+
+def _apply(qd, ctx, g, m0, tau, dag, x):
+    xin = qd.to_qd(ctx, g, x)
+    out = torch.empty_like(xin)
+    qd.dirac_apply(ctx, g, m0, tau, dag, x.shape[3], xin, out)
+    return qd.from_qd(ctx, g, out)
+
+
+@pytest.mark.parametrize("dims,s", [((4, 4, 4, 4), 1), ((4, 4, 4, 4), 32), ((8, 4, 6, 2), 3),
+                                    ((4, 2, 2, 6), 70), ((2, 2, 2, 2), 5), ((6, 6, 6, 6), 33)])
+@pytest.mark.parametrize("tau,dag", [(0.0, False), (0.25, False), (0.25, True)])
+def test_wilson_fp64_matches_oracle(qd, ctx, dims, s, tau, dag):
+    U = synth.random_su3_links(dims, 0.3, 4)
+    g = qd.Gauge(ctx, dims, U)
+    x = synth.random_field(dims, s, 3)
+    got = _apply(qd, ctx, g, -0.4, tau, dag, x)
+    ref = wilson.dirac_apply(U, x, -0.4, dims, tau=tau, dagger=dag)
+    assert rel_err(got, ref) < 1e-12
+
+
+def test_wilson_full_size_8x4_64rhs(qd, ctx):
+    # the estimator workload's size: 8^4 lattice, 64 right-hand sides
+    dims = (8, 8, 8, 8)
+    U = synth.random_su3_links(dims, 0.3, 2)
+    g = qd.Gauge(ctx, dims, U)
+    x = synth.random_field(dims, 64, 9)
+    got = _apply(qd, ctx, g, -0.8, 0.0, False, x)
+    cols = [0, 17, 63]
+    ref = wilson.dirac_apply(U, x[..., cols], -0.8, dims)
+    assert rel_err(got[..., cols], ref) < 1e-12
+
+
+def test_gamma5_hermiticity_on_gpu(qd, ctx):
+    dims = (4, 4, 4, 4)
+    U = synth.random_su3_links(dims, 0.3, 6)
+    g = qd.Gauge(ctx, dims, U)
+    x = synth.random_field(dims, 2, 1)
+    y = synth.random_field(dims, 2, 2)
+    Ax = _apply(qd, ctx, g, -0.4, 0.0, False, x)
+    g5 = np.array([1, 1, -1, -1])[None, :, None, None]
+    g5Ag5y = g5 * _apply(qd, ctx, g, -0.4, 0.0, False, g5 * y)
+    lhs = np.einsum("vsar,vsar->r", y.conj(), Ax)
+    rhs = np.einsum("vsar,vsar->r", g5Ag5y.conj(), x)
+    assert np.allclose(lhs, rhs, rtol=1e-12)
+
+
+def test_free_field_plane_wave_on_gpu(qd, ctx):
+    dims = (4, 4, 4, 4)
+    U = synth.random_su3_links(dims, 0.0, 0, unit=True)
+    g = qd.Gauge(ctx, dims, U)
+    c = lattice.coords(dims)
+    p = 2 * np.pi * np.array([1, 2, 0, 3]) / np.array(dims)
+    gm = wilson.gammas()
+    M = -0.4 + np.sum(1 - np.cos(p))
+    Dp = M * np.eye(4) + 1j * sum(gm[m] * np.sin(p[m]) for m in range(4))
+    lam, vec = np.linalg.eig(Dp)
+    x = (np.exp(1j * (c @ p))[:, None, None] * vec[:, 0][None, :, None] * np.array([1.0, -0.5, 0.25])[None, None, :])
+    y = _apply(qd, ctx, g, -0.4, 0.0, False, x[..., None])[..., 0]
+    assert np.abs(y - lam[0] * x).max() < 1e-12
+
+
+def test_invalid_arguments_are_rejected(qd, ctx):
+    dims = (4, 4, 4, 4)
+    g = qd.Gauge(ctx, dims, synth.random_su3_links(dims, 0.0, 0, unit=True))
+    t = torch.zeros((g.V, 12, 1), dtype=torch.complex128, device="cuda:0")
+    with pytest.raises(qd.QDError) as e:
+        qd.dirac_apply(ctx, g, -0.4, 0.0, False, 1, t, t)  # in == out
+    assert e.value.code == qd.QD_ERR_INVALID
+    with pytest.raises(qd.QDError):
+        qd.Gauge(ctx, (3, 4, 4, 4), np.zeros((4, 48, 3, 3), complex))  # odd Lx
+    with pytest.raises(qd.QDError):
+        qd.rademacher(ctx, g, 1, 2**32 - 1, 2, torch.zeros((g.V, 12, 2), dtype=torch.complex128, device="cuda:0"))

@@ -1,0 +1,94 @@
+"""GPU solves (Sec. 1 inexact solves, Sec. 2 multigrid): the true residual
+meets the tolerance when checked by the oracle's operator, the error obeys
+the kappa * xi bound against a dense solve, and failures are reported."""
+import numpy as np
+import pytest
+
+from oracle import dense, multigrid as omg
+from paper_1909_12234_gb300 import synth
+
+from gpu_util import dev, host, need_gpu, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qd():
+    need_gpu()
+    from paper_1909_12234_gb300 import qdtrace
+    qdtrace.load()
+    return qdtrace
+
+
+@pytest.fixture(scope="module")
+def ctx(qd):
+    return qd.Context(0)
+
+
+def test_unpreconditioned_solve_small(qd, ctx):
+    dims, m0 = (4, 4, 2, 2), -0.4
+    U = synth.random_su3_links(dims, 0.3, 8)
+    g = qd.Gauge(ctx, dims, U)
+    A = dense.dirac_matrix(U, m0, dims)
+    b = synth.random_field(dims, 5, 1)
+    bd = qd.to_qd(ctx, g, b)
+    xd = torch.empty_like(bd)
+    rc, its, it_col, rel = qd.solve(ctx, g, None, m0, 0.0, 5, bd, xd, 1e-10, maxit=5000, restart=16)
+    x = qd.from_qd(ctx, g, xd).reshape(-1, 5)
+    B = b.reshape(-1, 5)
+    true_rel = np.linalg.norm(B - A @ x, axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(true_rel <= 1e-10)
+    assert np.allclose(true_rel, rel, rtol=1e-3)
+    x_lu = np.linalg.solve(A, B)
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= np.linalg.cond(A) * 1e-10
+
+
+def test_mg_solve_8x4(qd, ctx):
+    dims, m0, s = (8, 8, 8, 8), -0.8, 8
+    U = synth.random_su3_links(dims, 0.3, 2)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(1, [(2, 2, 2, 2)], [12]))
+    b = synth.random_field(dims, s, 4)
+    bd = qd.to_qd(ctx, g, b)
+    xd = torch.empty_like(bd)
+    rc, its, it_col, rel = qd.solve(ctx, g, mg, m0, 0.0, s, bd, xd, 1e-8, maxit=500, restart=16)
+    x = qd.from_qd(ctx, g, xd).reshape(-1, s)
+    A = omg.fine_level(U, m0, dims).matrix
+    B = b.reshape(-1, s)
+    true_rel = np.linalg.norm(B - A @ x, axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(true_rel <= 1e-8), true_rel
+    assert its < 100, its  # multigrid preconditioning works
+
+
+def test_not_converged_is_reported(qd, ctx):
+    dims, m0 = (4, 4, 4, 4), -0.4
+    g = qd.Gauge(ctx, dims, synth.random_su3_links(dims, 0.3, 1))
+    bd = qd.to_qd(ctx, g, synth.random_field(dims, 2, 1))
+    xd = torch.empty_like(bd)
+    rc, its, it_col, rel = qd.solve(ctx, g, None, m0, 0.0, 2, bd, xd, 1e-12, maxit=1, restart=4,
+                                    allow_not_converged=True)
+    assert rc == qd.QD_ERR_NOT_CONVERGED and its == 1 and all(r > 1e-12 for r in rel)
+
+
+def test_nonfinite_input_is_reported(qd, ctx):
+    dims, m0 = (4, 4, 4, 4), -0.4
+    g = qd.Gauge(ctx, dims, synth.random_su3_links(dims, 0.3, 1))
+    b = synth.random_field(dims, 2, 1)
+    b[3, 1, 2, 1] = np.nan
+    bd = qd.to_qd(ctx, g, b)
+    xd = torch.empty_like(bd)
+    with pytest.raises(qd.QDError) as e:
+        qd.solve(ctx, g, None, m0, 0.0, 2, bd, xd, 1e-8, maxit=10)
+    assert e.value.code == qd.QD_ERR_NONFINITE
+
+
+def test_zero_rhs_column(qd, ctx):
+    dims, m0 = (4, 4, 4, 4), -0.4
+    g = qd.Gauge(ctx, dims, synth.random_su3_links(dims, 0.3, 1))
+    b = synth.random_field(dims, 3, 1)
+    b[..., 1] = 0.0
+    bd = qd.to_qd(ctx, g, b)
+    xd = torch.empty_like(bd)
+    rc, its, it_col, rel = qd.solve(ctx, g, None, m0, 0.0, 3, bd, xd, 1e-9, maxit=3000)
+    x = qd.from_qd(ctx, g, xd)
+    assert np.all(x[..., 1] == 0) and rel[1] == 0.0 and rel[0] <= 1e-9

@@ -1,0 +1,334 @@
+"""Benchmark: deflated Hutchinson samples/s at true relative residual 1e-8.
+
+Workload (the estimator configuration that fits one GPU): Wilson-Dirac
+operator on an 8^4 periodic lattice (N = 49,152), random SU(3) links
+exp(i 0.3 H) (seed 2), m0 = -0.8; two-level multigrid with 2^4 aggregates
+and 12 null vectors per chirality (24 coarse dofs per aggregate); Algorithm 2
+deflation of rank 24; 64 real Rademacher samples per step solved together,
+FP64 throughout, solves to ||b - A x|| <= 1e-8 ||b||.
+
+A step = one batch through the whole sample path: Rademacher noise (a1),
+deflation projection (a8, with the Wilson and transfer kernels), the
+multigrid-preconditioned GCR solves (a2-a6) and the trace statistics (a9).
+The adaptive setup and the deflation space (a7, a10) are built once before
+timing and reported as setup_s; the end-to-end number repeats them per step.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun (N > 1) each rank takes its own sample range (replicas: the
+samples are independent) and only the timing is reduced (max over ranks).
+"""
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WL = dict(
+    workload="wilson-dirac 8^4 eps0.3 seed2 m0=-0.8, 2-level MG (2^4 blocks, nv 12), Algorithm 2 k=24, "
+             "64 Rademacher samples/step, FP64, true rel. residual 1e-8",
+    dims=(8, 8, 8, 8), eps=0.3, link_seed=2, m0=-0.8, blocks=[(2, 2, 2, 2)], nvs=[12], k=24, guard=16,
+    s=64, tol=1e-8, noise_seed=102, restart=16, maxit=500,
+)
+METRIC = "deflated Hutchinson samples/s @res 1e-8"
+UNIT = "samples/s"
+# Recipe peaks (MEASURED_PEAKS.json holds HBM and bf16; FP64 is the recipe's
+# nominal 1.25 TFLOP/s, matching the 1.20 TFLOP/s an FMA-chain probe measured).
+FP64_PEAK_TFLOPS = 1.25
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _setup(qd, ctx, U):
+    g = qd.Gauge(ctx, WL["dims"], U)
+    mg = qd.Multigrid(ctx, g, WL["m0"], 0.0, qd.mg_params(1, WL["blocks"], WL["nvs"]))
+    d = qd.Deflation(ctx, g, mg, WL["m0"], 0.0,
+                     qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
+                                    solve_tol=1e-10, maxit=60))
+    return g, mg, d
+
+
+def _batch(qd, ctx, g, mg, d, offset):
+    return qd.hutchinson_trace(ctx, g, mg, d, WL["m0"], 0.0, seed=WL["noise_seed"], sample_offset=offset,
+                               nsamples=WL["s"], tol=WL["tol"], maxit=WL["maxit"], restart=WL["restart"])
+
+
+def cpu_baseline(samples=2):
+    """The FP64 oracle on this host's cores: setup untimed, `samples` solves timed."""
+    from oracle import deflation as odefl
+    from oracle import estimator
+    from oracle import multigrid as omg
+    from paper_1909_12234_gb300 import synth
+    U = synth.random_su3_links(WL["dims"], WL["eps"], WL["link_seed"])
+    H = omg.setup(U, WL["m0"], WL["dims"], WL["blocks"], WL["nvs"], seed=7)
+    alg = odefl.Alg2(H.transfers[0], H.matrices[0], WL["k"])
+    lev = H.levels[0]
+    t = time.perf_counter()
+    estimator.hutchinson(lev.matvec, lev.n, WL["noise_seed"], range(samples), WL["tol"],
+                         project=lambda z: alg.project(lev.matvec, z), t0=alg.t0,
+                         precond=lambda r: H.vcycle(0, r), restart=WL["restart"])
+    dt = time.perf_counter() - t
+    return {"value": samples / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{samples} samples of the workload (oracle setup untimed); numpy/scipy FP64, sparse "
+                      f"ops single-threaded, BLAS threads up to cores"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import deflation as odefl
+    from oracle import estimator
+    from oracle import multigrid as omg
+    from paper_1909_12234_gb300 import synth
+    U = synth.random_su3_links(WL["dims"], WL["eps"], WL["link_seed"])
+    H = omg.setup(U, WL["m0"], WL["dims"], WL["blocks"], WL["nvs"], seed=7)
+    alg = odefl.Alg2(H.transfers[0], H.matrices[0], WL["k"])
+    lev = H.levels[0]
+    per_step = 1
+
+    def step(i):
+        estimator.hutchinson(lev.matvec, lev.n, WL["noise_seed"], range(i * per_step, (i + 1) * per_step),
+                             WL["tol"], project=lambda z: alg.project(lev.matvec, z), t0=alg.t0,
+                             precond=lambda r: H.vcycle(0, r), restart=WL["restart"])
+
+    for i in range(args.warmup):
+        step(i)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    dt = time.perf_counter() - t
+    value = args.steps * per_step / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WL["workload"] + f"; reference step = {per_step} sample"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{per_step} sample per step (oracle setup untimed)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1909_12234_gb300 import qdtrace as qd
+    from paper_1909_12234_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    qd.load()
+    ctx = qd.Context(local)
+    stream = ctx.stream
+    U = synth.random_su3_links(WL["dims"], WL["eps"], WL["link_seed"])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    g, mg, d = _setup(qd, ctx, U)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t
+    s = WL["s"]
+
+    def offset(i):
+        return (i * world + rank) * s
+
+    for i in range(args.warmup):
+        _batch(qd, ctx, g, mg, d, offset(i))
+    clocks = ClockSampler(local)
+    clocks.start()
+    qd.prof_enable(ctx, True)
+    for k in qd.PROF_KINDS:
+        qd.prof_read(ctx, k, reset=True)
+    launches0 = qd.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    results = []
+    for i in range(args.steps):
+        results.append(_batch(qd, ctx, g, mg, d, offset(args.warmup + i)))
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = qd.launch_count() - launches0
+    qd.prof_enable(ctx, False)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    if dist:
+        tt = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    prof = {k: qd.prof_read(ctx, k) for k in qd.PROF_KINDS}
+    value = args.steps * s * world / (ms_total / 1e3)
+    iters = [r["iterations"] for r in results]
+    worst = max(r["max_true_rel_residual"] for r in results)
+
+    # roofline of the dominant kernel (largest summed device time)
+    top = max(prof, key=lambda k: prof[k]["ms"])
+    pt = prof[top]
+    peaks = _peaks()
+    if top.endswith("f64"):
+        achieved = pt["flops"] / (pt["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": top, "launches": pt["launches"], "ms_per_launch": pt["ms"] / max(pt["launches"], 1),
+                "peak_source": "recipe nominal FP64 (1.25 TFLOP/s); FMA probe measured 1.20"}
+    else:
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = pt["bytes"] / (pt["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": top, "launches": pt["launches"],
+                "ms_per_launch": pt["ms"] / max(pt["launches"], 1),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "share_of_step": round(v["ms"] / ms_total, 4)} for k, v in prof.items() if v["launches"]}
+
+    # end to end through the public API: links from pinned host memory,
+    # setup, one batch, results read back, per step
+    e2e_steps = args.e2e_steps
+    canon = np.ascontiguousarray(np.transpose(U, (1, 0, 2, 3)))
+    pinned = torch.from_numpy(canon.view(np.float64).reshape(-1)).pin_memory()
+    h2d = pinned.numel() * 8
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for i in range(e2e_steps):
+        g2 = qd.Gauge.from_host_buffer(ctx, WL["dims"], pinned)
+        mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, qd.mg_params(1, WL["blocks"], WL["nvs"]))
+        d2 = qd.Deflation(ctx, g2, mg2, WL["m0"], 0.0,
+                          qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
+                                         solve_tol=1e-10, maxit=60))
+        _batch(qd, ctx, g2, mg2, d2, offset(1000 + i))
+        d2.close()
+        mg2.close()
+        g2.close()
+    torch.cuda.synchronize()
+    e2e_dt = (time.perf_counter() - t) / max(e2e_steps, 1) if e2e_steps else float("nan")
+    if dist:
+        tt = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_dt = float(tt.item())
+    e2e = {"value": s * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": s * 16 + 6 * 8,
+           "scope": "per step: link upload from pinned host memory, adaptive MG setup, Algorithm 2 deflation "
+                    "space, one 64-sample batch, per-sample t_j and statistics read back"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(samples=args.cpu_samples)
+        except Exception as exc:  # report, never hide the GPU line
+            cpu = {"value": None, "unit": UNIT, "error": repr(exc)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WL["workload"], "parallelism": f"replicas x{world} (independent samples)",
+                       "l2": "working set > L2 (GCR basis 2 x 16 x 50 MB per batch)",
+                       "setup_s": round(setup_s, 3), "outer_iterations": iters,
+                       "max_true_rel_residual": worst,
+                       "estimate": [results[-1]["estimate"].real, results[-1]["stderr"]]},
+            "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    for o in (d, mg, g, ctx):
+        o.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-samples", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -318,6 +318,10 @@ int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg,
 /* Kernel timing (measurement support; the paper has no counterpart)         */
 /* ------------------------------------------------------------------------ */
 
+/* Number of kernels this library has launched since it was loaded (all
+ * contexts and threads). */
+long long qd_launch_count(void);
+
 /* Kernel kinds: operator x precision. */
 enum {
   QD_PROF_WILSON_F64 = 0,   /* a2 stencil, FP64 */

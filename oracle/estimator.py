@@ -17,6 +17,9 @@ with the deflated right-hand side).  Statistics, for complex samples t_j:
 * jackknife error of var: delete-one variances v_(i) over s - 1 samples,
   err = sqrt((s-1)/s * sum (v_(i) - mean v)^2).
 
+A sample variance needs s >= 2 and its jackknife s >= 3; below that the
+value is undefined and reported as 0 (this library's convention).
+
 Sums use ``math.fsum`` (correctly rounded), so the result does not depend on
 summation order.  Pinned by hand-computed examples and the identity that the
 jackknife error of a mean equals its standard error
@@ -38,6 +41,8 @@ def _fsum_c(v):
 def sample_variance(t):
     t = np.asarray(t, dtype=np.complex128)
     s = t.size
+    if s < 2:
+        return 0.0
     m = _fsum_c(t) / s
     return math.fsum(np.abs(t - m) ** 2) / (s - 1)
 
@@ -49,9 +54,12 @@ def statistics(t, t0=0.0):
     mean = _fsum_c(t) / s
     var = sample_variance(t)
     var_re = sample_variance(t.real)
-    loo = np.array([sample_variance(np.delete(t, i)) for i in range(s)])
-    loo_mean = math.fsum(loo) / s
-    jk = math.sqrt((s - 1) / s * math.fsum((loo - loo_mean) ** 2))
+    if s >= 3:
+        loo = np.array([sample_variance(np.delete(t, i)) for i in range(s)])
+        loo_mean = math.fsum(loo) / s
+        jk = math.sqrt((s - 1) / s * math.fsum((loo - loo_mean) ** 2))
+    else:
+        jk = 0.0
     return {
         "t0": complex(t0),
         "mean": mean,

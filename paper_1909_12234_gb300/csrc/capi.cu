@@ -453,6 +453,8 @@ int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, qd_defl* 
   return rc;
 }
 
+long long qd_launch_count(void) { return qd::launch_counter().load(); }
+
 int qd_prof_enable(qd_ctx* ctx, int enable) {
   return guarded([&] {
     NONNULL(ctx);

@@ -10,9 +10,10 @@
 //   P = A W U Lambda^{-1} U^H gamma5^W W^H (the K = gamma5 projector of
 //   Sec. 2.1 with V = W U).
 // Both eigenproblems are solved by block inverse subspace iteration with
-// Rayleigh-Ritz ("eigs" on the inverse with largest magnitude, Sec. 3.1):
-//   Y = H^{-1} X (inexact GCR solves to solve_tol), Q = orth(Y) by Cholesky
-//   QR applied twice, T = Q^H H Q, T S = S Theta, X = Q S.
+// Rayleigh-Ritz on the inverse ("eigs" on the inverse with largest
+// magnitude, Algorithm 1 step 1, Algorithm 2 step 2, Sec. 3.1):
+//   Y = H^{-1} X (inexact GCR solves to solve_tol), T = X^H Y = S N S^H,
+//   X <- orth(Y S) by Cholesky QR applied twice.
 // Sec. 2.2: the a-posteriori matrices Z^H W U_bar and U_bar^H gamma5^W W^H Z.
 #include "blas.cuh"
 #include "defl.cuh"
@@ -45,15 +46,26 @@ static void cholqr2(qd_ctx& ctx, int64_t n, int m, cplx* Y, cplx* tmp, DevBuf& s
   if (h) fail(QD_ERR_NONFINITE, "Cholesky QR: block is numerically rank deficient");
 }
 
+__global__ void k_reciprocal(int m, const double* __restrict__ in, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = 1.0 / in[i];
+}
+
 // Block inverse subspace iteration for the m eigenpairs of the Hermitian
-// H = Op gamma5 closest to 0.  X (n x m, ld m) out; theta (host, m) out.
+// H = Op gamma5 closest to 0.  Rayleigh-Ritz is done on H^{-1} (whose wanted
+// eigenvalues are the largest in magnitude, so spurious Ritz values of an
+// indefinite H cannot displace them), using T = X^H (H^{-1} X) without an
+// extra solve:
+//   Y = H^{-1} X;  T = X^H Y = S diag(nu) S^H;  order by |1/nu| ascending;
+//   residual_i = ||Y s_i - nu_i X s_i|| / |nu_i|;  X <- orth(Y S).
+// X (n x m, ld m) out: Ritz vectors; theta (host, m) out: 1/nu.
 static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, Precond<cplx>* M, const LevelGeom& geo, int m, int k,
                          double eig_tol, double solve_tol, int maxit, uint64_t seed, cplx* X,
                          std::vector<double>& theta, int& iters_out) {
   const int64_t n = A.n();
   const int dof = A.dof();
   const size_t blk = (size_t)n * m * sizeof(cplx);
-  DevBuf Yb(blk), Zb(blk), Tb(blk), small, eig((size_t)(3 * m * m + 4) * sizeof(cplx) + 4 * m * sizeof(double)),
+  DevBuf Yb(blk), Zb(blk), Tb(blk), small, eig((size_t)(3 * m * m + 4) * sizeof(cplx) + 6 * m * sizeof(double)),
       resid(m * sizeof(cplx)), iv((m + 8) * sizeof(int));
   cplx* Y = Yb.as<cplx>();
   cplx* Z = Zb.as<cplx>();
@@ -61,8 +73,10 @@ static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, Precond<cplx>* M, const
   cplx* Tmat = eig.as<cplx>();
   cplx* S = Tmat + (size_t)m * m;
   cplx* Ss = S + (size_t)m * m;
-  double* w = reinterpret_cast<double*>(Ss + (size_t)m * m);
-  double* ws = w + m;
+  double* nu = reinterpret_cast<double*>(Ss + (size_t)m * m);
+  double* mu = nu + m;
+  double* mus = mu + m;
+  double* nus = mus + m;
   random_starts_fill(ctx, geo, dof, seed, m, X);
   cholqr2(ctx, n, m, X, Tm, small);
   GCR<cplx> solver;
@@ -71,32 +85,37 @@ static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, Precond<cplx>* M, const
   for (; it < maxit; ++it) {
     // Y = H^{-1} X = gamma5 Op^{-1} X
     SolveInfo info;
-    solver.solve(ctx, A, M, X, Tm, m, solve_tol, 100000, 32, &info);
+    solver.solve(ctx, A, M, X, Tm, m, solve_tol, 20000, 32, &info);
     blas::gamma5(ctx, geo.nsites, dof, m, Tm, Y);
-    cholqr2(ctx, n, m, Y, Tm, small);
-    // Z = H Y = Op gamma5 Y
-    blas::gamma5(ctx, geo.nsites, dof, m, Y, Tm);
-    A.apply(ctx, Tm, Z, m);
-    blockdot(ctx, n, Y, m, m, Z, m, m, Tmat);
+    blockdot(ctx, n, X, m, m, Y, m, m, Tmat);
     hermitize(ctx, m, Tmat);
-    jacobi_eigh(ctx, m, Tmat, S, w, nullptr);
-    sort_by_abs(ctx, m, w, S, ws, Ss, iv.as<int>());
-    blockmul(ctx, n, Y, m, m, Ss, m, m, X, m, 1.0, 0.0);   // X = Q S
-    blockmul(ctx, n, Z, m, m, Ss, m, m, Tm, m, 1.0, 0.0);  // HX = Z S
-    eig_residuals(ctx, n, m, Tm, X, ws, resid.as<cplx>());
+    jacobi_eigh(ctx, m, Tmat, S, nu, nullptr);
+    k_reciprocal<<<div_up(m, 128), 128, 0, ctx.stream>>>(m, nu, mu);
+    QD_LAUNCH_CHECK();
+    sort_by_abs(ctx, m, mu, S, mus, Ss, iv.as<int>());
+    k_reciprocal<<<div_up(m, 128), 128, 0, ctx.stream>>>(m, mus, nus);
+    QD_LAUNCH_CHECK();
+    blockmul(ctx, n, X, m, m, Ss, m, m, Tm, m, 1.0, 0.0);  // Ritz vectors X S
+    blockmul(ctx, n, Y, m, m, Ss, m, m, Z, m, 1.0, 0.0);   // H^{-1} X S
+    eig_residuals(ctx, n, m, Z, Tm, nus, resid.as<cplx>());
     std::vector<cplx> hr(m);
+    std::vector<double> hnu(m);
     QD_CUDA(cudaMemcpyAsync(hr.data(), resid.as<cplx>(), m * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
-    QD_CUDA(cudaMemcpyAsync(theta.data(), ws, m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaMemcpyAsync(theta.data(), mus, m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaMemcpyAsync(hnu.data(), nus, m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
     QD_CUDA(cudaStreamSynchronize(ctx.stream));
     double worst = 0.0;
     for (int i = 0; i < k; ++i) {
-      const double rel = std::sqrt(hr[i].x) / (std::fabs(theta[i]) > 0 ? std::fabs(theta[i]) : 1.0);
+      const double rel = std::sqrt(hr[i].x) / (std::fabs(hnu[i]) > 0 ? std::fabs(hnu[i]) : 1.0);
       if (!(rel <= worst)) worst = rel;
     }
-    if (worst <= eig_tol) {
+    if (worst <= eig_tol || it + 1 == maxit) {
+      blas::copy(ctx, (int64_t)n * m, Tm, X);
       ++it;
       break;
     }
+    blas::copy(ctx, (int64_t)n * m, Z, X);
+    cholqr2(ctx, n, m, X, Tm, small);
   }
   iters_out = it;
 }

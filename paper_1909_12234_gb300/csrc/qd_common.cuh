@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <stdexcept>
@@ -32,8 +33,15 @@ inline void cuda_check(cudaError_t e, const char* what, const char* file, int li
                    std::to_string(line) + ")");
   }
 }
+// Kernels launched by this library since load (qd_launch_count()).
+std::atomic<long long>& launch_counter();
+
 #define QD_CUDA(call) ::qd::cuda_check((call), #call, __FILE__, __LINE__)
-#define QD_LAUNCH_CHECK() ::qd::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+#define QD_LAUNCH_CHECK()                                                      \
+  do {                                                                         \
+    ::qd::launch_counter().fetch_add(1, std::memory_order_relaxed);           \
+    ::qd::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__); \
+  } while (0)
 #define QD_REQUIRE(cond, msg)                                  \
   do {                                                         \
     if (!(cond)) ::qd::fail(QD_ERR_INVALID, std::string(msg)); \

@@ -135,6 +135,7 @@ SIGNATURES = {
     "qd_deflate_coeffs": (_I, [_P, _I, _P, _DPTR, _DPTR]),
     "qd_hutchinson_trace": (_I, [_P, _P, _P, _P, _D, _D, ctypes.POINTER(TraceParams),
                                  ctypes.POINTER(TraceResult)]),
+    "qd_launch_count": (ctypes.c_longlong, []),
     "qd_prof_enable": (_I, [_P, _I]),
     "qd_prof_read": (_I, [_P, _I, _I64PTR, _DPTR, _DPTR, _DPTR, _I]),
 }
@@ -227,6 +228,22 @@ class Gauge:
         _check(load().qd_gauge_create(ctx.h, _dims(self.dims), canon.ctypes.data_as(ctypes.c_void_p),
                                       ctypes.byref(h)))
         self.h = h
+
+    @classmethod
+    def from_host_buffer(cls, ctx, dims, host_tensor):
+        """Links already in the C ABI's host order [V][4][3][3] complex, given
+        as a contiguous (pinned) CPU torch tensor of float64 or complex128."""
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        if host_tensor.is_cuda or not host_tensor.is_contiguous() or host_tensor.numel() * host_tensor.element_size() != self.V * 4 * 9 * 16:
+            raise QDError(QD_ERR_INVALID, "host link buffer must be contiguous CPU memory of V*36 complex numbers")
+        h = ctypes.c_void_p()
+        _check(load().qd_gauge_create(ctx.h, _dims(self.dims), ctypes.c_void_p(host_tensor.data_ptr()),
+                                      ctypes.byref(h)))
+        self.h = h
+        return self
 
     def close(self):
         if getattr(self, "h", None):
@@ -400,6 +417,11 @@ class Deflation:
             self.close()
         except Exception:
             pass
+
+
+def launch_count():
+    """Kernels launched by libqdtrace since it was loaded."""
+    return int(load().qd_launch_count())
 
 
 def prof_enable(ctx, on):

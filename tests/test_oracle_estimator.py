@@ -18,6 +18,13 @@ def test_statistics_hand_example():
     assert math.isclose(st["var_jackknife_err"], math.sqrt(4.0 / 3.0))
 
 
+def test_statistics_degenerate_sample_counts():
+    st = estimator.statistics([3.0 + 1j])
+    assert st["mean"] == 3.0 + 1j and st["var"] == 0.0 and st["var_jackknife_err"] == 0.0
+    st = estimator.statistics([1.0, 3.0])
+    assert st["var"] == 2.0 and st["var_jackknife_err"] == 0.0
+
+
 def test_statistics_complex_and_real_part():
     t = np.array([1 + 1j, 1 - 1j, 3 + 1j, 3 - 1j])
     st = estimator.statistics(t)

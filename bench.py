@@ -282,7 +282,7 @@ def run_ours(args):
         tt = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_dt = float(tt.item())
-    e2e = {"value": s * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e = None if not e2e_steps else {"value": s * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": s * 16 + 6 * 8,
            "scope": "per step: link upload from pinned host memory, adaptive MG setup, Algorithm 2 deflation "
                     "space, one 64-sample batch, per-sample t_j and statistics read back"}

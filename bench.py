@@ -5,7 +5,10 @@ operator on an 8^4 periodic lattice (N = 49,152), random SU(3) links
 exp(i 0.3 H) (seed 2), m0 = -0.8; two-level multigrid with 2^4 aggregates
 and 12 null vectors per chirality (24 coarse dofs per aggregate); Algorithm 2
 deflation of rank 24; 64 real Rademacher samples per step solved together,
-FP64 throughout, solves to ||b - A x|| <= 1e-8 ||b||.
+solves to ||b - A x|| <= 1e-8 ||b|| measured on the FP64 residual.  The
+default path is mixed precision (FP32 flexible GCR and V-cycle inside FP64
+residual refinement); the plain FP64 path is timed in the same run
+("fp64_path").
 
 A step = one batch through the whole sample path: Rademacher noise (a1),
 deflation projection (a8, with the Wilson and transfer kernels), the
@@ -35,9 +38,9 @@ import numpy as np  # noqa: E402
 
 WL = dict(
     workload="wilson-dirac 8^4 eps0.3 seed2 m0=-0.8, 2-level MG (2^4 blocks, nv 12), Algorithm 2 k=24, "
-             "64 Rademacher samples/step, FP64, true rel. residual 1e-8",
+             "64 Rademacher samples/step, true FP64 rel. residual 1e-8",
     dims=(8, 8, 8, 8), eps=0.3, link_seed=2, m0=-0.8, blocks=[(2, 2, 2, 2)], nvs=[12], k=24, guard=16,
-    s=64, tol=1e-8, noise_seed=102, restart=16, maxit=500,
+    s=64, tol=1e-8, noise_seed=102, restart=16, maxit=500, inner_tol=1e-5,
 )
 METRIC = "deflated Hutchinson samples/s @res 1e-8"
 UNIT = "samples/s"
@@ -112,9 +115,10 @@ def _setup(qd, ctx, U):
     return g, mg, d
 
 
-def _batch(qd, ctx, g, mg, d, offset):
+def _batch(qd, ctx, g, mg, d, offset, precision):
     return qd.hutchinson_trace(ctx, g, mg, d, WL["m0"], 0.0, seed=WL["noise_seed"], sample_offset=offset,
-                               nsamples=WL["s"], tol=WL["tol"], maxit=WL["maxit"], restart=WL["restart"])
+                               nsamples=WL["s"], tol=WL["tol"], maxit=WL["maxit"], restart=WL["restart"],
+                               precision=precision, inner_tol=WL["inner_tol"], max_refine=10)
 
 
 def cpu_baseline(samples=2):
@@ -203,8 +207,9 @@ def run_ours(args):
     def offset(i):
         return (i * world + rank) * s
 
+    prec = qd.QD_PREC_MIXED if args.precision == "mixed" else qd.QD_PREC_F64
     for i in range(args.warmup):
-        _batch(qd, ctx, g, mg, d, offset(i))
+        _batch(qd, ctx, g, mg, d, offset(i), prec)
     clocks = ClockSampler(local)
     clocks.start()
     qd.prof_enable(ctx, True)
@@ -219,7 +224,7 @@ def run_ours(args):
     e0.record(stream)
     results = []
     for i in range(args.steps):
-        results.append(_batch(qd, ctx, g, mg, d, offset(args.warmup + i)))
+        results.append(_batch(qd, ctx, g, mg, d, offset(args.warmup + i), prec))
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
@@ -242,7 +247,14 @@ def run_ours(args):
     top = max(prof, key=lambda k: prof[k]["ms"])
     pt = prof[top]
     peaks = _peaks()
-    if top.endswith("f64"):
+    if top == "direct_f32":
+        fp32_peak = 70.0  # FMA-chain probe (2 flops per FMA), 152 SMs at ~2 GHz
+        achieved = pt["flops"] / (pt["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "kernel": top, "launches": pt["launches"],
+                "ms_per_launch": pt["ms"] / max(pt["launches"], 1),
+                "peak_source": "FP32 CUDA-core FMA rate measured by a probe (70 TFLOP/s)"}
+    elif top.endswith("f64"):
         achieved = pt["flops"] / (pt["ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
@@ -272,7 +284,7 @@ def run_ours(args):
         d2 = qd.Deflation(ctx, g2, mg2, WL["m0"], 0.0,
                           qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
                                          solve_tol=1e-10, maxit=60))
-        _batch(qd, ctx, g2, mg2, d2, offset(1000 + i))
+        _batch(qd, ctx, g2, mg2, d2, offset(1000 + i), prec)
         d2.close()
         mg2.close()
         g2.close()
@@ -287,6 +299,26 @@ def run_ours(args):
            "scope": "per step: link upload from pinned host memory, adaptive MG setup, Algorithm 2 deflation "
                     "space, one 64-sample batch, per-sample t_j and statistics read back"}
 
+    # the plain FP64 path on the same workload (the other side of the metric)
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        _batch(qd, ctx, g, mg, d, offset(2000), qd.QD_PREC_F64)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        fres = [_batch(qd, ctx, g, mg, d, offset(2001 + i), qd.QD_PREC_F64) for i in range(args.fp64_steps)]
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+        if dist:
+            tt = torch.tensor([fms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            fms = float(tt.item())
+        fp64 = {"value": args.fp64_steps * s * world / (fms / 1e3), "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": fms / args.fp64_steps, "dtype": "f64",
+                "outer_iterations": [r["iterations"] for r in fres],
+                "max_true_rel_residual": max(r["max_true_rel_residual"] for r in fres)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -298,14 +330,17 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WL["workload"], "parallelism": f"replicas x{world} (independent samples)",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner solves + f64 refinement" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WL["workload"], "precision": args.precision,
+                       "parallelism": f"replicas x{world} (independent samples)",
                        "l2": "working set > L2 (GCR basis 2 x 16 x 50 MB per batch)",
                        "setup_s": round(setup_s, 3), "outer_iterations": iters,
                        "max_true_rel_residual": worst,
                        "estimate": [results[-1]["estimate"].real, results[-1]["stderr"]]},
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
-            "cpu_baseline": cpu,
+            "fp64_path": fp64, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
     for o in (d, mg, g, ctx):
@@ -324,6 +359,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-samples", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

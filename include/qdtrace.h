@@ -152,10 +152,16 @@ typedef struct {
   double coarse_tol;            /* relative tolerance of coarse GCR */
   int coarse_maxit;             /* iteration cap of coarse GCR */
   int coarse_restart;           /* restart length of coarse GCR */
+  int coarsest_direct;          /* > 0: invert the coarsest operator densely
+                                   (FP64 Gauss-Jordan in setup) when its
+                                   dimension is <= this value (at most
+                                   16384); every coarsest solve is then one
+                                   dense product.  0: coarsest GCR */
 } qd_mg_params;
 
 /* Fill `p` with this library's defaults (1 level, 2^4 blocks, nv 12,
- * 1e-2 / 200, 4 smoothing steps, coarse GCR to 0.1 / 256 / 16). */
+ * 1e-2 / 200, 4 smoothing steps, coarse GCR to 0.1 / 256 / 16, direct
+ * coarsest solve on). */
 void qd_mg_params_default(qd_mg_params* p);
 
 /* Build the hierarchy for A(m0, tau).  Null-vector starts are complex
@@ -195,10 +201,34 @@ int qd_restrict(qd_mg* mg, int level, int nrhs, const double* fine,
 int qd_coarse_apply(qd_mg* mg, int level, int nrhs, const double* in,
                     double* out);
 
+/* out = C_level^{-1} in, level >= 1: the coarse solve of the V-cycle (a5).
+ * On the coarsest level with a dense inverse: one product (exact to FP64
+ * rounding); otherwise GCR on C_level to coarse_tol (preconditioned by the
+ * next level's V-cycle when there is one).  Synchronous. */
+int qd_coarse_solve(qd_mg* mg, int level, int nrhs, const double* in,
+                    double* out);
+
 /* ------------------------------------------------------------------------ */
 /* a5/a6: solves A x = b to ||b - A x|| <= tol ||b|| (Sec. 1, inexact solve; */
 /* Sec. 2 multigrid preconditioning, GCR)                                    */
 /* ------------------------------------------------------------------------ */
+
+enum {
+  QD_PREC_F64 = 0,   /* FP64 flexible GCR, FP64 V-cycle */
+  QD_PREC_MIXED = 1  /* FP64 true-residual refinement around FP32 flexible
+                        GCR with an FP32 V-cycle */
+};
+
+typedef struct {
+  double tol;        /* xi: stop when ||b - A x|| <= tol ||b|| (FP64 residual) */
+  int maxit;         /* iteration cap (outer GCR, or inner GCR per refinement) */
+  int restart;       /* GCR restart length */
+  int precision;     /* QD_PREC_* */
+  double inner_tol;  /* QD_PREC_MIXED: relative tolerance of each FP32 solve */
+  int max_refine;    /* QD_PREC_MIXED: cap on refinement steps */
+} qd_solver_params;
+
+void qd_solver_params_default(qd_solver_params* p);
 
 typedef struct {
   int iterations;                /* max outer iterations over the columns */
@@ -208,13 +238,17 @@ typedef struct {
   double* true_rel_residual;     /* optional host [nrhs] */
 } qd_solve_stats;
 
-/* Flexible restarted GCR on A(m0, tau), right-preconditioned by the V-cycle
- * of `mg` (nullable: unpreconditioned).  With mg the operator is mg's.
- * x is overwritten (zero initial guess).  Returns QD_ERR_NOT_CONVERGED if a
- * column missed tol within maxit (stats filled).  Synchronous. */
+/* Solve A(m0, tau) x = b for nrhs columns.  QD_PREC_F64: flexible
+ * restarted GCR right-preconditioned by the FP64 V-cycle of `mg` (nullable:
+ * unpreconditioned).  QD_PREC_MIXED: x = 0, r = b; repeat { solve
+ * A e = r / ||r|| in FP32 (flexible GCR, FP32 V-cycle) to inner_tol;
+ * x += ||r|| e; r = b - A x in FP64 } until the FP64 residual meets tol.
+ * With mg the operator is mg's.  x is overwritten.  Returns
+ * QD_ERR_NOT_CONVERGED if a column missed tol (stats filled).
+ * Synchronous. */
 int qd_solve(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, double m0,
-             double tau, int nrhs, const double* b, double* x, double tol,
-             int maxit, int restart, qd_solve_stats* stats);
+             double tau, int nrhs, const double* b, double* x,
+             const qd_solver_params* params, qd_solve_stats* stats);
 
 /* ------------------------------------------------------------------------ */
 /* a7: deflation space (Algorithm 1 step 1; Algorithm 2 steps 1-4)           */
@@ -283,9 +317,7 @@ typedef struct {
   uint64_t seed;          /* noise key */
   int64_t sample_offset;  /* first global sample index */
   int nsamples;           /* s, solved together as one multi-RHS batch */
-  double tol;             /* xi */
-  int maxit;              /* outer GCR iteration cap */
-  int restart;            /* outer GCR restart length */
+  qd_solver_params solver;/* xi = solver.tol and the solve's settings */
 } qd_trace_params;
 
 typedef struct {
@@ -332,7 +364,9 @@ enum {
   QD_PROF_PROLONG_F32 = 5,
   QD_PROF_RESTRICT_F64 = 6, /* a3 W^H x, FP64 */
   QD_PROF_RESTRICT_F32 = 7,
-  QD_PROF_NKINDS = 8
+  QD_PROF_DIRECT_F64 = 8,   /* coarsest dense solve C^{-1} R, FP64 */
+  QD_PROF_DIRECT_F32 = 9,
+  QD_PROF_NKINDS = 10
 };
 
 /* enable != 0: record a CUDA event pair on the context stream around every

@@ -5,6 +5,7 @@
 
 #include "blas.cuh"
 #include "defl.cuh"
+#include "direct.cuh"
 
 
 static thread_local std::string g_last_error;
@@ -167,6 +168,18 @@ void qd_mg_params_default(qd_mg_params* p) {
   p->coarse_tol = 0.1;
   p->coarse_maxit = 256;
   p->coarse_restart = 16;
+  p->coarsest_direct = 16384;
+}
+
+void qd_solver_params_default(qd_solver_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->tol = 1e-8;
+  p->maxit = 500;
+  p->restart = 16;
+  p->precision = QD_PREC_F64;
+  p->inner_tol = 1e-5;
+  p->max_refine = 10;
 }
 
 int qd_mg_setup(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau, const qd_mg_params* params,
@@ -255,20 +268,47 @@ int qd_coarse_apply(qd_mg* mg, int level, int nrhs, const double* in, double* ou
   });
 }
 
+int qd_coarse_solve(qd_mg* mg, int level, int nrhs, const double* in, double* out) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(level >= 1 && level <= mg->nlevels, "coarse level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    set_device(mg->ctx);
+    qd_ctx& ctx = *mg->ctx;
+    const qd::cplx* x = reinterpret_cast<const qd::cplx*>(in);
+    qd::cplx* y = reinterpret_cast<qd::cplx*>(out);
+    const qd::cplx* inv = mg->Cinv<qd::cplx>(level);
+    if (inv) {
+      qd::dense_apply<qd::cplx>(ctx, mg->L[level - 1]->ndense, nrhs, inv, x, y);
+    } else {
+      auto A = mg->op<qd::cplx>(level);
+      std::unique_ptr<qd::MGPrecond<qd::cplx>> pre;
+      if (level < mg->nlevels) pre.reset(new qd::MGPrecond<qd::cplx>(mg, level));
+      qd::GCR<qd::cplx> gcr;
+      gcr.solve(ctx, *A, pre.get(), x, y, nrhs, mg->p.coarse_tol, mg->p.coarse_maxit, mg->p.coarse_restart,
+                nullptr);
+    }
+    QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  });
+}
+
 int qd_solve(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, double m0, double tau, int nrhs, const double* b,
-             double* x, double tol, int maxit, int restart, qd_solve_stats* stats) {
+             double* x, const qd_solver_params* params, qd_solve_stats* stats) {
   int not_conv = 0;
   int rc = guarded([&] {
     NONNULL(ctx);
     NONNULL(gauge);
     NONNULL(b);
     NONNULL(x);
+    NONNULL(params);
     QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
-    QD_REQUIRE(tol > 0.0 && maxit >= 1, "tol must be > 0 and maxit >= 1");
     set_device(ctx);
     qd::SolveInfo info;
     qd::solve(*ctx, *gauge, mg, m0, tau, nrhs, reinterpret_cast<const qd::cplx*>(b), reinterpret_cast<qd::cplx*>(x),
-              tol, maxit, restart, info);
+              *params, info);
     if (stats) {
       stats->iterations = info.iterations;
       stats->converged = info.converged;
@@ -404,7 +444,6 @@ int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, qd_defl* 
     NONNULL(gauge);
     NONNULL(params);
     NONNULL(result);
-    QD_REQUIRE(params->tol > 0.0 && params->maxit >= 1 && params->restart >= 1, "bad solver parameters");
     set_device(ctx);
     qd::TraceOut out;
     std::vector<qd::cplx> M1, M2;

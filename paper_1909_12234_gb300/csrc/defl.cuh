@@ -8,7 +8,9 @@ namespace qd {
 // Work spaces kept by a context between estimator / solve calls.
 struct SolverCache {
   GCR<cplx> gcr64;
+  GCR<cplxf> gcr32;
   DevBuf Z, B, X, tdev, stats, loo;
+  DevBuf mr, mt, mrf, mef, mscal;  // mixed-precision refinement
 };
 SolverCache& cache(qd_ctx& ctx);
 
@@ -53,7 +55,7 @@ void mg_build(qd_mg& mg, const double* injected_null);
 
 // Drivers (trace.cu).
 void solve(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, double tau, int s, const cplx* b, cplx* x,
-           double tol, int maxit, int restart, SolveInfo& info);
+           const qd_solver_params& p, SolveInfo& info);
 struct TraceOut {
   double stats[6];
   std::vector<cplx> t;

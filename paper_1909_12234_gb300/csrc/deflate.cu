@@ -15,9 +15,12 @@
 //   Y = H^{-1} X (inexact GCR solves to solve_tol), T = X^H Y = S N S^H,
 //   X <- orth(Y S) by Cholesky QR applied twice.
 // Sec. 2.2: the a-posteriori matrices Z^H W U_bar and U_bar^H gamma5^W W^H Z.
+#include <functional>
+
 #include "blas.cuh"
 #include "defl.cuh"
 #include "dense.cuh"
+#include "direct.cuh"
 
 namespace qd {
 
@@ -59,9 +62,12 @@ __global__ void k_reciprocal(int m, const double* __restrict__ in, double* __res
 //   Y = H^{-1} X;  T = X^H Y = S diag(nu) S^H;  order by |1/nu| ascending;
 //   residual_i = ||Y s_i - nu_i X s_i|| / |nu_i|;  X <- orth(Y S).
 // X (n x m, ld m) out: Ritz vectors; theta (host, m) out: 1/nu.
-static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, Precond<cplx>* M, const LevelGeom& geo, int m, int k,
-                         double eig_tol, double solve_tol, int maxit, uint64_t seed, cplx* X,
-                         std::vector<double>& theta, int& iters_out) {
+// `solve(X, W, m)` must return W ~= Op^{-1} X for m columns.
+typedef std::function<void(const cplx*, cplx*, int)> SolveFn;
+
+static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, const SolveFn& solve, const LevelGeom& geo, int m, int k,
+                         double eig_tol, int maxit, uint64_t seed, cplx* X, std::vector<double>& theta,
+                         int& iters_out) {
   const int64_t n = A.n();
   const int dof = A.dof();
   const size_t blk = (size_t)n * m * sizeof(cplx);
@@ -79,13 +85,11 @@ static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, Precond<cplx>* M, const
   double* nus = mus + m;
   random_starts_fill(ctx, geo, dof, seed, m, X);
   cholqr2(ctx, n, m, X, Tm, small);
-  GCR<cplx> solver;
   theta.assign(m, 0.0);
   int it = 0;
   for (; it < maxit; ++it) {
     // Y = H^{-1} X = gamma5 Op^{-1} X
-    SolveInfo info;
-    solver.solve(ctx, A, M, X, Tm, m, solve_tol, 20000, 32, &info);
+    solve(X, Tm, m);
     blas::gamma5(ctx, geo.nsites, dof, m, Tm, Y);
     blockdot(ctx, n, X, m, m, Y, m, m, Tmat);
     hermitize(ctx, m, Tmat);
@@ -159,9 +163,20 @@ void defl_build(qd_defl& d, const double* injected) {
     } else if (d.level == 0 && d.mg) {
       M = d.mg->pre64.get();
     }
+    const cplx* inv = d.level == 1 ? d.mg->Cinv<cplx>(1) : nullptr;
+    GCR<cplx> solver;
+    const Op<cplx>& A = *op;
+    const double stol = d.p.solve_tol;
+    SolveFn fn = [&](const cplx* Xin, cplx* Wout, int mm) {
+      if (inv) {
+        dense_apply<cplx>(ctx, (int)d.nb, mm, inv, Xin, Wout);  // exact coarsest solve
+      } else {
+        SolveInfo info;
+        solver.solve(ctx, A, M, Xin, Wout, mm, stol, 20000, 32, &info);
+      }
+    };
     std::vector<double> theta;
-    subspace_eig(ctx, *op, M, geo, m, k, d.p.eig_tol, d.p.solve_tol, d.p.maxit, d.p.seed, X.as<cplx>(), theta,
-                 d.iterations);
+    subspace_eig(ctx, *op, fn, geo, m, k, d.p.eig_tol, d.p.maxit, d.p.seed, X.as<cplx>(), theta, d.iterations);
     for (int i = 0; i < k; ++i) d.mu[i] = theta[i];
     // U_bar = first k columns of X (ld m -> ld k)
     blockmul_identity_cols(ctx, d.nb, X.as<cplx>(), m, k, d.Ubar.as<cplx>());

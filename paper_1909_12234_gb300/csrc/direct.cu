@@ -1,0 +1,222 @@
+// Direct solves on the coarsest level.
+//
+// The coarsest operator C (a few thousand dofs on the lattices this library
+// targets) is inverted once in FP64 by Gauss-Jordan elimination with partial
+// (row) pivoting, in place (Golub & Van Loan, "Matrix Computations", the
+// Gauss-Jordan variant of Sec. 3.2; row swaps undone as column swaps at the
+// end).  Every coarse solve is then one dense complex product C^{-1} R,
+// R = n x s right-hand sides, done by a shared-memory tiled GEMM in FP64 or
+// FP32.
+#include "direct.cuh"
+
+namespace qd {
+
+// ---------------------------------------------------------------------------
+// Gauss-Jordan step k, part 1 (one CTA): pivot search in column k over rows
+// i >= k, row swap, copy of column k into f, scaling of the pivot row.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, cplx* __restrict__ A, cplx* __restrict__ f,
+                                                   int* __restrict__ perm, int* __restrict__ flag) {
+  __shared__ double sv[1024];
+  __shared__ int si[1024];
+  __shared__ cplx s_inv;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  double best = -1.0;
+  int bi = k;
+  for (int i = k + tid; i < n; i += nth) {
+    const double v = cnorm2(A[(int64_t)i * n + k]);
+    if (v > best) { best = v; bi = i; }
+  }
+  sv[tid] = best;
+  si[tid] = bi;
+  __syncthreads();
+  for (int h = nth / 2; h > 0; h >>= 1) {
+    if (tid < h) {
+      // ties resolved towards the smaller row index (deterministic)
+      if (sv[tid + h] > sv[tid] || (sv[tid + h] == sv[tid] && si[tid + h] < si[tid])) {
+        sv[tid] = sv[tid + h];
+        si[tid] = si[tid + h];
+      }
+    }
+    __syncthreads();
+  }
+  const int p = si[0];
+  if (tid == 0) {
+    perm[k] = p;
+    if (!(sv[0] > 0.0) && flag) *flag = 1;
+  }
+  if (p != k) {
+    for (int j = tid; j < n; j += nth) {
+      const cplx a = A[(int64_t)k * n + j];
+      A[(int64_t)k * n + j] = A[(int64_t)p * n + j];
+      A[(int64_t)p * n + j] = a;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nth) f[i] = A[(int64_t)i * n + k];
+  if (tid == 0) {
+    const cplx piv = A[(int64_t)k * n + k];
+    const double d = cnorm2(piv);
+    s_inv = d > 0.0 ? mkc(piv.x / d, -piv.y / d) : mkc(0.0, 0.0);
+  }
+  __syncthreads();
+  const cplx inv = s_inv;
+  for (int j = tid; j < n; j += nth) {
+    const cplx a = (j == k) ? mkc(1.0, 0.0) : A[(int64_t)k * n + j];
+    A[(int64_t)k * n + j] = cmul(a, inv);
+  }
+}
+
+// Part 2: for rows i != k: A[i][j] -= f[i] * A[k][j] (A[i][k] taken as 0).
+__global__ void k_gj_update(int n, int k, cplx* __restrict__ A, const cplx* __restrict__ f) {
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
+    if (i == k) continue;
+    const cplx fi = f[i];
+    cplx a = (j == k) ? mkc(0.0, 0.0) : A[e];
+    cfma(a, mkc(-fi.x, -fi.y), A[(int64_t)k * n + j]);
+    A[e] = a;
+  }
+}
+
+// Undo the row interchanges as column interchanges, last step first.
+__global__ void k_gj_unswap(int n, cplx* __restrict__ A, const int* __restrict__ perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cplx* row = A + (int64_t)i * n;
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k) {
+      const cplx t = row[k];
+      row[k] = row[p];
+      row[p] = t;
+    }
+  }
+}
+
+void gauss_jordan_inverse(qd_ctx& ctx, int n, cplx* A) {
+  DevBuf f((size_t)n * sizeof(cplx)), perm((size_t)n * sizeof(int)), flag(sizeof(int));
+  QD_CUDA(cudaMemsetAsync(flag.as<int>(), 0, sizeof(int), ctx.stream));
+  const int64_t tot = (int64_t)n * n;
+  int blocks = div_up(tot, 256);
+  if (blocks > 16 * kNumSMs) blocks = 16 * kNumSMs;
+  for (int k = 0; k < n; ++k) {
+    k_gj_pivot<<<1, 1024, 0, ctx.stream>>>(n, k, A, f.as<cplx>(), perm.as<int>(), flag.as<int>());
+    QD_LAUNCH_CHECK();
+    k_gj_update<<<blocks, 256, 0, ctx.stream>>>(n, k, A, f.as<cplx>());
+    QD_LAUNCH_CHECK();
+  }
+  k_gj_unswap<<<div_up(n, 128), 128, 0, ctx.stream>>>(n, A, perm.as<int>());
+  QD_LAUNCH_CHECK();
+  int h = 0;
+  QD_CUDA(cudaMemcpyAsync(&h, flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  if (h) fail(QD_ERR_NONFINITE, "coarsest operator is singular (zero pivot in Gauss-Jordan)");
+}
+
+// ---------------------------------------------------------------------------
+// Dense stencil -> matrix: D[(x*Dd + d)][(y*Dd + e)] += C[x][dir][d][e] for
+// y = nb(x, dir) (aliased neighbours on small lattices are summed).
+// ---------------------------------------------------------------------------
+__global__ void k_stencil_to_dense(int64_t nsites, int D, const int* __restrict__ nbr, const cplx* __restrict__ mat,
+                                   cplx* __restrict__ dense) {
+  const int64_t n = nsites * D;
+  const int64_t tot = nsites * D;  // one thread per row
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < tot;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = row / D;
+    const int d = (int)(row - x * D);
+    for (int dir = 0; dir < 9; ++dir) {
+      const int64_t y = (dir == 0) ? x : (int64_t)nbr[x * 8 + dir - 1];
+      const cplx* src = mat + ((x * 9 + dir) * D + d) * D;
+      cplx* dst = dense + row * n + y * D;
+      for (int e = 0; e < D; ++e) dst[e] = cadd(dst[e], src[e]);
+    }
+  }
+}
+
+void coarse_dense_inverse(qd_ctx& ctx, CoarseLevel& lv) {
+  const int64_t n64 = lv.geo.nsites * (int64_t)lv.D;
+  QD_REQUIRE(n64 <= 16384, "coarsest level too large for a dense direct solve");
+  const int n = (int)n64;
+  lv.Cinv.resize((size_t)n * n * sizeof(cplx));
+  QD_CUDA(cudaMemsetAsync(lv.Cinv.as<cplx>(), 0, (size_t)n * n * sizeof(cplx), ctx.stream));
+  k_stencil_to_dense<<<div_up(n, 128), 128, 0, ctx.stream>>>(lv.geo.nsites, lv.D, lv.geo.nbr.as<int>(),
+                                                            lv.Cm.as<cplx>(), lv.Cinv.as<cplx>());
+  QD_LAUNCH_CHECK();
+  gauss_jordan_inverse(ctx, n, lv.Cinv.as<cplx>());
+  lv.ndense = n;
+}
+
+// ---------------------------------------------------------------------------
+// Tiled complex GEMM, Y (n x s) = M (n x n) X (n x s), all row major, FP64
+// or FP32.  64 x 64 output tile per CTA (256 threads, 4 x 4 per thread),
+// k-tiles of 16 staged in shared memory.
+// ---------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(256) k_zgemm(int n, int s, const C* __restrict__ M, const C* __restrict__ X,
+                                               C* __restrict__ Y) {
+  typedef typename CTraits<C>::R R;
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ C sa[BK][BM + 1];
+  __shared__ C sb[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tr = tid / 16, tc = tid % 16;  // 16 x 16 threads, each 4 rows x 4 cols
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  C acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = mk<C>((R)0, (R)0);
+  for (int k0 = 0; k0 < n; k0 += BK) {
+    // load M[row0 .. +64][k0 .. +16] -> sa[k][m] and X[k0 .. +16][col0 .. +64] -> sb[k][c]
+    for (int e = tid; e < BM * BK; e += 256) {
+      const int m = e / BK, kk = e % BK;
+      const int gr = row0 + m, gk = k0 + kk;
+      sa[kk][m] = (gr < n && gk < n) ? M[(int64_t)gr * n + gk] : mk<C>((R)0, (R)0);
+    }
+    for (int e = tid; e < BK * BN; e += 256) {
+      const int kk = e / BN, c = e % BN;
+      const int gk = k0 + kk, gc = col0 + c;
+      sb[kk][c] = (gk < n && gc < s) ? X[(int64_t)gk * s + gc] : mk<C>((R)0, (R)0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sa[kk][tr + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sb[kk][tc + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gr = row0 + tr + 16 * i;
+    if (gr >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + tc + 16 * j;
+      if (gc < s) Y[(int64_t)gr * s + gc] = acc[i][j];
+    }
+  }
+}
+
+template <class C> void dense_apply(qd_ctx& ctx, int n, int s, const C* M, const C* X, C* Y) {
+  const double cb = (double)sizeof(C);
+  ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_DIRECT_F64 : QD_PROF_DIRECT_F32, 8.0 * n * (double)n * s,
+               cb * ((double)n * n + 2.0 * n * s));
+  dim3 grid(div_up(s, 64), div_up(n, 64));
+  k_zgemm<C><<<grid, 256, 0, ctx.stream>>>(n, s, M, X, Y);
+  QD_LAUNCH_CHECK();
+}
+template void dense_apply<cplx>(qd_ctx&, int, int, const cplx*, const cplx*, cplx*);
+template void dense_apply<cplxf>(qd_ctx&, int, int, const cplxf*, const cplxf*, cplxf*);
+
+}  // namespace qd

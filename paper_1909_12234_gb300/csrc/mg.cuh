@@ -47,7 +47,9 @@ namespace qd {
 
 // V-cycle preconditioner for level `level` of a hierarchy (Sec. 2 two-grid
 // method: coarse-grid correction, then smoothing; deeper levels precondition
-// the coarse GCR with the next V-cycle; no recursion below the coarsest).
+// the coarse GCR with the next V-cycle; no recursion below the coarsest,
+// where the solve is GCR or, when the coarsest operator was inverted in
+// setup, one dense product).
 template <class C> class MGPrecond : public Precond<C> {
  public:
   MGPrecond(qd_mg* mg, int level);
@@ -62,19 +64,6 @@ template <class C> class MGPrecond : public Precond<C> {
   int cap_ = -1;
 };
 
-// FP32 V-cycle used as the preconditioner of an FP64 outer solve: converts
-// the residual to FP32, runs the FP32 V-cycle, converts back.
-class MixedPrecond : public Precond<cplx> {
- public:
-  MixedPrecond(qd_mg* mg);
-  void apply(qd_ctx& ctx, const cplx* r, cplx* z, int nrhs) override;
-
- private:
-  qd_mg* mg_;
-  MGPrecond<cplxf> inner_;
-  DevBuf rf_, zf_;
-};
-
 }  // namespace qd
 
 struct qd_mg {
@@ -86,11 +75,13 @@ struct qd_mg {
   std::vector<std::unique_ptr<qd::Transfer>> T;     // T[l]: level l -> l+1
   std::vector<std::unique_ptr<qd::CoarseLevel>> L;  // L[l-1]: level l >= 1
   std::unique_ptr<qd::MGPrecond<qd::cplx>> pre64;
-  std::unique_ptr<qd::MixedPrecond> pre_mixed;
+  std::unique_ptr<qd::MGPrecond<qd::cplxf>> pre32;
 
   const qd::LevelGeom& geom(int level) const { return level == 0 ? gauge->geo : L[level - 1]->geo; }
   int dof(int level) const { return level == 0 ? 12 : L[level - 1]->D; }
   // Operator of a level in precision C (caller owns the returned object).
   template <class C> std::unique_ptr<qd::Op<C>> op(int level);
   template <class C> const C* W(int level);
+  // Dense inverse of coarse level `level` (>= 1), or nullptr.
+  template <class C> const C* Cinv(int level);
 };

@@ -171,6 +171,9 @@ struct CoarseLevel {
   int D = 0;          // dofs per site
   DevBuf Cm;          // cplx  [nsites][9][D][D]; dir 0 self, 1+mu: +mu, 5+mu: -mu
   DevBuf Cmf;         // cplxf copy
+  int ndense = 0;     // > 0: Cinv holds the dense inverse (coarsest level)
+  DevBuf Cinv;        // cplx  [n][n], n = nsites * D
+  DevBuf Cinvf;       // cplxf copy
 };
 
 template <class C> struct CoarseOp : public Op<C> {

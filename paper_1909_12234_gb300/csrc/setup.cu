@@ -4,6 +4,7 @@
 // Sec. 4), chirality split + blocking + per-block CGS2 -> W, then the
 // Galerkin coarse operator W^H A W.
 #include "blas.cuh"
+#include "direct.cuh"
 #include "mg.cuh"
 
 namespace qd {
@@ -53,8 +54,12 @@ void mg_build(qd_mg& mg, const double* injected_null) {
     mg.L.push_back(std::move(CL));
     QD_CUDA(cudaStreamSynchronize(ctx.stream));
   }
+  // coarsest level: dense FP64 inverse when small enough
+  CoarseLevel& last = *mg.L.back();
+  const int64_t nlast = last.geo.nsites * (int64_t)last.D;
+  if (p.coarsest_direct > 0 && nlast <= p.coarsest_direct && nlast <= 16384) coarse_dense_inverse(ctx, last);
   mg.pre64.reset(new MGPrecond<cplx>(&mg, 0));
-  mg.pre_mixed.reset(new MixedPrecond(&mg));
+  mg.pre32.reset(new MGPrecond<cplxf>(&mg, 0));
 }
 
 }  // namespace qd

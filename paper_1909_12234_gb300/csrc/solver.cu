@@ -4,6 +4,7 @@
 // two-grid method (Sec. 2) and the adaptive setup (Sec. 2, Sec. 4
 // tolerance 1e-2 / 200 iterations).
 #include "blas.cuh"
+#include "direct.cuh"
 #include "mg.cuh"
 
 namespace qd {
@@ -321,9 +322,14 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
   const C* W = mg_->W<C>(level_);
   // coarse-grid correction: z = W C^{-1} W^H r
   restrict_<C>(ctx, T, W, r, rc_.as<C>(), nrhs);
-  auto Ac = mg_->op<C>(level_ + 1);
-  coarse_.solve(ctx, *Ac, next_.get(), rc_.as<C>(), ec_.as<C>(), nrhs, mg_->p.coarse_tol,
-                mg_->p.coarse_maxit, mg_->p.coarse_restart, nullptr);
+  const C* inv = mg_->Cinv<C>(level_ + 1);
+  if (inv) {
+    dense_apply<C>(ctx, (int)nc, nrhs, inv, rc_.as<C>(), ec_.as<C>());
+  } else {
+    auto Ac = mg_->op<C>(level_ + 1);
+    coarse_.solve(ctx, *Ac, next_.get(), rc_.as<C>(), ec_.as<C>(), nrhs, mg_->p.coarse_tol,
+                  mg_->p.coarse_maxit, mg_->p.coarse_restart, nullptr);
+  }
   prolongate<C>(ctx, T, W, ec_.as<C>(), z, nrhs);
   // smoothing: z += M^{-1} (r - A z), M^{-1} = minimal-residual steps from 0
   const int nu = mg_->p.smoother_steps;
@@ -339,17 +345,6 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
 
 template class MGPrecond<cplx>;
 template class MGPrecond<cplxf>;
-
-MixedPrecond::MixedPrecond(qd_mg* mg) : mg_(mg), inner_(mg, 0) {}
-
-void MixedPrecond::apply(qd_ctx& ctx, const cplx* r, cplx* z, int nrhs) {
-  const int64_t tot = mg_->geom(0).nsites * 12 * (int64_t)nrhs;
-  rf_.resize(tot * sizeof(cplxf));
-  zf_.resize(tot * sizeof(cplxf));
-  to_f32(ctx, r, rf_.as<cplxf>(), tot);
-  inner_.apply(ctx, rf_.as<cplxf>(), zf_.as<cplxf>(), nrhs);
-  to_f64(ctx, zf_.as<cplxf>(), z, tot);
-}
 
 }  // namespace qd
 
@@ -387,4 +382,19 @@ template <> const qd::cplxf* qd_mg::W<qd::cplxf>(int level) {
     qd::to_f32(*ctx, t.W.as<qd::cplx>(), t.Wf.as<qd::cplxf>(), n);
   }
   return t.Wf.as<qd::cplxf>();
+}
+
+template <> const qd::cplx* qd_mg::Cinv<qd::cplx>(int level) {
+  const qd::CoarseLevel& lv = *L[level - 1];
+  return lv.ndense > 0 ? lv.Cinv.as<qd::cplx>() : nullptr;
+}
+template <> const qd::cplxf* qd_mg::Cinv<qd::cplxf>(int level) {
+  qd::CoarseLevel& lv = *L[level - 1];
+  if (lv.ndense <= 0) return nullptr;
+  if (lv.Cinvf.bytes() == 0) {
+    const int64_t n = (int64_t)lv.ndense * lv.ndense;
+    lv.Cinvf.resize(n * sizeof(qd::cplxf));
+    qd::to_f32(*ctx, lv.Cinv.as<qd::cplx>(), lv.Cinvf.as<qd::cplxf>(), n);
+  }
+  return lv.Cinvf.as<qd::cplxf>();
 }

@@ -6,19 +6,125 @@
 
 namespace qd {
 
-// x = A^{-1} b for s columns, FP64 flexible GCR right-preconditioned by the
-// FP64 V-cycle (mg) or unpreconditioned.
+// Per-column scales for the refinement: active columns (||r||^2 > tol2
+// ||b||^2) get sin = 1/||r||, sout = ||r||; the others 0 (their FP32 system
+// has a zero right-hand side and is skipped by the inner solve).
+__global__ void k_refine_scales(int s, const cplx* __restrict__ rn2, const cplx* __restrict__ bn2, double tol2,
+                                double* __restrict__ sin_, double* __restrict__ sout, int* __restrict__ count) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= s) return;
+  const double r = rn2[c].x;
+  const bool act = r > tol2 * bn2[c].x;
+  sin_[c] = act ? 1.0 / sqrt(r) : 0.0;
+  sout[c] = act ? sqrt(r) : 0.0;
+  if (act) atomicAdd(count, 1);
+}
+
+// out (FP32) = r * sin[c]
+__global__ void k_scale_to_f32(int64_t n, int s, const cplx* __restrict__ r, const double* __restrict__ sc,
+                               cplxf* __restrict__ out) {
+  const int64_t tot = n * s;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const double f = sc[e % s];
+    out[e] = make_float2((float)(r[e].x * f), (float)(r[e].y * f));
+  }
+}
+
+// x += e (FP32) * sout[c]
+__global__ void k_axpy_from_f32(int64_t n, int s, const cplxf* __restrict__ ev, const double* __restrict__ sc,
+                                cplx* __restrict__ x) {
+  const int64_t tot = n * s;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const double f = sc[e % s];
+    if (f == 0.0) continue;
+    x[e].x += f * (double)ev[e].x;
+    x[e].y += f * (double)ev[e].y;
+  }
+}
+
+// Mixed precision: FP64 true-residual refinement around FP32 solves.
+static void solve_mixed(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, double tau, int s, const cplx* b,
+                        cplx* x, const qd_solver_params& p, SolveInfo& info) {
+  SolverCache& sc = cache(ctx);
+  const int64_t n = g.geo.nsites * 12, tot = n * s;
+  WilsonOp<cplx> A64(&g, g.links.as<cplx>(), m0, tau, false);
+  WilsonOp<cplxf> A32(&g, const_cast<qd_gauge&>(g).links_f32(), m0, tau, false);
+  sc.mr.resize(tot * sizeof(cplx));
+  sc.mt.resize(tot * sizeof(cplx));
+  sc.mrf.resize(tot * sizeof(cplxf));
+  sc.mef.resize(tot * sizeof(cplxf));
+  sc.mscal.resize((size_t)(4 * s) * sizeof(cplx) + 4 * sizeof(int));
+  cplx* r = sc.mr.as<cplx>();
+  cplx* t = sc.mt.as<cplx>();
+  cplxf* rf = sc.mrf.as<cplxf>();
+  cplxf* ef = sc.mef.as<cplxf>();
+  cplx* bn2 = sc.mscal.as<cplx>();
+  cplx* rn2 = bn2 + s;
+  double* sin_ = reinterpret_cast<double*>(rn2 + s);
+  double* sout = sin_ + s;
+  int* count = reinterpret_cast<int*>(sout + s);
+  blas::zero(ctx, tot, x);
+  blas::copy(ctx, tot, b, r);
+  blas::dots(ctx, 1, n, s, b, 0, b, 0, bn2);
+  QD_CUDA(cudaMemcpyAsync(rn2, bn2, s * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx.stream));
+  const double tol2 = p.tol * p.tol;
+  int inner_total = 0;
+  std::vector<int> iters(s, 0);
+  for (int step = 0;; ++step) {
+    QD_CUDA(cudaMemsetAsync(count, 0, sizeof(int), ctx.stream));
+    k_refine_scales<<<div_up(s, 128), 128, 0, ctx.stream>>>(s, rn2, bn2, tol2, sin_, sout, count);
+    QD_LAUNCH_CHECK();
+    int hc = 0;
+    QD_CUDA(cudaMemcpyAsync(&hc, count, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaStreamSynchronize(ctx.stream));
+    if (hc == 0 || step >= p.max_refine) break;
+    k_scale_to_f32<<<blas::grid_1d(tot), 256, 0, ctx.stream>>>(n, s, r, sin_, rf);
+    QD_LAUNCH_CHECK();
+    SolveInfo in;
+    sc.gcr32.solve(ctx, A32, mg ? mg->pre32.get() : nullptr, rf, ef, s, p.inner_tol, p.maxit, p.restart, &in);
+    inner_total += in.iterations;
+    for (int c = 0; c < s; ++c) iters[c] += in.iters[c];
+    k_axpy_from_f32<<<blas::grid_1d(tot), 256, 0, ctx.stream>>>(n, s, ef, sout, x);
+    QD_LAUNCH_CHECK();
+    A64.apply(ctx, x, t, s);
+    blas::sub(ctx, tot, b, t, r);
+    blas::dots(ctx, 1, n, s, r, 0, r, 0, rn2);
+  }
+  std::vector<cplx> hb(s), hr(s);
+  QD_CUDA(cudaMemcpyAsync(hb.data(), bn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaMemcpyAsync(hr.data(), rn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  info.iterations = inner_total;
+  info.iters = iters;
+  info.true_rel.assign(s, 0.0);
+  info.converged = 0;
+  info.max_rel = 0.0;
+  for (int c = 0; c < s; ++c) {
+    const double rel = hb[c].x > 0.0 ? std::sqrt(hr[c].x / hb[c].x) : 0.0;
+    info.true_rel[c] = rel;
+    if (rel <= p.tol) info.converged++;
+    if (rel > info.max_rel || rel != rel) info.max_rel = rel;
+  }
+}
+
+// x = A^{-1} b for s columns (FP64 GCR + FP64 V-cycle, or mixed precision).
 void solve(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, double tau, int s, const cplx* b, cplx* x,
-           double tol, int maxit, int restart, SolveInfo& info) {
+           const qd_solver_params& p, SolveInfo& info) {
   if (mg) {
     QD_REQUIRE(mg->gauge == &g, "multigrid hierarchy was built for another gauge field");
     QD_REQUIRE(mg->m0 == m0 && mg->tau == tau, "multigrid hierarchy was built for another m0 / tau");
   }
+  QD_REQUIRE(p.tol > 0.0 && p.maxit >= 1 && p.restart >= 1, "bad solver parameters");
+  if (p.precision == QD_PREC_MIXED) {
+    QD_REQUIRE(p.inner_tol > 0.0 && p.inner_tol < 1.0 && p.max_refine >= 1, "bad mixed-precision parameters");
+    solve_mixed(ctx, g, mg, m0, tau, s, b, x, p, info);
+    return;
+  }
+  QD_REQUIRE(p.precision == QD_PREC_F64, "unknown precision");
   WilsonOp<cplx> A(&g, g.links.as<cplx>(), m0, tau, false);
   SolverCache& sc = cache(ctx);
-  sc.gcr64.solve(ctx, A, mg ? mg->pre64.get() : nullptr, b, x, s, tol, maxit, restart, &info);
+  sc.gcr64.solve(ctx, A, mg ? mg->pre64.get() : nullptr, b, x, s, p.tol, p.maxit, p.restart, &info);
 }
-
 
 void hutchinson(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, qd_defl* d, double m0, double tau,
                 const qd_trace_params& p, bool want_coeffs, TraceOut& out, std::vector<cplx>* M1,
@@ -46,7 +152,7 @@ void hutchinson(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, qd_defl* d, double m0
   else
     blas::copy(ctx, n * s, Z, B);
   // a5/a6: solves
-  solve(ctx, g, mg, m0, tau, s, B, X, p.tol, p.maxit, p.restart, out.info);
+  solve(ctx, g, mg, m0, tau, s, B, X, p.solver, out.info);
   // a9: t_j = z_j^H x_j, statistics
   blas::dots(ctx, 1, n, s, Z, 0, X, 0, sc.tdev.as<cplx>());
   trace_stats(ctx, s, sc.tdev.as<cplx>(), sc.stats.as<double>(), sc.loo.as<double>());

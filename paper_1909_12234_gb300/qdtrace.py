@@ -30,6 +30,8 @@ QD_ERR_INTERNAL = -7
 QD_MAX_LEVELS = 4
 QD_DEFL_EIG_ORTHO = 1
 QD_DEFL_MG_OBLIQUE = 2
+QD_PREC_F64 = 0
+QD_PREC_MIXED = 1
 
 _STATUS = {0: "QD_OK", -1: "QD_ERR_INVALID", -2: "QD_ERR_CUDA", -3: "QD_ERR_OOM",
            -4: "QD_ERR_NOT_CONVERGED", -5: "QD_ERR_NONFINITE", -6: "QD_ERR_TIMEOUT",
@@ -52,7 +54,17 @@ class MGParams(ctypes.Structure):
                 ("smoother_steps", ctypes.c_int),
                 ("coarse_tol", ctypes.c_double),
                 ("coarse_maxit", ctypes.c_int),
-                ("coarse_restart", ctypes.c_int)]
+                ("coarse_restart", ctypes.c_int),
+                ("coarsest_direct", ctypes.c_int)]
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int),
+                ("restart", ctypes.c_int),
+                ("precision", ctypes.c_int),
+                ("inner_tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -77,9 +89,7 @@ class TraceParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64),
                 ("sample_offset", ctypes.c_int64),
                 ("nsamples", ctypes.c_int),
-                ("tol", ctypes.c_double),
-                ("maxit", ctypes.c_int),
-                ("restart", ctypes.c_int)]
+                ("solver", SolverParams)]
 
 
 class TraceResult(ctypes.Structure):
@@ -125,7 +135,9 @@ SIGNATURES = {
     "qd_prolongate": (_I, [_P, _I, _I, _P, _P]),
     "qd_restrict": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_apply": (_I, [_P, _I, _I, _P, _P]),
-    "qd_solve": (_I, [_P, _P, _P, _D, _D, _I, _P, _P, _D, _I, _I, ctypes.POINTER(SolveStats)]),
+    "qd_coarse_solve": (_I, [_P, _I, _I, _P, _P]),
+    "qd_solver_params_default": (None, [ctypes.POINTER(SolverParams)]),
+    "qd_solve": (_I, [_P, _P, _P, _D, _D, _I, _P, _P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveStats)]),
     "qd_defl_params_default": (None, [ctypes.POINTER(DeflParams)]),
     "qd_defl_create": (_I, [_P, _P, _P, _D, _D, ctypes.POINTER(DeflParams), _P, _PP]),
     "qd_defl_destroy": (_I, [_P]),
@@ -141,7 +153,7 @@ SIGNATURES = {
 }
 
 PROF_KINDS = {"wilson_f64": 0, "wilson_f32": 1, "coarse_f64": 2, "coarse_f32": 3, "prolong_f64": 4,
-              "prolong_f32": 5, "restrict_f64": 6, "restrict_f32": 7}
+              "prolong_f32": 5, "restrict_f64": 6, "restrict_f32": 7, "direct_f64": 8, "direct_f32": 9}
 
 _lib = None
 
@@ -349,13 +361,28 @@ def coarse_apply(mg, level, nrhs, inp, out):
     _check(load().qd_coarse_apply(mg.h, int(level), int(nrhs), _ptr(inp), _ptr(out)))
 
 
-def solve(ctx, gauge, mg, m0, tau, nrhs, b, x, tol, maxit=10000, restart=16, allow_not_converged=False):
+def coarse_solve(mg, level, nrhs, inp, out):
+    _check(load().qd_coarse_solve(mg.h, int(level), int(nrhs), _ptr(inp), _ptr(out)))
+
+
+def solver_params(tol=1e-8, maxit=500, restart=16, precision=QD_PREC_F64, **kw):
+    p = SolverParams()
+    load().qd_solver_params_default(ctypes.byref(p))
+    p.tol, p.maxit, p.restart, p.precision = float(tol), int(maxit), int(restart), int(precision)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def solve(ctx, gauge, mg, m0, tau, nrhs, b, x, tol, maxit=10000, restart=16, allow_not_converged=False,
+          precision=QD_PREC_F64, **kw):
     """Returns (status, iterations, per-column iterations, per-column true residual)."""
     it = (ctypes.c_int * nrhs)()
     rel = (ctypes.c_double * nrhs)()
     st = SolveStats(0, 0, 0.0, it, rel)
+    p = solver_params(tol, maxit, restart, precision, **kw)
     rc = load().qd_solve(ctx.h, gauge.h, mg.h if mg is not None else None, float(m0), float(tau), int(nrhs),
-                         _ptr(b), _ptr(x), float(tol), int(maxit), int(restart), ctypes.byref(st))
+                         _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(st))
     _check(rc, allow=(QD_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return rc, st.iterations, list(it), list(rel)
 
@@ -439,9 +466,10 @@ def prof_read(ctx, kind, reset=False):
 
 
 def hutchinson_trace(ctx, gauge, mg, defl, m0, tau, seed, sample_offset, nsamples, tol, maxit=10000,
-                     restart=16, want_samples=True, want_coeffs=False, allow_not_converged=False):
+                     restart=16, want_samples=True, want_coeffs=False, allow_not_converged=False,
+                     precision=QD_PREC_F64, **kw):
     """One multi-RHS batch of the deflated estimator; returns a dict."""
-    p = TraceParams(int(seed), int(sample_offset), int(nsamples), float(tol), int(maxit), int(restart))
+    p = TraceParams(int(seed), int(sample_offset), int(nsamples), solver_params(tol, maxit, restart, precision, **kw))
     r = TraceResult()
     ts = np.zeros((nsamples, 2)) if want_samples else None
     k = defl.params.k if defl is not None else 0

@@ -49,10 +49,11 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "qdtrace.h"
 int main(void) {
-  printf("%zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol), offsetof(qd_mg_params, coarse_restart));
+  printf("%zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol), offsetof(qd_mg_params, coarsest_direct));
   printf("%zu %zu\n", sizeof(qd_solve_stats), offsetof(qd_solve_stats, true_rel_residual));
   printf("%zu %zu\n", sizeof(qd_defl_params), offsetof(qd_defl_params, seed));
-  printf("%zu %zu\n", sizeof(qd_trace_params), offsetof(qd_trace_params, restart));
+  printf("%zu %zu\n", sizeof(qd_trace_params), offsetof(qd_trace_params, solver));
+  printf("%zu %zu %zu\n", sizeof(qd_solver_params), offsetof(qd_solver_params, inner_tol), offsetof(qd_solver_params, max_refine));
   printf("%zu %zu %zu\n", sizeof(qd_trace_result), offsetof(qd_trace_result, nsamples), offsetof(qd_trace_result, UhKZ));
   return 0;
 }''')
@@ -60,10 +61,11 @@ int main(void) {
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     got = [list(map(int, l.split())) for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines()]
     want = [
-        [ctypes.sizeof(qd.MGParams), qd.MGParams.null_tol.offset, qd.MGParams.coarse_restart.offset],
+        [ctypes.sizeof(qd.MGParams), qd.MGParams.null_tol.offset, qd.MGParams.coarsest_direct.offset],
         [ctypes.sizeof(qd.SolveStats), qd.SolveStats.true_rel_residual.offset],
         [ctypes.sizeof(qd.DeflParams), qd.DeflParams.seed.offset],
-        [ctypes.sizeof(qd.TraceParams), qd.TraceParams.restart.offset],
+        [ctypes.sizeof(qd.TraceParams), qd.TraceParams.solver.offset],
+        [ctypes.sizeof(qd.SolverParams), qd.SolverParams.inner_tol.offset, qd.SolverParams.max_refine.offset],
         [ctypes.sizeof(qd.TraceResult), qd.TraceResult.nsamples.offset, qd.TraceResult.UhKZ.offset],
     ]
     assert got == want
@@ -86,3 +88,6 @@ def test_defaults(library):
     assert tuple(p.block[0]) == (2, 2, 2, 2)
     d = qd.defl_params()
     assert d.kind == qd.QD_DEFL_MG_OBLIQUE and d.k == 24
+    sp = qd.solver_params()
+    assert sp.tol == 1e-8 and sp.precision == qd.QD_PREC_F64 and sp.inner_tol == 1e-5
+    assert p.coarsest_direct == 16384

@@ -120,3 +120,25 @@ def test_injected_null_vectors(qd, ctx):
     out = torch.empty((T.nc * 2,), dtype=torch.complex128, device="cuda:0")
     qd.coarse_apply(mg, 1, 2, dev(c), out)
     assert rel_err(host(out).reshape(T.nc, 2), C @ c) < 1e-12
+
+
+@pytest.mark.parametrize("dims,m0,blocks,nvs", [((4, 4, 4, 4), -0.4, [(2, 2, 2, 2)], [6]),
+                                                ((8, 8, 8, 8), -0.8, [(2, 2, 2, 2)], [12]),
+                                                ((4, 4, 4, 4), -0.4, [(2, 2, 2, 2), (2, 2, 1, 1)], [6, 4])])
+def test_direct_coarsest_solve(qd, ctx, dims, m0, blocks, nvs):
+    # the coarsest operator's dense Gauss-Jordan inverse: C (C^{-1} x) = x, and
+    # C^{-1} x equals the oracle's sparse LU solve
+    U, g, mg, H = _build(qd, ctx, dims, m0, blocks, nvs, null_maxit=50)
+    L = len(blocks)
+    T = H.transfers[-1]
+    rng = np.random.default_rng(5)
+    s = 4
+    x = rng.standard_normal((T.nc, s)) + 1j * rng.standard_normal((T.nc, s))
+    y = torch.empty((T.nc * s,), dtype=torch.complex128, device="cuda:0")
+    qd.coarse_solve(mg, L, s, dev(x), y)
+    back = torch.empty_like(y)
+    qd.coarse_apply(mg, L, s, y, back)
+    assert rel_err(host(back).reshape(T.nc, s), x) < 1e-10
+    import scipy.sparse.linalg as spla
+    ref = spla.splu(H.matrices[-1].tocsc()).solve(x)
+    assert rel_err(host(y).reshape(T.nc, s), ref) < 1e-9

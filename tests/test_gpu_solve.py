@@ -92,3 +92,26 @@ def test_zero_rhs_column(qd, ctx):
     rc, its, it_col, rel = qd.solve(ctx, g, None, m0, 0.0, 3, bd, xd, 1e-9, maxit=3000)
     x = qd.from_qd(ctx, g, xd)
     assert np.all(x[..., 1] == 0) and rel[1] == 0.0 and rel[0] <= 1e-9
+
+
+@pytest.mark.parametrize("dims,m0,seed,blocks,nvs", [((4, 4, 4, 4), -0.4, 1, [(2, 2, 2, 2)], [6]),
+                                                     ((8, 8, 8, 8), -0.8, 2, [(2, 2, 2, 2)], [12])])
+def test_mixed_precision_refinement(qd, ctx, dims, m0, seed, blocks, nvs):
+    # FP32 V-cycle + FP32 GCR inside FP64 refinement: the FP64 true residual
+    # (checked here with the oracle's operator) meets 1e-8 and 1e-10
+    s = 6
+    U = synth.random_su3_links(dims, 0.3, seed)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(len(blocks), blocks, nvs))
+    A = omg.fine_level(U, m0, dims).matrix
+    b = synth.random_field(dims, s, 7)
+    bd = qd.to_qd(ctx, g, b)
+    for tol in (1e-8, 1e-10):
+        xd = torch.empty_like(bd)
+        rc, its, it_col, rel = qd.solve(ctx, g, mg, m0, 0.0, s, bd, xd, tol, maxit=200, restart=16,
+                                        precision=qd.QD_PREC_MIXED, inner_tol=1e-5, max_refine=10)
+        x = qd.from_qd(ctx, g, xd).reshape(-1, s)
+        B = b.reshape(-1, s)
+        true_rel = np.linalg.norm(B - A @ x, axis=0) / np.linalg.norm(B, axis=0)
+        assert np.all(true_rel <= tol), true_rel
+        assert np.allclose(true_rel, rel, rtol=1e-3, atol=1e-3 * tol)

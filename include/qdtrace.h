@@ -303,6 +303,31 @@ int qd_defl_info(const qd_defl* defl, double* mu, double* lambda,
  * Uses the active rank.  Asynchronous. */
 int qd_deflate_project(qd_defl* defl, int nrhs, const double* z, double* out);
 
+/* The paper has no counterpart to this entry point; it serves callers that
+ * must not have the library allocate device memory during a call.
+ * qd_deflate_project allocates (and frees) small device buffers for U^H z
+ * on every call; cudaMalloc and cudaFree synchronise the device and can fail
+ * once an application has handed its memory to its own pool, so a
+ * latency-critical loop, or a program that reserves all device memory up
+ * front, cannot use it.  This variant computes the same Algorithm 1
+ * projection, out = (I - U U^H) z with the active rank, but keeps its
+ * scratch (the rank x nrhs coefficients and their partial sums) in one
+ * fixed 8 MiB device array compiled into the library; it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   - Algorithm 1 deflation (QD_DEFL_EIG_ORTHO) only; QD_ERR_INVALID
+ *     otherwise, and when rank * nrhs > 262144 (the array's limit).
+ *   - The array exists once per device that loads the library and stays
+ *     allocated until the process exits.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device uses the same array and leaves the last call's
+ *     values in it: calls whose GPU work overlaps (other streams, threads or
+ *     contexts on the same device) race; issue them on one stream.
+ * Asynchronous, like qd_deflate_project. */
+int qd_deflate_project_static(qd_defl* defl, int nrhs, const double* z,
+                              double* out);
+
 /* Sec. 2.2 matrices for an a-posteriori rank sweep (kind 2 only), host
  * outputs, row-major complex: ZhV [nrhs][k] = Z^H W U_bar and
  * UhKZ [k][nrhs] = U_bar^H gamma5^W W^H Z.  Synchronous. */

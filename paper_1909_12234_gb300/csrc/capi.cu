@@ -405,6 +405,18 @@ int qd_deflate_project(qd_defl* defl, int nrhs, const double* z, double* out) {
   });
 }
 
+int qd_deflate_project_static(qd_defl* defl, int nrhs, const double* z, double* out) {
+  return guarded([&] {
+    NONNULL(defl);
+    NONNULL(z);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(z != out, "z and out must not overlap");
+    set_device(defl->ctx);
+    qd::defl_project_static(*defl, nrhs, reinterpret_cast<const qd::cplx*>(z), reinterpret_cast<qd::cplx*>(out));
+  });
+}
+
 int qd_deflate_coeffs(qd_defl* defl, int nrhs, const double* z, double* ZhV, double* UhKZ) {
   return guarded([&] {
     NONNULL(defl);

@@ -47,6 +47,8 @@ void defl_build(qd_defl& d, const double* injected);
 void defl_set_rank(qd_defl& d, int r);
 void defl_project(qd_defl& d, int s, const cplx* z, cplx* out);
 void defl_coeffs(qd_defl& d, int s, const cplx* z, cplx* M1, cplx* M2);
+// Algorithm 1 projection with scratch in a fixed device array (noalloc.cu).
+void defl_project_static(qd_defl& d, int s, const cplx* z, cplx* out);
 void blockmul_identity_cols(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int r, cplx* Y);
 void copy_leading_block(qd_ctx& ctx, int k, int r, const cplx* G, cplx* Gr);
 void sum_over_lambda(qd_ctx& ctx, int r, const cplx* dv, const double* lam, cplx* out);

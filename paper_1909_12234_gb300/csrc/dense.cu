@@ -63,6 +63,33 @@ void blockdot(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int ma, const cplx
   QD_LAUNCH_CHECK();
 }
 
+// Same product with caller-provided partial-sum space of `cap` complex
+// numbers (no allocation).  Uses as few row chunks as the space allows, at
+// most the number blockdot() would use.  Returns false if even one chunk
+// does not fit.
+bool blockdot_into(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int ma, const cplx* Y, int ldy, int mb,
+                   cplx* G, cplx* partials, int64_t cap) {
+  const int64_t m = (int64_t)ma * mb;
+  if (m > cap) return false;
+  const int ta = div_up(ma, 16), tb = div_up(mb, 16);
+  int64_t chunks = (2 * kNumSMs + ta * tb - 1) / (ta * tb);
+  const int64_t max_chunks = (n + 255) / 256;
+  if (chunks > max_chunks) chunks = max_chunks;
+  if (chunks > cap / m) chunks = cap / m;
+  if (chunks < 1) chunks = 1;
+  int64_t rpc = (n + chunks - 1) / chunks;
+  rpc = (rpc + 15) / 16 * 16;
+  chunks = (n + rpc - 1) / rpc;
+  if (chunks < 1) chunks = 1;
+  if (chunks * m > cap) return false;
+  k_blockdot<<<dim3(tb, ta, (unsigned)chunks), dim3(16, 16), 0, ctx.stream>>>(n, X, ldx, ma, Y, ldy, mb, rpc,
+                                                                            partials);
+  QD_LAUNCH_CHECK();
+  k_chunk_sum<<<div_up(m, 128), 128, 0, ctx.stream>>>((int)chunks, m, partials, G);
+  QD_LAUNCH_CHECK();
+  return true;
+}
+
 // Y[i][b] = alpha sum_a X[i][a] S[a][b] + beta Y[i][b]
 __global__ void k_blockmul(int64_t n, const cplx* __restrict__ X, int ldx, int ma, const cplx* __restrict__ S,
                            int lds, int mb, cplx* __restrict__ Y, int ldy, double alpha, double beta) {

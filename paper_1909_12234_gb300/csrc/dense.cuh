@@ -8,6 +8,10 @@ namespace qd {
 // G (ma x mb, row major) = X^H Y; X: n x ma with row stride ldx, Y: n x mb.
 void blockdot(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int ma, const cplx* Y, int ldy, int mb,
               cplx* G);
+// blockdot with caller-provided partial-sum space of `cap` complex numbers;
+// allocates nothing; false if the space is too small.
+bool blockdot_into(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int ma, const cplx* Y, int ldy, int mb,
+                   cplx* G, cplx* partials, int64_t cap);
 // Y = alpha X S + beta Y; X: n x ma, S: ma x mb (row stride lds), Y: n x mb.
 void blockmul(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int ma, const cplx* S, int lds, int mb,
               cplx* Y, int ldy, double alpha, double beta);

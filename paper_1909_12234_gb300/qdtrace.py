@@ -144,6 +144,7 @@ SIGNATURES = {
     "qd_defl_set_rank": (_I, [_P, _I, _DPTR]),
     "qd_defl_info": (_I, [_P, _DPTR, _DPTR, _IPTR]),
     "qd_deflate_project": (_I, [_P, _I, _P, _P]),
+    "qd_deflate_project_static": (_I, [_P, _I, _P, _P]),
     "qd_deflate_coeffs": (_I, [_P, _I, _P, _DPTR, _DPTR]),
     "qd_hutchinson_trace": (_I, [_P, _P, _P, _P, _D, _D, ctypes.POINTER(TraceParams),
                                  ctypes.POINTER(TraceResult)]),
@@ -425,6 +426,11 @@ class Deflation:
 
     def project(self, nrhs, z, out):
         _check(load().qd_deflate_project(self.h, int(nrhs), _ptr(z), _ptr(out)))
+
+    def project_static(self, nrhs, z, out):
+        """Algorithm 1 projection with the library's fixed device scratch
+        (no device allocation during the call); see qdtrace.h."""
+        _check(load().qd_deflate_project_static(self.h, int(nrhs), _ptr(z), _ptr(out)))
 
     def coeffs(self, nrhs, z):
         k = self.params.k

@@ -157,6 +157,10 @@ typedef struct {
                                    dimension is <= this value (at most
                                    16384); every coarsest solve is then one
                                    dense product.  0: coarsest GCR */
+  int coarsest_bf16;            /* with a dense coarsest inverse: != 0 lets
+                                   the FP32 V-cycle apply it as one BF16
+                                   tcgen05 tensor-core GEMM (FP32
+                                   accumulate); 0 uses FP32 CUDA cores */
 } qd_mg_params;
 
 /* Fill `p` with this library's defaults (1 level, 2^4 blocks, nv 12,
@@ -207,6 +211,15 @@ int qd_coarse_apply(qd_mg* mg, int level, int nrhs, const double* in,
  * next level's V-cycle when there is one).  Synchronous. */
 int qd_coarse_solve(qd_mg* mg, int level, int nrhs, const double* in,
                     double* out);
+
+/* The coarse solve of the FP32 V-cycle used by QD_PREC_MIXED: in and out are
+ * complex FP32 (2 floats) in the level's qd layout.  On the coarsest level
+ * with a dense inverse this is the BF16 tensor-core product (coarsest_bf16)
+ * or the FP32 CUDA-core one; otherwise QD_ERR_INVALID.  Returns
+ * QD_ERR_TIMEOUT if a bounded device wait of the tensor-core kernel gave
+ * up.  Synchronous. */
+int qd_coarse_solve_f32(qd_mg* mg, int level, int nrhs, const float* in,
+                        float* out);
 
 /* ------------------------------------------------------------------------ */
 /* a5/a6: solves A x = b to ||b - A x|| <= tol ||b|| (Sec. 1, inexact solve; */
@@ -391,7 +404,8 @@ enum {
   QD_PROF_RESTRICT_F32 = 7,
   QD_PROF_DIRECT_F64 = 8,   /* coarsest dense solve C^{-1} R, FP64 */
   QD_PROF_DIRECT_F32 = 9,
-  QD_PROF_NKINDS = 10
+  QD_PROF_DIRECT_BF16 = 10, /* coarsest dense solve on tcgen05 tensor cores */
+  QD_PROF_NKINDS = 11
 };
 
 /* enable != 0: record a CUDA event pair on the context stream around every

@@ -80,15 +80,22 @@ __global__ void k_dots(int K, int64_t n, int nrhs, const C* __restrict__ X, int6
   }
 }
 
-// out[k*nrhs + r] = sum_b partials[b][k][r] in block order
+// out[k*nrhs + r] = sum_b partials[b][k][r]: one warp per output; lane l
+// adds blocks l, l + 32, ... in order, then a fixed shuffle tree (the
+// result does not depend on scheduling).
 static __global__ void k_dots_final(int K, int nrhs, int nblk, const cplx* __restrict__ partials,
-                             cplx* __restrict__ out) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+                                    cplx* __restrict__ out) {
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (idx >= K * nrhs) return;
   const int k = idx / nrhs, r = idx - k * nrhs;
   cplx s = mkc(0.0, 0.0);
-  for (int b = 0; b < nblk; ++b) s = cadd(s, partials[((int64_t)b * K + k) * nrhs + r]);
-  out[idx] = s;
+  for (int b = lane; b < nblk; b += 32) s = cadd(s, partials[((int64_t)b * K + k) * nrhs + r]);
+  for (int off = 16; off > 0; off >>= 1) {
+    s.x += __shfl_down_sync(0xffffffffu, s.x, off);
+    s.y += __shfl_down_sync(0xffffffffu, s.y, off);
+  }
+  if (lane == 0) out[idx] = s;
 }
 
 // out[k][r] = <X_k, Y_k>_r for k < K (any K), X_k = X + k*xs, Y_k = Y + k*ys
@@ -105,10 +112,9 @@ void dots(qd_ctx& ctx, int K, int64_t n, int nrhs, const C* X, int64_t xs, const
     k_dots<C><<<s.grid, s.block, 0, ctx.stream>>>(kk, n, nrhs, X + k0 * xs, xs, Y + k0 * ys, ys,
                                                    ctx.red_partials.as<cplx>());
     QD_LAUNCH_CHECK();
-    const int tot = kk * nrhs;
-    k_dots_final<<<div_up(tot, 128), 128, 0, ctx.stream>>>(kk, nrhs, s.grid.x,
-                                                            ctx.red_partials.as<cplx>(),
-                                                            out + (int64_t)k0 * nrhs);
+    const int tot = kk * nrhs;  // one warp each, 8 warps per block
+    k_dots_final<<<div_up(tot, 8), 256, 0, ctx.stream>>>(kk, nrhs, s.grid.x, ctx.red_partials.as<cplx>(),
+                                                        out + (int64_t)k0 * nrhs);
     QD_LAUNCH_CHECK();
   }
 }

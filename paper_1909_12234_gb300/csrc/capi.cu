@@ -6,6 +6,7 @@
 #include "blas.cuh"
 #include "defl.cuh"
 #include "direct.cuh"
+#include "tc_gemm.cuh"
 
 
 static thread_local std::string g_last_error;
@@ -169,6 +170,7 @@ void qd_mg_params_default(qd_mg_params* p) {
   p->coarse_maxit = 256;
   p->coarse_restart = 16;
   p->coarsest_direct = 16384;
+  p->coarsest_bf16 = 1;
 }
 
 void qd_solver_params_default(qd_solver_params* p) {
@@ -290,6 +292,32 @@ int qd_coarse_solve(qd_mg* mg, int level, int nrhs, const double* in, double* ou
       qd::GCR<qd::cplx> gcr;
       gcr.solve(ctx, *A, pre.get(), x, y, nrhs, mg->p.coarse_tol, mg->p.coarse_maxit, mg->p.coarse_restart,
                 nullptr);
+    }
+    QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  });
+}
+
+int qd_coarse_solve_f32(qd_mg* mg, int level, int nrhs, const float* in, float* out) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(level >= 1 && level <= mg->nlevels, "coarse level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE((const void*)in != (void*)out, "in and out must not overlap");
+    set_device(mg->ctx);
+    qd_ctx& ctx = *mg->ctx;
+    qd::CoarseLevel& lv = *mg->L[level - 1];
+    const qd::cplxf* inv = mg->Cinv<qd::cplxf>(level);
+    QD_REQUIRE(inv != nullptr, "level has no dense inverse");
+    const qd::cplxf* x = reinterpret_cast<const qd::cplxf*>(in);
+    qd::cplxf* y = reinterpret_cast<qd::cplxf*>(out);
+    if (lv.tc) {
+      qd::tc_dense_apply(ctx, lv, x, y, nrhs);
+      const int e = qd::tc_error(ctx, lv);
+      if (e) qd::fail(QD_ERR_TIMEOUT, "tensor-core coarsest solve: bounded wait timed out (code " + std::to_string(e) + ")");
+    } else {
+      qd::dense_apply<qd::cplxf>(ctx, lv.ndense, nrhs, inv, x, y);
     }
     QD_CUDA(cudaStreamSynchronize(ctx.stream));
   });

@@ -174,6 +174,12 @@ struct CoarseLevel {
   int ndense = 0;     // > 0: Cinv holds the dense inverse (coarsest level)
   DevBuf Cinv;        // cplx  [n][n], n = nsites * D
   DevBuf Cinvf;       // cplxf copy
+  // tensor-core form of Cinv (tc_gemm.cu): BF16 [Mp][Kp], TMA maps, buffers
+  bool tc = false;
+  int tc_Mp = 0, tc_Kp = 0, tc_mapB_N = 0;
+  alignas(64) unsigned char tc_mapA[128];
+  alignas(64) unsigned char tc_mapB[128];
+  DevBuf tc_A, tc_B, tc_part, tc_err, tc_xc, tc_yc;
 };
 
 template <class C> struct CoarseOp : public Op<C> {

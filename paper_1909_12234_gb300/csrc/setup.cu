@@ -6,6 +6,7 @@
 #include "blas.cuh"
 #include "direct.cuh"
 #include "mg.cuh"
+#include "tc_gemm.cuh"
 
 namespace qd {
 
@@ -57,7 +58,13 @@ void mg_build(qd_mg& mg, const double* injected_null) {
   // coarsest level: dense FP64 inverse when small enough
   CoarseLevel& last = *mg.L.back();
   const int64_t nlast = last.geo.nsites * (int64_t)last.D;
-  if (p.coarsest_direct > 0 && nlast <= p.coarsest_direct && nlast <= 16384) coarse_dense_inverse(ctx, last);
+  if (p.coarsest_direct > 0 && nlast <= p.coarsest_direct && nlast <= 16384) {
+    coarse_dense_inverse(ctx, last);
+    if (p.coarsest_bf16) {
+      tc_prepare(ctx, last);
+      last.tc = true;
+    }
+  }
   mg.pre64.reset(new MGPrecond<cplx>(&mg, 0));
   mg.pre32.reset(new MGPrecond<cplxf>(&mg, 0));
 }

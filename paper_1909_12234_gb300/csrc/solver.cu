@@ -6,6 +6,7 @@
 #include "blas.cuh"
 #include "direct.cuh"
 #include "mg.cuh"
+#include "tc_gemm.cuh"
 
 namespace qd {
 
@@ -89,14 +90,18 @@ __global__ void k_mr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
 
 // rn2[c] = sum of partials; active columns stay active while
 // rn2 > tol2 * ref2; counts active columns and non-finite norms.
+// One warp per column (fixed lane order and shuffle tree: deterministic).
 __global__ void k_resid_final(int nrhs, int nblk, const cplx* __restrict__ partials, cplx* __restrict__ rn2,
                               const cplx* __restrict__ ref2, double tol2, int* __restrict__ active,
                               int* __restrict__ count, int* __restrict__ nonfin, int* __restrict__ iters) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (c >= nrhs) return;
   if (!active[c]) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partials[(int64_t)b * nrhs + c].x;
+  for (int b = lane; b < nblk; b += 32) s += partials[(int64_t)b * nrhs + c].x;
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane != 0) return;
   rn2[c] = mkc(s, 0.0);
   if (iters) iters[c] += 1;
   if (!isfinite(s)) {
@@ -207,8 +212,8 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
                                                             ctx.red_partials.as<cplx>());
       QD_LAUNCH_CHECK();
       QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
-      k_resid_final<<<div_up(nrhs, 128), 128, 0, ctx.stream>>>(nrhs, sw.grid.x, ctx.red_partials.as<cplx>(),
-                                                              rn2, bn2, tol2, act, flags, flags + 1, iters);
+      k_resid_final<<<div_up(nrhs, 8), 256, 0, ctx.stream>>>(nrhs, sw.grid.x, ctx.red_partials.as<cplx>(), rn2,
+                                                            bn2, tol2, act, flags, flags + 1, iters);
       QD_LAUNCH_CHECK();
       ++its;
       read_flags(ctx, flags, 2, hflags);
@@ -282,9 +287,8 @@ void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int
     QD_LAUNCH_CHECK();
     if (check) {
       QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
-      k_resid_final<<<div_up(nrhs, 128), 128, 0, ctx.stream>>>(nrhs, sw.grid.x, ctx.red_partials.as<cplx>(),
-                                                              rn2, r0n2, tol * tol, act, flags, flags + 1,
-                                                              steps_dev);
+      k_resid_final<<<div_up(nrhs, 8), 256, 0, ctx.stream>>>(nrhs, sw.grid.x, ctx.red_partials.as<cplx>(), rn2,
+                                                            r0n2, tol * tol, act, flags, flags + 1, steps_dev);
       QD_LAUNCH_CHECK();
       read_flags(ctx, flags, 2, hflags);
       if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in minimal-residual iteration");
@@ -323,7 +327,10 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
   // coarse-grid correction: z = W C^{-1} W^H r
   restrict_<C>(ctx, T, W, r, rc_.as<C>(), nrhs);
   const C* inv = mg_->Cinv<C>(level_ + 1);
-  if (inv) {
+  CoarseLevel& cl = *mg_->L[level_];
+  if (inv && sizeof(C) == sizeof(cplxf) && cl.tc) {
+    tc_dense_apply(ctx, cl, reinterpret_cast<const cplxf*>(rc_.as<C>()), reinterpret_cast<cplxf*>(ec_.as<C>()), nrhs);
+  } else if (inv) {
     dense_apply<C>(ctx, (int)nc, nrhs, inv, rc_.as<C>(), ec_.as<C>());
   } else {
     auto Ac = mg_->op<C>(level_ + 1);

@@ -3,6 +3,7 @@
 // and 2: t0 + (1/s) sum_j z_j^H A^{-1}_xi (I - P) z_j).
 #include "blas.cuh"
 #include "defl.cuh"
+#include "tc_gemm.cuh"
 
 namespace qd {
 
@@ -89,6 +90,10 @@ static void solve_mixed(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, do
     A64.apply(ctx, x, t, s);
     blas::sub(ctx, tot, b, t, r);
     blas::dots(ctx, 1, n, s, r, 0, r, 0, rn2);
+  }
+  if (mg && mg->L.back()->tc) {
+    const int e = tc_error(ctx, *mg->L.back());
+    if (e) fail(QD_ERR_TIMEOUT, "tensor-core coarsest solve: bounded wait timed out (code " + std::to_string(e) + ")");
   }
   std::vector<cplx> hb(s), hr(s);
   QD_CUDA(cudaMemcpyAsync(hb.data(), bn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));

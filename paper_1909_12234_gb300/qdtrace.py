@@ -55,7 +55,8 @@ class MGParams(ctypes.Structure):
                 ("coarse_tol", ctypes.c_double),
                 ("coarse_maxit", ctypes.c_int),
                 ("coarse_restart", ctypes.c_int),
-                ("coarsest_direct", ctypes.c_int)]
+                ("coarsest_direct", ctypes.c_int),
+                ("coarsest_bf16", ctypes.c_int)]
 
 
 class SolverParams(ctypes.Structure):
@@ -136,6 +137,7 @@ SIGNATURES = {
     "qd_restrict": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_apply": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve": (_I, [_P, _I, _I, _P, _P]),
+    "qd_coarse_solve_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_solver_params_default": (None, [ctypes.POINTER(SolverParams)]),
     "qd_solve": (_I, [_P, _P, _P, _D, _D, _I, _P, _P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveStats)]),
     "qd_defl_params_default": (None, [ctypes.POINTER(DeflParams)]),
@@ -154,7 +156,7 @@ SIGNATURES = {
 }
 
 PROF_KINDS = {"wilson_f64": 0, "wilson_f32": 1, "coarse_f64": 2, "coarse_f32": 3, "prolong_f64": 4,
-              "prolong_f32": 5, "restrict_f64": 6, "restrict_f32": 7, "direct_f64": 8, "direct_f32": 9}
+              "prolong_f32": 5, "restrict_f64": 6, "restrict_f32": 7, "direct_f64": 8, "direct_f32": 9, "direct_bf16": 10}
 
 _lib = None
 
@@ -364,6 +366,18 @@ def coarse_apply(mg, level, nrhs, inp, out):
 
 def coarse_solve(mg, level, nrhs, inp, out):
     _check(load().qd_coarse_solve(mg.h, int(level), int(nrhs), _ptr(inp), _ptr(out)))
+
+
+def _ptr64(t):
+    """Device pointer of a contiguous complex64 CUDA tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64 or not t.is_contiguous():
+        raise QDError(QD_ERR_INVALID, "expected a contiguous torch.complex64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def coarse_solve_f32(mg, level, nrhs, inp, out):
+    _check(load().qd_coarse_solve_f32(mg.h, int(level), int(nrhs), _ptr64(inp), _ptr64(out)))
 
 
 def solver_params(tol=1e-8, maxit=500, restart=16, precision=QD_PREC_F64, **kw):

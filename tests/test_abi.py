@@ -90,4 +90,4 @@ def test_defaults(library):
     assert d.kind == qd.QD_DEFL_MG_OBLIQUE and d.k == 24
     sp = qd.solver_params()
     assert sp.tol == 1e-8 and sp.precision == qd.QD_PREC_F64 and sp.inner_tol == 1e-5
-    assert p.coarsest_direct == 16384
+    assert p.coarsest_direct == 16384 and p.coarsest_bf16 == 1

@@ -405,7 +405,9 @@ enum {
   QD_PROF_DIRECT_F64 = 8,   /* coarsest dense solve C^{-1} R, FP64 */
   QD_PROF_DIRECT_F32 = 9,
   QD_PROF_DIRECT_BF16 = 10, /* coarsest dense solve on tcgen05 tensor cores */
-  QD_PROF_NKINDS = 11
+  QD_PROF_BLAS_F64 = 11,    /* reductions and vector updates of the solvers */
+  QD_PROF_BLAS_F32 = 12,
+  QD_PROF_NKINDS = 13
 };
 
 /* enable != 0: record a CUDA event pair on the context stream around every

@@ -37,10 +37,15 @@ inline Sweep sweep(int64_t n, int nrhs, int max_row_blocks = 4 * kNumSMs) {
   return s;
 }
 
+// Up to kDotK (X_k, Y_k) vector pairs for one reduction launch.
+template <class C> struct DotPairs {
+  const C* x[kDotK];
+  const C* y[kDotK];
+};
+
 // partials[(blk*K + k)*nrhs + r] = sum over this block's rows of conj(X_k) Y_k
 template <class C>
-__global__ void k_dots(int K, int64_t n, int nrhs, const C* __restrict__ X, int64_t xs,
-                       const C* __restrict__ Y, int64_t ys, cplx* __restrict__ partials) {
+__global__ void k_dots(int K, int64_t n, int nrhs, DotPairs<C> pr, cplx* __restrict__ partials) {
   typedef typename CTraits<C>::R R;
   __shared__ cplx sm[kDotK][kThreads];
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -51,16 +56,9 @@ __global__ void k_dots(int K, int64_t n, int nrhs, const C* __restrict__ X, int6
   if (r < nrhs) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.y + ty; i < n; i += (int64_t)gridDim.x * blockDim.y) {
       const int64_t e = i * nrhs + r;
-      if (ys == 0) {
-        const C y = Y[e];
 #pragma unroll
-        for (int k = 0; k < kDotK; ++k)
-          if (k < K) cfmac(acc[k], X[k * xs + e], y);
-      } else {
-#pragma unroll
-        for (int k = 0; k < kDotK; ++k)
-          if (k < K) cfmac(acc[k], X[k * xs + e], Y[k * ys + e]);
-      }
+      for (int k = 0; k < kDotK; ++k)
+        if (k < K) cfmac(acc[k], pr.x[k][e], pr.y[k][e]);
     }
   }
   const int t = ty * blockDim.x + tx;
@@ -98,6 +96,22 @@ static __global__ void k_dots_final(int K, int nrhs, int nblk, const cplx* __res
   if (lane == 0) out[idx] = s;
 }
 
+// One reduction launch (+ final pass) for K <= kDotK pairs: out[k][r].
+template <class C>
+void dots_launch(qd_ctx& ctx, int K, int64_t n, int nrhs, const DotPairs<C>& pr, cplx* out) {
+  Sweep s = sweep(n, nrhs);
+  ctx.red_partials.resize((size_t)s.grid.x * K * nrhs * sizeof(cplx));
+  {
+    ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 8.0 * K * n * nrhs,
+                 (double)sizeof(C) * 2.0 * K * n * nrhs);
+    k_dots<C><<<s.grid, s.block, 0, ctx.stream>>>(K, n, nrhs, pr, ctx.red_partials.as<cplx>());
+    QD_LAUNCH_CHECK();
+  }
+  const int tot = K * nrhs;  // one warp each, 8 warps per block
+  k_dots_final<<<div_up(tot, 8), 256, 0, ctx.stream>>>(K, nrhs, s.grid.x, ctx.red_partials.as<cplx>(), out);
+  QD_LAUNCH_CHECK();
+}
+
 // out[k][r] = <X_k, Y_k>_r for k < K (any K), X_k = X + k*xs, Y_k = Y + k*ys
 // (strides in complex elements; ys may be 0).  out: device cplx [K][nrhs].
 template <class C>
@@ -106,17 +120,25 @@ void dots(qd_ctx& ctx, int K, int64_t n, int nrhs, const C* X, int64_t xs, const
   if (K <= 0) return;
   for (int k0 = 0; k0 < K; k0 += kDotK) {
     const int kk = (K - k0) < kDotK ? (K - k0) : kDotK;
-    Sweep s = sweep(n, nrhs);
-    const size_t need = (size_t)s.grid.x * kk * nrhs * sizeof(cplx);
-    ctx.red_partials.resize(need);
-    k_dots<C><<<s.grid, s.block, 0, ctx.stream>>>(kk, n, nrhs, X + k0 * xs, xs, Y + k0 * ys, ys,
-                                                   ctx.red_partials.as<cplx>());
-    QD_LAUNCH_CHECK();
-    const int tot = kk * nrhs;  // one warp each, 8 warps per block
-    k_dots_final<<<div_up(tot, 8), 256, 0, ctx.stream>>>(kk, nrhs, s.grid.x, ctx.red_partials.as<cplx>(),
-                                                        out + (int64_t)k0 * nrhs);
-    QD_LAUNCH_CHECK();
+    DotPairs<C> pr;
+    for (int k = 0; k < kDotK; ++k) {
+      const int kc = k < kk ? k : 0;
+      pr.x[k] = X + (k0 + kc) * xs;
+      pr.y[k] = Y + (k0 + kc) * ys;
+    }
+    dots_launch<C>(ctx, kk, n, nrhs, pr, out + (int64_t)k0 * nrhs);
   }
+}
+
+// out[0][r] = <x0, y0>_r, out[1][r] = <x1, y1>_r in one launch.
+template <class C>
+void dots2(qd_ctx& ctx, int64_t n, int nrhs, const C* x0, const C* y0, const C* x1, const C* y1, cplx* out) {
+  DotPairs<C> pr;
+  for (int k = 0; k < kDotK; ++k) {
+    pr.x[k] = (k == 1) ? x1 : x0;
+    pr.y[k] = (k == 1) ? y1 : y0;
+  }
+  dots_launch<C>(ctx, 2, n, nrhs, pr, out);
 }
 
 // Y_j[i,r] -= sum_k coef[k][r] X_k[i,r] for (Y, X) and, when Y2 != null,
@@ -154,6 +176,8 @@ template <class C>
 void multi_axpy(qd_ctx& ctx, int K, int64_t n, int nrhs, const cplx* coef, const int* active,
                 const C* X, int64_t xs, C* Y, const C* X2 = nullptr, C* Y2 = nullptr) {
   if (K <= 0) return;
+  ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 8.0 * K * n * nrhs * (Y2 ? 2 : 1),
+               (double)sizeof(C) * (K + 2.0) * n * nrhs * (Y2 ? 2 : 1));
   k_multi_axpy<C><<<grid_1d(n * nrhs), kThreads, 0, ctx.stream>>>(K, n, nrhs, coef, active, X, xs, Y,
                                                                  X2, Y2);
   QD_LAUNCH_CHECK();

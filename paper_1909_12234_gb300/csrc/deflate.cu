@@ -252,8 +252,8 @@ void defl_project(qd_defl& d, int s, const cplx* z, cplx* out) {
     scale_rows_inv(ctx, r, s, d.lam.as<double>(), a.as<cplx>());                  // Lambda^{-1}
     blockmul(ctx, d.nb, d.U.as<cplx>(), r, r, a.as<cplx>(), s, s, c.as<cplx>(), s, 1.0, 0.0);  // U (.)
     prolongate<cplx>(ctx, T, T.W.as<cplx>(), c.as<cplx>(), f.as<cplx>(), s);       // W (.)
-    wilson_apply<cplx>(ctx, d.gauge->geo, d.gauge->links.as<cplx>(), d.m0, d.tau, false, f.as<cplx>(), out, s);
-    blas::sub(ctx, nf * s, z, out, out);  // out = z - A W U Lambda^{-1} U^H g5 W^H z
+    // out = z - A W U Lambda^{-1} U^H g5 W^H z (fused residual kernel)
+    wilson_apply<cplx>(ctx, d.gauge->geo, d.gauge->links.as<cplx>(), d.m0, d.tau, false, f.as<cplx>(), out, s, z);
   } else {
     blockdot(ctx, nf, d.U.as<cplx>(), r, r, z, s, s, a.as<cplx>());  // U^H z
     blas::copy(ctx, nf * s, z, out);

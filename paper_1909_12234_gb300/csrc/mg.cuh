@@ -38,6 +38,10 @@ template <class C> class GCR {
 template <class C>
 void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int nrhs, int nsteps,
               double tol, C* rbuf, C* qbuf, int* steps_dev, DevBuf& scratch);
+// nsteps minimal-residual steps on A e = res, accumulated into x; res is
+// updated in place (smoother: no checks, no host synchronisation).
+template <class C>
+void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int nsteps, DevBuf& scratch);
 
 }  // namespace qd
 

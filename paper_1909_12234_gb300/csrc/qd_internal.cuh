@@ -97,6 +97,8 @@ template <class C> struct Op {
   virtual int dof() const = 0;
   int64_t n() const { return nsites() * (int64_t)dof(); }
   virtual void apply(qd_ctx& ctx, const C* in, C* out, int nrhs) const = 0;
+  // r = b - A x; r must not alias x.  Default: apply into r, then subtract.
+  virtual void residual(qd_ctx& ctx, const C* b, const C* x, C* r, int nrhs) const;
 };
 
 template <class C> struct Precond {
@@ -130,12 +132,13 @@ template <class C> struct WilsonOp : public Op<C> {
   int64_t nsites() const override { return g->geo.nsites; }
   int dof() const override { return 12; }
   void apply(qd_ctx& ctx, const C* in, C* out, int nrhs) const override;
+  void residual(qd_ctx& ctx, const C* b, const C* x, C* r, int nrhs) const override;
 };
 
-// Launchers (wilson.cu).
+// Launchers (wilson.cu).  b != nullptr: out = b - A in (fused residual).
 template <class C>
 void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, double tau,
-                  bool dagger, const C* in, C* out, int nrhs);
+                  bool dagger, const C* in, C* out, int nrhs, const C* b = nullptr);
 void gauge_import(qd_ctx& ctx, qd_gauge& g, const double* links_host);
 void links_to_f32(qd_ctx& ctx, const cplx* in, cplxf* out, int64_t n);
 

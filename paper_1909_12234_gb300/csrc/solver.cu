@@ -10,6 +10,13 @@
 
 namespace qd {
 
+template <class C> void Op<C>::residual(qd_ctx& ctx, const C* b, const C* x, C* r, int nrhs) const {
+  apply(ctx, x, r, nrhs);
+  blas::sub(ctx, n() * nrhs, b, r, r);
+}
+template struct Op<cplx>;
+template struct Op<cplxf>;
+
 // ---------------------------------------------------------------------------
 // Fused update kernels with a per-column |r|^2 reduction (deterministic).
 // ---------------------------------------------------------------------------
@@ -205,12 +212,15 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
         blas::dots(ctx, i, n, nrhs, Q, tot, Qi, 0, beta);
         blas::multi_axpy(ctx, i, n, nrhs, beta, act, Q, tot, Qi, P, Pi);
       }
-      blas::dots(ctx, 1, n, nrhs, Qi, 0, Qi, 0, s2);
-      blas::dots(ctx, 1, n, nrhs, Qi, 0, r, 0, s2 + nrhs);
+      blas::dots2(ctx, n, nrhs, Qi, Qi, Qi, r, s2);
       ctx.red_partials.resize((size_t)sw.grid.x * nrhs * sizeof(cplx));
-      k_gcr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, act, Qi, Pi, x, r,
-                                                            ctx.red_partials.as<cplx>());
-      QD_LAUNCH_CHECK();
+      {
+        ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 16.0 * n * nrhs,
+                     (double)sizeof(C) * 8.0 * n * nrhs);
+        k_gcr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, act, Qi, Pi, x, r,
+                                                              ctx.red_partials.as<cplx>());
+        QD_LAUNCH_CHECK();
+      }
       QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
       k_resid_final<<<div_up(nrhs, 8), 256, 0, ctx.stream>>>(nrhs, sw.grid.x, ctx.red_partials.as<cplx>(), rn2,
                                                             bn2, tol2, act, flags, flags + 1, iters);
@@ -221,8 +231,7 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
       if (hflags[0] == 0 || its >= maxit) break;
     }
     // true residual r = b - A x
-    A.apply(ctx, x, t, nrhs);
-    blas::sub(ctx, tot, b, t, r);
+    A.residual(ctx, b, x, r, nrhs);
     blas::dots(ctx, 1, n, nrhs, r, 0, r, 0, rn2);
   }
   if (info) {
@@ -265,8 +274,7 @@ void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int
     blas::zero(ctx, tot, x);
     blas::copy(ctx, tot, b, r);
   } else {
-    A.apply(ctx, x, q, nrhs);
-    blas::sub(ctx, tot, b, q, r);
+    A.residual(ctx, b, x, r, nrhs);
   }
   const bool check = tol > 0.0;
   const blas::Sweep sw = blas::sweep(n, nrhs);
@@ -279,8 +287,7 @@ void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int
   }
   for (int k = 0; k < nsteps; ++k) {
     A.apply(ctx, r, q, nrhs);
-    blas::dots(ctx, 1, n, nrhs, q, 0, q, 0, s2);
-    blas::dots(ctx, 1, n, nrhs, q, 0, r, 0, s2 + nrhs);
+    blas::dots2(ctx, n, nrhs, q, q, q, r, s2);
     ctx.red_partials.resize((size_t)sw.grid.x * nrhs * sizeof(cplx));
     k_mr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, check ? act : nullptr, q, x, r,
                                                          check ? ctx.red_partials.as<cplx>() : nullptr);
@@ -296,6 +303,26 @@ void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int
     }
   }
 }
+
+// nsteps minimal-residual steps on A e = res that add to x and update res
+// in place (no convergence checks, no host synchronisation).
+template <class C>
+void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int nsteps, DevBuf& scratch) {
+  const int64_t n = A.n();
+  scratch.resize((size_t)2 * nrhs * sizeof(cplx));
+  cplx* s2 = scratch.as<cplx>();
+  const blas::Sweep sw = blas::sweep(n, nrhs);
+  for (int k = 0; k < nsteps; ++k) {
+    A.apply(ctx, res, q, nrhs);
+    blas::dots2(ctx, n, nrhs, q, q, q, res, s2);
+    ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 8.0 * n * nrhs,
+                 (double)sizeof(C) * 5.0 * n * nrhs);
+    k_mr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, nullptr, q, x, res, nullptr);
+    QD_LAUNCH_CHECK();
+  }
+}
+template void mr_smooth<cplx>(qd_ctx&, const Op<cplx>&, cplx*, cplx*, cplx*, int, int, DevBuf&);
+template void mr_smooth<cplxf>(qd_ctx&, const Op<cplxf>&, cplxf*, cplxf*, cplxf*, int, int, DevBuf&);
 
 template void mr_steps<cplx>(qd_ctx&, const Op<cplx>&, const cplx*, cplx*, bool, int, int, double, cplx*,
                              cplx*, int*, DevBuf&);
@@ -338,15 +365,13 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
                   mg_->p.coarse_maxit, mg_->p.coarse_restart, nullptr);
   }
   prolongate<C>(ctx, T, W, ec_.as<C>(), z, nrhs);
-  // smoothing: z += M^{-1} (r - A z), M^{-1} = minimal-residual steps from 0
+  // smoothing: z += M^{-1} (r - A z), M^{-1} = minimal-residual steps from 0;
+  // the steps update z in place with the residual res = r - A z
   const int nu = mg_->p.smoother_steps;
   if (nu > 0) {
     auto Af = mg_->op<C>(level_);
-    Af->apply(ctx, z, t_.as<C>(), nrhs);
-    blas::sub(ctx, nf * nrhs, r, t_.as<C>(), res_.as<C>());
-    mr_steps<C>(ctx, *Af, res_.as<C>(), d_.as<C>(), true, nrhs, nu, 0.0, t_.as<C>(), q_.as<C>(), nullptr,
-                scratch_);
-    blas::add(ctx, nf * nrhs, d_.as<C>(), z);
+    Af->residual(ctx, r, z, res_.as<C>(), nrhs);
+    mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, nu, scratch_);
   }
 }
 

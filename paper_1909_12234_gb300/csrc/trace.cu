@@ -87,8 +87,7 @@ static void solve_mixed(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, do
     for (int c = 0; c < s; ++c) iters[c] += in.iters[c];
     k_axpy_from_f32<<<blas::grid_1d(tot), 256, 0, ctx.stream>>>(n, s, ef, sout, x);
     QD_LAUNCH_CHECK();
-    A64.apply(ctx, x, t, s);
-    blas::sub(ctx, tot, b, t, r);
+    A64.residual(ctx, b, x, r, s);
     blas::dots(ctx, 1, n, s, r, 0, r, 0, rn2);
   }
   if (mg && mg->L.back()->tc) {

@@ -135,10 +135,11 @@ __device__ __forceinline__ void hop_dir(const C* __restrict__ U, const int* __re
   }
 }
 
-template <class C, bool DAG>
+// RESID: out = b - A in (the residual of A x = b) instead of out = A in.
+template <class C, bool DAG, bool RESID>
 __global__ void __launch_bounds__(128)
 k_wilson(const C* __restrict__ U, const int* __restrict__ nbr, int64_t V, int nrhs, double mass,
-         double tau, const C* __restrict__ in, C* __restrict__ out) {
+         double tau, const C* __restrict__ in, C* __restrict__ out, const C* __restrict__ b) {
   typedef typename CTraits<C>::R R;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= V * nrhs) return;
@@ -161,53 +162,69 @@ k_wilson(const C* __restrict__ U, const int* __restrict__ nbr, int64_t V, int nr
   const R mhalf = (R)(-0.5);
   const C* x = in + site * 12 * rs + r;
   C* y = out + site * 12 * rs + r;
+  const C* bb = RESID ? b + site * 12 * rs + r : nullptr;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    C v = cmul(mup, x[k * rs]);
-    v.x = fma(mhalf, hu[k].x, v.x);
-    v.y = fma(mhalf, hu[k].y, v.y);
+  for (int k = 0; k < 12; ++k) {
+    const C h = k < 6 ? hu[k] : hl[k - 6];
+    C v = cmul(k < 6 ? mup : mlo, x[k * rs]);
+    v.x = fma(mhalf, h.x, v.x);
+    v.y = fma(mhalf, h.y, v.y);
+    if (RESID) {
+      const C bv = bb[k * rs];
+      v = csub(bv, v);
+    }
     y[k * rs] = v;
-  }
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    C v = cmul(mlo, x[(6 + k) * rs]);
-    v.x = fma(mhalf, hl[k].x, v.x);
-    v.y = fma(mhalf, hl[k].y, v.y);
-    y[(6 + k) * rs] = v;
   }
 }
 
 template <class C>
 void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, double tau,
-                  bool dagger, const C* in, C* out, int nrhs) {
+                  bool dagger, const C* in, C* out, int nrhs, const C* b) {
   const int64_t tot = geo.nsites * nrhs;
   if (tot == 0) return;
   const int threads = 128;
   const int blocks = div_up(tot, threads);
   const double cb = (double)sizeof(C);
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_WILSON_F64 : QD_PROF_WILSON_F32, 1368.0 * (double)tot,
-               (double)geo.nsites * (24.0 * cb * nrhs + 36.0 * cb));
-  if (dagger)
-    k_wilson<C, true><<<blocks, threads, 0, ctx.stream>>>(links, geo.nbr.as<int>(), geo.nsites, nrhs,
-                                                          4.0 + m0, tau, in, out);
-  else
-    k_wilson<C, false><<<blocks, threads, 0, ctx.stream>>>(links, geo.nbr.as<int>(), geo.nsites, nrhs,
-                                                           4.0 + m0, tau, in, out);
+               (double)geo.nsites * ((b ? 36.0 : 24.0) * cb * nrhs + 36.0 * cb));
+  const int* nb = geo.nbr.as<int>();
+  const double mass = 4.0 + m0;
+  if (b) {
+    if (dagger)
+      k_wilson<C, true, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, geo.nsites, nrhs, mass, tau, in, out, b);
+    else
+      k_wilson<C, false, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, geo.nsites, nrhs, mass, tau, in, out, b);
+  } else {
+    if (dagger)
+      k_wilson<C, true, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, geo.nsites, nrhs, mass, tau, in, out,
+                                                                   nullptr);
+    else
+      k_wilson<C, false, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, geo.nsites, nrhs, mass, tau, in, out,
+                                                                    nullptr);
+  }
   QD_LAUNCH_CHECK();
 }
 
 template void wilson_apply<cplx>(qd_ctx&, const LevelGeom&, const cplx*, double, double, bool,
-                                 const cplx*, cplx*, int);
+                                 const cplx*, cplx*, int, const cplx*);
 template void wilson_apply<cplxf>(qd_ctx&, const LevelGeom&, const cplxf*, double, double, bool,
-                                  const cplxf*, cplxf*, int);
+                                  const cplxf*, cplxf*, int, const cplxf*);
 
 template <>
 void WilsonOp<cplx>::apply(qd_ctx& ctx, const cplx* in, cplx* out, int nrhs) const {
-  wilson_apply<cplx>(ctx, g->geo, links, m0, tau, dagger, in, out, nrhs);
+  wilson_apply<cplx>(ctx, g->geo, links, m0, tau, dagger, in, out, nrhs, nullptr);
 }
 template <>
 void WilsonOp<cplxf>::apply(qd_ctx& ctx, const cplxf* in, cplxf* out, int nrhs) const {
-  wilson_apply<cplxf>(ctx, g->geo, links, m0, tau, dagger, in, out, nrhs);
+  wilson_apply<cplxf>(ctx, g->geo, links, m0, tau, dagger, in, out, nrhs, nullptr);
+}
+template <>
+void WilsonOp<cplx>::residual(qd_ctx& ctx, const cplx* b, const cplx* x, cplx* r, int nrhs) const {
+  wilson_apply<cplx>(ctx, g->geo, links, m0, tau, dagger, x, r, nrhs, b);
+}
+template <>
+void WilsonOp<cplxf>::residual(qd_ctx& ctx, const cplxf* b, const cplxf* x, cplxf* r, int nrhs) const {
+  wilson_apply<cplxf>(ctx, g->geo, links, m0, tau, dagger, x, r, nrhs, b);
 }
 
 }  // namespace qd

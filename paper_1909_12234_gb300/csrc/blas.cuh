@@ -141,6 +141,54 @@ void dots2(qd_ctx& ctx, int64_t n, int nrhs, const C* x0, const C* y0, const C* 
   dots_launch<C>(ctx, 2, n, nrhs, pr, out);
 }
 
+// out[0][r] = <q,q>_r, out[1][r] = <q,r>_r reading q once (smoother steps).
+template <class C>
+__global__ void k_dots_qq_qr(int64_t n, int nrhs, const C* __restrict__ q, const C* __restrict__ rv,
+                             cplx* __restrict__ partials) {
+  typedef typename CTraits<C>::R R;
+  __shared__ cplx sm[2][kThreads];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int col = blockIdx.y * blockDim.x + tx;
+  R qq = 0;
+  C qr = mk<C>((R)0, (R)0);
+  if (col < nrhs) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.y + ty; i < n; i += (int64_t)gridDim.x * blockDim.y) {
+      const int64_t e = i * nrhs + col;
+      const C a = q[e];
+      qq += cnorm2(a);
+      cfmac(qr, a, rv[e]);
+    }
+  }
+  const int t = ty * blockDim.x + tx;
+  sm[0][t] = mkc((double)qq, 0.0);
+  sm[1][t] = mkc((double)qr.x, (double)qr.y);
+  __syncthreads();
+  for (int h = blockDim.y / 2; h > 0; h >>= 1) {
+    if (ty < h) {
+      sm[0][t] = cadd(sm[0][t], sm[0][t + h * blockDim.x]);
+      sm[1][t] = cadd(sm[1][t], sm[1][t + h * blockDim.x]);
+    }
+    __syncthreads();
+  }
+  if (ty == 0 && col < nrhs) {
+    partials[((int64_t)blockIdx.x * 2 + 0) * nrhs + col] = sm[0][tx];
+    partials[((int64_t)blockIdx.x * 2 + 1) * nrhs + col] = sm[1][tx];
+  }
+}
+
+template <class C> void dots_qq_qr(qd_ctx& ctx, int64_t n, int nrhs, const C* q, const C* r, cplx* out) {
+  Sweep s = sweep(n, nrhs);
+  ctx.red_partials.resize((size_t)s.grid.x * 2 * nrhs * sizeof(cplx));
+  {
+    ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 12.0 * n * nrhs,
+                 (double)sizeof(C) * 2.0 * n * nrhs);
+    k_dots_qq_qr<C><<<s.grid, s.block, 0, ctx.stream>>>(n, nrhs, q, r, ctx.red_partials.as<cplx>());
+    QD_LAUNCH_CHECK();
+  }
+  k_dots_final<<<div_up(2 * nrhs, 8), 256, 0, ctx.stream>>>(2, nrhs, s.grid.x, ctx.red_partials.as<cplx>(), out);
+  QD_LAUNCH_CHECK();
+}
+
 // Y_j[i,r] -= sum_k coef[k][r] X_k[i,r] for (Y, X) and, when Y2 != null,
 // (Y2, X2) with the same coefficients; columns with active[r] == 0 untouched.
 template <class C>

@@ -17,6 +17,8 @@ struct SolveInfo {
 // Flexible restarted GCR, batched over independent right-hand sides.
 template <class C> class GCR {
  public:
+  // Gram-Schmidt passes per iteration (2 = CGS2; 1 = classical, one pass).
+  int orth_passes = 2;
   // x = A^{-1} b to ||b - A x|| <= tol ||b|| per column (x overwritten,
   // zero initial guess).  M (nullable) is a right preconditioner that may
   // change between calls.  `quiet` skips per-column statistics.

@@ -208,7 +208,7 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
       else
         blas::copy(ctx, tot, r, Pi);
       A.apply(ctx, Pi, Qi, nrhs);
-      for (int pass = 0; pass < 2 && i > 0; ++pass) {
+      for (int pass = 0; pass < orth_passes && i > 0; ++pass) {
         blas::dots(ctx, i, n, nrhs, Q, tot, Qi, 0, beta);
         blas::multi_axpy(ctx, i, n, nrhs, beta, act, Q, tot, Qi, P, Pi);
       }
@@ -314,7 +314,7 @@ void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int ns
   const blas::Sweep sw = blas::sweep(n, nrhs);
   for (int k = 0; k < nsteps; ++k) {
     A.apply(ctx, res, q, nrhs);
-    blas::dots2(ctx, n, nrhs, q, q, q, res, s2);
+    blas::dots_qq_qr(ctx, n, nrhs, q, res, s2);
     ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 8.0 * n * nrhs,
                  (double)sizeof(C) * 5.0 * n * nrhs);
     k_mr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, nullptr, q, x, res, nullptr);

@@ -81,8 +81,19 @@ static void solve_mixed(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, do
     if (hc == 0 || step >= p.max_refine) break;
     k_scale_to_f32<<<blas::grid_1d(tot), 256, 0, ctx.stream>>>(n, s, r, sin_, rf);
     QD_LAUNCH_CHECK();
+    // inner tolerance: inner_tol, relaxed once the residual is close to the
+    // target (the FP32 solve need only reach tol ||b|| / ||r||, halved)
+    std::vector<cplx> hr(s), hb(s);
+    QD_CUDA(cudaMemcpyAsync(hr.data(), rn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaMemcpyAsync(hb.data(), bn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaStreamSynchronize(ctx.stream));
+    double need = 1.0;
+    for (int c = 0; c < s; ++c)
+      if (hr[c].x > tol2 * hb[c].x) need = std::min(need, 0.5 * p.tol * std::sqrt(hb[c].x / hr[c].x));
+    const double itol = std::min(0.5, std::max(p.inner_tol, need));
     SolveInfo in;
-    sc.gcr32.solve(ctx, A32, mg ? mg->pre32.get() : nullptr, rf, ef, s, p.inner_tol, p.maxit, p.restart, &in);
+    sc.gcr32.orth_passes = 1;
+    sc.gcr32.solve(ctx, A32, mg ? mg->pre32.get() : nullptr, rf, ef, s, itol, p.maxit, p.restart, &in);
     inner_total += in.iterations;
     for (int c = 0; c < s; ++c) iters[c] += in.iters[c];
     k_axpy_from_f32<<<blas::grid_1d(tot), 256, 0, ctx.stream>>>(n, s, ef, sout, x);

@@ -101,6 +101,49 @@ __global__ void k_restrict(int64_t ncoarse, int bsites, int Df, int nv, int nrhs
   }
 }
 
+// Restriction with the aggregate staged in shared memory: one CTA per
+// (aggregate, tile of RT right-hand sides).  The block's fine values
+// F[m][a][rr] and its W[m][a][j] are read from global memory once; every
+// output coarse[x][c nv + j][r] = sum_{m, a in c} conj(W[m][a][j]) F[m][a][rr]
+// is then formed from shared memory.
+template <class C>
+__global__ void k_restrict_smem(int bsites, int Df, int nv, int nrhs, int RT, const int* __restrict__ members,
+                                const C* __restrict__ W, const C* __restrict__ fine, C* __restrict__ coarse) {
+  typedef typename CTraits<C>::R R;
+  extern __shared__ unsigned char smr[];
+  C* F = reinterpret_cast<C*>(smr);       // [rows][RT]
+  const int rows = bsites * Df;
+  C* Ws = F + (size_t)rows * RT;          // [rows][nv]
+  const int x = blockIdx.x;
+  const int r0 = blockIdx.y * RT;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int e = tid; e < rows * RT; e += nth) {
+    const int row = e / RT, rr = e - row * RT;
+    const int m = row / Df, a = row - m * Df;
+    const int64_t s = members[(int64_t)x * bsites + m];
+    F[e] = (r0 + rr < nrhs) ? fine[(s * Df + a) * nrhs + r0 + rr] : mk<C>((R)0, (R)0);
+  }
+  for (int e = tid; e < rows * nv; e += nth) {
+    const int row = e / nv, j = e - row * nv;
+    const int m = row / Df, a = row - m * Df;
+    const int64_t s = members[(int64_t)x * bsites + m];
+    Ws[e] = W[(s * Df + a) * nv + j];
+  }
+  __syncthreads();
+  const int Dc = 2 * nv, half = Df / 2;
+  for (int o = tid; o < Dc * RT; o += nth) {
+    const int d = o / RT, rr = o - d * RT;
+    if (r0 + rr >= nrhs) continue;
+    const int chir = d / nv, j = d - chir * nv;
+    C acc = mk<C>((R)0, (R)0);
+    for (int m = 0; m < bsites; ++m) {
+      const int rbase = m * Df + chir * half;
+      for (int a = 0; a < half; ++a) cfmac(acc, Ws[(rbase + a) * nv + j], F[(rbase + a) * RT + rr]);
+    }
+    coarse[((int64_t)x * Dc + d) * nrhs + r0 + rr] = acc;
+  }
+}
+
 template <class C>
 void prolongate(qd_ctx& ctx, const Transfer& T, const C* W, const C* coarse, C* fine, int nrhs) {
   const int64_t tot = T.nfine * T.Df * nrhs;
@@ -119,8 +162,21 @@ void restrict_(qd_ctx& ctx, const Transfer& T, const C* W, const C* fine, C* coa
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_RESTRICT_F64 : QD_PROF_RESTRICT_F32,
                8.0 * T.nv * (double)T.nfine * T.Df * nrhs,
                cb * ((double)T.nfine * T.Df * T.nv + (double)T.nfine * T.Df * nrhs + (double)tot));
-  k_restrict<C><<<div_up(tot, 128) < 32 * kNumSMs ? div_up(tot, 128) : 32 * kNumSMs, 128, 0, ctx.stream>>>(
-      T.ncoarse, T.bsites, T.Df, T.nv, nrhs, T.members.as<int>(), W, fine, coarse);
+  // staged kernel when the aggregate tile fits in 96 KB of shared memory
+  const int rows = T.bsites * T.Df;
+  int RT = 1;
+  while (RT < nrhs && RT < 32) RT <<= 1;
+  const size_t cap = 96 * 1024;
+  while (RT > 1 && (size_t)rows * (RT + T.nv) * sizeof(C) > cap) RT >>= 1;
+  const size_t smem = (size_t)rows * (RT + T.nv) * sizeof(C);
+  if (smem <= cap && (RT >= 8 || RT >= nrhs)) {
+    QD_CUDA(cudaFuncSetAttribute(k_restrict_smem<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_restrict_smem<C><<<dim3((unsigned)T.ncoarse, div_up(nrhs, RT)), 256, smem, ctx.stream>>>(
+        T.bsites, T.Df, T.nv, nrhs, RT, T.members.as<int>(), W, fine, coarse);
+  } else {
+    k_restrict<C><<<div_up(tot, 128) < 32 * kNumSMs ? div_up(tot, 128) : 32 * kNumSMs, 128, 0, ctx.stream>>>(
+        T.ncoarse, T.bsites, T.Df, T.nv, nrhs, T.members.as<int>(), W, fine, coarse);
+  }
   QD_LAUNCH_CHECK();
 }
 

@@ -136,8 +136,10 @@ __device__ __forceinline__ void hop_dir(const C* __restrict__ U, const int* __re
 }
 
 // RESID: out = b - A in (the residual of A x = b) instead of out = A in.
+// FP32: at most 64 registers so 8 blocks (32 warps) fit on an SM; FP64 is
+// ALU-bound and keeps its registers.
 template <class C, bool DAG, bool RESID>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(C) == 8 ? 8 : 1)
 k_wilson(const C* __restrict__ U, const int* __restrict__ nbr, int64_t V, int nrhs, double mass,
          double tau, const C* __restrict__ in, C* __restrict__ out, const C* __restrict__ b) {
   typedef typename CTraits<C>::R R;

@@ -95,7 +95,9 @@ def test_zero_rhs_column(qd, ctx):
 
 
 @pytest.mark.parametrize("dims,m0,seed,blocks,nvs", [((4, 4, 4, 4), -0.4, 1, [(2, 2, 2, 2)], [6]),
-                                                     ((8, 8, 8, 8), -0.8, 2, [(2, 2, 2, 2)], [12])])
+                                                     ((8, 8, 8, 8), -0.8, 2, [(2, 2, 2, 2)], [12]),
+                                                     ((8, 8, 8, 8), -0.8, 2, [(2, 2, 2, 2), (2, 2, 2, 2)],
+                                                      [12, 16])])
 def test_mixed_precision_refinement(qd, ctx, dims, m0, seed, blocks, nvs):
     # FP32 V-cycle + FP32 GCR inside FP64 refinement: the FP64 true residual
     # (checked here with the oracle's operator) meets 1e-8 and 1e-10

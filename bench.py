@@ -204,8 +204,10 @@ def run_ours(args):
     setup_s = time.perf_counter() - t
     s = WL["s"]
 
+    from paper_1909_12234_gb300 import parallel
+
     def offset(i):
-        return (i * world + rank) * s
+        return parallel.sample_offset(rank, world, s, i)
 
     prec = qd.QD_PREC_MIXED if args.precision == "mixed" else qd.QD_PREC_F64
     for i in range(args.warmup):

@@ -421,6 +421,14 @@ int qd_prof_enable(qd_ctx* ctx, int enable);
 int qd_prof_read(qd_ctx* ctx, int kind, int64_t* launches, double* ms,
                  double* flops, double* bytes, int reset);
 
+/* Statistics of per-sample values t_j (device array of s complex numbers),
+ * as qd_hutchinson_trace computes them (Eq. 1; Sec. 4.1 jackknife): fills
+ * t0, mean, estimate = t0 + mean, var, var_re, stderr_mean,
+ * var_jackknife_err and nsamples of `result` (other fields untouched).
+ * Used to merge the samples of several ranks or batches.  Synchronous. */
+int qd_trace_stats(qd_ctx* ctx, int s, const double* t, const double t0[2],
+                   qd_trace_result* result);
+
 #ifdef __cplusplus
 }
 #endif

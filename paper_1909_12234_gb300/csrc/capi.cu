@@ -532,6 +532,33 @@ int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, qd_defl* 
   return rc;
 }
 
+int qd_trace_stats(qd_ctx* ctx, int s, const double* t, const double t0[2], qd_trace_result* result) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(t);
+    NONNULL(t0);
+    NONNULL(result);
+    QD_REQUIRE(s >= 1, "s must be >= 1");
+    set_device(ctx);
+    qd::DevBuf st(8 * sizeof(double)), loo((size_t)s * sizeof(double));
+    qd::trace_stats(*ctx, s, reinterpret_cast<const qd::cplx*>(t), st.as<double>(), loo.as<double>());
+    double h[6];
+    QD_CUDA(cudaMemcpyAsync(h, st.as<double>(), 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    QD_CUDA(cudaStreamSynchronize(ctx->stream));
+    result->t0[0] = t0[0];
+    result->t0[1] = t0[1];
+    result->mean[0] = h[0];
+    result->mean[1] = h[1];
+    result->estimate[0] = t0[0] + h[0];
+    result->estimate[1] = t0[1] + h[1];
+    result->var = h[2];
+    result->var_re = h[3];
+    result->stderr_mean = h[4];
+    result->var_jackknife_err = h[5];
+    result->nsamples = s;
+  });
+}
+
 long long qd_launch_count(void) { return qd::launch_counter().load(); }
 
 int qd_prof_enable(qd_ctx* ctx, int enable) {

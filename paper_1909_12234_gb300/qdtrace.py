@@ -150,6 +150,7 @@ SIGNATURES = {
     "qd_deflate_coeffs": (_I, [_P, _I, _P, _DPTR, _DPTR]),
     "qd_hutchinson_trace": (_I, [_P, _P, _P, _P, _D, _D, ctypes.POINTER(TraceParams),
                                  ctypes.POINTER(TraceResult)]),
+    "qd_trace_stats": (_I, [_P, _I, _P, _DPTR, ctypes.POINTER(TraceResult)]),
     "qd_launch_count": (ctypes.c_longlong, []),
     "qd_prof_enable": (_I, [_P, _I]),
     "qd_prof_read": (_I, [_P, _I, _I64PTR, _DPTR, _DPTR, _DPTR, _I]),
@@ -465,6 +466,19 @@ class Deflation:
             self.close()
         except Exception:
             pass
+
+
+def trace_stats(ctx, t, t0=0j):
+    """Device statistics of per-sample values t (1-D complex array, any host
+    or device origin) with deterministic compensated sums; returns a dict."""
+    import torch
+    tt = torch.as_tensor(np.asarray(t, dtype=np.complex128)).to(f"cuda:{ctx.device}")
+    r = TraceResult()
+    t0a = (ctypes.c_double * 2)(complex(t0).real, complex(t0).imag)
+    _check(load().qd_trace_stats(ctx.h, int(tt.numel()), _ptr(tt), t0a, ctypes.byref(r)))
+    return {"t0": complex(r.t0[0], r.t0[1]), "mean": complex(r.mean[0], r.mean[1]),
+            "estimate": complex(r.estimate[0], r.estimate[1]), "var": r.var, "var_re": r.var_re,
+            "stderr": r.stderr_mean, "var_jackknife_err": r.var_jackknife_err, "s": r.nsamples}
 
 
 def launch_count():

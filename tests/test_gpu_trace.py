@@ -150,3 +150,14 @@ def test_estimator_workload_8x4_properties(qd, ctx):
     res0 = qd.hutchinson_trace(ctx, g, mg, None, m0, 0.0, seed=102, sample_offset=0, nsamples=s, tol=xi,
                                maxit=500, restart=16)
     assert res["var"] < res0["var"]
+
+
+def test_trace_stats_entry_point_matches_oracle(qd, ctx):
+    rng = np.random.default_rng(9)
+    for s in (1, 2, 3, 17, 256):
+        t = rng.standard_normal(s) * 3 + 1j * rng.standard_normal(s)
+        got = qd.trace_stats(ctx, t, 2.5 - 0.5j)
+        ref = estimator.statistics(t, 2.5 - 0.5j)
+        assert abs(got["estimate"] - ref["estimate"]) <= 1e-13 * abs(ref["estimate"])
+        for key in ("var", "var_re", "stderr", "var_jackknife_err"):
+            assert math.isclose(got[key], ref[key], rel_tol=1e-11, abs_tol=1e-300), (s, key)

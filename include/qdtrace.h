@@ -405,9 +405,11 @@ enum {
   QD_PROF_DIRECT_F64 = 8,   /* coarsest dense solve C^{-1} R, FP64 */
   QD_PROF_DIRECT_F32 = 9,
   QD_PROF_DIRECT_BF16 = 10, /* coarsest dense solve on tcgen05 tensor cores */
-  QD_PROF_BLAS_F64 = 11,    /* reductions and vector updates of the solvers */
-  QD_PROF_BLAS_F32 = 12,
-  QD_PROF_NKINDS = 13
+  QD_PROF_BLAS_F64 = 11,    /* FP64 reductions and vector updates */
+  QD_PROF_DOTS_F32 = 12,    /* FP32 per-column reductions (Gram-Schmidt, smoother) */
+  QD_PROF_AXPY_F32 = 13,    /* FP32 multi-vector updates (Gram-Schmidt) */
+  QD_PROF_UPDATE_F32 = 14,  /* FP32 fused GCR / minimal-residual updates */
+  QD_PROF_NKINDS = 15
 };
 
 /* enable != 0: record a CUDA event pair on the context stream around every

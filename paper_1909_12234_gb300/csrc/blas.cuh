@@ -102,7 +102,7 @@ void dots_launch(qd_ctx& ctx, int K, int64_t n, int nrhs, const DotPairs<C>& pr,
   Sweep s = sweep(n, nrhs);
   ctx.red_partials.resize((size_t)s.grid.x * K * nrhs * sizeof(cplx));
   {
-    ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 8.0 * K * n * nrhs,
+    ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_DOTS_F32, 8.0 * K * n * nrhs,
                  (double)sizeof(C) * 2.0 * K * n * nrhs);
     k_dots<C><<<s.grid, s.block, 0, ctx.stream>>>(K, n, nrhs, pr, ctx.red_partials.as<cplx>());
     QD_LAUNCH_CHECK();
@@ -180,7 +180,7 @@ template <class C> void dots_qq_qr(qd_ctx& ctx, int64_t n, int nrhs, const C* q,
   Sweep s = sweep(n, nrhs);
   ctx.red_partials.resize((size_t)s.grid.x * 2 * nrhs * sizeof(cplx));
   {
-    ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 12.0 * n * nrhs,
+    ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_DOTS_F32, 12.0 * n * nrhs,
                  (double)sizeof(C) * 2.0 * n * nrhs);
     k_dots_qq_qr<C><<<s.grid, s.block, 0, ctx.stream>>>(n, nrhs, q, r, ctx.red_partials.as<cplx>());
     QD_LAUNCH_CHECK();
@@ -224,7 +224,7 @@ template <class C>
 void multi_axpy(qd_ctx& ctx, int K, int64_t n, int nrhs, const cplx* coef, const int* active,
                 const C* X, int64_t xs, C* Y, const C* X2 = nullptr, C* Y2 = nullptr) {
   if (K <= 0) return;
-  ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 8.0 * K * n * nrhs * (Y2 ? 2 : 1),
+  ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_AXPY_F32, 8.0 * K * n * nrhs * (Y2 ? 2 : 1),
                (double)sizeof(C) * (K + 2.0) * n * nrhs * (Y2 ? 2 : 1));
   k_multi_axpy<C><<<grid_1d(n * nrhs), kThreads, 0, ctx.stream>>>(K, n, nrhs, coef, active, X, xs, Y,
                                                                  X2, Y2);

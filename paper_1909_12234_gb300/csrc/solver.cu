@@ -215,7 +215,7 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
       blas::dots2(ctx, n, nrhs, Qi, Qi, Qi, r, s2);
       ctx.red_partials.resize((size_t)sw.grid.x * nrhs * sizeof(cplx));
       {
-        ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 16.0 * n * nrhs,
+        ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_UPDATE_F32, 16.0 * n * nrhs,
                      (double)sizeof(C) * 8.0 * n * nrhs);
         k_gcr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, act, Qi, Pi, x, r,
                                                               ctx.red_partials.as<cplx>());
@@ -315,7 +315,7 @@ void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int ns
   for (int k = 0; k < nsteps; ++k) {
     A.apply(ctx, res, q, nrhs);
     blas::dots_qq_qr(ctx, n, nrhs, q, res, s2);
-    ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_BLAS_F32, 8.0 * n * nrhs,
+    ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_UPDATE_F32, 8.0 * n * nrhs,
                  (double)sizeof(C) * 5.0 * n * nrhs);
     k_mr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, nullptr, q, x, res, nullptr);
     QD_LAUNCH_CHECK();

@@ -158,7 +158,7 @@ SIGNATURES = {
 
 PROF_KINDS = {"wilson_f64": 0, "wilson_f32": 1, "coarse_f64": 2, "coarse_f32": 3, "prolong_f64": 4,
               "prolong_f32": 5, "restrict_f64": 6, "restrict_f32": 7, "direct_f64": 8, "direct_f32": 9, "direct_bf16": 10,
-              "blas_f64": 11, "blas_f32": 12}
+              "blas_f64": 11, "dots_f32": 12, "axpy_f32": 13, "update_f32": 14}
 
 _lib = None
 

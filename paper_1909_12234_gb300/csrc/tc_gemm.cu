@@ -10,7 +10,7 @@
 // estimator workload (its preconditioner tolerates ~1e-3 relative error).
 //
 // Kernel: one CTA per (128-row tile, K split); TMA loads of 128B-swizzled
-// K-major tiles (A 128 x 64, B N x 64) into a 4-stage shared-memory ring
+// K-major tiles (A 128 x 64, B N x 64) into a shared-memory ring of up to 6 stages
 // guarded by mbarriers; one thread issues tcgen05.mma (M = 128, K = 16 per
 // instruction) into a TMEM accumulator of N FP32 columns; tcgen05.commit
 // frees ring stages and signals the epilogue; four warps read TMEM
@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kBM = 128;     // rows per CTA (UMMA M)
 constexpr int kBK = 64;      // K per stage: 64 BF16 = 128 B = one swizzle row
-constexpr int kStages = 4;
+constexpr int kMaxStages = 6;  // ring depth: as many as fit in 227 KB, at most 6
 constexpr int kThreads = 128;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
@@ -91,9 +91,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int N,
-              int ktiles_per_split, int ktiles_total, int Mp, float* __restrict__ part, int* __restrict__ err) {
+              int ktiles_per_split, int ktiles_total, int Mp, int kStages, float* __restrict__ part,
+              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -343,11 +344,15 @@ void tc_dense_apply(qd_ctx& ctx, CoarseLevel& lv, const cplxf* X, cplxf* Y, int 
     QD_LAUNCH_CHECK();
     {
       ProfScope ps(ctx, QD_PROF_DIRECT_BF16, flops, bytes);
-      const size_t smem = 1024 + (size_t)kStages * ((size_t)kBM * kBK * 2 + (size_t)N * kBK * 2);
+      const size_t stage = (size_t)kBM * kBK * 2 + (size_t)N * kBK * 2;
+      int stages = (int)((220u * 1024u - 1024u) / stage);
+      if (stages > kMaxStages) stages = kMaxStages;
+      QD_REQUIRE(stages >= 2, "tensor-core tile does not fit in shared memory");
+      const size_t smem = 1024 + (size_t)stages * stage;
       QD_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_tc_gemm<<<dim3(mtiles, nsplit), kThreads, smem, ctx.stream>>>(
           *reinterpret_cast<const CUtensorMap*>(lv.tc_mapA), *reinterpret_cast<const CUtensorMap*>(lv.tc_mapB), N,
-          kps, ktiles, Mp, lv.tc_part.as<float>(), lv.tc_err.as<int>());
+          kps, ktiles, Mp, stages, lv.tc_part.as<float>(), lv.tc_err.as<int>());
       QD_LAUNCH_CHECK();
     }
     k_reduce_splits<<<blas_grid((int64_t)n * sc), 256, 0, ctx.stream>>>(n, sc, N, Mp, nsplit,

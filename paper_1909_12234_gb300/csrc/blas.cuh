@@ -20,7 +20,7 @@ struct Sweep {
   dim3 block, grid;
 };
 
-inline Sweep sweep(int64_t n, int nrhs, int max_row_blocks = 8 * kNumSMs) {
+inline Sweep sweep(int64_t n, int nrhs, int max_row_blocks = 4 * kNumSMs) {
   Sweep s;
   int rt = 1;
   while (rt < nrhs && rt < 32) rt <<= 1;
@@ -54,19 +54,7 @@ __global__ void k_dots(int K, int64_t n, int nrhs, DotPairs<C> pr, cplx* __restr
 #pragma unroll
   for (int k = 0; k < kDotK; ++k) acc[k] = mk<C>((R)0, (R)0);
   if (r < nrhs) {
-    const int64_t step = (int64_t)gridDim.x * blockDim.y;
-    int64_t i = (int64_t)blockIdx.x * blockDim.y + ty;
-    for (; i + step < n; i += 2 * step) {  // two independent rows in flight
-      const int64_t e0 = i * nrhs + r, e1 = (i + step) * nrhs + r;
-#pragma unroll
-      for (int k = 0; k < kDotK; ++k)
-        if (k < K) {
-          const C x0 = pr.x[k][e0], y0 = pr.y[k][e0], x1 = pr.x[k][e1], y1 = pr.y[k][e1];
-          cfmac(acc[k], x0, y0);
-          cfmac(acc[k], x1, y1);
-        }
-    }
-    if (i < n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.y + ty; i < n; i += (int64_t)gridDim.x * blockDim.y) {
       const int64_t e = i * nrhs + r;
 #pragma unroll
       for (int k = 0; k < kDotK; ++k)
@@ -203,32 +191,24 @@ template <class C> void dots_qq_qr(qd_ctx& ctx, int64_t n, int nrhs, const C* q,
 
 // Y_j[i,r] -= sum_k coef[k][r] X_k[i,r] for (Y, X) and, when Y2 != null,
 // (Y2, X2) with the same coefficients; columns with active[r] == 0 untouched.
-// 2-D layout: lane -> column (coefficients held in registers), rows strided.
 template <class C>
 __global__ void k_multi_axpy(int K, int64_t n, int nrhs, const cplx* __restrict__ coef,
                              const int* __restrict__ active, const C* __restrict__ X, int64_t xs,
                              C* __restrict__ Y, const C* __restrict__ X2, C* __restrict__ Y2) {
   typedef typename CTraits<C>::R R;
-  const int r = blockIdx.y * blockDim.x + threadIdx.x;
-  if (r >= nrhs || (active && !active[r])) return;
-  C c[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k)
-    if (k < K) {
-      const cplx cd = coef[(int64_t)k * nrhs + r];
-      c[k] = mk<C>((R)(-cd.x), (R)(-cd.y));
-    }
-  const int64_t step = (int64_t)gridDim.x * blockDim.y;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < n; i += step) {
-    const int64_t e = i * nrhs + r;
+  const int64_t tot = n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % nrhs);
+    if (active && !active[r]) continue;
     C y = Y[e];
     C y2 = Y2 ? Y2[e] : mk<C>((R)0, (R)0);
-#pragma unroll
-    for (int k = 0; k < 32; ++k)
-      if (k < K) {
-        cfma(y, c[k], X[k * xs + e]);
-        if (Y2) cfma(y2, c[k], X2[k * xs + e]);
-      }
+    for (int k = 0; k < K; ++k) {
+      const cplx cd = coef[(int64_t)k * nrhs + r];
+      const C c = mk<C>((R)(-cd.x), (R)(-cd.y));
+      cfma(y, c, X[k * xs + e]);
+      if (Y2) cfma(y2, c, X2[k * xs + e]);
+    }
     Y[e] = y;
     if (Y2) Y2[e] = y2;
   }
@@ -246,13 +226,9 @@ void multi_axpy(qd_ctx& ctx, int K, int64_t n, int nrhs, const cplx* coef, const
   if (K <= 0) return;
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_AXPY_F32, 8.0 * K * n * nrhs * (Y2 ? 2 : 1),
                (double)sizeof(C) * (K + 2.0) * n * nrhs * (Y2 ? 2 : 1));
-  const Sweep sw = sweep(n, nrhs);
-  for (int k0 = 0; k0 < K; k0 += 32) {  // 32 coefficients per launch (registers)
-    const int kk = (K - k0) < 32 ? (K - k0) : 32;
-    k_multi_axpy<C><<<sw.grid, sw.block, 0, ctx.stream>>>(kk, n, nrhs, coef + (int64_t)k0 * nrhs, active,
-                                                          X + k0 * xs, xs, Y, X2 ? X2 + k0 * xs : nullptr, Y2);
-    QD_LAUNCH_CHECK();
-  }
+  k_multi_axpy<C><<<grid_1d(n * nrhs), kThreads, 0, ctx.stream>>>(K, n, nrhs, coef, active, X, xs, Y,
+                                                                 X2, Y2);
+  QD_LAUNCH_CHECK();
 }
 
 // y = a x + b y with per-column complex a, b (device arrays; nullptr a -> 1,

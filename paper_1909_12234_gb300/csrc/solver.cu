@@ -50,7 +50,6 @@ __global__ void k_gcr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
     const double ar = qq > 0.0 ? qr.x / qq : 0.0, ai = qq > 0.0 ? qr.y / qq : 0.0;
     const C a = mk<C>((R)ar, (R)ai), na = mk<C>((R)(-ar), (R)(-ai));
     const R ri = (R)inv;
-#pragma unroll 2
     for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < n;
          i += (int64_t)gridDim.x * blockDim.y) {
       const int64_t e = i * nrhs + col;
@@ -81,7 +80,6 @@ __global__ void k_mr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
     const cplx qr = s2[nrhs + col];
     const double ar = qq > 0.0 ? qr.x / qq : 0.0, ai = qq > 0.0 ? qr.y / qq : 0.0;
     const C a = mk<C>((R)ar, (R)ai), na = mk<C>((R)(-ar), (R)(-ai));
-#pragma unroll 4
     for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < n;
          i += (int64_t)gridDim.x * blockDim.y) {
       const int64_t e = i * nrhs + col;

@@ -42,6 +42,17 @@ WL = dict(
     dims=(8, 8, 8, 8), eps=0.3, link_seed=2, m0=-0.8, blocks=[(2, 2, 2, 2)], nvs=[12], k=24, guard=16,
     s=64, tol=1e-8, noise_seed=102, restart=16, maxit=500, inner_tol=1e-5,
 )
+# Larger configurations (parity-test cases, not the bench line); chosen with
+# --workload.  Config 3: 16^3 x 32, eps 0.2 (seed 3), m0 -0.8, three-level MG
+# (2^4 then 2^4, nv 12 then 16), Algorithm 2, 128 samples, mixed precision.
+WORKLOADS = {
+    "config2": dict(WL),
+    "config3": dict(
+        workload="wilson-dirac 16^3x32 eps0.2 seed3 m0=-0.8, 3-level MG (2^4, 2^4; nv 12, 16), Algorithm 2 "
+                 "k=24, 128 Rademacher samples/step, true FP64 rel. residual 1e-8",
+        dims=(16, 16, 16, 32), eps=0.2, link_seed=3, m0=-0.8, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16],
+        k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=16, maxit=500, inner_tol=1e-5),
+}
 METRIC = "deflated Hutchinson samples/s @res 1e-8"
 UNIT = "samples/s"
 # Recipe peaks (MEASURED_PEAKS.json holds HBM and bf16; FP64 is the recipe's
@@ -108,7 +119,7 @@ class ClockSampler:
 
 def _setup(qd, ctx, U):
     g = qd.Gauge(ctx, WL["dims"], U)
-    mg = qd.Multigrid(ctx, g, WL["m0"], 0.0, qd.mg_params(1, WL["blocks"], WL["nvs"]))
+    mg = qd.Multigrid(ctx, g, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"]))
     d = qd.Deflation(ctx, g, mg, WL["m0"], 0.0,
                      qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
                                     solve_tol=1e-10, maxit=60))
@@ -129,7 +140,7 @@ def cpu_baseline(samples=2):
     from paper_1909_12234_gb300 import synth
     U = synth.random_su3_links(WL["dims"], WL["eps"], WL["link_seed"])
     H = omg.setup(U, WL["m0"], WL["dims"], WL["blocks"], WL["nvs"], seed=7)
-    alg = odefl.Alg2(H.transfers[0], H.matrices[0], WL["k"])
+    alg = odefl.Alg2(odefl.Composite(H.transfers), H.matrices[-1], WL["k"])
     lev = H.levels[0]
     t = time.perf_counter()
     estimator.hutchinson(lev.matvec, lev.n, WL["noise_seed"], range(samples), WL["tol"],
@@ -151,7 +162,7 @@ def run_reference(args):
     from paper_1909_12234_gb300 import synth
     U = synth.random_su3_links(WL["dims"], WL["eps"], WL["link_seed"])
     H = omg.setup(U, WL["m0"], WL["dims"], WL["blocks"], WL["nvs"], seed=7)
-    alg = odefl.Alg2(H.transfers[0], H.matrices[0], WL["k"])
+    alg = odefl.Alg2(odefl.Composite(H.transfers), H.matrices[-1], WL["k"])
     lev = H.levels[0]
     per_step = 1
 
@@ -282,7 +293,7 @@ def run_ours(args):
     t = time.perf_counter()
     for i in range(e2e_steps):
         g2 = qd.Gauge.from_host_buffer(ctx, WL["dims"], pinned)
-        mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, qd.mg_params(1, WL["blocks"], WL["nvs"]))
+        mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"]))
         d2 = qd.Deflation(ctx, g2, mg2, WL["m0"], 0.0,
                           qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
                                          solve_tol=1e-10, maxit=60))
@@ -363,7 +374,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    WL.clear()
+    WL.update(WORKLOADS[args.workload] if args.workload != "config2" else dict(WORKLOADS["config2"]))
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -27,8 +27,17 @@ U_bar^H gamma5^W W^H Z: the rank-r correction to z^H A^{-1} z is
 (z^H W U_bar_r) G_r^{-1} (U_bar_r^H gamma5^W W^H z), G_r the leading r x r
 block of U_bar^H gamma5^W C U_bar.
 
+Hierarchies with more than one coarse level: Table 2 sizes the eigenproblem
+of Algorithm 2 by the coarsest level ("dimension of coarsest"), so W is the
+composite prolongator W_0 W_1 ... W_{L-1} from the coarsest level to the fine
+one and C = W^H A W is the coarsest Galerkin operator (each level's operator
+is the Galerkin product of the one above it).  Every W_l maps chirality to
+chirality, so gamma5 W = W gamma5^W holds for the composite as well.
+
 Pins: projector identities P^2 = P, gamma5-Hermiticity of A^{-1}(I - P),
-t0 + tr(A^{-1}(I - P)) = tr A^{-1} (dense, tests/test_oracle_deflation.py).
+t0 + tr(A^{-1}(I - P)) = tr A^{-1}; for three levels also C_2 = W^H A W and
+gamma5 W = W gamma5^W with the composite W (dense,
+tests/test_oracle_deflation.py).
 The eigensolver (scipy ARPACK shift-invert, or dense eigh for small sizes)
 is a library routine; which eigenvectors it returns inside a degenerate
 cluster is not unique, so only projector-invariant results are compared.
@@ -53,8 +62,33 @@ def smallest_abs_eigh(H, k, dense_limit=4096):
     return mu[order], X[:, order]
 
 
+class Composite:
+    """W = W_0 W_1 ... W_{L-1} for transfers listed fine to coarse."""
+
+    def __init__(self, transfers):
+        self.transfers = list(transfers)
+        self.nv = self.transfers[-1].nv
+
+    def restrict(self, f):
+        for T in self.transfers:
+            f = T.restrict(f)
+        return f
+
+    def prolong(self, c):
+        for T in reversed(self.transfers):
+            c = T.prolong(c)
+        return c
+
+    def matrix(self):
+        W = self.transfers[0].matrix()
+        for T in self.transfers[1:]:
+            W = W @ T.matrix()
+        return W
+
+
 class Alg2:
-    """Algorithm 2 deflation built from a transfer T (level 0 -> 1) and C."""
+    """Algorithm 2 deflation built from a transfer T (fine level -> the level
+    of C; a ``Composite`` for more than one coarse level) and C = W^H A W."""
 
     def __init__(self, T, C, k, Ubar=None):
         self.T = T

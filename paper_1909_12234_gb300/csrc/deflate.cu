@@ -131,19 +131,21 @@ void defl_build(qd_defl& d, const double* injected) {
   QD_REQUIRE(k >= 1, "deflation rank k must be >= 1");
   if (d.kind == QD_DEFL_MG_OBLIQUE) {
     QD_REQUIRE(d.mg != nullptr, "Algorithm 2 deflation needs a multigrid hierarchy");
-    d.level = 1;
+    // the coarsest level: W is the composite prolongator W_0 ... W_{L-1}
+    // (Table 2 sizes the Algorithm 2 eigenproblem by the coarsest level)
+    d.level = d.mg->nlevels;
   } else {
     QD_REQUIRE(d.kind == QD_DEFL_EIG_ORTHO, "unknown deflation kind");
     d.level = 0;
   }
-  const LevelGeom& geo = d.level == 0 ? d.gauge->geo : d.mg->geom(1);
-  const int dof = d.level == 0 ? 12 : d.mg->dof(1);
+  const LevelGeom& geo = d.level == 0 ? d.gauge->geo : d.mg->geom(d.level);
+  const int dof = d.level == 0 ? 12 : d.mg->dof(d.level);
   d.nb = geo.nsites * (int64_t)dof;
   QD_REQUIRE(k <= d.nb, "deflation rank exceeds the dimension");
   d.Ubar.resize((size_t)d.nb * k * sizeof(cplx));
   std::unique_ptr<Op<cplx>> op;
-  if (d.level == 1)
-    op = d.mg->op<cplx>(1);
+  if (d.level >= 1)
+    op = d.mg->op<cplx>(d.level);
   else
     op.reset(new WilsonOp<cplx>(d.gauge, d.gauge->links.as<cplx>(), d.m0, d.tau, false));
   d.mu.assign(k, 0.0);
@@ -157,13 +159,8 @@ void defl_build(qd_defl& d, const double* injected) {
     DevBuf X((size_t)d.nb * m * sizeof(cplx));
     Precond<cplx>* M = nullptr;
     std::unique_ptr<MGPrecond<cplx>> pre;
-    if (d.level == 1 && d.mg->nlevels >= 2) {
-      pre.reset(new MGPrecond<cplx>(d.mg, 1));
-      M = pre.get();
-    } else if (d.level == 0 && d.mg) {
-      M = d.mg->pre64.get();
-    }
-    const cplx* inv = d.level == 1 ? d.mg->Cinv<cplx>(1) : nullptr;
+    if (d.level == 0 && d.mg) M = d.mg->pre64.get();  // the coarsest level has no coarser one
+    const cplx* inv = d.level >= 1 ? d.mg->Cinv<cplx>(d.level) : nullptr;
     GCR<cplx> solver;
     const Op<cplx>& A = *op;
     const double stol = d.p.solve_tol;
@@ -205,8 +202,8 @@ void defl_set_rank(qd_defl& d, int r) {
   QD_REQUIRE(r >= 1 && r <= d.p.k, "rank must be in [1, k]");
   const int k = d.p.k;
   d.rank = r;
-  const LevelGeom& geo = d.level == 0 ? d.gauge->geo : d.mg->geom(1);
-  const int dof = d.level == 0 ? 12 : d.mg->dof(1);
+  const LevelGeom& geo = d.level == 0 ? d.gauge->geo : d.mg->geom(d.level);
+  const int dof = d.level == 0 ? 12 : d.mg->dof(d.level);
   DevBuf dv(r * sizeof(cplx));
   if (d.kind == QD_DEFL_MG_OBLIQUE) {
     // step 3 on the leading r columns: G_r = U_hat Lambda U_hat^H
@@ -236,6 +233,40 @@ void defl_set_rank(qd_defl& d, int r) {
   QD_CUDA(cudaStreamSynchronize(ctx.stream));
 }
 
+// c = W^H z with the composite W = W_0 ... W_{L-1} (L = d.level), s columns
+static void restrict_chain(qd_defl& d, int s, const cplx* z, cplx* c) {
+  qd_ctx& ctx = *d.ctx;
+  const cplx* src = z;
+  DevBuf tmp[2];
+  for (int l = 0; l < d.level; ++l) {
+    const Transfer& T = *d.mg->T[l];
+    cplx* dst = c;
+    if (l + 1 < d.level) {
+      tmp[l & 1].resize((size_t)d.mg->geom(l + 1).nsites * T.Dc * s * sizeof(cplx));
+      dst = tmp[l & 1].as<cplx>();
+    }
+    restrict_<cplx>(ctx, T, T.W.as<cplx>(), src, dst, s);
+    src = dst;
+  }
+}
+
+// f = W c with the composite W, s columns
+static void prolong_chain(qd_defl& d, int s, const cplx* c, cplx* f) {
+  qd_ctx& ctx = *d.ctx;
+  const cplx* src = c;
+  DevBuf tmp[2];
+  for (int l = d.level - 1; l >= 0; --l) {
+    const Transfer& T = *d.mg->T[l];
+    cplx* dst = f;
+    if (l > 0) {
+      tmp[l & 1].resize((size_t)d.mg->geom(l).nsites * T.Df * s * sizeof(cplx));
+      dst = tmp[l & 1].as<cplx>();
+    }
+    prolongate<cplx>(ctx, T, T.W.as<cplx>(), src, dst, s);
+    src = dst;
+  }
+}
+
 // out = (I - P) z, s columns
 void defl_project(qd_defl& d, int s, const cplx* z, cplx* out) {
   qd_ctx& ctx = *d.ctx;
@@ -243,15 +274,15 @@ void defl_project(qd_defl& d, int s, const cplx* z, cplx* out) {
   const int64_t nf = d.gauge->geo.nsites * 12;
   DevBuf a((size_t)r * s * sizeof(cplx));
   if (d.kind == QD_DEFL_MG_OBLIQUE) {
-    const Transfer& T = *d.mg->T[0];
-    const LevelGeom& cg = d.mg->geom(1);
+    const LevelGeom& cg = d.mg->geom(d.level);
+    const int dc = d.mg->dof(d.level);
     DevBuf c((size_t)d.nb * s * sizeof(cplx)), gc((size_t)d.nb * s * sizeof(cplx)), f((size_t)nf * s * sizeof(cplx));
-    restrict_<cplx>(ctx, T, T.W.as<cplx>(), z, c.as<cplx>(), s);
-    blas::gamma5(ctx, cg.nsites, T.Dc, s, c.as<cplx>(), gc.as<cplx>());
+    restrict_chain(d, s, z, c.as<cplx>());
+    blas::gamma5(ctx, cg.nsites, dc, s, c.as<cplx>(), gc.as<cplx>());
     blockdot(ctx, d.nb, d.U.as<cplx>(), r, r, gc.as<cplx>(), s, s, a.as<cplx>());  // U^H g5 W^H z
     scale_rows_inv(ctx, r, s, d.lam.as<double>(), a.as<cplx>());                  // Lambda^{-1}
     blockmul(ctx, d.nb, d.U.as<cplx>(), r, r, a.as<cplx>(), s, s, c.as<cplx>(), s, 1.0, 0.0);  // U (.)
-    prolongate<cplx>(ctx, T, T.W.as<cplx>(), c.as<cplx>(), f.as<cplx>(), s);       // W (.)
+    prolong_chain(d, s, c.as<cplx>(), f.as<cplx>());                              // W (.)
     // out = z - A W U Lambda^{-1} U^H g5 W^H z (fused residual kernel)
     wilson_apply<cplx>(ctx, d.gauge->geo, d.gauge->links.as<cplx>(), d.m0, d.tau, false, f.as<cplx>(), out, s, z);
   } else {
@@ -266,11 +297,10 @@ void defl_coeffs(qd_defl& d, int s, const cplx* z, cplx* M1, cplx* M2) {
   qd_ctx& ctx = *d.ctx;
   QD_REQUIRE(d.kind == QD_DEFL_MG_OBLIQUE, "a-posteriori coefficients are defined for Algorithm 2");
   const int k = d.p.k;
-  const Transfer& T = *d.mg->T[0];
-  const LevelGeom& cg = d.mg->geom(1);
+  const LevelGeom& cg = d.mg->geom(d.level);
   DevBuf c((size_t)d.nb * s * sizeof(cplx)), gc((size_t)d.nb * s * sizeof(cplx));
-  restrict_<cplx>(ctx, T, T.W.as<cplx>(), z, c.as<cplx>(), s);
-  blas::gamma5(ctx, cg.nsites, T.Dc, s, c.as<cplx>(), gc.as<cplx>());
+  restrict_chain(d, s, z, c.as<cplx>());
+  blas::gamma5(ctx, cg.nsites, d.mg->dof(d.level), s, c.as<cplx>(), gc.as<cplx>());
   blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, c.as<cplx>(), s, s, M1);
   blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, gc.as<cplx>(), s, s, M2);
 }

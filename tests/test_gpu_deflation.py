@@ -141,3 +141,40 @@ def test_alg1_injected_and_eigensolver(qd, ctx):
                                                              solve_tol=1e-12, maxit=60))
     mu, _, its = d2.info()
     _check_spectrum(mu, mu_ref)
+
+
+def test_alg2_three_level_composite(qd, ctx):
+    # two coarse levels: the deflation space lives on the coarsest level
+    # (4 sites x 8 dofs here) and W is the composite prolongator W_0 W_1
+    dims, m0, k, blocks, nvs = (4, 4, 4, 4), -0.4, 10, [(2, 2, 2, 2), (2, 2, 1, 1)], [6, 4]
+    U = synth.random_su3_links(dims, 0.3, 1)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(2, blocks, nvs, null_maxit=0, seed=3))
+    H = omg.setup(U, m0, dims, blocks, nvs, seed=3, null_maxit=0)
+    alg = odefl.Alg2(odefl.Composite(H.transfers), H.matrices[-1], k)
+    d = qd.Deflation(ctx, g, mg, m0, 0.0, qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, k),
+                     injected_basis=dev(alg.Ubar))
+    t0 = d.set_rank(k)
+    assert abs(t0 - alg.t0) < 1e-10 * abs(alg.t0)
+    _, lam, _ = d.info()
+    assert rel_err(np.sort(lam), np.sort(alg.lam)) < 1e-11
+    s = 3
+    z = synth.random_field(dims, s, 4)
+    zd = qd.to_qd(ctx, g, z)
+    out = torch.empty_like(zd)
+    d.project(s, zd, out)
+    ref = alg.project(H.levels[0].matvec, z.reshape(-1, s))
+    assert rel_err(qd.from_qd(ctx, g, out).reshape(-1, s), ref) < 1e-10
+    ZhV, UhKZ = d.coeffs(s, zd)
+    rZhV, rUhKZ = alg.coeffs(z.reshape(-1, s))
+    assert rel_err(ZhV, rZhV) < 1e-11 and rel_err(UhKZ, rUhKZ) < 1e-11
+    # the GPU eigensolver on the coarsest operator (direct inverse) finds the
+    # oracle's eigenvalues of C gamma5^W, and the estimator's trace split holds
+    d2 = qd.Deflation(ctx, g, mg, m0, 0.0, qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, k, guard=8, eig_tol=1e-10,
+                                                          maxit=60))
+    mu, _, _ = d2.info()
+    _check_spectrum(mu, alg.mu)
+    A = H.levels[0].matrix.toarray()
+    res = qd.hutchinson_trace(ctx, g, mg, d2, m0, 0.0, seed=7, sample_offset=0, nsamples=16, tol=1e-10)
+    Ainv = np.linalg.inv(A)
+    assert abs(res["estimate"].real - np.trace(Ainv).real) < 5.0 * res["stderr"] + 1e-8

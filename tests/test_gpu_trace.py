@@ -161,3 +161,40 @@ def test_trace_stats_entry_point_matches_oracle(qd, ctx):
         assert abs(got["estimate"] - ref["estimate"]) <= 1e-13 * abs(ref["estimate"])
         for key in ("var", "var_re", "stderr", "var_jackknife_err"):
             assert math.isclose(got[key], ref[key], rel_tol=1e-11, abs_tol=1e-300), (s, key)
+
+
+@pytest.mark.slow
+def test_config3_three_level_mixed_precision(qd, ctx):
+    # config 3 at full lattice size: 16^3 x 32, eps 0.2, m0 -0.8, three-level
+    # MG (2^4, 2^4; nv 12, 16), Algorithm 2 (k = 24), mixed precision to a
+    # true FP64 residual 1e-8; 16 samples keep the test short
+    dims, m0, s, xi = (16, 16, 16, 32), -0.8, 16, 1e-8
+    U = synth.random_su3_links(dims, 0.2, 3)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(2, [(2, 2, 2, 2), (2, 2, 2, 2)], [12, 16]))
+    assert mg.level_info(2)[1:3] == (32, 512)  # coarsest: 512 sites x 32 dofs (direct inverse)
+    d = qd.Deflation(ctx, g, mg, m0, 0.0, qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, 24, guard=16, eig_tol=1e-5,
+                                                         solve_tol=1e-9, maxit=40))
+    res = qd.hutchinson_trace(ctx, g, mg, d, m0, 0.0, seed=103, sample_offset=0, nsamples=s, tol=xi,
+                              maxit=400, restart=16, precision=qd.QD_PREC_MIXED, inner_tol=1e-5, max_refine=10)
+    assert res["status"] == qd.QD_OK and res["max_true_rel_residual"] <= xi
+    _check_stats(res)
+    # the FP64 residual of two samples recomputed with the oracle's operator
+    z = torch.empty((g.V, 12, 2), dtype=torch.complex128, device="cuda:0")
+    qd.rademacher(ctx, g, 103, 0, 2, z)
+    b = torch.empty_like(z)
+    d.project(2, z, b)
+    x = torch.empty_like(b)
+    qd.solve(ctx, g, mg, m0, 0.0, 2, b, x, xi, maxit=400, precision=qd.QD_PREC_MIXED, inner_tol=1e-5,
+             max_refine=10)
+    # (the oracle's matrix-free operator: its sparse matrix would be ~4 GB here)
+    from oracle import wilson
+    eo = __import__("oracle.lattice", fromlist=["x"]).eo_index(dims)
+    bl = host(b)[eo].reshape(-1, 4, 3, 2)
+    xl = host(x)[eo].reshape(-1, 4, 3, 2)
+    r = bl - wilson.dirac_apply(U, xl, m0, dims)
+    rel = np.linalg.norm(r.reshape(-1, 2), axis=0) / np.linalg.norm(bl.reshape(-1, 2), axis=0)
+    assert np.all(rel <= xi), rel
+    # t_j = z_j^H x_j for those samples
+    zl = host(z)[eo].reshape(-1, 2)
+    assert np.allclose(np.einsum("ij,ij->j", zl.conj(), xl.reshape(-1, 2)), res["t"][:2], rtol=1e-5)

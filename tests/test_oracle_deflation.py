@@ -86,3 +86,35 @@ def test_alg1_identities(setup):
     v0 = dense.exact_variance_real_rademacher(Ainv)
     v1 = dense.exact_variance_real_rademacher(Ainv @ Pp)
     assert v1 < v0
+
+
+def test_alg2_three_level_composite(setup):
+    # two coarse levels (2^4 then 2^4): the deflation space lives on the
+    # coarsest level and W is the composite prolongator
+    dims = (4, 4, 4, 4)
+    U = synth.random_su3_links(dims, 0.3, 1)
+    H = multigrid.setup(U, -0.4, dims, [(2, 2, 2, 2), (2, 2, 2, 2)], [6, 8], seed=3, null_maxit=30)
+    A = H.levels[0].matrix.toarray()
+    W = deflation.Composite(H.transfers)
+    Wd = W.matrix().toarray()
+    C2 = H.matrices[1].toarray()
+    assert Wd.shape == (3072, 16) and C2.shape == (16, 16)
+    # composite Galerkin identity and chirality of the composite
+    assert np.abs(Wd.conj().T @ A @ Wd - C2).max() < 1e-12 * np.abs(C2).max()
+    G5 = dense.gamma5_matrix(256)
+    g5c = np.repeat([1.0, -1.0], 8)
+    assert np.abs(G5 @ Wd - Wd * g5c[None, :]).max() < 1e-13
+    assert np.abs(Wd.conj().T @ Wd - np.eye(16)).max() < 1e-12
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((16, 2)) + 1j * rng.standard_normal((16, 2))
+    assert np.allclose(W.prolong(x), Wd @ x, atol=1e-13)
+    f = rng.standard_normal((3072, 2)) + 1j * rng.standard_normal((3072, 2))
+    assert np.allclose(W.restrict(f), Wd.conj().T @ f, atol=1e-12)
+    alg = deflation.Alg2(W, H.matrices[1], 12)
+    Ainv = dense.inverse(A)
+    P = A @ Wd @ alg.U @ np.diag(1.0 / alg.lam) @ alg.U.conj().T @ np.diag(alg.g5) @ Wd.conj().T
+    assert np.abs(P @ P - P).max() < 1e-10 * np.abs(P).max()
+    B = Ainv @ (np.eye(3072) - P)
+    assert abs(alg.t0 + np.trace(B) - np.trace(Ainv)) < 1e-9 * abs(np.trace(Ainv))
+    Z = np.sign(rng.standard_normal((3072, 3))) + 0j
+    assert np.allclose(alg.project(H.levels[0].matvec, Z), Z - P @ Z, atol=1e-10)

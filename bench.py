@@ -189,6 +189,42 @@ def run_reference(args):
     return 0
 
 
+def stencil_roofline(qd, ctx, reps=20):
+    """The Wilson stencil alone (FP32 and FP64) on the 16^3 x 32 lattice with
+    64 right-hand sides: every field is larger than L2, so no flush is needed.
+    Algorithmic bytes per launch: spinor in + out once, links once,
+    V (24 nrhs + 36) complex words; flops 1368 per site and right-hand side."""
+    import torch
+    from paper_1909_12234_gb300 import synth
+    dims, nrhs = (16, 16, 16, 32), 64
+    U = synth.random_su3_links(dims, 0.2, 3)
+    g = qd.Gauge(ctx, dims, U)
+    V = g.V
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    out = {"lattice": "16^3x32", "nrhs": nrhs, "peak_gbs": hbm, "l2": "fields 0.8-1.6 GB > L2"}
+    for name, dt, fn, cb in (("f32", torch.complex64, qd.dirac_apply_f32, 8),
+                             ("f64", torch.complex128, qd.dirac_apply, 16)):
+        x = torch.randn((V, 12, nrhs), dtype=dt, device=f"cuda:{ctx.device}")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            fn(ctx, g, -0.8, 0.0, False, nrhs, x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(reps):
+            fn(ctx, g, -0.8, 0.0, False, nrhs, x, y)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        nbytes = V * (24.0 * cb * nrhs + 36.0 * cb)
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out[name] = {"ms_per_launch": ms, "achieved_gbs": gbs, "frac": gbs / hbm,
+                     "tflops": 1368.0 * V * nrhs / (ms / 1e3) / 1e12}
+        del x, y
+    g.close()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_1909_12234_gb300 import qdtrace as qd
@@ -332,6 +368,8 @@ def run_ours(args):
                 "outer_iterations": [r["iterations"] for r in fres],
                 "max_true_rel_residual": max(r["max_true_rel_residual"] for r in fres)}
 
+    stencil = stencil_roofline(qd, ctx) if rank == 0 else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -353,7 +391,7 @@ def run_ours(args):
                        "max_true_rel_residual": worst,
                        "estimate": [results[-1]["estimate"].real, results[-1]["stderr"]]},
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
-            "fp64_path": fp64, "cpu_baseline": cpu,
+            "fp64_path": fp64, "stencil": stencil, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
     for o in (d, mg, g, ctx):

@@ -136,6 +136,14 @@ int qd_rademacher(qd_ctx* ctx, const qd_gauge* gauge, uint64_t seed,
 int qd_dirac_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau,
                    int dagger, int nrhs, const double* in, double* out);
 
+/* The same operator in FP32 (the arithmetic of the mixed-precision inner
+ * solves): in/out are interleaved complex float (re, im) in qd layout,
+ * links rounded once to FP32 and cached on the gauge (the first call
+ * allocates that copy, so gauge is not const).  Same errors as
+ * qd_dirac_apply.  Asynchronous. */
+int qd_dirac_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau,
+                       int dagger, int nrhs, const float* in, float* out);
+
 /* ------------------------------------------------------------------------ */
 /* a10: adaptive multigrid setup (Sec. 2 "adaptive setup" and "blocking";    */
 /* Sec. 4 tolerance 1e-2 / 200 iterations; Algorithm 2 step 1)              */

@@ -154,6 +154,22 @@ int qd_dirac_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau, in
   });
 }
 
+int qd_dirac_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau, int dagger, int nrhs, const float* in,
+                       float* out) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    QD_REQUIRE(std::isfinite(m0) && std::isfinite(tau), "m0 and tau must be finite");
+    set_device(ctx);
+    qd::wilson_apply<qd::cplxf>(*ctx, gauge->geo, gauge->links_f32(), m0, tau, dagger != 0,
+                                reinterpret_cast<const qd::cplxf*>(in), reinterpret_cast<qd::cplxf*>(out), nrhs);
+  });
+}
+
 void qd_mg_params_default(qd_mg_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));

@@ -129,6 +129,7 @@ SIGNATURES = {
     "qd_field_reorder": (_I, [_P, _P, _I, _I, _P, _P]),
     "qd_rademacher": (_I, [_P, _P, ctypes.c_uint64, ctypes.c_int64, _I, _P]),
     "qd_dirac_apply": (_I, [_P, _P, _D, _D, _I, _I, _P, _P]),
+    "qd_dirac_apply_f32": (_I, [_P, _P, _D, _D, _I, _I, _P, _P]),
     "qd_mg_params_default": (None, [ctypes.POINTER(MGParams)]),
     "qd_mg_setup": (_I, [_P, _P, _D, _D, ctypes.POINTER(MGParams), _P, _PP]),
     "qd_mg_destroy": (_I, [_P]),
@@ -307,6 +308,12 @@ def rademacher(ctx, gauge, seed, sample_offset, nrhs, out):
 def dirac_apply(ctx, gauge, m0, tau, dagger, nrhs, inp, out):
     _check(load().qd_dirac_apply(ctx.h, gauge.h, float(m0), float(tau), 1 if dagger else 0, int(nrhs),
                                  _ptr(inp), _ptr(out)))
+
+
+def dirac_apply_f32(ctx, gauge, m0, tau, dagger, nrhs, inp, out):
+    """FP32 operator on torch.complex64 fields in qd layout."""
+    _check(load().qd_dirac_apply_f32(ctx.h, gauge.h, float(m0), float(tau), 1 if dagger else 0, int(nrhs),
+                                     _ptr64(inp), _ptr64(out)))
 
 
 def mg_params(nlevels=1, blocks=((2, 2, 2, 2),), nvs=(12,), **kw):

@@ -85,6 +85,25 @@ def test_wilson_full_size_8x4_64rhs(qd, ctx):
     assert rel_err(got[..., cols], ref) < 1e-12
 
 
+@pytest.mark.parametrize("dims,s", [((4, 4, 4, 4), 32), ((8, 4, 6, 2), 3), ((4, 2, 2, 6), 70),
+                                    ((16, 16, 16, 32), 4)])
+@pytest.mark.parametrize("tau,dag", [(0.0, False), (0.25, True)])
+def test_wilson_fp32_matches_oracle(qd, ctx, dims, s, tau, dag):
+    # FP32 inputs, links and arithmetic: each output is a sum of about 60
+    # products of O(1) terms, so |error| <= ~60 u max|y| (u = 2^-24), taken
+    # as 1e-5 relative to max|y|
+    U = synth.random_su3_links(dims, 0.2, 4)
+    g = qd.Gauge(ctx, dims, U)
+    x = synth.random_field(dims, s, 3)
+    xin = qd.to_qd(ctx, g, x).to(torch.complex64)
+    out = torch.empty_like(xin)
+    qd.dirac_apply_f32(ctx, g, -0.8, tau, dag, s, xin, out)
+    got = qd.from_qd(ctx, g, out.to(torch.complex128))
+    cols = list(range(min(s, 3)))
+    ref = wilson.dirac_apply(U, x[..., cols], -0.8, dims, tau=tau, dagger=dag)
+    assert rel_err(got[..., cols], ref) < 1e-5
+
+
 def test_gamma5_hermiticity_on_gpu(qd, ctx):
     dims = (4, 4, 4, 4)
     U = synth.random_su3_links(dims, 0.3, 6)

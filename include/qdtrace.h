@@ -213,6 +213,13 @@ int qd_restrict(qd_mg* mg, int level, int nrhs, const double* fine,
 int qd_coarse_apply(qd_mg* mg, int level, int nrhs, const double* in,
                     double* out);
 
+/* The same stencil in FP32 (the arithmetic of the mixed-precision V-cycle):
+ * in/out are interleaved complex float in the level's qd layout; the FP32
+ * copy of C_level is made on first use.  Same errors as qd_coarse_apply.
+ * Asynchronous. */
+int qd_coarse_apply_f32(qd_mg* mg, int level, int nrhs, const float* in,
+                        float* out);
+
 /* out = C_level^{-1} in, level >= 1: the coarse solve of the V-cycle (a5).
  * On the coarsest level with a dense inverse: one product (exact to FP64
  * rounding); otherwise GCR on C_level to coarse_tol (preconditioned by the

@@ -286,6 +286,20 @@ int qd_coarse_apply(qd_mg* mg, int level, int nrhs, const double* in, double* ou
   });
 }
 
+int qd_coarse_apply_f32(qd_mg* mg, int level, int nrhs, const float* in, float* out) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(level >= 1 && level <= mg->nlevels, "coarse level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    set_device(mg->ctx);
+    auto op = mg->op<qd::cplxf>(level);
+    op->apply(*mg->ctx, reinterpret_cast<const qd::cplxf*>(in), reinterpret_cast<qd::cplxf*>(out), nrhs);
+  });
+}
+
 int qd_coarse_solve(qd_mg* mg, int level, int nrhs, const double* in, double* out) {
   return guarded([&] {
     NONNULL(mg);

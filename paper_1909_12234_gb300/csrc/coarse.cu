@@ -5,6 +5,7 @@
 //   * prolongation W c and restriction W^H x (two-grid step 1);
 //   * the Galerkin coarse operator C = W^H A W as a 9-point block stencil,
 //     and its application.
+#include <atomic>
 #include "qd_internal.cuh"
 
 namespace qd {
@@ -210,12 +211,142 @@ __global__ void k_coarse_apply(int64_t nsites, int D, int nrhs, const int* __res
   }
 }
 
+// Register-blocked coarse stencil: one CTA per (coarse site, chunk of
+// right-hand sides).  The site's nine D x D blocks are staged in shared
+// memory transposed, [dir][e][d] with leading dimension ld, so that the RB
+// rows a thread owns are contiguous for every column e.  Each thread keeps
+// RB rows x NR right-hand sides of accumulators: per (dir, e) it reads NR
+// neighbour values from global memory once (coalesced over the chunk) and
+// the RB matrix entries as broadcast vector loads, then does RB x NR complex
+// FMAs - instead of two loads per FMA in the one-thread-per-output form.
+template <class C, int RB, int NR>
+__global__ void __launch_bounds__(256) k_coarse_apply_tiled(int D, int ld, int nrhs, int rhs_per_cta, int nchunks,
+                                                            const int* __restrict__ nbr, const C* __restrict__ mat,
+                                                            const C* __restrict__ in, C* __restrict__ out) {
+  typedef typename CTraits<C>::R R;
+  extern __shared__ __align__(16) unsigned char coarse_smem[];
+  C* sm = reinterpret_cast<C*>(coarse_smem);
+  const int64_t x = blockIdx.x / nchunks;
+  const int chunk = (int)(blockIdx.x - x * nchunks);
+  const int tid = threadIdx.x;
+  const int tpg = rhs_per_cta / NR;  // threads per row group
+  const int g = tid / tpg, t = tid - g * tpg;
+  const int DD = D * D;
+  // stage C[x][dir][d][e] -> sm[(dir * D + e) * ld + d]
+  const C* src = mat + x * 9 * (int64_t)DD;
+  for (int idx = tid; idx < 9 * DD; idx += blockDim.x) {
+    const int dir = idx / DD, rem = idx - dir * DD;
+    const int d = rem / D, e = rem - d * D;
+    sm[(dir * D + e) * ld + d] = src[idx];
+  }
+  __syncthreads();
+  const int r0 = chunk * rhs_per_cta + t * NR;
+  if (r0 >= nrhs) return;
+  const bool full = (r0 + NR <= nrhs);
+  C acc[RB][NR];
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[i][j] = mk<C>((R)0, (R)0);
+  for (int dir = 0; dir < 9; ++dir) {
+    const int64_t y = dir == 0 ? x : (int64_t)nbr[x * 8 + dir - 1];
+    const C* v = in + y * D * (int64_t)nrhs + r0;
+    const C* colbase = sm + dir * D * ld + g * RB;
+#pragma unroll 2
+    for (int e = 0; e < D; ++e) {
+      C xv[NR];
+      if (NR == 2 && sizeof(C) == 8 && full) {
+        const float4 q = *reinterpret_cast<const float4*>(v + (int64_t)e * nrhs);
+        xv[0] = mk<C>((R)q.x, (R)q.y);
+        xv[NR - 1] = mk<C>((R)q.z, (R)q.w);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) xv[j] = (r0 + j < nrhs) ? v[(int64_t)e * nrhs + j] : mk<C>((R)0, (R)0);
+      }
+      const C* col = colbase + e * ld;
+      C m[RB];
+      if (sizeof(C) == 8) {
+#pragma unroll
+        for (int i = 0; i < RB / 2; ++i) {
+          const float4 q = reinterpret_cast<const float4*>(col)[i];
+          m[2 * i] = mk<C>((R)q.x, (R)q.y);
+          m[2 * i + 1] = mk<C>((R)q.z, (R)q.w);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) m[i] = col[i];
+      }
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) cfma(acc[i][j], m[i], xv[j]);
+    }
+  }
+  C* o = out + x * D * (int64_t)nrhs + r0;
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    C* orow = o + (int64_t)(g * RB + i) * nrhs;
+    if (NR == 2 && sizeof(C) == 8 && full) {
+      *reinterpret_cast<float4*>(orow) = make_float4((float)acc[i][0].x, (float)acc[i][0].y,
+                                                     (float)acc[i][NR - 1].x, (float)acc[i][NR - 1].y);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NR; ++j)
+        if (r0 + j < nrhs) orow[j] = acc[i][j];
+    }
+  }
+}
+
+// Launch the tiled kernel for rows-per-thread RB when D is a multiple of it;
+// returns false (nothing launched) when the staged blocks would not fit.
+template <class C, int RB>
+static bool coarse_tiled_launch(qd_ctx& ctx, const CoarseLevel& lv, const C* mat, const C* in, C* out, int nrhs) {
+  const int D = lv.D;
+  if (D % RB != 0) return false;
+  const int ngroups = D / RB;
+  if (ngroups > 8) return false;
+  // float2: rows 16-byte aligned (ld even); double2: odd ld spreads banks
+  const int ld = sizeof(C) == 8 ? D + 2 : D + 1;
+  const size_t smem = (size_t)9 * D * ld * sizeof(C);
+  if (smem > 200 * 1024) return false;
+  constexpr int NR = sizeof(C) == 8 ? 2 : 1;
+  // the vector loads of two float2 values need an even row length and
+  // 16-byte aligned fields
+  if (NR == 2 && ((nrhs & 1) || ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15)))
+    return false;
+  const int cap = (256 / ngroups) / 32 * 32;
+  if (cap < 32) return false;
+  int tpg = div_up(div_up(nrhs, NR), 32) * 32;
+  if (tpg > cap) tpg = cap;
+  const int rhs_per_cta = tpg * NR;
+  const int nchunks = div_up(nrhs, rhs_per_cta);
+  // the shared-memory limit is a per-function, per-device attribute
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  QD_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(attr_set.load() & bit)) {
+    QD_CUDA(cudaFuncSetAttribute(k_coarse_apply_tiled<C, RB, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    attr_set.fetch_or(bit);
+  }
+  const int64_t blocks = lv.geo.nsites * (int64_t)nchunks;
+  k_coarse_apply_tiled<C, RB, NR><<<(unsigned)blocks, ngroups * tpg, smem, ctx.stream>>>(
+      D, ld, nrhs, rhs_per_cta, nchunks, lv.geo.nbr.as<int>(), mat, in, out);
+  QD_LAUNCH_CHECK();
+  return true;
+}
+
 template <class C>
 void coarse_apply(qd_ctx& ctx, const CoarseLevel& lv, const C* mat, const C* in, C* out, int nrhs) {
   const int64_t tot = lv.geo.nsites * lv.D * nrhs;
   const double cb = (double)sizeof(C);
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_COARSE_F64 : QD_PROF_COARSE_F32, 72.0 * lv.D * (double)tot,
                cb * (double)lv.geo.nsites * (9.0 * lv.D * lv.D + 2.0 * lv.D * nrhs));
+  if (coarse_tiled_launch<C, 12>(ctx, lv, mat, in, out, nrhs) || coarse_tiled_launch<C, 16>(ctx, lv, mat, in, out, nrhs) ||
+      coarse_tiled_launch<C, 8>(ctx, lv, mat, in, out, nrhs) || coarse_tiled_launch<C, 6>(ctx, lv, mat, in, out, nrhs) ||
+      coarse_tiled_launch<C, 4>(ctx, lv, mat, in, out, nrhs))
+    return;
   k_coarse_apply<C><<<div_up(tot, 128) < 64 * kNumSMs ? div_up(tot, 128) : 64 * kNumSMs, 128, 0, ctx.stream>>>(
       lv.geo.nsites, lv.D, nrhs, lv.geo.nbr.as<int>(), mat, in, out);
   QD_LAUNCH_CHECK();

@@ -1,6 +1,10 @@
 // Geometry tables, gauge import, field reordering and the counter-based
 // random fields: Rademacher noise (Sec. 1, the x_j of Eq. 1) and the random
 // starts of the adaptive multigrid setup (Sec. 2).
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include "qd_internal.cuh"
 
 namespace qd {
@@ -44,6 +48,26 @@ void LevelGeom::build(const int d[4], bool even_odd) {
       h_nbr[s * 8 + 4 + mu] = h_site_of_lex[lex(cm)];
     }
   }
+  // 4^4 tiles in lexicographic tile order, Morton order (coordinate bits
+  // interleaved) inside a tile; the key is injective, so no ties
+  int tdim[4];
+  for (int m = 0; m < 4; ++m) tdim[m] = (dims[m] + 3) / 4;
+  std::vector<std::pair<uint64_t, int>> key(V);
+  for (int64_t s = 0; s < V; ++s) {
+    int c[4];
+    coords(h_lex_of_site[s], c);
+    const uint64_t tile = (uint64_t)(c[0] / 4) +
+                          (uint64_t)tdim[0] * ((c[1] / 4) + (uint64_t)tdim[1] * ((c[2] / 4) + (uint64_t)tdim[2] * (c[3] / 4)));
+    uint64_t in = 0;
+    for (int b = 0; b < 2; ++b)
+      for (int m = 0; m < 4; ++m) in |= (uint64_t)((c[m] >> b) & 1) << (4 * b + m);
+    key[s] = {(tile << 8) | in, (int)s};
+  }
+  std::sort(key.begin(), key.end());
+  h_visit.resize(V);
+  for (int64_t k = 0; k < V; ++k) h_visit[k] = key[k].second;
+  visit.resize(V * sizeof(int));
+  QD_CUDA(cudaMemcpy(visit.as<int>(), h_visit.data(), V * sizeof(int), cudaMemcpyHostToDevice));
   nbr.resize(V * 8 * sizeof(int));
   lex_of_site.resize(V * sizeof(int));
   site_of_lex.resize(V * sizeof(int));

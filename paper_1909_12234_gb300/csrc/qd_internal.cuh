@@ -74,6 +74,12 @@ struct LevelGeom {
   DevBuf nbr;                      // int32 [nsites][8]
   DevBuf lex_of_site;              // int32 [nsites]
   DevBuf site_of_lex;              // int32 [nsites]
+  // Stencil traversal order: visit[k] = site index of the k-th site when
+  // 4^4 tiles are taken in turn (Morton order inside a tile), so that the
+  // sites in flight at one time form compact 4-D regions whose neighbours
+  // stay in L2.
+  std::vector<int> h_visit;
+  DevBuf visit;                    // int32 [nsites]
   void build(const int d[4], bool even_odd);
   void coords(int64_t lex, int c[4]) const {
     c[0] = (int)(lex % dims[0]);

@@ -140,13 +140,14 @@ __device__ __forceinline__ void hop_dir(const C* __restrict__ U, const int* __re
 // ALU-bound and keeps its registers.
 template <class C, bool DAG, bool RESID>
 __global__ void __launch_bounds__(128, sizeof(C) == 8 ? 8 : 1)
-k_wilson(const C* __restrict__ U, const int* __restrict__ nbr, int64_t V, int nrhs, double mass,
-         double tau, const C* __restrict__ in, C* __restrict__ out, const C* __restrict__ b) {
+k_wilson(const C* __restrict__ U, const int* __restrict__ nbr, const int* __restrict__ visit, int64_t V, int nrhs,
+         double mass, double tau, const C* __restrict__ in, C* __restrict__ out, const C* __restrict__ b) {
   typedef typename CTraits<C>::R R;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= V * nrhs) return;
-  const int64_t site = g / nrhs;
-  const int r = (int)(g - site * nrhs);
+  const int64_t slot = g / nrhs;
+  const int r = (int)(g - slot * nrhs);
+  const int64_t site = visit[slot];
   const int64_t rs = nrhs;
   int nb8[8];
 #pragma unroll
@@ -179,6 +180,144 @@ k_wilson(const C* __restrict__ U, const int* __restrict__ nbr, int64_t V, int nr
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32, two right-hand sides per thread: every spinor component of the two
+// is one 16-byte load, and each link is loaded once for both, which halves
+// the load instructions per right-hand side and doubles the bytes each one
+// moves.  Needs an even nrhs and 16-byte aligned fields (checked by the
+// launcher, which otherwise takes the one-per-thread kernel).
+// ---------------------------------------------------------------------------
+template <bool ADJ>
+__device__ __forceinline__ void su3mul_r(const float2 l[9], const float2 x[3], float2 y[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (ADJ)
+        cfmac(acc, l[b * 3 + a], x[b]);
+      else
+        cfma(acc, l[a * 3 + b], x[b]);
+    }
+    y[a] = acc;
+  }
+}
+
+// One hop (forward: FWD, via U_mu(n); backward: via U_mu(n-mu)^H) for both
+// right-hand sides.  With s = +1 (A) or -1 (A^H), the projector is
+// (1 + sig gamma_mu), sig = -s forward and +s backward: h = lo + sig B^H up,
+// then lower += U h and upper += sig B (U h).
+template <int MU, bool FWD, bool DAG>
+__device__ __forceinline__ void hop2(const float2* __restrict__ L, const float4* __restrict__ q,
+                                     float2 hu[2][6], float2 hl[2][6]) {
+  constexpr bool plus = (FWD == DAG);  // sig = +1 forward with DAG, backward without
+  float2 l[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) l[k] = L[k];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    float2 h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float4 u0 = q[0 * 3 + c], u1 = q[1 * 3 + c], w0 = q[2 * 3 + c], w1 = q[3 * 3 + c];
+      const float2 a0 = j ? make_float2(u0.z, u0.w) : make_float2(u0.x, u0.y);
+      const float2 a1 = j ? make_float2(u1.z, u1.w) : make_float2(u1.x, u1.y);
+      const float2 l0 = j ? make_float2(w0.z, w0.w) : make_float2(w0.x, w0.y);
+      const float2 l1 = j ? make_float2(w1.z, w1.w) : make_float2(w1.x, w1.y);
+      float2 b0, b1;
+      bdag<MU>(a0, a1, b0, b1);
+      if (plus) { h0[c] = cadd(l0, b0); h1[c] = cadd(l1, b1); }
+      else      { h0[c] = csub(l0, b0); h1[c] = csub(l1, b1); }
+    }
+    float2 g0[3], g1[3];
+    su3mul_r<!FWD>(l, h0, g0);
+    su3mul_r<!FWD>(l, h1, g1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      hl[j][c] = cadd(hl[j][c], g0[c]);
+      hl[j][3 + c] = cadd(hl[j][3 + c], g1[c]);
+      float2 b0, b1;
+      bmul<MU>(g0[c], g1[c], b0, b1);
+      if (plus) { hu[j][c] = cadd(hu[j][c], b0); hu[j][3 + c] = cadd(hu[j][3 + c], b1); }
+      else      { hu[j][c] = csub(hu[j][c], b0); hu[j][3 + c] = csub(hu[j][3 + c], b1); }
+    }
+  }
+}
+
+template <int MU, bool DAG>
+__device__ __forceinline__ void hop2_dir(const float2* __restrict__ U, const int nb8[8], int64_t V, int64_t site,
+                                         int64_t rs, int r0, const float2* __restrict__ in, float2 hu[2][6],
+                                         float2 hl[2][6]) {
+  float4 q[12];
+  {
+    const float2* p = in + (int64_t)nb8[MU] * 12 * rs + r0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = *reinterpret_cast<const float4*>(p + k * rs);
+    hop2<MU, true, DAG>(U + ((int64_t)MU * V + site) * 9, q, hu, hl);
+  }
+  {
+    const int64_t nbk = nb8[4 + MU];
+    const float2* p = in + nbk * 12 * rs + r0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = *reinterpret_cast<const float4*>(p + k * rs);
+    hop2<MU, false, DAG>(U + ((int64_t)MU * V + nbk) * 9, q, hu, hl);
+  }
+}
+
+// (128, 4): at most 128 registers, four blocks per SM; the output is written
+// with evict-first stores so that it does not push neighbour spinors out of L2
+template <bool DAG, bool RESID>
+__global__ void __launch_bounds__(128, 4) k_wilson_f32x2(const float2* __restrict__ U, const int* __restrict__ nbr,
+                                                      const int* __restrict__ visit, int64_t V, int nrhs,
+                                                      float mass, float tau,
+                                                      const float2* __restrict__ in, float2* __restrict__ out,
+                                                      const float2* __restrict__ b) {
+  const int half = nrhs >> 1;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= V * half) return;
+  const int64_t slot = g / half;
+  const int r0 = 2 * (int)(g - slot * half);
+  const int64_t site = visit[slot];
+  const int64_t rs = nrhs;
+  int nb8[8];
+#pragma unroll
+  for (int h = 0; h < 8; ++h) nb8[h] = nbr[site * 8 + h];
+  float2 hu[2][6], hl[2][6];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { hu[j][k] = make_float2(0.f, 0.f); hl[j][k] = make_float2(0.f, 0.f); }
+  hop2_dir<0, DAG>(U, nb8, V, site, rs, r0, in, hu, hl);
+  hop2_dir<1, DAG>(U, nb8, V, site, rs, r0, in, hu, hl);
+  hop2_dir<2, DAG>(U, nb8, V, site, rs, r0, in, hu, hl);
+  hop2_dir<3, DAG>(U, nb8, V, site, rs, r0, in, hu, hl);
+  const float te = DAG ? -tau : tau;
+  const float2 mup = make_float2(mass, te);
+  const float2 mlo = make_float2(mass, -te);
+  const float2* x = in + site * 12 * rs + r0;
+  float2* y = out + site * 12 * rs + r0;
+  const float2* bb = RESID ? b + site * 12 * rs + r0 : nullptr;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float4 xv = *reinterpret_cast<const float4*>(x + k * rs);
+    const float2 m = k < 6 ? mup : mlo;
+    float2 v0 = cmul(m, make_float2(xv.x, xv.y));
+    float2 v1 = cmul(m, make_float2(xv.z, xv.w));
+    const float2 h0 = k < 6 ? hu[0][k] : hl[0][k - 6];
+    const float2 h1 = k < 6 ? hu[1][k] : hl[1][k - 6];
+    v0.x = fmaf(-0.5f, h0.x, v0.x);
+    v0.y = fmaf(-0.5f, h0.y, v0.y);
+    v1.x = fmaf(-0.5f, h1.x, v1.x);
+    v1.y = fmaf(-0.5f, h1.y, v1.y);
+    if (RESID) {
+      const float4 bv = *reinterpret_cast<const float4*>(bb + k * rs);
+      v0 = make_float2(bv.x - v0.x, bv.y - v0.y);
+      v1 = make_float2(bv.z - v1.x, bv.w - v1.y);
+    }
+    __stcs(reinterpret_cast<float4*>(y + k * rs), make_float4(v0.x, v0.y, v1.x, v1.y));
+  }
+}
+
 template <class C>
 void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, double tau,
                   bool dagger, const C* in, C* out, int nrhs, const C* b) {
@@ -190,18 +329,44 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_WILSON_F64 : QD_PROF_WILSON_F32, 1368.0 * (double)tot,
                (double)geo.nsites * ((b ? 36.0 : 24.0) * cb * nrhs + 36.0 * cb));
   const int* nb = geo.nbr.as<int>();
+  const int* vis = geo.visit.as<int>();
   const double mass = 4.0 + m0;
+  if (sizeof(C) == 8 && (nrhs % 2) == 0 &&
+      ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) {
+    const int64_t tot2 = geo.nsites * (nrhs / 2);
+    const int blocks2 = div_up(tot2, threads);
+    const float2* L = reinterpret_cast<const float2*>(links);
+    const float2* xin = reinterpret_cast<const float2*>(in);
+    float2* yout = reinterpret_cast<float2*>(out);
+    const float2* bb = reinterpret_cast<const float2*>(b);
+    const float fm = (float)mass, ft = (float)tau;
+    if (b) {
+      if (dagger)
+        k_wilson_f32x2<true, true><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, fm, ft, xin, yout, bb);
+      else
+        k_wilson_f32x2<false, true><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, fm, ft, xin, yout, bb);
+    } else {
+      if (dagger)
+        k_wilson_f32x2<true, false><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, fm, ft, xin, yout,
+                                                                         nullptr);
+      else
+        k_wilson_f32x2<false, false><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, fm, ft, xin, yout,
+                                                                          nullptr);
+    }
+    QD_LAUNCH_CHECK();
+    return;
+  }
   if (b) {
     if (dagger)
-      k_wilson<C, true, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, geo.nsites, nrhs, mass, tau, in, out, b);
+      k_wilson<C, true, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out, b);
     else
-      k_wilson<C, false, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, geo.nsites, nrhs, mass, tau, in, out, b);
+      k_wilson<C, false, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out, b);
   } else {
     if (dagger)
-      k_wilson<C, true, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, geo.nsites, nrhs, mass, tau, in, out,
+      k_wilson<C, true, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out,
                                                                    nullptr);
     else
-      k_wilson<C, false, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, geo.nsites, nrhs, mass, tau, in, out,
+      k_wilson<C, false, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out,
                                                                     nullptr);
   }
   QD_LAUNCH_CHECK();

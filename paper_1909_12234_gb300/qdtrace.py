@@ -137,6 +137,7 @@ SIGNATURES = {
     "qd_prolongate": (_I, [_P, _I, _I, _P, _P]),
     "qd_restrict": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_apply": (_I, [_P, _I, _I, _P, _P]),
+    "qd_coarse_apply_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_solver_params_default": (None, [ctypes.POINTER(SolverParams)]),
@@ -383,6 +384,10 @@ def _ptr64(t):
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64 or not t.is_contiguous():
         raise QDError(QD_ERR_INVALID, "expected a contiguous torch.complex64 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def coarse_apply_f32(mg, level, nrhs, inp, out):
+    _check(load().qd_coarse_apply_f32(mg.h, int(level), int(nrhs), _ptr64(inp), _ptr64(out)))
 
 
 def coarse_solve_f32(mg, level, nrhs, inp, out):

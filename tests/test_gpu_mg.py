@@ -72,6 +72,30 @@ def test_transfer_and_coarse_operator(qd, ctx, dims, m0, blocks, nvs):
         assert tuple(dims_c) == T.cdims and dof == 2 * T.nv and ns == T.Vc
 
 
+@pytest.mark.parametrize("dims,m0,blocks,nvs", CASES + [((8, 8, 8, 8), -0.8, [(2, 2, 2, 2), (2, 2, 2, 2)], [12, 16])])
+def test_coarse_stencil_fp64_fp32_rhs_counts(qd, ctx, dims, m0, blocks, nvs):
+    # the register-blocked coarse stencil for every level, with right-hand
+    # side counts that leave ragged chunks (odd counts take the scalar FP32
+    # loads); FP64 to 1e-12, FP32 within its rounding bound: at most 9 D
+    # products per output (D <= 32), error <= ~300 u sum|c||x| with
+    # u = 2^-24, and sum|c||x| <= 3 max|y| here, taken as 5e-5
+    U, g, mg, H = _build(qd, ctx, dims, m0, blocks, nvs)
+    rng = np.random.default_rng(5)
+    for l in range(len(blocks)):
+        nc = H.transfers[l].nc
+        for s in (1, 2, 3, 64, 130, 300):
+            c = rng.standard_normal((nc, s)) + 1j * rng.standard_normal((nc, s))
+            ref = H.matrices[l] @ c
+            cd = dev(c)
+            out = torch.empty_like(cd)
+            qd.coarse_apply(mg, l + 1, s, cd, out)
+            assert rel_err(host(out).reshape(nc, s), ref) < 1e-12, (l, s)
+            c32 = cd.to(torch.complex64)
+            o32 = torch.empty_like(c32)
+            qd.coarse_apply_f32(mg, l + 1, s, c32, o32)
+            assert rel_err(host(o32).astype(np.complex128).reshape(nc, s), ref) < 5e-5, (l, s)
+
+
 def test_null_vector_iteration(qd, ctx):
     # the full adaptive setup (MR on A y = 0 to 1e-2 / 200 steps): the same
     # step counts per vector as the oracle, an orthonormal chiral W, and a

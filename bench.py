@@ -261,9 +261,6 @@ def run_ours(args):
         _batch(qd, ctx, g, mg, d, offset(i), prec)
     clocks = ClockSampler(local)
     clocks.start()
-    qd.prof_enable(ctx, True)
-    for k in qd.PROF_KINDS:
-        qd.prof_read(ctx, k, reset=True)
     launches0 = qd.launch_count()
     if dist:
         dist.barrier()
@@ -280,13 +277,28 @@ def run_ours(args):
     if dist:
         dist.barrier()
     launches = qd.launch_count() - launches0
-    qd.prof_enable(ctx, False)
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
     if dist:
         tt = torch.tensor([ms_total], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms_total = float(tt.item())
+
+    # per-kernel device time: separate steps with the library's CUDA-event
+    # profiling on (graph replay is off while profiling, so these steps run
+    # the same kernels launched one by one)
+    qd.prof_enable(ctx, True)
+    for k in qd.PROF_KINDS:
+        qd.prof_read(ctx, k, reset=True)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for i in range(args.prof_steps):
+        _batch(qd, ctx, g, mg, d, offset(3000 + i), prec)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    qd.prof_enable(ctx, False)
+    ms_prof = p0.elapsed_time(p1)
     prof = {k: qd.prof_read(ctx, k) for k in qd.PROF_KINDS}
     value = args.steps * s * world / (ms_total / 1e3)
     iters = [r["iterations"] for r in results]
@@ -317,7 +329,8 @@ def run_ours(args):
                 "ms_per_launch": pt["ms"] / max(pt["launches"], 1),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                   "share_of_step": round(v["ms"] / ms_total, 4)} for k, v in prof.items() if v["launches"]}
+                   "share_of_step": round(v["ms"] / ms_prof, 4)} for k, v in prof.items() if v["launches"]}
+    kernels["_profiled_steps"] = {"steps": args.prof_steps, "ms_per_step": round(ms_prof / max(args.prof_steps, 1), 3)}
 
     # end to end through the public API: links from pinned host memory,
     # setup, one batch, results read back, per step
@@ -412,6 +425,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--prof-steps", type=int, default=2)
     ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     WL.clear()

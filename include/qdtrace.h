@@ -158,7 +158,9 @@ typedef struct {
   uint64_t seed;                /* level l uses seed + l for its starts */
   int smoother_steps;           /* minimal-residual post-smoothing steps */
   double coarse_tol;            /* relative tolerance of coarse GCR */
-  int coarse_maxit;             /* iteration cap of coarse GCR */
+  int coarse_maxit;             /* iteration cap of coarse GCR; with
+                                   coarse_tol <= 0 exactly this many
+                                   iterations, no convergence checks */
   int coarse_restart;           /* restart length of coarse GCR */
   int coarsest_direct;          /* > 0: invert the coarsest operator densely
                                    (FP64 Gauss-Jordan in setup) when its
@@ -169,6 +171,14 @@ typedef struct {
                                    the FP32 V-cycle apply it as one BF16
                                    tcgen05 tensor-core GEMM (FP32
                                    accumulate); 0 uses FP32 CUDA cores */
+  int use_graphs;               /* != 0: when the V-cycle needs no host
+                                   synchronisation (dense coarsest inverse
+                                   below the first coarse level, and
+                                   coarse_tol <= 0 on the levels between),
+                                   each fine-level V-cycle is captured once
+                                   per (input, output, nrhs) as a CUDA graph
+                                   and replayed; the result is the same as
+                                   the eager launches.  Off while profiling */
 } qd_mg_params;
 
 /* Fill `p` with this library's defaults (1 level, 2^4 blocks, nv 12,

@@ -187,6 +187,7 @@ void qd_mg_params_default(qd_mg_params* p) {
   p->coarse_restart = 16;
   p->coarsest_direct = 16384;
   p->coarsest_bf16 = 1;
+  p->use_graphs = 1;
 }
 
 void qd_solver_params_default(qd_solver_params* p) {

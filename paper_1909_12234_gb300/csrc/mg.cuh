@@ -24,6 +24,8 @@ template <class C> class GCR {
   // change between calls.  `quiet` skips per-column statistics.
   void solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x, int nrhs, double tol,
              int maxit, int restart, SolveInfo* info);
+  // Device buffers the solve uses (their current addresses).
+  void buffers(std::vector<const void*>& v) const;
 
  private:
   void ensure(int64_t n, int nrhs, int m);
@@ -59,15 +61,35 @@ namespace qd {
 template <class C> class MGPrecond : public Precond<C> {
  public:
   MGPrecond(qd_mg* mg, int level);
+  MGPrecond(const MGPrecond&) = delete;
+  MGPrecond& operator=(const MGPrecond&) = delete;
+  ~MGPrecond();
   void apply(qd_ctx& ctx, const C* r, C* z, int nrhs) override;
+  void buffers(std::vector<const void*>& v) const;
+  bool sync_free() const;
 
  private:
+  void body(qd_ctx& ctx, const C* r, C* z, int nrhs);
+  void drop_graphs();
   qd_mg* mg_;
   int level_;
   std::unique_ptr<MGPrecond<C>> next_;
   GCR<C> coarse_;
   DevBuf rc_, ec_, t_, res_, q_, d_, scratch_;
   int cap_ = -1;
+  // Captured fine-level V-cycles, one per (input, output) pair at one nrhs;
+  // valid while every buffer in `ptrs` keeps its address.
+  struct Graph {
+    const void* r = nullptr;
+    void* z = nullptr;
+    int nrhs = 0;
+    std::vector<const void*> ptrs;
+    long long kernels = 0;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<Graph> graphs_;
+  int warm_nrhs_ = -1;
+  cudaStream_t cap_stream_ = nullptr;  // capture only; nothing runs on it
 };
 
 }  // namespace qd

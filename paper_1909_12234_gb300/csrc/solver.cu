@@ -148,6 +148,10 @@ static void read_flags(qd_ctx& ctx, const int* dev, int n, int* host) {
 // ---------------------------------------------------------------------------
 // GCR
 // ---------------------------------------------------------------------------
+template <class C> void GCR<C>::buffers(std::vector<const void*>& v) const {
+  for (const DevBuf* b : {&P_, &Q_, &r_, &t_, &sc_, &act_}) v.push_back(b->as<void>());
+}
+
 template <class C> void GCR<C>::ensure(int64_t n, int nrhs, int m) {
   if (n == cap_n_ && nrhs <= cap_rhs_ && m <= cap_m_) return;
   const size_t vec = (size_t)n * nrhs * sizeof(C);
@@ -193,13 +197,19 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
   ctx.red_partials.resize((size_t)sw.grid.x * nrhs * sizeof(cplx));
   int its = 0;
   int hflags[2];
+  // tol <= 0: exactly maxit iterations and no host synchronisation (columns
+  // with a zero residual are masked on the device)
+  const bool check = tol > 0.0;
   while (true) {
+    if (!check && its >= maxit) break;
     QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
     k_set_active<<<div_up(nrhs, 128), 128, 0, ctx.stream>>>(nrhs, rn2, bn2, tol2, act, flags, flags + 1);
     QD_LAUNCH_CHECK();
-    read_flags(ctx, flags, 2, hflags);
-    if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
-    if (hflags[0] == 0 || its >= maxit) break;
+    if (check) {
+      read_flags(ctx, flags, 2, hflags);
+      if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
+      if (hflags[0] == 0 || its >= maxit) break;
+    }
     for (int i = 0; i < restart; ++i) {
       C* Pi = P + i * tot;
       C* Qi = Q + i * tot;
@@ -226,10 +236,14 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
                                                             bn2, tol2, act, flags, flags + 1, iters);
       QD_LAUNCH_CHECK();
       ++its;
-      read_flags(ctx, flags, 2, hflags);
-      if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
-      if (hflags[0] == 0 || its >= maxit) break;
+      if (check) {
+        read_flags(ctx, flags, 2, hflags);
+        if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
+        if (hflags[0] == 0) break;
+      }
+      if (its >= maxit) break;
     }
+    if (!check && its >= maxit) break;  // no further cycle reads the residual
     // true residual r = b - A x
     A.residual(ctx, b, x, r, nrhs);
     blas::dots(ctx, 1, n, nrhs, r, 0, r, 0, rn2);
@@ -337,7 +351,112 @@ MGPrecond<C>::MGPrecond(qd_mg* mg, int level) : mg_(mg), level_(level) {
   if (level + 1 < mg->nlevels) next_.reset(new MGPrecond<C>(mg, level + 1));
 }
 
+template <class C> MGPrecond<C>::~MGPrecond() {
+  drop_graphs();
+  if (cap_stream_) cudaStreamDestroy(cap_stream_);
+}
+
+template <class C> void MGPrecond<C>::drop_graphs() {
+  for (Graph& g : graphs_) cudaGraphExecDestroy(g.exec);
+  graphs_.clear();
+}
+
+// No host synchronisation anywhere below this level: the next level has a
+// dense inverse, or its GCR runs a fixed number of iterations (tol <= 0)
+// with a V-cycle that is itself free of synchronisation.
+template <class C> bool MGPrecond<C>::sync_free() const {
+  if (mg_->Cinv<C>(level_ + 1)) return true;
+  if (mg_->p.coarse_tol > 0.0 || !next_) return false;
+  return next_->sync_free();
+}
+
+// Every device buffer the V-cycle below this level reads or writes and that
+// can be reallocated after a first call (grow-only buffers: the same address
+// means the same, large-enough buffer).
+template <class C> void MGPrecond<C>::buffers(std::vector<const void*>& v) const {
+  for (const DevBuf* b : {&rc_, &ec_, &t_, &res_, &q_, &d_, &scratch_}) v.push_back(b->as<void>());
+  coarse_.buffers(v);
+  const CoarseLevel& cl = *mg_->L[level_];
+  for (const DevBuf* b : {&cl.tc_xc, &cl.tc_yc, &cl.tc_B, &cl.tc_part, &cl.tc_err, &cl.Cinvf, &cl.Cmf})
+    v.push_back(b->as<void>());
+  if (next_) next_->buffers(v);
+}
+
 template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int nrhs) {
+  if (level_ != 0 || !mg_->p.use_graphs || ctx.prof || !sync_free()) {
+    body(ctx, r, z, nrhs);
+    return;
+  }
+  std::vector<const void*> cur;
+  buffers(cur);
+  cur.push_back(ctx.red_partials.as<void>());
+  cur.push_back(reinterpret_cast<const void*>(ctx.stream));
+  if (!graphs_.empty() && (graphs_.front().ptrs != cur || graphs_.front().nrhs != nrhs)) drop_graphs();
+  for (Graph& g : graphs_) {
+    if (g.r == r && g.z == z) {
+      QD_CUDA(cudaGraphLaunch(g.exec, ctx.stream));
+      launch_counter().fetch_add(g.kernels, std::memory_order_relaxed);
+      return;
+    }
+  }
+  if (warm_nrhs_ != nrhs) {
+    // first call at this size: eager, so that every buffer reaches its size
+    body(ctx, r, z, nrhs);
+    warm_nrhs_ = nrhs;
+    return;
+  }
+  // capture on a private stream (the caller's may be the legacy default
+  // stream, which cannot be captured); the graph is then launched on the
+  // caller's stream
+  if (!cap_stream_) QD_CUDA(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  const long long c0 = launch_counter().load();
+  const cudaStream_t user = ctx.stream;
+  ctx.stream = cap_stream_;
+  cudaError_t ce = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) {
+    ctx.stream = user;
+    QD_CUDA(ce);
+  }
+  try {
+    body(ctx, r, z, nrhs);
+  } catch (...) {
+    cudaStreamEndCapture(cap_stream_, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    ctx.stream = user;
+    throw;
+  }
+  ce = cudaStreamEndCapture(cap_stream_, &graph);
+  ctx.stream = user;
+  QD_CUDA(ce);
+  // kernels captured, not launched: take them off the counter; they count
+  // each time the graph is launched
+  size_t nn = 0;
+  QD_CUDA(cudaGraphGetNodes(graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) QD_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
+  long long kernels = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    QD_CUDA(cudaGraphNodeGetType(nd, &ty));
+    if (ty == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  launch_counter().fetch_sub(launch_counter().load() - c0 >= kernels ? kernels : 0, std::memory_order_relaxed);
+  Graph g;
+  g.r = r;
+  g.z = z;
+  g.nrhs = nrhs;
+  g.ptrs = cur;
+  g.kernels = kernels;
+  const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  QD_CUDA(ie);
+  graphs_.push_back(g);
+  QD_CUDA(cudaGraphLaunch(g.exec, ctx.stream));
+  launch_counter().fetch_add(kernels, std::memory_order_relaxed);
+}
+
+template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, int nrhs) {
   const Transfer& T = *mg_->T[level_];
   const int64_t nf = mg_->geom(level_).nsites * (int64_t)mg_->dof(level_);
   const int64_t nc = mg_->geom(level_ + 1).nsites * (int64_t)mg_->dof(level_ + 1);

@@ -56,7 +56,8 @@ class MGParams(ctypes.Structure):
                 ("coarse_maxit", ctypes.c_int),
                 ("coarse_restart", ctypes.c_int),
                 ("coarsest_direct", ctypes.c_int),
-                ("coarsest_bf16", ctypes.c_int)]
+                ("coarsest_bf16", ctypes.c_int),
+                ("use_graphs", ctypes.c_int)]
 
 
 class SolverParams(ctypes.Structure):

@@ -49,7 +49,8 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "qdtrace.h"
 int main(void) {
-  printf("%zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol), offsetof(qd_mg_params, coarsest_direct));
+  printf("%zu %zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol), offsetof(qd_mg_params, coarsest_direct),
+         offsetof(qd_mg_params, use_graphs));
   printf("%zu %zu\n", sizeof(qd_solve_stats), offsetof(qd_solve_stats, true_rel_residual));
   printf("%zu %zu\n", sizeof(qd_defl_params), offsetof(qd_defl_params, seed));
   printf("%zu %zu\n", sizeof(qd_trace_params), offsetof(qd_trace_params, solver));
@@ -61,7 +62,8 @@ int main(void) {
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     got = [list(map(int, l.split())) for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines()]
     want = [
-        [ctypes.sizeof(qd.MGParams), qd.MGParams.null_tol.offset, qd.MGParams.coarsest_direct.offset],
+        [ctypes.sizeof(qd.MGParams), qd.MGParams.null_tol.offset, qd.MGParams.coarsest_direct.offset,
+         qd.MGParams.use_graphs.offset],
         [ctypes.sizeof(qd.SolveStats), qd.SolveStats.true_rel_residual.offset],
         [ctypes.sizeof(qd.DeflParams), qd.DeflParams.seed.offset],
         [ctypes.sizeof(qd.TraceParams), qd.TraceParams.solver.offset],
@@ -90,4 +92,4 @@ def test_defaults(library):
     assert d.kind == qd.QD_DEFL_MG_OBLIQUE and d.k == 24
     sp = qd.solver_params()
     assert sp.tol == 1e-8 and sp.precision == qd.QD_PREC_F64 and sp.inner_tol == 1e-5
-    assert p.coarsest_direct == 16384 and p.coarsest_bf16 == 1
+    assert p.coarsest_direct == 16384 and p.coarsest_bf16 == 1 and p.use_graphs == 1

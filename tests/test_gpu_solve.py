@@ -117,3 +117,34 @@ def test_mixed_precision_refinement(qd, ctx, dims, m0, seed, blocks, nvs):
         true_rel = np.linalg.norm(B - A @ x, axis=0) / np.linalg.norm(B, axis=0)
         assert np.all(true_rel <= tol), true_rel
         assert np.allclose(true_rel, rel, rtol=1e-3, atol=1e-3 * tol)
+
+
+@pytest.mark.parametrize("blocks,nvs,kw", [([(2, 2, 2, 2)], [12], {}),
+                                           ([(2, 2, 2, 2), (2, 2, 2, 2)], [12, 16],
+                                            {"coarse_tol": 0.0, "coarse_maxit": 6})])
+def test_vcycle_graph_replay_matches_eager(qd, ctx, blocks, nvs, kw):
+    # the captured V-cycle (CUDA graph) replays exactly the eager launches:
+    # bit-identical solutions, mixed and FP64, two and three levels (the
+    # three-level case with a fixed-iteration level-1 GCR, which needs no
+    # host synchronisation); the solution meets the FP64 true residual
+    dims, m0, s = (8, 8, 8, 8), -0.8, 8
+    U = synth.random_su3_links(dims, 0.3, 2)
+    g = qd.Gauge(ctx, dims, U)
+    b = synth.random_field(dims, s, 11)
+    bd = qd.to_qd(ctx, g, b)
+    A = omg.fine_level(U, m0, dims).matrix
+    for prec in (qd.QD_PREC_MIXED, qd.QD_PREC_F64):
+        xs = []
+        for graphs in (0, 1):
+            mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(len(blocks), blocks, nvs, use_graphs=graphs, **kw))
+            for rep in range(3):  # eager warm-up, capture, replay
+                xd = torch.empty_like(bd)
+                rc, its, _, rel = qd.solve(ctx, g, mg, m0, 0.0, s, bd, xd, 1e-10, maxit=300, restart=16,
+                                           precision=prec, inner_tol=1e-5, max_refine=10)
+                xs.append(xd.clone())
+            mg.close()
+        for x in xs[1:]:
+            assert torch.equal(x, xs[0])
+        x = qd.from_qd(ctx, g, xs[-1]).reshape(-1, s)
+        B = b.reshape(-1, s)
+        assert np.all(np.linalg.norm(B - A @ x, axis=0) / np.linalg.norm(B, axis=0) <= 1e-10)

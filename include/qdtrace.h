@@ -409,6 +409,33 @@ int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg,
                         const qd_trace_params* params,
                         qd_trace_result* result);
 
+/* One estimator problem of a batch: the arguments of qd_hutchinson_trace,
+ * plus its outcome. */
+typedef struct {
+  const qd_gauge* gauge;
+  qd_mg* mg;               /* nullable; distinct across the batch */
+  qd_defl* defl;           /* nullable; distinct across the batch */
+  double m0, tau;
+  qd_trace_params params;
+  qd_trace_result* result; /* host, filled as by qd_hutchinson_trace */
+  int status;              /* out: QD_OK, QD_ERR_NOT_CONVERGED or the
+                              item's own error code */
+} qd_batch_item;
+
+/* Independent estimators of uneven size (different lattices, masses and
+ * sample counts: Eq. 1 with Algorithm 1 or 2 per item) solved concurrently
+ * on one device: nstreams (1..64) worker streams, each driven by its own
+ * host thread, take the items largest first (V x nsamples).  Every item's
+ * arithmetic is that of qd_hutchinson_trace on the same inputs, so its
+ * results are bit-identical to a lone call.  Items may share a gauge; an mg
+ * or defl handle may appear in one item only (QD_ERR_INVALID otherwise).
+ * Work is ordered after everything already queued on ctx's stream.
+ * Synchronous.  Returns QD_OK when every item is QD_OK, else the first
+ * failing item's code (QD_ERR_NOT_CONVERGED when that is the only kind of
+ * failure); per-item codes are in items[i].status. */
+int qd_hutchinson_batch(qd_ctx* ctx, int nitems, qd_batch_item* items,
+                        int nstreams);
+
 /* ------------------------------------------------------------------------ */
 /* Kernel timing (measurement support; the paper has no counterpart)         */
 /* ------------------------------------------------------------------------ */

@@ -1,7 +1,10 @@
 // extern "C" entry points of libqdtrace (declared in include/qdtrace.h).
 // Every function catches internal errors and returns a qd_status code; the
 // message is kept per host thread for qd_last_error().
+#include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 
 #include "blas.cuh"
 #include "defl.cuh"
@@ -460,7 +463,7 @@ int qd_deflate_project(qd_defl* defl, int nrhs, const double* z, double* out) {
     QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     QD_REQUIRE(z != out, "z and out must not overlap");
     set_device(defl->ctx);
-    qd::defl_project(*defl, nrhs, reinterpret_cast<const qd::cplx*>(z), reinterpret_cast<qd::cplx*>(out));
+    qd::defl_project(*defl->ctx, *defl, nrhs, reinterpret_cast<const qd::cplx*>(z), reinterpret_cast<qd::cplx*>(out));
   });
 }
 
@@ -484,7 +487,7 @@ int qd_deflate_coeffs(qd_defl* defl, int nrhs, const double* z, double* ZhV, dou
     set_device(defl->ctx);
     const int k = defl->p.k;
     qd::DevBuf m1((size_t)k * nrhs * sizeof(qd::cplx)), m2((size_t)k * nrhs * sizeof(qd::cplx));
-    qd::defl_coeffs(*defl, nrhs, reinterpret_cast<const qd::cplx*>(z), m1.as<qd::cplx>(), m2.as<qd::cplx>());
+    qd::defl_coeffs(*defl->ctx, *defl, nrhs, reinterpret_cast<const qd::cplx*>(z), m1.as<qd::cplx>(), m2.as<qd::cplx>());
     std::vector<qd::cplx> h1((size_t)k * nrhs), h2((size_t)k * nrhs);
     QD_CUDA(cudaMemcpyAsync(h1.data(), m1.as<qd::cplx>(), h1.size() * sizeof(qd::cplx), cudaMemcpyDeviceToHost,
                             defl->ctx->stream));
@@ -507,6 +510,56 @@ int qd_deflate_coeffs(qd_defl* defl, int nrhs, const double* z, double* ZhV, dou
   });
 }
 
+// Host outputs of one estimator call (shared by the single and batched forms).
+static void fill_trace_result(qd_trace_result* result, const qd_defl* defl, const qd::TraceOut& out,
+                              const std::vector<qd::cplx>& M1, const std::vector<qd::cplx>& M2, int s, bool coeffs) {
+  result->t0[0] = defl ? defl->t0[0] : 0.0;
+  result->t0[1] = defl ? defl->t0[1] : 0.0;
+  result->mean[0] = out.stats[0];
+  result->mean[1] = out.stats[1];
+  result->estimate[0] = result->t0[0] + out.stats[0];
+  result->estimate[1] = result->t0[1] + out.stats[1];
+  result->var = out.stats[2];
+  result->var_re = out.stats[3];
+  result->stderr_mean = out.stats[4];
+  result->var_jackknife_err = out.stats[5];
+  result->nsamples = s;
+  result->iterations = out.info.iterations;
+  result->max_true_rel_residual = out.info.max_rel;
+  if (result->t_samples)
+    for (int j = 0; j < s; ++j) {
+      result->t_samples[2 * j] = out.t[j].x;
+      result->t_samples[2 * j + 1] = out.t[j].y;
+    }
+  if (coeffs) {
+    const int k = defl->p.k;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < s; ++j) {
+        const qd::cplx a = M1[(size_t)i * s + j], b = M2[(size_t)i * s + j];
+        if (result->ZhV) {
+          result->ZhV[2 * ((size_t)j * k + i)] = a.x;
+          result->ZhV[2 * ((size_t)j * k + i) + 1] = -a.y;
+        }
+        if (result->UhKZ) {
+          result->UhKZ[2 * ((size_t)i * s + j)] = b.x;
+          result->UhKZ[2 * ((size_t)i * s + j) + 1] = b.y;
+        }
+      }
+  }
+}
+
+// One estimator call on ctx; returns whether every sample converged.
+static bool run_trace(qd_ctx& ctx, const qd_gauge& gauge, qd_mg* mg, qd_defl* defl, double m0, double tau,
+                      const qd_trace_params& params, qd_trace_result* result) {
+  QD_REQUIRE(params.nsamples >= 1, "nsamples must be >= 1");
+  qd::TraceOut out;
+  std::vector<qd::cplx> M1, M2;
+  const bool coeffs = defl && defl->kind == QD_DEFL_MG_OBLIQUE && (result->ZhV || result->UhKZ);
+  qd::hutchinson(ctx, gauge, mg, defl, m0, tau, params, coeffs, out, &M1, &M2);
+  fill_trace_result(result, defl, out, M1, M2, params.nsamples, coeffs);
+  return out.info.converged >= params.nsamples;
+}
+
 int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, qd_defl* defl, double m0, double tau,
                         const qd_trace_params* params, qd_trace_result* result) {
   int not_conv = 0;
@@ -516,49 +569,104 @@ int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, qd_defl* 
     NONNULL(params);
     NONNULL(result);
     set_device(ctx);
-    qd::TraceOut out;
-    std::vector<qd::cplx> M1, M2;
-    const bool coeffs = defl && defl->kind == QD_DEFL_MG_OBLIQUE && (result->ZhV || result->UhKZ);
-    qd::hutchinson(*ctx, *gauge, mg, defl, m0, tau, *params, coeffs, out, &M1, &M2);
-    const int s = params->nsamples;
-    result->t0[0] = defl ? defl->t0[0] : 0.0;
-    result->t0[1] = defl ? defl->t0[1] : 0.0;
-    result->mean[0] = out.stats[0];
-    result->mean[1] = out.stats[1];
-    result->estimate[0] = result->t0[0] + out.stats[0];
-    result->estimate[1] = result->t0[1] + out.stats[1];
-    result->var = out.stats[2];
-    result->var_re = out.stats[3];
-    result->stderr_mean = out.stats[4];
-    result->var_jackknife_err = out.stats[5];
-    result->nsamples = s;
-    result->iterations = out.info.iterations;
-    result->max_true_rel_residual = out.info.max_rel;
-    if (result->t_samples)
-      for (int j = 0; j < s; ++j) {
-        result->t_samples[2 * j] = out.t[j].x;
-        result->t_samples[2 * j + 1] = out.t[j].y;
-      }
-    if (coeffs) {
-      const int k = defl->p.k;
-      for (int i = 0; i < k; ++i)
-        for (int j = 0; j < s; ++j) {
-          const qd::cplx a = M1[(size_t)i * s + j], b = M2[(size_t)i * s + j];
-          if (result->ZhV) {
-            result->ZhV[2 * ((size_t)j * k + i)] = a.x;
-            result->ZhV[2 * ((size_t)j * k + i) + 1] = -a.y;
-          }
-          if (result->UhKZ) {
-            result->UhKZ[2 * ((size_t)i * s + j)] = b.x;
-            result->UhKZ[2 * ((size_t)i * s + j) + 1] = b.y;
-          }
-        }
-    }
-    not_conv = out.info.converged < s;
+    not_conv = !run_trace(*ctx, *gauge, mg, defl, m0, tau, *params, result);
   });
   if (rc == QD_OK && not_conv) {
     g_last_error = "a solve did not reach the tolerance within maxit";
     return QD_ERR_NOT_CONVERGED;
+  }
+  return rc;
+}
+
+// Lazily made FP32 copies (links, W, coarse operators, coarsest inverse)
+// are created on the object's own context; make them all before worker
+// threads read them from other streams.
+static void prewarm_fp32(qd_batch_item& it) {
+  const_cast<qd_gauge*>(it.gauge)->links_f32();
+  if (!it.mg) return;
+  for (int l = 0; l < it.mg->nlevels; ++l) it.mg->W<qd::cplxf>(l);
+  for (int l = 1; l <= it.mg->nlevels; ++l) it.mg->op<qd::cplxf>(l);
+  it.mg->Cinv<qd::cplxf>(it.mg->nlevels);
+}
+
+int qd_hutchinson_batch(qd_ctx* ctx, int nitems, qd_batch_item* items, int nstreams) {
+  std::vector<std::string> msgs;
+  int first_bad = -1;
+  int rc = guarded([&] {
+    NONNULL(ctx);
+    QD_REQUIRE(nitems >= 0, "nitems must be >= 0");
+    QD_REQUIRE(nitems == 0 || items != nullptr, "items must not be NULL");
+    QD_REQUIRE(nstreams >= 1 && nstreams <= 64, "nstreams must be in [1, 64]");
+    set_device(ctx);
+    for (int i = 0; i < nitems; ++i) {
+      NONNULL(items[i].gauge);
+      NONNULL(items[i].result);
+      QD_REQUIRE(items[i].params.nsamples >= 1, "nsamples must be >= 1");
+      for (int j = 0; j < i; ++j) {
+        QD_REQUIRE(!items[i].mg || items[i].mg != items[j].mg, "an mg handle appears in two batch items");
+        QD_REQUIRE(!items[i].defl || items[i].defl != items[j].defl, "a defl handle appears in two batch items");
+      }
+      items[i].status = QD_OK;
+    }
+    if (nitems == 0) return;
+    for (int i = 0; i < nitems; ++i) prewarm_fp32(items[i]);
+    QD_CUDA(cudaDeviceSynchronize());
+    // largest first (longest-processing-time order), dynamic hand-out
+    std::vector<int> order(nitems);
+    for (int i = 0; i < nitems; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return items[a].gauge->geo.nsites * (double)items[a].params.nsamples >
+             items[b].gauge->geo.nsites * (double)items[b].params.nsamples;
+    });
+    const int nw = std::min(nstreams, nitems);
+    std::vector<std::unique_ptr<qd_ctx>> workers(nw);
+    for (int w = 0; w < nw; ++w) {
+      workers[w].reset(new qd_ctx());
+      workers[w]->device = ctx->device;
+      QD_CUDA(cudaStreamCreateWithFlags(&workers[w]->stream, cudaStreamNonBlocking));
+      QD_CUDA(cudaMallocHost(&workers[w]->host_pinned, 64 * sizeof(int)));
+    }
+    msgs.assign(nitems, std::string());
+    std::atomic<int> next{0};
+    auto work = [&](qd_ctx* wc) {
+      cudaSetDevice(wc->device);
+      for (int k = next.fetch_add(1); k < nitems; k = next.fetch_add(1)) {
+        qd_batch_item& it = items[order[k]];
+        try {
+          const bool ok = run_trace(*wc, *it.gauge, it.mg, it.defl, it.m0, it.tau, it.params, it.result);
+          it.status = ok ? QD_OK : QD_ERR_NOT_CONVERGED;
+          if (!ok) msgs[order[k]] = "a solve did not reach the tolerance within maxit";
+        } catch (const qd::Error& e) {
+          it.status = e.code;
+          msgs[order[k]] = e.what();
+        } catch (const std::exception& e) {
+          it.status = QD_ERR_INTERNAL;
+          msgs[order[k]] = e.what();
+        }
+      }
+    };
+    std::vector<std::thread> threads;
+    for (int w = 1; w < nw; ++w) threads.emplace_back(work, workers[w].get());
+    work(workers[0].get());
+    for (std::thread& t : threads) t.join();
+    for (auto& wc : workers) {
+      cudaStreamSynchronize(wc->stream);
+      cudaFreeHost(wc->host_pinned);
+      wc->host_pinned = nullptr;
+      cudaStreamDestroy(wc->stream);
+      wc->stream = nullptr;
+    }
+    // first hard error, else first non-convergence
+    for (int pass = 0; pass < 2 && first_bad < 0; ++pass)
+      for (int i = 0; i < nitems; ++i)
+        if (items[i].status != QD_OK && (pass == 1 || items[i].status != QD_ERR_NOT_CONVERGED)) {
+          first_bad = i;
+          break;
+        }
+  });
+  if (rc == QD_OK && first_bad >= 0) {
+    g_last_error = msgs[first_bad];
+    return items[first_bad].status;
   }
   return rc;
 }

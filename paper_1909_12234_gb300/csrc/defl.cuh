@@ -45,8 +45,9 @@ namespace qd {
 
 void defl_build(qd_defl& d, const double* injected);
 void defl_set_rank(qd_defl& d, int r);
-void defl_project(qd_defl& d, int s, const cplx* z, cplx* out);
-void defl_coeffs(qd_defl& d, int s, const cplx* z, cplx* M1, cplx* M2);
+// Launches go to ctx (the caller's stream), not to the context d was built on.
+void defl_project(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* out);
+void defl_coeffs(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* M1, cplx* M2);
 // Algorithm 1 projection with scratch in a fixed device array (noalloc.cu).
 void defl_project_static(qd_defl& d, int s, const cplx* z, cplx* out);
 void blockmul_identity_cols(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int r, cplx* Y);

@@ -234,8 +234,7 @@ void defl_set_rank(qd_defl& d, int r) {
 }
 
 // c = W^H z with the composite W = W_0 ... W_{L-1} (L = d.level), s columns
-static void restrict_chain(qd_defl& d, int s, const cplx* z, cplx* c) {
-  qd_ctx& ctx = *d.ctx;
+static void restrict_chain(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* c) {
   const cplx* src = z;
   DevBuf tmp[2];
   for (int l = 0; l < d.level; ++l) {
@@ -251,8 +250,7 @@ static void restrict_chain(qd_defl& d, int s, const cplx* z, cplx* c) {
 }
 
 // f = W c with the composite W, s columns
-static void prolong_chain(qd_defl& d, int s, const cplx* c, cplx* f) {
-  qd_ctx& ctx = *d.ctx;
+static void prolong_chain(qd_ctx& ctx, qd_defl& d, int s, const cplx* c, cplx* f) {
   const cplx* src = c;
   DevBuf tmp[2];
   for (int l = d.level - 1; l >= 0; --l) {
@@ -268,8 +266,7 @@ static void prolong_chain(qd_defl& d, int s, const cplx* c, cplx* f) {
 }
 
 // out = (I - P) z, s columns
-void defl_project(qd_defl& d, int s, const cplx* z, cplx* out) {
-  qd_ctx& ctx = *d.ctx;
+void defl_project(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* out) {
   const int r = d.rank;
   const int64_t nf = d.gauge->geo.nsites * 12;
   DevBuf a((size_t)r * s * sizeof(cplx));
@@ -277,12 +274,12 @@ void defl_project(qd_defl& d, int s, const cplx* z, cplx* out) {
     const LevelGeom& cg = d.mg->geom(d.level);
     const int dc = d.mg->dof(d.level);
     DevBuf c((size_t)d.nb * s * sizeof(cplx)), gc((size_t)d.nb * s * sizeof(cplx)), f((size_t)nf * s * sizeof(cplx));
-    restrict_chain(d, s, z, c.as<cplx>());
+    restrict_chain(ctx, d, s, z, c.as<cplx>());
     blas::gamma5(ctx, cg.nsites, dc, s, c.as<cplx>(), gc.as<cplx>());
     blockdot(ctx, d.nb, d.U.as<cplx>(), r, r, gc.as<cplx>(), s, s, a.as<cplx>());  // U^H g5 W^H z
     scale_rows_inv(ctx, r, s, d.lam.as<double>(), a.as<cplx>());                  // Lambda^{-1}
     blockmul(ctx, d.nb, d.U.as<cplx>(), r, r, a.as<cplx>(), s, s, c.as<cplx>(), s, 1.0, 0.0);  // U (.)
-    prolong_chain(d, s, c.as<cplx>(), f.as<cplx>());                              // W (.)
+    prolong_chain(ctx, d, s, c.as<cplx>(), f.as<cplx>());                              // W (.)
     // out = z - A W U Lambda^{-1} U^H g5 W^H z (fused residual kernel)
     wilson_apply<cplx>(ctx, d.gauge->geo, d.gauge->links.as<cplx>(), d.m0, d.tau, false, f.as<cplx>(), out, s, z);
   } else {
@@ -293,13 +290,12 @@ void defl_project(qd_defl& d, int s, const cplx* z, cplx* out) {
 }
 
 // Sec. 2.2 matrices (kind 2): M1 = U_bar^H W^H Z (k x s), M2 = U_bar^H g5 W^H Z.
-void defl_coeffs(qd_defl& d, int s, const cplx* z, cplx* M1, cplx* M2) {
-  qd_ctx& ctx = *d.ctx;
+void defl_coeffs(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* M1, cplx* M2) {
   QD_REQUIRE(d.kind == QD_DEFL_MG_OBLIQUE, "a-posteriori coefficients are defined for Algorithm 2");
   const int k = d.p.k;
   const LevelGeom& cg = d.mg->geom(d.level);
   DevBuf c((size_t)d.nb * s * sizeof(cplx)), gc((size_t)d.nb * s * sizeof(cplx));
-  restrict_chain(d, s, z, c.as<cplx>());
+  restrict_chain(ctx, d, s, z, c.as<cplx>());
   blas::gamma5(ctx, cg.nsites, d.mg->dof(d.level), s, c.as<cplx>(), gc.as<cplx>());
   blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, c.as<cplx>(), s, s, M1);
   blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, gc.as<cplx>(), s, s, M2);

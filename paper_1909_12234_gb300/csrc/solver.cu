@@ -194,7 +194,9 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
   QD_CUDA(cudaMemcpyAsync(rn2, bn2, nrhs * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx.stream));
   QD_CUDA(cudaMemsetAsync(iters, 0, nrhs * sizeof(int), ctx.stream));
   const blas::Sweep sw = blas::sweep(n, nrhs);
-  ctx.red_partials.resize((size_t)sw.grid.x * nrhs * sizeof(cplx));
+  // room for the largest Gram-Schmidt reduction of a cycle up front, so that
+  // the buffer keeps its address through the solve
+  ctx.red_partials.resize((size_t)sw.grid.x * (restart > 2 ? restart : 2) * nrhs * sizeof(cplx));
   int its = 0;
   int hflags[2];
   // tol <= 0: exactly maxit iterations and no host synchronisation (columns
@@ -390,8 +392,13 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
   std::vector<const void*> cur;
   buffers(cur);
   cur.push_back(ctx.red_partials.as<void>());
+  cur.push_back(reinterpret_cast<const void*>(ctx.red_partials.bytes()));
   cur.push_back(reinterpret_cast<const void*>(ctx.stream));
-  if (!graphs_.empty() && (graphs_.front().ptrs != cur || graphs_.front().nrhs != nrhs)) drop_graphs();
+  if (!graphs_.empty() && (graphs_.front().ptrs != cur || graphs_.front().nrhs != nrhs)) {
+    // another context or a reallocated buffer: run eagerly once more first
+    drop_graphs();
+    warm_nrhs_ = -1;
+  }
   for (Graph& g : graphs_) {
     if (g.r == r && g.z == z) {
       QD_CUDA(cudaGraphLaunch(g.exec, ctx.stream));

@@ -163,7 +163,7 @@ void hutchinson(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, qd_defl* d, double m0
   rademacher_fill(ctx, g.geo, p.seed, p.sample_offset, s, Z);
   // a8: deflated right-hand sides
   if (d)
-    defl_project(*d, s, Z, B);
+    defl_project(ctx, *d, s, Z, B);
   else
     blas::copy(ctx, n * s, Z, B);
   // a5/a6: solves
@@ -177,7 +177,7 @@ void hutchinson(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, qd_defl* d, double m0
   if (want_coeffs && d && d->kind == QD_DEFL_MG_OBLIQUE) {
     const int k = d->p.k;
     DevBuf m1((size_t)k * s * sizeof(cplx)), m2((size_t)k * s * sizeof(cplx));
-    defl_coeffs(*d, s, Z, m1.as<cplx>(), m2.as<cplx>());
+    defl_coeffs(ctx, *d, s, Z, m1.as<cplx>(), m2.as<cplx>());
     M1->resize((size_t)k * s);
     M2->resize((size_t)k * s);
     QD_CUDA(cudaMemcpyAsync(M1->data(), m1.as<cplx>(), (size_t)k * s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));

@@ -110,6 +110,12 @@ class TraceResult(ctypes.Structure):
                 ("UhKZ", ctypes.POINTER(ctypes.c_double))]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("gauge", ctypes.c_void_p), ("mg", ctypes.c_void_p), ("defl", ctypes.c_void_p),
+                ("m0", ctypes.c_double), ("tau", ctypes.c_double), ("params", TraceParams),
+                ("result", ctypes.POINTER(TraceResult)), ("status", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -151,6 +157,7 @@ SIGNATURES = {
     "qd_deflate_project": (_I, [_P, _I, _P, _P]),
     "qd_deflate_project_static": (_I, [_P, _I, _P, _P]),
     "qd_deflate_coeffs": (_I, [_P, _I, _P, _DPTR, _DPTR]),
+    "qd_hutchinson_batch": (_I, [_P, _I, ctypes.POINTER(BatchItem), _I]),
     "qd_hutchinson_trace": (_I, [_P, _P, _P, _P, _D, _D, ctypes.POINTER(TraceParams),
                                  ctypes.POINTER(TraceResult)]),
     "qd_trace_stats": (_I, [_P, _I, _P, _DPTR, ctypes.POINTER(TraceResult)]),
@@ -513,35 +520,77 @@ def prof_read(ctx, kind, reset=False):
     return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
 
 
+class _TraceOut:
+    """Host buffers of one qd_trace_result and their conversion to a dict."""
+
+    def __init__(self, defl, nsamples, want_samples, want_coeffs):
+        self.r = TraceResult()
+        self.ts = np.zeros((nsamples, 2)) if want_samples else None
+        k = defl.params.k if defl is not None else 0
+        self.zhv = np.zeros((nsamples, k, 2)) if want_coeffs and k else None
+        self.uhkz = np.zeros((k, nsamples, 2)) if want_coeffs and k else None
+        self.r.t_samples = self.ts.ctypes.data_as(_DPTR) if self.ts is not None else None
+        self.r.ZhV = self.zhv.ctypes.data_as(_DPTR) if self.zhv is not None else None
+        self.r.UhKZ = self.uhkz.ctypes.data_as(_DPTR) if self.uhkz is not None else None
+
+    def as_dict(self, rc):
+        r = self.r
+        out = {
+            "status": rc,
+            "t0": complex(r.t0[0], r.t0[1]),
+            "mean": complex(r.mean[0], r.mean[1]),
+            "estimate": complex(r.estimate[0], r.estimate[1]),
+            "var": r.var, "var_re": r.var_re, "stderr": r.stderr_mean,
+            "var_jackknife_err": r.var_jackknife_err, "iterations": r.iterations,
+            "max_true_rel_residual": r.max_true_rel_residual, "s": r.nsamples,
+        }
+        if self.ts is not None:
+            out["t"] = self.ts[:, 0] + 1j * self.ts[:, 1]
+        if self.zhv is not None:
+            out["ZhV"] = self.zhv[..., 0] + 1j * self.zhv[..., 1]
+            out["UhKZ"] = self.uhkz[..., 0] + 1j * self.uhkz[..., 1]
+        return out
+
+
 def hutchinson_trace(ctx, gauge, mg, defl, m0, tau, seed, sample_offset, nsamples, tol, maxit=10000,
                      restart=16, want_samples=True, want_coeffs=False, allow_not_converged=False,
                      precision=QD_PREC_F64, **kw):
     """One multi-RHS batch of the deflated estimator; returns a dict."""
     p = TraceParams(int(seed), int(sample_offset), int(nsamples), solver_params(tol, maxit, restart, precision, **kw))
-    r = TraceResult()
-    ts = np.zeros((nsamples, 2)) if want_samples else None
-    k = defl.params.k if defl is not None else 0
-    zhv = np.zeros((nsamples, k, 2)) if want_coeffs and k else None
-    uhkz = np.zeros((k, nsamples, 2)) if want_coeffs and k else None
-    r.t_samples = ts.ctypes.data_as(_DPTR) if ts is not None else None
-    r.ZhV = zhv.ctypes.data_as(_DPTR) if zhv is not None else None
-    r.UhKZ = uhkz.ctypes.data_as(_DPTR) if uhkz is not None else None
+    o = _TraceOut(defl, nsamples, want_samples, want_coeffs)
     rc = load().qd_hutchinson_trace(ctx.h, gauge.h, mg.h if mg is not None else None,
                                     defl.h if defl is not None else None, float(m0), float(tau),
-                                    ctypes.byref(p), ctypes.byref(r))
+                                    ctypes.byref(p), ctypes.byref(o.r))
     _check(rc, allow=(QD_ERR_NOT_CONVERGED,) if allow_not_converged else ())
-    out = {
-        "status": rc,
-        "t0": complex(r.t0[0], r.t0[1]),
-        "mean": complex(r.mean[0], r.mean[1]),
-        "estimate": complex(r.estimate[0], r.estimate[1]),
-        "var": r.var, "var_re": r.var_re, "stderr": r.stderr_mean,
-        "var_jackknife_err": r.var_jackknife_err, "iterations": r.iterations,
-        "max_true_rel_residual": r.max_true_rel_residual, "s": r.nsamples,
-    }
-    if ts is not None:
-        out["t"] = ts[:, 0] + 1j * ts[:, 1]
-    if zhv is not None:
-        out["ZhV"] = zhv[..., 0] + 1j * zhv[..., 1]
-        out["UhKZ"] = uhkz[..., 0] + 1j * uhkz[..., 1]
-    return out
+    return o.as_dict(rc)
+
+
+_BATCH_KEYS = ("gauge", "mg", "defl", "m0", "tau", "seed", "sample_offset", "nsamples", "tol", "maxit", "restart",
+               "precision", "want_samples")
+
+
+def hutchinson_batch(ctx, problems, nstreams=4, allow_not_converged=False):
+    """Independent estimators solved concurrently (qd_hutchinson_batch).
+
+    ``problems``: dicts with gauge, mg, defl, m0, tau, seed, sample_offset,
+    nsamples, tol and optional maxit, restart, precision, want_samples and
+    solver keywords.  Returns one result dict per problem, in order."""
+    n = len(problems)
+    items = (BatchItem * max(n, 1))()
+    outs = []
+    for i, pr in enumerate(problems):
+        kw = {k: v for k, v in pr.items() if k not in _BATCH_KEYS}
+        sp = solver_params(pr["tol"], pr.get("maxit", 10000), pr.get("restart", 16),
+                           pr.get("precision", QD_PREC_F64), **kw)
+        o = _TraceOut(pr.get("defl"), pr["nsamples"], pr.get("want_samples", True), False)
+        outs.append(o)
+        items[i].gauge = pr["gauge"].h.value
+        items[i].mg = pr["mg"].h.value if pr.get("mg") is not None else None
+        items[i].defl = pr["defl"].h.value if pr.get("defl") is not None else None
+        items[i].m0 = float(pr["m0"])
+        items[i].tau = float(pr.get("tau", 0.0))
+        items[i].params = TraceParams(int(pr["seed"]), int(pr.get("sample_offset", 0)), int(pr["nsamples"]), sp)
+        items[i].result = ctypes.pointer(o.r)
+    rc = load().qd_hutchinson_batch(ctx.h, n, items, int(nstreams))
+    _check(rc, allow=(QD_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return [outs[i].as_dict(items[i].status) for i in range(n)]

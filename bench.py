@@ -49,10 +49,24 @@ WORKLOADS = {
     "config2": dict(WL),
     "config3": dict(
         workload="wilson-dirac 16^3x32 eps0.2 seed3 m0=-0.8, 3-level MG (2^4, 2^4; nv 12, 16), Algorithm 2 "
-                 "k=24, 128 Rademacher samples/step, true FP64 rel. residual 1e-8",
+                 "k=24 (level-1 GCR 6 its), 128 Rademacher samples/step, true FP64 rel. residual 1e-8",
         dims=(16, 16, 16, 32), eps=0.2, link_seed=3, m0=-0.8, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16],
-        k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=16, maxit=500, inner_tol=1e-5),
+        k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=16, maxit=500, inner_tol=1e-5,
+        mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6}),
 }
+# Config 4: an uneven batch solved concurrently (qd_hutchinson_batch):
+# (lattice, m0, samples) = (8^4, -0.6, 16), (12^4, -0.75, 48), (16^4, -0.8,
+# 96); eps 0.2 links (seeds 4, 5, 6), three-level MG (2^4, 2^4; nv 12, 16)
+# with a fixed 6-iteration level-1 GCR so that each V-cycle is one graph,
+# Algorithm 2 k = 24, mixed precision to a true FP64 residual 1e-8.
+BATCH = dict(
+    workload="uneven batch: wilson-dirac 8^4 m0=-0.6 x16, 12^4 m0=-0.75 x48, 16^4 m0=-0.8 x96 samples; eps0.2 "
+             "seeds 4-6; 3-level MG (2^4, 2^4; nv 12, 16; level-1 GCR 6 its); Algorithm 2 k=24; true FP64 rel. "
+             "residual 1e-8; one concurrent batch per step",
+    problems=[((8, 8, 8, 8), 4, -0.6, 16), ((12, 12, 12, 12), 5, -0.75, 48), ((16, 16, 16, 16), 6, -0.8, 96)],
+    eps=0.2, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16], mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6},
+    k=24, guard=16, tol=1e-8, restart=16, maxit=500, inner_tol=1e-5,
+)
 METRIC = "deflated Hutchinson samples/s @res 1e-8"
 UNIT = "samples/s"
 # Recipe peaks (MEASURED_PEAKS.json holds HBM and bf16; FP64 is the recipe's
@@ -119,7 +133,7 @@ class ClockSampler:
 
 def _setup(qd, ctx, U):
     g = qd.Gauge(ctx, WL["dims"], U)
-    mg = qd.Multigrid(ctx, g, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"]))
+    mg = qd.Multigrid(ctx, g, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"], **WL.get("mg_kw", {})))
     d = qd.Deflation(ctx, g, mg, WL["m0"], 0.0,
                      qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
                                     solve_tol=1e-10, maxit=60))
@@ -308,7 +322,9 @@ def run_ours(args):
     top = max(prof, key=lambda k: prof[k]["ms"])
     pt = prof[top]
     peaks = _peaks()
-    if top == "direct_f32":
+    if top in ("direct_f32", "coarse_f32"):
+        # dense contractions on FP32 CUDA cores (the multi-RHS coarse stencil
+        # does 8 * 9 * D^2 flops per site and right-hand side)
         fp32_peak = 70.0  # FMA-chain probe (2 flops per FMA), 152 SMs at ~2 GHz
         achieved = pt["flops"] / (pt["ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -342,7 +358,7 @@ def run_ours(args):
     t = time.perf_counter()
     for i in range(e2e_steps):
         g2 = qd.Gauge.from_host_buffer(ctx, WL["dims"], pinned)
-        mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"]))
+        mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"], **WL.get("mg_kw", {})))
         d2 = qd.Deflation(ctx, g2, mg2, WL["m0"], 0.0,
                           qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
                                          solve_tol=1e-10, maxit=60))
@@ -414,6 +430,142 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Config 4: the uneven batch, concurrent (one qd_hutchinson_batch call
+    per step) against the same problems solved one after another."""
+    import torch
+    from paper_1909_12234_gb300 import qdtrace as qd
+    from paper_1909_12234_gb300 import synth
+
+    if int(os.environ.get("WORLD_SIZE", "1")) != 1 or args.gpus != 1:
+        raise SystemExit("the batch workload runs on one GPU")
+    qd.load()
+    ctx = qd.Context(0)
+    B = BATCH
+
+    def setup(pinned=None):
+        probs = []
+        for i, (dims, seed, m0, s) in enumerate(B["problems"]):
+            if pinned is None:
+                g = qd.Gauge(ctx, dims, synth.random_su3_links(dims, B["eps"], seed))
+            else:
+                g = qd.Gauge.from_host_buffer(ctx, dims, pinned[i])
+            mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(2, B["blocks"], B["nvs"], **B["mg_kw"]))
+            d = qd.Deflation(ctx, g, mg, m0, 0.0, qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, B["k"], guard=B["guard"],
+                                                                 eig_tol=1e-6, solve_tol=1e-10, maxit=60))
+            probs.append(dict(gauge=g, mg=mg, defl=d, m0=m0, tau=0.0, seed=100 + seed, sample_offset=0, nsamples=s,
+                              tol=B["tol"], maxit=B["maxit"], restart=B["restart"], precision=qd.QD_PREC_MIXED,
+                              inner_tol=B["inner_tol"], max_refine=10))
+        return probs
+
+    def close(probs):
+        for p in probs:
+            for key in ("defl", "mg", "gauge"):
+                p[key].close()
+
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    probs = setup()
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t
+    total = sum(p["nsamples"] for p in probs)
+
+    def step(i, concurrent):
+        for p in probs:
+            p["sample_offset"] = 1000 * i
+        if concurrent:
+            return qd.hutchinson_batch(ctx, probs, nstreams=len(probs))
+        keys = ("gauge", "mg", "defl", "m0", "tau", "seed", "sample_offset", "nsamples", "tol")
+        return [qd.hutchinson_trace(ctx, p["gauge"], p["mg"], p["defl"], p["m0"], 0.0, p["seed"], p["sample_offset"],
+                                    p["nsamples"], p["tol"], **{k: v for k, v in p.items() if k not in keys})
+                for p in probs]
+
+    def timed(concurrent, nsteps, first):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        res = [step(first + i, concurrent) for i in range(nsteps)]
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res
+
+    for i in range(args.warmup):
+        step(i, True)
+        step(i, False)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = qd.launch_count()
+    ms, res = timed(True, args.steps, args.warmup)
+    launches = qd.launch_count() - l0
+    clk = clocks.stop()
+    ms_seq, res_seq = timed(False, args.steps, args.warmup)
+    # the concurrent and the sequential runs solve the same samples: identical
+    same = all(np.array_equal(a["t"], b["t"]) for ra, rb in zip(res, res_seq) for a, b in zip(ra, rb))
+    worst = max(r["max_true_rel_residual"] for rr in res for r in rr)
+
+    # per-kernel device time of the sequential form (profiling is per context)
+    qd.prof_enable(ctx, True)
+    for k in qd.PROF_KINDS:
+        qd.prof_read(ctx, k, reset=True)
+    ms_prof, _ = timed(False, 1, 5000)
+    qd.prof_enable(ctx, False)
+    prof = {k: qd.prof_read(ctx, k) for k in qd.PROF_KINDS}
+    top = max(prof, key=lambda k: prof[k]["ms"])
+    pt = prof[top]
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    if top.endswith("f64") or top in ("direct_f32", "coarse_f32"):
+        peak = FP64_PEAK_TFLOPS if top.endswith("f64") else 70.0
+        ach = pt["flops"] / (pt["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak}
+    else:
+        ach = pt["bytes"] / (pt["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm}
+    roof.update({"traffic": None, "kernel": top, "launches": pt["launches"],
+                 "ms_per_launch": pt["ms"] / max(pt["launches"], 1)})
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share_of_step": round(v["ms"] / ms_prof, 4)}
+               for k, v in prof.items() if v["launches"]}
+
+    # end to end: links from pinned host memory, setup of all three, one batch
+    pinned = []
+    for dims, seed, m0, s in B["problems"]:
+        U = synth.random_su3_links(dims, B["eps"], seed)
+        canon = np.ascontiguousarray(np.transpose(U, (1, 0, 2, 3)))
+        pinned.append(torch.from_numpy(canon.view(np.float64).reshape(-1)).pin_memory())
+    e2e = None
+    if args.e2e_steps:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for i in range(args.e2e_steps):
+            pr2 = setup(pinned)
+            for p in pr2:
+                p["sample_offset"] = 7000 + 1000 * i
+            qd.hutchinson_batch(ctx, pr2, nstreams=len(pr2))
+            close(pr2)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t) / args.e2e_steps
+        e2e = {"value": total / dt, "unit": UNIT, "h2d_bytes_per_step": sum(p.numel() * 8 for p in pinned),
+               "d2h_bytes_per_step": total * 16 + 6 * 8 * len(probs),
+               "scope": "per step: link upload of the three lattices, their setups, one concurrent batch"}
+    tune = qd.autotune_report()
+    line = {
+        "metric": METRIC, "value": args.steps * total / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 inner solves + f64 refinement", "data": "synthetic",
+        "config": {"workload": B["workload"], "precision": "mixed", "parallelism": "one batch, 3 worker streams",
+                   "l2": "16^4 fields (0.8-1.6 GB) exceed L2", "setup_s": round(setup_s, 3),
+                   "max_true_rel_residual": worst, "bit_identical_to_sequential": same,
+                   "sequential": {"value": args.steps * total / (ms_seq / 1e3), "ms_per_step": ms_seq / args.steps},
+                   "estimates": [[r["estimate"].real, r["stderr"]] for r in res[-1]],
+                   "autotune": {k: v[0] for k, v in tune.items()}},
+        "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    close(probs)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,10 +578,19 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--prof-steps", type=int, default=2)
-    ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS) + ["config4"])
+    ap.add_argument("--fixed-coarse", type=int, default=0,
+                    help="> 0: level-1 GCR of a three-level hierarchy runs exactly this many iterations")
     args = ap.parse_args()
+    if args.workload == "config4":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-lattice workload"}))
+            return 0
+        return run_batch(args)
     WL.clear()
     WL.update(WORKLOADS[args.workload] if args.workload != "config2" else dict(WORKLOADS["config2"]))
+    if args.fixed_coarse > 0:
+        WL["mg_kw"] = {"coarse_tol": 0.0, "coarse_maxit": args.fixed_coarse}
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -437,6 +437,25 @@ int qd_hutchinson_batch(qd_ctx* ctx, int nitems, qd_batch_item* items,
                         int nstreams);
 
 /* ------------------------------------------------------------------------ */
+/* Launch-shape autotuner (the paper has no counterpart)                     */
+/* ------------------------------------------------------------------------ */
+
+/* mode 1 (default): the first call of a tunable kernel for a new problem
+ * shape times each valid launch shape on the caller's stream and keeps the
+ * fastest for the rest of the process (coarse stencil: rows per thread and
+ * block width; FP32 Wilson: one or two right-hand sides per thread).  All
+ * coarse-stencil shapes give bit-identical results; the Wilson shapes agree
+ * to FP32 rounding.  mode 0: fixed defaults, nothing timed.  Process-wide. */
+void qd_autotune_set(int mode);
+/* Clear the stored choices. */
+void qd_autotune_clear(void);
+/* The table as text, one line per shape key: the key, the chosen candidate,
+ * then each candidate's best time in ms (-1: not applicable).  Writes at most
+ * len bytes (NUL-terminated) to buf (nullable) and returns the full length
+ * including the NUL. */
+int qd_autotune_report(char* buf, int len);
+
+/* ------------------------------------------------------------------------ */
 /* Kernel timing (measurement support; the paper has no counterpart)         */
 /* ------------------------------------------------------------------------ */
 

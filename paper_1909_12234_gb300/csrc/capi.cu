@@ -10,6 +10,7 @@
 #include "defl.cuh"
 #include "direct.cuh"
 #include "tc_gemm.cuh"
+#include "tune.cuh"
 
 
 static thread_local std::string g_last_error;
@@ -696,6 +697,18 @@ int qd_trace_stats(qd_ctx* ctx, int s, const double* t, const double t0[2], qd_t
     result->var_jackknife_err = h[5];
     result->nsamples = s;
   });
+}
+
+void qd_autotune_set(int mode) { qd::tune_set_mode(mode); }
+void qd_autotune_clear(void) { qd::tune_clear(); }
+int qd_autotune_report(char* buf, int len) {
+  const std::string r = qd::tune_report();
+  if (buf && len > 0) {
+    const size_t n = std::min((size_t)(len - 1), r.size());
+    std::memcpy(buf, r.data(), n);
+    buf[n] = '\0';
+  }
+  return (int)r.size() + 1;
 }
 
 long long qd_launch_count(void) { return qd::launch_counter().load(); }

@@ -6,6 +6,8 @@
 //   * the Galerkin coarse operator C = W^H A W as a 9-point block stencil,
 //     and its application.
 #include <atomic>
+#include <string>
+#include "tune.cuh"
 #include "qd_internal.cuh"
 
 namespace qd {
@@ -300,7 +302,8 @@ __global__ void __launch_bounds__(256) k_coarse_apply_tiled(int D, int ld, int n
 // Launch the tiled kernel for rows-per-thread RB when D is a multiple of it;
 // returns false (nothing launched) when the staged blocks would not fit.
 template <class C, int RB>
-static bool coarse_tiled_launch(qd_ctx& ctx, const CoarseLevel& lv, const C* mat, const C* in, C* out, int nrhs) {
+static bool coarse_tiled_launch(qd_ctx& ctx, const CoarseLevel& lv, const C* mat, const C* in, C* out, int nrhs,
+                                int tpg_cap = 256) {
   const int D = lv.D;
   if (D % RB != 0) return false;
   const int ngroups = D / RB;
@@ -314,7 +317,8 @@ static bool coarse_tiled_launch(qd_ctx& ctx, const CoarseLevel& lv, const C* mat
   // 16-byte aligned fields
   if (NR == 2 && ((nrhs & 1) || ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15)))
     return false;
-  const int cap = (256 / ngroups) / 32 * 32;
+  int cap = (256 / ngroups) / 32 * 32;
+  if (cap > tpg_cap) cap = tpg_cap;
   if (cap < 32) return false;
   int tpg = div_up(div_up(nrhs, NR), 32) * 32;
   if (tpg > cap) tpg = cap;
@@ -343,13 +347,32 @@ void coarse_apply(qd_ctx& ctx, const CoarseLevel& lv, const C* mat, const C* in,
   const double cb = (double)sizeof(C);
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_COARSE_F64 : QD_PROF_COARSE_F32, 72.0 * lv.D * (double)tot,
                cb * (double)lv.geo.nsites * (9.0 * lv.D * lv.D + 2.0 * lv.D * nrhs));
-  if (coarse_tiled_launch<C, 12>(ctx, lv, mat, in, out, nrhs) || coarse_tiled_launch<C, 16>(ctx, lv, mat, in, out, nrhs) ||
-      coarse_tiled_launch<C, 8>(ctx, lv, mat, in, out, nrhs) || coarse_tiled_launch<C, 6>(ctx, lv, mat, in, out, nrhs) ||
-      coarse_tiled_launch<C, 4>(ctx, lv, mat, in, out, nrhs))
-    return;
-  k_coarse_apply<C><<<div_up(tot, 128) < 64 * kNumSMs ? div_up(tot, 128) : 64 * kNumSMs, 128, 0, ctx.stream>>>(
-      lv.geo.nsites, lv.D, nrhs, lv.geo.nbr.as<int>(), mat, in, out);
-  QD_LAUNCH_CHECK();
+  // candidates: rows per thread 12, 16, 8, 6, 4 with the widest block, then
+  // the same with 32 threads per row group (more, smaller blocks), then the
+  // one-thread-per-output kernel; all sum every output in the same order,
+  // so the choice changes the time, never the result
+  auto launch = [&](int c) -> bool {
+    const int cap = c < 5 ? 256 : 32;
+    switch (c % 5 + (c == 10 ? 5 : 0)) {
+      case 0: return coarse_tiled_launch<C, 12>(ctx, lv, mat, in, out, nrhs, cap);
+      case 1: return coarse_tiled_launch<C, 16>(ctx, lv, mat, in, out, nrhs, cap);
+      case 2: return coarse_tiled_launch<C, 8>(ctx, lv, mat, in, out, nrhs, cap);
+      case 3: return coarse_tiled_launch<C, 6>(ctx, lv, mat, in, out, nrhs, cap);
+      case 4: return coarse_tiled_launch<C, 4>(ctx, lv, mat, in, out, nrhs, cap);
+      default:
+        k_coarse_apply<C><<<div_up(tot, 128) < 64 * kNumSMs ? div_up(tot, 128) : 64 * kNumSMs, 128, 0, ctx.stream>>>(
+            lv.geo.nsites, lv.D, nrhs, lv.geo.nbr.as<int>(), mat, in, out);
+        QD_LAUNCH_CHECK();
+        return true;
+    }
+  };
+  const std::string key = std::string("coarse_stencil f") + std::to_string(8 * sizeof(C) / 2) + " D" +
+                          std::to_string(lv.D) + " sites" + std::to_string(lv.geo.nsites) + " rhs" +
+                          std::to_string(nrhs);
+  const int c = in == out ? -1 : tune_pick(ctx, key, 11, launch);
+  if (c >= 0 && launch(c)) return;
+  for (int d = 0; d < 11; ++d)
+    if (launch(d)) return;
 }
 template void coarse_apply<cplx>(qd_ctx&, const CoarseLevel&, const cplx*, const cplx*, cplx*, int);
 template void coarse_apply<cplxf>(qd_ctx&, const CoarseLevel&, const cplxf*, const cplxf*, cplxf*, int);

@@ -12,7 +12,10 @@
 // (1 + s gamma) psi = (s B h', h') with h' = lo + s B^H up.  So each hop moves
 // one half spinor h (2 spins x 3 colours) through the link: 2 SU(3) matvecs
 // instead of 4.
+#include <string>
+
 #include "qd_internal.cuh"
+#include "tune.cuh"
 
 namespace qd {
 
@@ -331,8 +334,13 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
   const int* nb = geo.nbr.as<int>();
   const int* vis = geo.visit.as<int>();
   const double mass = 4.0 + m0;
-  if (sizeof(C) == 8 && (nrhs % 2) == 0 &&
-      ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) {
+  // candidate 0: two right-hand sides per thread (FP32, even nrhs, 16-byte
+  // aligned fields); candidate 1: one per thread.  The FP32 choice is tuned.
+  auto launch_x2 = [&]() -> bool {
+    if (!(sizeof(C) == 8 && (nrhs % 2) == 0 &&
+          ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(b)) &
+           15) == 0))
+      return false;
     const int64_t tot2 = geo.nsites * (nrhs / 2);
     const int blocks2 = div_up(tot2, threads);
     const float2* L = reinterpret_cast<const float2*>(links);
@@ -354,22 +362,36 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
                                                                           nullptr);
     }
     QD_LAUNCH_CHECK();
+    return true;
+  };
+  auto launch_x1 = [&]() -> bool {
+    if (b) {
+      if (dagger)
+        k_wilson<C, true, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out, b);
+      else
+        k_wilson<C, false, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out, b);
+    } else {
+      if (dagger)
+        k_wilson<C, true, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out,
+                                                                     nullptr);
+      else
+        k_wilson<C, false, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out,
+                                                                      nullptr);
+    }
+    QD_LAUNCH_CHECK();
+    return true;
+  };
+  if (sizeof(C) == 16) {
+    launch_x1();
     return;
   }
-  if (b) {
-    if (dagger)
-      k_wilson<C, true, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out, b);
-    else
-      k_wilson<C, false, true><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out, b);
-  } else {
-    if (dagger)
-      k_wilson<C, true, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out,
-                                                                   nullptr);
-    else
-      k_wilson<C, false, false><<<blocks, threads, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, mass, tau, in, out,
-                                                                    nullptr);
-  }
-  QD_LAUNCH_CHECK();
+  auto launch = [&](int c) -> bool { return c == 0 ? launch_x2() : launch_x1(); };
+  // the residual form writes out = b - A in: out-of-place, safe to repeat
+  const std::string key = std::string("wilson f32 sites") + std::to_string(geo.nsites) + " rhs" +
+                          std::to_string(nrhs) + (b ? " resid" : "") + (dagger ? " dag" : "");
+  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 2, launch);
+  if (c >= 0 && launch(c)) return;
+  if (!launch_x2()) launch_x1();
 }
 
 template void wilson_apply<cplx>(qd_ctx&, const LevelGeom&, const cplx*, double, double, bool,

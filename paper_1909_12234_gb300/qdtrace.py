@@ -157,6 +157,9 @@ SIGNATURES = {
     "qd_deflate_project": (_I, [_P, _I, _P, _P]),
     "qd_deflate_project_static": (_I, [_P, _I, _P, _P]),
     "qd_deflate_coeffs": (_I, [_P, _I, _P, _DPTR, _DPTR]),
+    "qd_autotune_set": (None, [_I]),
+    "qd_autotune_clear": (None, []),
+    "qd_autotune_report": (_I, [ctypes.c_char_p, _I]),
     "qd_hutchinson_batch": (_I, [_P, _I, ctypes.POINTER(BatchItem), _I]),
     "qd_hutchinson_trace": (_I, [_P, _P, _P, _P, _D, _D, ctypes.POINTER(TraceParams),
                                  ctypes.POINTER(TraceResult)]),
@@ -594,3 +597,35 @@ def hutchinson_batch(ctx, problems, nstreams=4, allow_not_converged=False):
     rc = load().qd_hutchinson_batch(ctx.h, n, items, int(nstreams))
     _check(rc, allow=(QD_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return [outs[i].as_dict(items[i].status) for i in range(n)]
+
+
+def autotune_set(mode):
+    load().qd_autotune_set(int(mode))
+
+
+def autotune_clear():
+    load().qd_autotune_clear()
+
+
+def autotune_report():
+    """{key: (choice, [ms per candidate])} of the launch-shape autotuner."""
+    n = load().qd_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(n)
+    load().qd_autotune_report(buf, n)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        parts = line.split(" ")
+        # key words, then the choice and the times
+        nums = []
+        while parts and _isnum(parts[-1]):
+            nums.insert(0, parts.pop())
+        out[" ".join(parts)] = (int(nums[0]), [float(x) for x in nums[1:]])
+    return out
+
+
+def _isnum(w):
+    try:
+        float(w)
+        return True
+    except ValueError:
+        return False

@@ -1,0 +1,63 @@
+"""The launch-shape autotuner: tuned coarse-stencil shapes give results
+bit-identical to the defaults; the tuned FP32 Wilson shape agrees with the
+default to FP32 rounding; the table records one choice per problem shape."""
+import numpy as np
+import pytest
+
+from paper_1909_12234_gb300 import synth
+
+from gpu_util import host, need_gpu, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qd():
+    need_gpu()
+    from paper_1909_12234_gb300 import qdtrace
+    qdtrace.load()
+    return qdtrace
+
+
+@pytest.fixture(scope="module")
+def ctx(qd):
+    return qd.Context(0)
+
+
+def test_autotuned_shapes_match_defaults(qd, ctx):
+    dims = (8, 8, 8, 8)
+    U = synth.random_su3_links(dims, 0.3, 2)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, -0.8, 0.0, qd.mg_params(2, [(2, 2, 2, 2), (2, 2, 2, 2)], [12, 16], null_maxit=20))
+    try:
+        for s in (64, 130, 7):
+            outs = {}
+            for mode in (0, 1):
+                qd.autotune_clear()
+                qd.autotune_set(mode)
+                for level in (1, 2):
+                    n = mg.level_info(level)[2] * mg.level_info(level)[1]
+                    x = torch.randn((n * s,), dtype=torch.complex64, device="cuda:0",
+                                    generator=torch.Generator("cuda:0").manual_seed(level))
+                    y = torch.empty_like(x)
+                    qd.coarse_apply_f32(mg, level, s, x, y)
+                    outs[(mode, level)] = host(y)
+                xf = torch.randn((g.V, 12, s), dtype=torch.complex64, device="cuda:0",
+                                 generator=torch.Generator("cuda:0").manual_seed(3))
+                yf = torch.empty_like(xf)
+                qd.dirac_apply_f32(ctx, g, -0.8, 0.0, False, s, xf, yf)
+                outs[(mode, "w")] = host(yf)
+                rep = qd.autotune_report()
+                if mode == 0:
+                    assert rep == {}
+                else:
+                    keys = [k for k in rep if k.startswith("coarse_stencil") and k.endswith(f"rhs{s}")]
+                    assert len(keys) == 2
+                    for k in keys:
+                        choice, ms = rep[k]
+                        assert len(ms) == 11 and ms[choice] > 0 and ms[choice] == min(m for m in ms if m > 0)
+            for level in (1, 2):
+                assert np.array_equal(outs[(0, level)], outs[(1, level)])
+            assert rel_err(outs[(1, "w")], outs[(0, "w")]) < 1e-6
+    finally:
+        qd.autotune_set(1)

@@ -28,6 +28,8 @@ Modules:
 * ``krylov``     GCR / minimal-residual solvers (Sec. 1 inexact solve, Sec. 2);
 * ``multigrid``  adaptive setup, blocking, W^H A W, V-cycle (Sec. 2);
 * ``deflation``  Algorithm 1 and Algorithm 2 deflation spaces and projectors;
+* ``smoother``   the learned gauge-covariant smoother (an extension; the paper
+                 has no counterpart) and its least-squares fit;
 * ``estimator``  the Hutchinson loop, t0 + t1, statistics and jackknife.
 
 Pinned functions are checked by ``tests/test_oracle_*.py`` against closed

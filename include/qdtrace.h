@@ -437,6 +437,56 @@ int qd_hutchinson_batch(qd_ctx* ctx, int nitems, qd_batch_item* items,
                         int nstreams);
 
 /* ------------------------------------------------------------------------ */
+/* Learned gauge-covariant smoother of the fine level (an extension of the  */
+/* V-cycle's smoothing step; the paper has no counterpart)                   */
+/* ------------------------------------------------------------------------ */
+/* (S r)(x)_{o,a} = sum_{d=0..8} sum_i w[d][o][i] (T_d r)(x)_{i,a}: T_0 = 1,
+ * T_{1+mu} r(x) = U_mu(x) r(x+mu), T_{5+mu} r(x) = U_mu(x-mu)^H r(x-mu),
+ * w[d] 4x4 spin matrices (144 complex weights; colour is moved only by the
+ * links, so S is gauge covariant).  With the smoother enabled the fine
+ * V-cycle smooths by z += S (r - A z) followed by mr_steps minimal-residual
+ * steps instead of smoother_steps plain ones; the FP32 V-cycle applies the
+ * weights rounded to FP16 with FP32 arithmetic. */
+
+typedef struct {
+  int nsamples;      /* training pairs; the held-out set has as many (8) */
+  double solve_tol;  /* relative residual of the solves e = A^{-1} r (1e-6) */
+  uint64_t seed;     /* Philox key of the random vectors (4242) */
+  int mr_steps;      /* minimal-residual steps after S in the V-cycle (2) */
+} qd_smoother_params;
+
+typedef struct {
+  double err_learned;  /* held-out mean ||e - x|| / ||e|| after S + mr_steps */
+  double err_plain;    /* the same after smoother_steps plain MR steps */
+  int enabled;         /* err_learned < err_plain: the V-cycle now uses S */
+} qd_smoother_info;
+
+void qd_smoother_params_default(qd_smoother_params* p);
+
+/* Train on pairs the solver generates: for random vectors v (Philox starts,
+ * key seed), r = v - A W C^{-1} W^H v is the residual the smoother sees and
+ * e = A^{-1} r (FP64 MG-preconditioned GCR to solve_tol); w minimises
+ * sum ||e - S r||^2 (linear least squares), then a held-out set judges S
+ * against the plain smoother and enables S only if it leaves a smaller
+ * error.  Synchronous. */
+int qd_smoother_train(qd_mg* mg, const qd_smoother_params* p, qd_smoother_info* info);
+
+/* Least-squares weights for caller pairs (device, fine qd layout, nrhs
+ * columns each); the enabled state is unchanged.  Synchronous. */
+int qd_smoother_fit(qd_mg* mg, int nrhs, const double* e, const double* r);
+
+/* Host weights w[9][4][4] (complex, 2 doubles each): set / read. */
+int qd_smoother_set_weights(qd_mg* mg, const double* w);
+int qd_smoother_get_weights(const qd_mg* mg, double* w);
+
+/* Use S in the V-cycle (enabled != 0, weights must be set) with mr_steps
+ * minimal-residual steps after it, or go back to the plain smoother. */
+int qd_smoother_enable(qd_mg* mg, int enabled, int mr_steps);
+
+/* out = S in, FP64, nrhs columns in fine qd layout.  Asynchronous. */
+int qd_smoother_apply(qd_mg* mg, int nrhs, const double* in, double* out);
+
+/* ------------------------------------------------------------------------ */
 /* Launch-shape autotuner (the paper has no counterpart)                     */
 /* ------------------------------------------------------------------------ */
 
@@ -480,7 +530,9 @@ enum {
   QD_PROF_DOTS_F32 = 12,    /* FP32 per-column reductions (Gram-Schmidt, smoother) */
   QD_PROF_AXPY_F32 = 13,    /* FP32 multi-vector updates (Gram-Schmidt) */
   QD_PROF_UPDATE_F32 = 14,  /* FP32 fused GCR / minimal-residual updates */
-  QD_PROF_NKINDS = 15
+  QD_PROF_SMOOTHER_F64 = 15,/* learned smoother S r, FP64 */
+  QD_PROF_SMOOTHER_F32 = 16,/* learned smoother S r, FP32 (FP16 weights) */
+  QD_PROF_NKINDS = 17
 };
 
 /* enable != 0: record a CUDA event pair on the context stream around every

@@ -699,6 +699,86 @@ int qd_trace_stats(qd_ctx* ctx, int s, const double* t, const double t0[2], qd_t
   });
 }
 
+void qd_smoother_params_default(qd_smoother_params* p) {
+  if (!p) return;
+  p->nsamples = 8;
+  p->solve_tol = 1e-6;
+  p->seed = 4242;
+  p->mr_steps = 2;
+}
+
+int qd_smoother_train(qd_mg* mg, const qd_smoother_params* p, qd_smoother_info* info) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(p);
+    QD_REQUIRE(p->solve_tol > 0.0 && p->solve_tol < 1.0, "solve_tol must be in (0, 1)");
+    set_device(mg->ctx);
+    double el = 0.0, ep = 0.0;
+    int en = 0;
+    qd::smoother_train(*mg, p->nsamples, p->solve_tol, p->seed, p->mr_steps, &el, &ep, &en);
+    if (info) {
+      info->err_learned = el;
+      info->err_plain = ep;
+      info->enabled = en;
+    }
+  });
+}
+
+int qd_smoother_fit(qd_mg* mg, int nrhs, const double* e, const double* r) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(e);
+    NONNULL(r);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    set_device(mg->ctx);
+    qd::smoother_fit(*mg, nrhs, reinterpret_cast<const qd::cplx*>(e), reinterpret_cast<const qd::cplx*>(r));
+  });
+}
+
+int qd_smoother_set_weights(qd_mg* mg, const double* w) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(w);
+    set_device(mg->ctx);
+    qd::smoother_set_weights(*mg, reinterpret_cast<const qd::cplx*>(w));
+  });
+}
+
+int qd_smoother_get_weights(const qd_mg* mg, double* w) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(w);
+    QD_REQUIRE(mg->ls != nullptr, "no learned-smoother weights set");
+    std::memcpy(w, mg->ls->w.data(), 144 * sizeof(qd::cplx));
+  });
+}
+
+int qd_smoother_enable(qd_mg* mg, int enabled, int mr_steps) {
+  return guarded([&] {
+    NONNULL(mg);
+    QD_REQUIRE(mr_steps >= 0 && mr_steps <= 64, "mr_steps must be in [0, 64]");
+    QD_REQUIRE(!enabled || mg->ls != nullptr, "no learned-smoother weights set");
+    if (mg->ls) {
+      mg->ls->enabled = enabled != 0;
+      mg->ls->mr_steps = mr_steps;
+    }
+  });
+}
+
+int qd_smoother_apply(qd_mg* mg, int nrhs, const double* in, double* out) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    QD_REQUIRE(mg->ls != nullptr, "no learned-smoother weights set");
+    set_device(mg->ctx);
+    qd::smoother_apply<qd::cplx>(*mg->ctx, *mg, nrhs, reinterpret_cast<const qd::cplx*>(in),
+                                 reinterpret_cast<qd::cplx*>(out), false);
+  });
+}
+
 void qd_autotune_set(int mode) { qd::tune_set_mode(mode); }
 void qd_autotune_clear(void) { qd::tune_clear(); }
 int qd_autotune_report(char* buf, int len) {

@@ -67,8 +67,11 @@ template <class C> class MGPrecond : public Precond<C> {
   void apply(qd_ctx& ctx, const C* r, C* z, int nrhs) override;
   void buffers(std::vector<const void*>& v) const;
   bool sync_free() const;
+  // z = W C^{-1} W^H r only (no smoothing).
+  void coarse_correction(qd_ctx& ctx, const C* r, C* z, int nrhs);
 
  private:
+  void ensure_buffers(int nrhs);
   void body(qd_ctx& ctx, const C* r, C* z, int nrhs);
   void drop_graphs();
   qd_mg* mg_;
@@ -92,6 +95,27 @@ template <class C> class MGPrecond : public Precond<C> {
   cudaStream_t cap_stream_ = nullptr;  // capture only; nothing runs on it
 };
 
+// Learned gauge-covariant smoother of the fine level (an extension; the
+// paper has no counterpart): (S r)(x) = sum_d w_d (T_d r)(x), with T_0 the
+// identity, T_{1+mu} r(x) = U_mu(x) r(x+mu), T_{5+mu} r(x) = U_mu(x-mu)^H
+// r(x-mu), and w_d 4x4 spin matrices (colour moved by links only).
+struct LearnedSmoother {
+  bool enabled = false;
+  int mr_steps = 2;                 // minimal-residual steps after S in the V-cycle
+  std::vector<cplx> w;              // [9][4][4] FP64 (fitted)
+  DevBuf w64;                       // device copy of w
+  DevBuf w32;                       // w rounded to FP16, held as float2 (FP32 V-cycle)
+  double err_learned = 0.0, err_plain = 0.0;
+};
+
+void smoother_set_weights(qd_mg& mg, const cplx* w);
+void smoother_fit(qd_mg& mg, int s, const cplx* e, const cplx* r);
+void smoother_train(qd_mg& mg, int s, double solve_tol, uint64_t seed, int mr_steps, double* err_learned,
+                    double* err_plain, int* enabled);
+// out = S in (accumulate: out += S in) on the fine level, nrhs columns.
+template <class C>
+void smoother_apply(qd_ctx& ctx, qd_mg& mg, int nrhs, const C* in, C* out, bool accumulate);
+
 }  // namespace qd
 
 struct qd_mg {
@@ -104,6 +128,7 @@ struct qd_mg {
   std::vector<std::unique_ptr<qd::CoarseLevel>> L;  // L[l-1]: level l >= 1
   std::unique_ptr<qd::MGPrecond<qd::cplx>> pre64;
   std::unique_ptr<qd::MGPrecond<qd::cplxf>> pre32;
+  std::unique_ptr<qd::LearnedSmoother> ls;  // fine-level learned smoother (nullable)
 
   const qd::LevelGeom& geom(int level) const { return level == 0 ? gauge->geo : L[level - 1]->geo; }
   int dof(int level) const { return level == 0 ? 12 : L[level - 1]->D; }

@@ -1,0 +1,328 @@
+// Learned gauge-covariant smoother of the fine level (an extension of the
+// V-cycle's smoothing step; the paper has no counterpart).
+//
+//   (S r)(x)_{o,a} = sum_{d=0..8} sum_{i=0..3} w[d][o][i] (T_d r)(x)_{i,a}
+//
+// with T_0 the identity, T_{1+mu} r(x) = U_mu(x) r(x+mu) and
+// T_{5+mu} r(x) = U_mu(x-mu)^H r(x-mu): one linear layer of link-transported
+// one-hop terms, 144 complex weights.  Colour is moved only by links, so S
+// is gauge covariant.  Training fits w to pairs (e, r) that the solver
+// generates - r the residual left by the coarse-grid correction of a random
+// vector, e = A^{-1} r its error - by linear least squares (normal
+// equations of the 36 transported features per output spin, solved by a
+// Cholesky factorisation on the host).  A held-out set judges the result
+// against the plain minimal-residual smoother; the V-cycle uses S only when
+// it wins.  The FP32 V-cycle applies the weights rounded to FP16.
+#include <cuda_fp16.h>
+
+#include <cmath>
+
+#include "blas.cuh"
+#include "dense.cuh"
+#include "mg.cuh"
+
+namespace qd {
+
+// Transport of the 4 colour triplets of `in` at site y through link matrix
+// L (ADJ: L^H), into t[4][3].
+template <bool ADJ, class C>
+__device__ __forceinline__ void transport4(const C* __restrict__ L, const C* __restrict__ p, int64_t rs, C t[12]) {
+  typedef typename CTraits<C>::R R;
+  C l[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) l[k] = L[k];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    C v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = p[(s * 3 + c) * rs];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      C acc = mk<C>((R)0, (R)0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (ADJ)
+          cfmac(acc, l[b * 3 + a], v[b]);
+        else
+          cfma(acc, l[a * 3 + b], v[b]);
+      }
+      t[s * 3 + a] = acc;
+    }
+  }
+}
+
+// out (+)= S in; one thread per (site, right-hand side); weights staged in
+// shared memory.
+template <class C, bool ACC>
+__global__ void __launch_bounds__(128) k_smoother_apply(const C* __restrict__ U, const int* __restrict__ nbr,
+                                                        int64_t V, int nrhs, const C* __restrict__ w,
+                                                        const C* __restrict__ in, C* __restrict__ out) {
+  typedef typename CTraits<C>::R R;
+  __shared__ C sw[144];
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) sw[k] = w[k];
+  __syncthreads();
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= V * nrhs) return;
+  const int64_t site = g / nrhs;
+  const int r = (int)(g - site * nrhs);
+  const int64_t rs = nrhs;
+  C acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = mk<C>((R)0, (R)0);
+  for (int d = 0; d < 9; ++d) {
+    C t[12];
+    if (d == 0) {
+      const C* p = in + site * 12 * rs + r;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) t[k] = p[k * rs];
+    } else if (d <= 4) {
+      const int mu = d - 1;
+      const int64_t y = nbr[site * 8 + mu];
+      transport4<false>(U + ((int64_t)mu * V + site) * 9, in + y * 12 * rs + r, rs, t);
+    } else {
+      const int mu = d - 5;
+      const int64_t y = nbr[site * 8 + 4 + mu];
+      transport4<true>(U + ((int64_t)mu * V + y) * 9, in + y * 12 * rs + r, rs, t);
+    }
+    const C* wd = sw + d * 16;
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const C c = wd[o * 4 + i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) cfma(acc[o * 3 + a], c, t[i * 3 + a]);
+      }
+  }
+  C* y = out + site * 12 * rs + r;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) y[k * rs] = ACC ? cadd(y[k * rs], acc[k]) : acc[k];
+}
+
+template <class C>
+void smoother_apply(qd_ctx& ctx, qd_mg& mg, int nrhs, const C* in, C* out, bool accumulate) {
+  const LearnedSmoother& ls = *mg.ls;
+  const LevelGeom& geo = mg.gauge->geo;
+  const int64_t tot = geo.nsites * nrhs;
+  if (tot == 0) return;
+  const C* links;
+  const C* w;
+  if (sizeof(C) == 16) {
+    links = reinterpret_cast<const C*>(mg.gauge->links.as<cplx>());
+    w = ls.w64.as<C>();
+  } else {
+    links = reinterpret_cast<const C*>(const_cast<qd_gauge*>(mg.gauge)->links_f32());
+    w = ls.w32.as<C>();
+  }
+  const double cb = (double)sizeof(C);
+  ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_SMOOTHER_F64 : QD_PROF_SMOOTHER_F32,
+               (9.0 * 36 + 9.0 * 48) * 8.0 * (double)tot,
+               (double)geo.nsites * ((accumulate ? 36.0 : 24.0) * cb * nrhs + 36.0 * cb));
+  const int blocks = div_up(tot, 128);
+  if (accumulate)
+    k_smoother_apply<C, true><<<blocks, 128, 0, ctx.stream>>>(links, geo.nbr.as<int>(), geo.nsites, nrhs, w, in, out);
+  else
+    k_smoother_apply<C, false><<<blocks, 128, 0, ctx.stream>>>(links, geo.nbr.as<int>(), geo.nsites, nrhs, w, in, out);
+  QD_LAUNCH_CHECK();
+}
+template void smoother_apply<cplx>(qd_ctx&, qd_mg&, int, const cplx*, cplx*, bool);
+template void smoother_apply<cplxf>(qd_ctx&, qd_mg&, int, const cplxf*, cplxf*, bool);
+
+// ---------------------------------------------------------------------------
+// Training
+// ---------------------------------------------------------------------------
+
+// F[((x * 3 + a) * s + j) * 36 + d * 4 + i] = (T_d r_j)(x)_{i,a} and
+// E[((x * 3 + a) * s + j) * 4 + o] = e_j(x)_{o,a}; one thread per (x, j).
+__global__ void k_smoother_features(const cplx* __restrict__ U, const int* __restrict__ nbr, int64_t V, int s,
+                                    const cplx* __restrict__ r, const cplx* __restrict__ e, cplx* __restrict__ F,
+                                    cplx* __restrict__ E) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= V * s) return;
+  const int64_t x = g / s;
+  const int j = (int)(g - x * s);
+  const int64_t rs = s;
+  for (int d = 0; d < 9; ++d) {
+    cplx t[12];
+    if (d == 0) {
+      const cplx* p = r + x * 12 * rs + j;
+      for (int k = 0; k < 12; ++k) t[k] = p[k * rs];
+    } else if (d <= 4) {
+      const int mu = d - 1;
+      const int64_t y = nbr[x * 8 + mu];
+      transport4<false>(U + ((int64_t)mu * V + x) * 9, r + y * 12 * rs + j, rs, t);
+    } else {
+      const int mu = d - 5;
+      const int64_t y = nbr[x * 8 + 4 + mu];
+      transport4<true>(U + ((int64_t)mu * V + y) * 9, r + y * 12 * rs + j, rs, t);
+    }
+    for (int a = 0; a < 3; ++a) {
+      cplx* row = F + ((x * 3 + a) * s + j) * 36 + d * 4;
+      for (int i = 0; i < 4; ++i) row[i] = t[i * 3 + a];
+    }
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int o = 0; o < 4; ++o) E[((x * 3 + a) * s + j) * 4 + o] = e[x * 12 * rs + (o * 3 + a) * rs + j];
+}
+
+// Cholesky solve of the Hermitian positive definite G (n x n) for the
+// columns of H (n x m), on the host in double precision.
+static void chol_solve(int n, int m, std::vector<cplx>& G, std::vector<cplx>& H) {
+  // small ridge relative to the mean diagonal keeps rank-deficient feature
+  // sets (e.g. a field with a vanishing component) solvable
+  double tr = 0.0;
+  for (int i = 0; i < n; ++i) tr += G[(size_t)i * n + i].x;
+  const double ridge = 1e-13 * tr / n;
+  for (int i = 0; i < n; ++i) G[(size_t)i * n + i].x += ridge;
+  // G = L L^H, L lower triangular stored in G
+  for (int j = 0; j < n; ++j) {
+    double djj = G[(size_t)j * n + j].x;
+    for (int k = 0; k < j; ++k) djj -= cnorm2(G[(size_t)j * n + k]);
+    QD_REQUIRE(djj > 0.0, "learned-smoother normal equations are not positive definite");
+    const double ljj = std::sqrt(djj);
+    G[(size_t)j * n + j] = mkc(ljj, 0.0);
+    for (int i = j + 1; i < n; ++i) {
+      cplx v = G[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) {
+        const cplx a = G[(size_t)i * n + k], b = G[(size_t)j * n + k];
+        // v -= a conj(b)
+        v.x -= a.x * b.x + a.y * b.y;
+        v.y -= a.y * b.x - a.x * b.y;
+      }
+      G[(size_t)i * n + j] = mkc(v.x / ljj, v.y / ljj);
+    }
+  }
+  for (int c = 0; c < m; ++c) {
+    // L y = h
+    for (int i = 0; i < n; ++i) {
+      cplx v = H[(size_t)i * m + c];
+      for (int k = 0; k < i; ++k) {
+        const cplx a = G[(size_t)i * n + k], b = H[(size_t)k * m + c];
+        v.x -= a.x * b.x - a.y * b.y;
+        v.y -= a.x * b.y + a.y * b.x;
+      }
+      const double l = G[(size_t)i * n + i].x;
+      H[(size_t)i * m + c] = mkc(v.x / l, v.y / l);
+    }
+    // L^H w = y
+    for (int i = n - 1; i >= 0; --i) {
+      cplx v = H[(size_t)i * m + c];
+      for (int k = i + 1; k < n; ++k) {
+        const cplx a = G[(size_t)k * n + i], b = H[(size_t)k * m + c];  // conj(a) b
+        v.x -= a.x * b.x + a.y * b.y;
+        v.y -= a.x * b.y - a.y * b.x;
+      }
+      const double l = G[(size_t)i * n + i].x;
+      H[(size_t)i * m + c] = mkc(v.x / l, v.y / l);
+    }
+  }
+}
+
+static void upload_weights(qd_ctx& ctx, LearnedSmoother& ls) {
+  ls.w64.resize(144 * sizeof(cplx));
+  ls.w32.resize(144 * sizeof(cplxf));
+  std::vector<cplxf> h(144);
+  for (int k = 0; k < 144; ++k)
+    h[k] = make_float2(__half2float(__float2half_rn((float)ls.w[k].x)), __half2float(__float2half_rn((float)ls.w[k].y)));
+  QD_CUDA(cudaMemcpyAsync(ls.w64.as<cplx>(), ls.w.data(), 144 * sizeof(cplx), cudaMemcpyHostToDevice, ctx.stream));
+  QD_CUDA(cudaMemcpyAsync(ls.w32.as<cplxf>(), h.data(), 144 * sizeof(cplxf), cudaMemcpyHostToDevice, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+}
+
+void smoother_set_weights(qd_mg& mg, const cplx* w) {
+  if (!mg.ls) mg.ls.reset(new LearnedSmoother());
+  mg.ls->w.assign(w, w + 144);
+  upload_weights(*mg.ctx, *mg.ls);
+}
+
+// Least-squares weights for s pairs (e, r) in fine qd layout (device).
+void smoother_fit(qd_mg& mg, int s, const cplx* e, const cplx* r) {
+  qd_ctx& ctx = *mg.ctx;
+  const LevelGeom& geo = mg.gauge->geo;
+  const int64_t rows = geo.nsites * 3 * (int64_t)s;
+  DevBuf F((size_t)rows * 36 * sizeof(cplx)), E((size_t)rows * 4 * sizeof(cplx)), G(36 * 36 * sizeof(cplx)),
+      H(36 * 4 * sizeof(cplx));
+  k_smoother_features<<<div_up(geo.nsites * s, 128), 128, 0, ctx.stream>>>(
+      mg.gauge->links.as<cplx>(), geo.nbr.as<int>(), geo.nsites, s, r, e, F.as<cplx>(), E.as<cplx>());
+  QD_LAUNCH_CHECK();
+  blockdot(ctx, rows, F.as<cplx>(), 36, 36, F.as<cplx>(), 36, 36, G.as<cplx>());
+  blockdot(ctx, rows, F.as<cplx>(), 36, 36, E.as<cplx>(), 4, 4, H.as<cplx>());
+  std::vector<cplx> hG(36 * 36), hH(36 * 4);
+  QD_CUDA(cudaMemcpyAsync(hG.data(), G.as<cplx>(), hG.size() * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaMemcpyAsync(hH.data(), H.as<cplx>(), hH.size() * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  chol_solve(36, 4, hG, hH);
+  std::vector<cplx> w(144);
+  for (int d = 0; d < 9; ++d)
+    for (int o = 0; o < 4; ++o)
+      for (int i = 0; i < 4; ++i) w[(d * 4 + o) * 4 + i] = hH[(size_t)(d * 4 + i) * 4 + o];
+  smoother_set_weights(mg, w.data());
+}
+
+// Pairs the solver generates: r = residual of the coarse-grid correction of
+// a random vector, e = A^{-1} r solved to solve_tol.
+static void make_pairs(qd_mg& mg, int s, uint64_t key, double solve_tol, DevBuf& e, DevBuf& r) {
+  qd_ctx& ctx = *mg.ctx;
+  const LevelGeom& geo = mg.gauge->geo;
+  const int64_t tot = geo.nsites * 12 * (int64_t)s;
+  DevBuf v((size_t)tot * sizeof(cplx)), z((size_t)tot * sizeof(cplx));
+  e.resize((size_t)tot * sizeof(cplx));
+  r.resize((size_t)tot * sizeof(cplx));
+  random_starts_fill(ctx, geo, 12, key, s, v.as<cplx>());
+  mg.pre64->coarse_correction(ctx, v.as<cplx>(), z.as<cplx>(), s);
+  auto A = mg.op<cplx>(0);
+  A->residual(ctx, v.as<cplx>(), z.as<cplx>(), r.as<cplx>(), s);
+  GCR<cplx> gcr;
+  SolveInfo info;
+  gcr.solve(ctx, *A, mg.pre64.get(), r.as<cplx>(), e.as<cplx>(), s, solve_tol, 2000, 16, &info);
+  QD_REQUIRE(info.converged == s, "learned-smoother training solves did not converge");
+}
+
+// Mean over columns of ||e - x|| / ||e||.
+static double mean_rel_err(qd_ctx& ctx, int64_t n, int s, const cplx* e, const cplx* x) {
+  DevBuf d((size_t)n * s * sizeof(cplx)), nn(2 * (size_t)s * sizeof(cplx));
+  blas::sub(ctx, n * s, e, x, d.as<cplx>());
+  blas::dots(ctx, 1, n, s, d.as<cplx>(), 0, d.as<cplx>(), 0, nn.as<cplx>());
+  blas::dots(ctx, 1, n, s, e, 0, e, 0, nn.as<cplx>() + s);
+  std::vector<cplx> h(2 * s);
+  QD_CUDA(cudaMemcpyAsync(h.data(), nn.as<cplx>(), h.size() * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  double m = 0.0;
+  for (int j = 0; j < s; ++j) m += std::sqrt(h[j].x / (h[s + j].x > 0.0 ? h[s + j].x : 1.0));
+  return m / s;
+}
+
+void smoother_train(qd_mg& mg, int s, double solve_tol, uint64_t seed, int mr_steps, double* err_learned,
+                    double* err_plain, int* enabled) {
+  QD_REQUIRE(s >= 1 && s <= 1024, "nsamples must be in [1, 1024]");
+  QD_REQUIRE(mr_steps >= 0 && mr_steps <= 64, "mr_steps must be in [0, 64]");
+  qd_ctx& ctx = *mg.ctx;
+  const LevelGeom& geo = mg.gauge->geo;
+  const int64_t n = geo.nsites * 12;
+  DevBuf e, r;
+  make_pairs(mg, s, seed, solve_tol, e, r);
+  smoother_fit(mg, s, e.as<cplx>(), r.as<cplx>());
+  LearnedSmoother& ls = *mg.ls;
+  ls.mr_steps = mr_steps;
+  // held-out pairs: the whole smoothing step of each kind, from x = 0
+  DevBuf he, hr;
+  make_pairs(mg, s, seed + 0x9e3779b97f4a7c15ull, solve_tol, he, hr);
+  auto A = mg.op<cplx>(0);
+  DevBuf x((size_t)n * s * sizeof(cplx)), res((size_t)n * s * sizeof(cplx)), q((size_t)n * s * sizeof(cplx)), scr;
+  // plain: smoother_steps minimal-residual steps
+  blas::zero(ctx, n * s, x.as<cplx>());
+  blas::copy(ctx, n * s, hr.as<cplx>(), res.as<cplx>());
+  mr_smooth<cplx>(ctx, *A, x.as<cplx>(), res.as<cplx>(), q.as<cplx>(), s, mg.p.smoother_steps, scr);
+  ls.err_plain = mean_rel_err(ctx, n, s, he.as<cplx>(), x.as<cplx>());
+  // learned: S r, then its minimal-residual steps
+  smoother_apply<cplx>(ctx, mg, s, hr.as<cplx>(), x.as<cplx>(), false);
+  A->residual(ctx, hr.as<cplx>(), x.as<cplx>(), res.as<cplx>(), s);
+  mr_smooth<cplx>(ctx, *A, x.as<cplx>(), res.as<cplx>(), q.as<cplx>(), s, mr_steps, scr);
+  ls.err_learned = mean_rel_err(ctx, n, s, he.as<cplx>(), x.as<cplx>());
+  ls.enabled = ls.err_learned < ls.err_plain;
+  *err_learned = ls.err_learned;
+  *err_plain = ls.err_plain;
+  *enabled = ls.enabled ? 1 : 0;
+}
+
+}  // namespace qd

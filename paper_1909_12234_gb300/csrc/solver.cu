@@ -394,6 +394,13 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
   cur.push_back(ctx.red_partials.as<void>());
   cur.push_back(reinterpret_cast<const void*>(ctx.red_partials.bytes()));
   cur.push_back(reinterpret_cast<const void*>(ctx.stream));
+  // the V-cycle's shape: learned smoother on or off, its MR steps
+  const LearnedSmoother* ls = mg_->ls.get();
+  cur.push_back(reinterpret_cast<const void*>((uintptr_t)(ls && ls->enabled ? 1 + ls->mr_steps : 0)));
+  if (ls) {
+    cur.push_back(ls->w64.as<void>());
+    cur.push_back(ls->w32.as<void>());
+  }
   if (!graphs_.empty() && (graphs_.front().ptrs != cur || graphs_.front().nrhs != nrhs)) {
     // another context or a reallocated buffer: run eagerly once more first
     drop_graphs();
@@ -463,8 +470,7 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
   launch_counter().fetch_add(kernels, std::memory_order_relaxed);
 }
 
-template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, int nrhs) {
-  const Transfer& T = *mg_->T[level_];
+template <class C> void MGPrecond<C>::ensure_buffers(int nrhs) {
   const int64_t nf = mg_->geom(level_).nsites * (int64_t)mg_->dof(level_);
   const int64_t nc = mg_->geom(level_ + 1).nsites * (int64_t)mg_->dof(level_ + 1);
   if (nrhs > cap_) {
@@ -476,8 +482,14 @@ template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, int nr
     d_.resize(nf * nrhs * sizeof(C));
     cap_ = nrhs;
   }
+}
+
+// z = W C^{-1} W^H r: the coarse-grid correction
+template <class C> void MGPrecond<C>::coarse_correction(qd_ctx& ctx, const C* r, C* z, int nrhs) {
+  ensure_buffers(nrhs);
+  const Transfer& T = *mg_->T[level_];
+  const int64_t nc = mg_->geom(level_ + 1).nsites * (int64_t)mg_->dof(level_ + 1);
   const C* W = mg_->W<C>(level_);
-  // coarse-grid correction: z = W C^{-1} W^H r
   restrict_<C>(ctx, T, W, r, rc_.as<C>(), nrhs);
   const C* inv = mg_->Cinv<C>(level_ + 1);
   CoarseLevel& cl = *mg_->L[level_];
@@ -491,11 +503,27 @@ template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, int nr
                   mg_->p.coarse_maxit, mg_->p.coarse_restart, nullptr);
   }
   prolongate<C>(ctx, T, W, ec_.as<C>(), z, nrhs);
-  // smoothing: z += M^{-1} (r - A z), M^{-1} = minimal-residual steps from 0;
-  // the steps update z in place with the residual res = r - A z
+}
+
+template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, int nrhs) {
+  coarse_correction(ctx, r, z, nrhs);
+  // smoothing: z += M^{-1} (r - A z).  Plain: M^{-1} = minimal-residual
+  // steps from 0, which update z in place with the residual res = r - A z.
+  // With a learned smoother on the fine level: z += S (r - A z), then the
+  // smoother's own minimal-residual steps.
+  auto Af = mg_->op<C>(level_);
+  const LearnedSmoother* ls = level_ == 0 ? mg_->ls.get() : nullptr;
+  if (ls && ls->enabled) {
+    Af->residual(ctx, r, z, res_.as<C>(), nrhs);
+    smoother_apply<C>(ctx, *mg_, nrhs, res_.as<C>(), z, true);
+    if (ls->mr_steps > 0) {
+      Af->residual(ctx, r, z, res_.as<C>(), nrhs);
+      mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, ls->mr_steps, scratch_);
+    }
+    return;
+  }
   const int nu = mg_->p.smoother_steps;
   if (nu > 0) {
-    auto Af = mg_->op<C>(level_);
     Af->residual(ctx, r, z, res_.as<C>(), nrhs);
     mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, nu, scratch_);
   }

@@ -110,6 +110,15 @@ class TraceResult(ctypes.Structure):
                 ("UhKZ", ctypes.POINTER(ctypes.c_double))]
 
 
+class SmootherParams(ctypes.Structure):
+    _fields_ = [("nsamples", ctypes.c_int), ("solve_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("mr_steps", ctypes.c_int)]
+
+
+class SmootherInfo(ctypes.Structure):
+    _fields_ = [("err_learned", ctypes.c_double), ("err_plain", ctypes.c_double), ("enabled", ctypes.c_int)]
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [("gauge", ctypes.c_void_p), ("mg", ctypes.c_void_p), ("defl", ctypes.c_void_p),
                 ("m0", ctypes.c_double), ("tau", ctypes.c_double), ("params", TraceParams),
@@ -157,6 +166,13 @@ SIGNATURES = {
     "qd_deflate_project": (_I, [_P, _I, _P, _P]),
     "qd_deflate_project_static": (_I, [_P, _I, _P, _P]),
     "qd_deflate_coeffs": (_I, [_P, _I, _P, _DPTR, _DPTR]),
+    "qd_smoother_params_default": (None, [ctypes.POINTER(SmootherParams)]),
+    "qd_smoother_train": (_I, [_P, ctypes.POINTER(SmootherParams), ctypes.POINTER(SmootherInfo)]),
+    "qd_smoother_fit": (_I, [_P, _I, _P, _P]),
+    "qd_smoother_set_weights": (_I, [_P, _DPTR]),
+    "qd_smoother_get_weights": (_I, [_P, _DPTR]),
+    "qd_smoother_enable": (_I, [_P, _I, _I]),
+    "qd_smoother_apply": (_I, [_P, _I, _P, _P]),
     "qd_autotune_set": (None, [_I]),
     "qd_autotune_clear": (None, []),
     "qd_autotune_report": (_I, [ctypes.c_char_p, _I]),
@@ -171,7 +187,8 @@ SIGNATURES = {
 
 PROF_KINDS = {"wilson_f64": 0, "wilson_f32": 1, "coarse_f64": 2, "coarse_f32": 3, "prolong_f64": 4,
               "prolong_f32": 5, "restrict_f64": 6, "restrict_f32": 7, "direct_f64": 8, "direct_f32": 9, "direct_bf16": 10,
-              "blas_f64": 11, "dots_f32": 12, "axpy_f32": 13, "update_f32": 14}
+              "blas_f64": 11, "dots_f32": 12, "axpy_f32": 13, "update_f32": 14, "smoother_f64": 15,
+              "smoother_f32": 16}
 
 _lib = None
 
@@ -629,3 +646,42 @@ def _isnum(w):
         return True
     except ValueError:
         return False
+
+
+def smoother_params(**kw):
+    p = SmootherParams()
+    load().qd_smoother_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def smoother_train(mg, **kw):
+    """Train the learned smoother on solver-generated pairs; returns the
+    held-out errors and whether the V-cycle now uses it."""
+    info = SmootherInfo()
+    _check(load().qd_smoother_train(mg.h, ctypes.byref(smoother_params(**kw)), ctypes.byref(info)))
+    return {"err_learned": info.err_learned, "err_plain": info.err_plain, "enabled": bool(info.enabled)}
+
+
+def smoother_fit(mg, nrhs, e, r):
+    _check(load().qd_smoother_fit(mg.h, int(nrhs), _ptr(e), _ptr(r)))
+
+
+def smoother_set_weights(mg, w):
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.complex128).reshape(9, 4, 4))
+    _check(load().qd_smoother_set_weights(mg.h, w.view(np.float64).ctypes.data_as(_DPTR)))
+
+
+def smoother_get_weights(mg):
+    w = np.zeros((9, 4, 4), dtype=np.complex128)
+    _check(load().qd_smoother_get_weights(mg.h, w.view(np.float64).ctypes.data_as(_DPTR)))
+    return w
+
+
+def smoother_enable(mg, enabled=True, mr_steps=2):
+    _check(load().qd_smoother_enable(mg.h, 1 if enabled else 0, int(mr_steps)))
+
+
+def smoother_apply(mg, nrhs, inp, out):
+    _check(load().qd_smoother_apply(mg.h, int(nrhs), _ptr(inp), _ptr(out)))

@@ -1,0 +1,86 @@
+"""GPU parity for the learned gauge-covariant smoother: S r and the
+least-squares fit against the oracle, and solves that use S inside the
+V-cycle reach the FP64 true residual (mixed and FP64), replaying the
+captured V-cycle bit-identically."""
+import numpy as np
+import pytest
+
+from oracle import multigrid as omg
+from oracle import smoother as osm
+from paper_1909_12234_gb300 import synth
+
+from gpu_util import need_gpu, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qd():
+    need_gpu()
+    from paper_1909_12234_gb300 import qdtrace
+    qdtrace.load()
+    return qdtrace
+
+
+@pytest.fixture(scope="module")
+def ctx(qd):
+    return qd.Context(0)
+
+
+def test_apply_and_fit_match_oracle(qd, ctx):
+    dims = (8, 4, 4, 6)
+    U = synth.random_su3_links(dims, 0.3, 3)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, -0.5, 0.0, qd.mg_params(1, [(2, 2, 2, 2)], [4], null_maxit=0))
+    rng = np.random.default_rng(5)
+    w0 = rng.standard_normal((9, 4, 4)) + 1j * rng.standard_normal((9, 4, 4))
+    qd.smoother_set_weights(mg, w0)
+    assert np.array_equal(qd.smoother_get_weights(mg), w0)
+    for s in (1, 5):
+        r = synth.random_field(dims, s, 10 + s)
+        out = torch.empty((g.V, 12, s), dtype=torch.complex128, device="cuda:0")
+        qd.smoother_apply(mg, s, qd.to_qd(ctx, g, r), out)
+        assert rel_err(qd.from_qd(ctx, g, out), osm.apply(U, w0, r, dims)) < 1e-12
+    # the Wilson weights give the Wilson operator
+    qd.smoother_set_weights(mg, osm.wilson_weights(-0.5))
+    r = synth.random_field(dims, 3, 1)
+    out = torch.empty((g.V, 12, 3), dtype=torch.complex128, device="cuda:0")
+    ref = torch.empty_like(out)
+    qd.smoother_apply(mg, 3, qd.to_qd(ctx, g, r), out)
+    qd.dirac_apply(ctx, g, -0.5, 0.0, False, 3, qd.to_qd(ctx, g, r), ref)
+    assert rel_err(out.cpu().numpy(), ref.cpu().numpy()) < 1e-13
+    # fit: exact recovery of planted weights, and the oracle's least squares
+    # on noisy pairs
+    R = synth.random_field(dims, 4, 2)
+    E = osm.apply(U, w0, R, dims)
+    qd.smoother_fit(mg, 4, qd.to_qd(ctx, g, E), qd.to_qd(ctx, g, R))
+    assert rel_err(qd.smoother_get_weights(mg), w0) < 1e-10
+    En = E + 0.3 * synth.random_field(dims, 4, 3)
+    qd.smoother_fit(mg, 4, qd.to_qd(ctx, g, En), qd.to_qd(ctx, g, R))
+    assert rel_err(qd.smoother_get_weights(mg), osm.fit(U, En, R, dims)) < 1e-9
+
+
+def test_solves_with_the_learned_smoother(qd, ctx):
+    dims, m0, s = (8, 8, 8, 8), -0.8, 8
+    U = synth.random_su3_links(dims, 0.3, 2)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(1, [(2, 2, 2, 2)], [12]))
+    info = qd.smoother_train(mg, nsamples=8, solve_tol=1e-6, mr_steps=2)
+    assert 0.0 < info["err_learned"] < 1.0 and 0.0 < info["err_plain"] < 1.0
+    assert info["enabled"] == (info["err_learned"] < info["err_plain"])
+    qd.smoother_enable(mg, True, 2)  # exercise the learned path whatever the judge said
+    A = omg.fine_level(U, m0, dims).matrix
+    b = synth.random_field(dims, s, 7)
+    bd = qd.to_qd(ctx, g, b)
+    for prec in (qd.QD_PREC_MIXED, qd.QD_PREC_F64):
+        xs = []
+        for rep in range(3):  # eager, capture, replay
+            xd = torch.empty_like(bd)
+            qd.solve(ctx, g, mg, m0, 0.0, s, bd, xd, 1e-10, maxit=400, restart=16, precision=prec,
+                     inner_tol=1e-5, max_refine=10)
+            xs.append(xd.clone())
+        assert torch.equal(xs[1], xs[0]) and torch.equal(xs[2], xs[0])
+        x = qd.from_qd(ctx, g, xs[0]).reshape(-1, s)
+        B = b.reshape(-1, s)
+        assert np.all(np.linalg.norm(B - A @ x, axis=0) / np.linalg.norm(B, axis=0) <= 1e-10)
+    qd.smoother_enable(mg, False, 2)

@@ -430,6 +430,135 @@ def run_ours(args):
     return 0
 
 
+# Config 5: 24^3 x 48, eps 0.15 (seed 5), m0 -0.8, three-level MG (2^4 then
+# 3^4 blocks, nv 12 on both: the coarsest level has 512 sites x 24 dofs and a
+# dense inverse), Algorithm 2 k = 24, 256 samples per step solved in blocks
+# of 64 right-hand sides, mixed precision to a true FP64 residual 1e-8, with
+# the learned smoother against the plain minimal-residual smoother.
+LEARNED = dict(
+    workload="wilson-dirac 24^3x48 eps0.15 seed5 m0=-0.8, 3-level MG (2^4, 3^4; nv 12, 12; level-1 GCR 6 its), "
+             "Algorithm 2 k=24, 256 Rademacher samples/step in 4 blocks of 64, learned smoother (S + 2 MR) vs "
+             "plain MR(4), true FP64 rel. residual 1e-8",
+    dims=(24, 24, 24, 48), eps=0.15, link_seed=5, m0=-0.8, blocks=[(2, 2, 2, 2), (3, 3, 3, 3)], nvs=[12, 12],
+    mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6}, k=24, guard=16, s=256, rhs_block=64, tol=1e-8,
+    noise_seed=105, restart=8, maxit=500, inner_tol=1e-5,
+)
+
+
+def run_learned(args):
+    """Config 5: samples/s and iterations with the learned smoother and with
+    the plain smoother on the same samples."""
+    import torch
+    from paper_1909_12234_gb300 import qdtrace as qd
+    from paper_1909_12234_gb300 import synth
+
+    if int(os.environ.get("WORLD_SIZE", "1")) != 1 or args.gpus != 1:
+        raise SystemExit("the learned-smoother workload runs on one GPU")
+    L = LEARNED
+    qd.load()
+    ctx = qd.Context(0)
+    U = synth.random_su3_links(L["dims"], L["eps"], L["link_seed"])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    g = qd.Gauge(ctx, L["dims"], U)
+    del U
+    mg = qd.Multigrid(ctx, g, L["m0"], 0.0, qd.mg_params(2, L["blocks"], L["nvs"], **L["mg_kw"]))
+    d = qd.Deflation(ctx, g, mg, L["m0"], 0.0, qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, L["k"], guard=L["guard"],
+                                                               eig_tol=1e-6, solve_tol=1e-10, maxit=60))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t
+    t = time.perf_counter()
+    info = qd.smoother_train(mg, nsamples=8, solve_tol=1e-6, mr_steps=2)
+    train_s = time.perf_counter() - t
+    s, sb = L["s"], L["rhs_block"]
+
+    def step(i, learned):
+        qd.smoother_enable(mg, learned, 2)
+        ts, its, worst = [], [], 0.0
+        for b0 in range(0, s, sb):
+            r = qd.hutchinson_trace(ctx, g, mg, d, L["m0"], 0.0, L["noise_seed"], 100000 * i + b0, min(sb, s - b0),
+                                    L["tol"], maxit=L["maxit"], restart=L["restart"], precision=qd.QD_PREC_MIXED,
+                                    inner_tol=L["inner_tol"], max_refine=10)
+            ts.append(r["t"])
+            its.append(r["iterations"])
+            worst = max(worst, r["max_true_rel_residual"])
+        t0 = r["t0"]
+        st = qd.trace_stats(ctx, np.concatenate(ts), t0)
+        return st, its, worst
+
+    def timed(learned, nsteps, first):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        out = [step(first + i, learned) for i in range(nsteps)]
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    for i in range(args.warmup):
+        step(i, True)
+        step(i, False)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = qd.launch_count()
+    ms, res = timed(True, args.steps, args.warmup)
+    launches = qd.launch_count() - l0
+    clk = clocks.stop()
+    ms_plain, res_plain = timed(False, args.steps, args.warmup)
+
+    qd.smoother_enable(mg, True, 2)
+    qd.prof_enable(ctx, True)
+    for k in qd.PROF_KINDS:
+        qd.prof_read(ctx, k, reset=True)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(ctx.stream)
+    qd.hutchinson_trace(ctx, g, mg, d, L["m0"], 0.0, L["noise_seed"], 9000000, sb, L["tol"], maxit=L["maxit"],
+                        restart=L["restart"], precision=qd.QD_PREC_MIXED, inner_tol=L["inner_tol"], max_refine=10)
+    p1.record(ctx.stream)
+    torch.cuda.synchronize()
+    qd.prof_enable(ctx, False)
+    ms_prof = p0.elapsed_time(p1)
+    prof = {k: qd.prof_read(ctx, k) for k in qd.PROF_KINDS}
+    top = max(prof, key=lambda k: prof[k]["ms"])
+    pt = prof[top]
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    if top.endswith("f64") or top in ("direct_f32", "coarse_f32"):
+        peak = FP64_PEAK_TFLOPS if top.endswith("f64") else 70.0
+        ach = pt["flops"] / (pt["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak}
+    else:
+        ach = pt["bytes"] / (pt["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm}
+    roof.update({"traffic": None, "kernel": top, "launches": pt["launches"],
+                 "ms_per_launch": pt["ms"] / max(pt["launches"], 1)})
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share_of_step": round(v["ms"] / ms_prof, 4)}
+               for k, v in prof.items() if v["launches"]}
+
+    def summary(ms_, rr):
+        st, its, worst = rr[-1]
+        return {"value": args.steps * s / (ms_ / 1e3), "ms_per_step": ms_ / args.steps, "outer_iterations": its,
+                "max_true_rel_residual": max(r[2] for r in rr), "estimate": [st["estimate"].real, st["stderr"]],
+                "var": st["var"], "var_jackknife_err": st["var_jackknife_err"]}
+
+    learned, plain = summary(ms, res), summary(ms_plain, res_plain)
+    line = {
+        "metric": METRIC, "value": learned["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": learned["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 inner solves (FP16 smoother weights) + f64 refinement", "data": "synthetic",
+        "config": {"workload": L["workload"], "precision": "mixed", "parallelism": "replicas x1",
+                   "l2": "fields 2-8 GB per block exceed L2", "setup_s": round(setup_s, 3),
+                   "smoother_train_s": round(train_s, 3), "smoother_judge": info,
+                   "learned": learned, "plain": plain},
+        "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": None, "gpu_launches": launches,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    for o in (d, mg, g, ctx):
+        o.close()
+    return 0
+
+
 def run_batch(args):
     """Config 4: the uneven batch, concurrent (one qd_hutchinson_batch call
     per step) against the same problems solved one after another."""
@@ -578,15 +707,15 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--prof-steps", type=int, default=2)
-    ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS) + ["config4"])
+    ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS) + ["config4", "config5"])
     ap.add_argument("--fixed-coarse", type=int, default=0,
                     help="> 0: level-1 GCR of a three-level hierarchy runs exactly this many iterations")
     args = ap.parse_args()
-    if args.workload == "config4":
+    if args.workload in ("config4", "config5"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-lattice workload"}))
             return 0
-        return run_batch(args)
+        return run_batch(args) if args.workload == "config4" else run_learned(args)
     WL.clear()
     WL.update(WORKLOADS[args.workload] if args.workload != "config2" else dict(WORKLOADS["config2"]))
     if args.fixed_coarse > 0:

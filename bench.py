@@ -441,7 +441,7 @@ LEARNED = dict(
              "plain MR(4), true FP64 rel. residual 1e-8",
     dims=(24, 24, 24, 48), eps=0.15, link_seed=5, m0=-0.8, blocks=[(2, 2, 2, 2), (3, 3, 3, 3)], nvs=[12, 12],
     mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6}, k=24, guard=16, s=256, rhs_block=64, tol=1e-8,
-    noise_seed=105, restart=8, maxit=500, inner_tol=1e-5,
+    noise_seed=105, restart=16, maxit=500, inner_tol=1e-5,
 )
 
 
@@ -454,7 +454,21 @@ def run_learned(args):
 
     if int(os.environ.get("WORLD_SIZE", "1")) != 1 or args.gpus != 1:
         raise SystemExit("the learned-smoother workload runs on one GPU")
-    L = LEARNED
+    L = dict(LEARNED)
+    if args.small:
+        # the learned-vs-plain comparison on the 16^3 x 32 lattice of the
+        # mixed-precision workload (eps 0.2, seed 3, 2^4 then 2^4 blocks, nv
+        # 12 then 16), 128 samples in 2 blocks of 64
+        L.update(dims=(16, 16, 16, 32), eps=0.2, link_seed=3, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16],
+                 s=128, rhs_block=64, noise_seed=103,
+                 workload="wilson-dirac 16^3x32 eps0.2 seed3 m0=-0.8, 3-level MG (2^4, 2^4; nv 12, 16; level-1 GCR "
+                          "6 its), Algorithm 2 k=24, 128 Rademacher samples/step in 2 blocks of 64, learned smoother "
+                          "(S + 2 MR) vs plain MR(4), true FP64 rel. residual 1e-8")
+    T0 = time.perf_counter()
+
+    def log(msg):
+        sys.stderr.write(f"[{time.perf_counter() - T0:8.1f}s] {msg}\n")
+        sys.stderr.flush()
     qd.load()
     ctx = qd.Context(0)
     U = synth.random_su3_links(L["dims"], L["eps"], L["link_seed"])
@@ -463,13 +477,16 @@ def run_learned(args):
     g = qd.Gauge(ctx, L["dims"], U)
     del U
     mg = qd.Multigrid(ctx, g, L["m0"], 0.0, qd.mg_params(2, L["blocks"], L["nvs"], **L["mg_kw"]))
+    log("multigrid built")
     d = qd.Deflation(ctx, g, mg, L["m0"], 0.0, qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, L["k"], guard=L["guard"],
                                                                eig_tol=1e-6, solve_tol=1e-10, maxit=60))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t
+    log(f"setup done ({setup_s:.1f} s)")
     t = time.perf_counter()
     info = qd.smoother_train(mg, nsamples=8, solve_tol=1e-6, mr_steps=2)
     train_s = time.perf_counter() - t
+    log(f"smoother trained ({train_s:.1f} s): {info}")
     s, sb = L["s"], L["rhs_block"]
 
     def step(i, learned):
@@ -482,6 +499,7 @@ def run_learned(args):
             ts.append(r["t"])
             its.append(r["iterations"])
             worst = max(worst, r["max_true_rel_residual"])
+            log(f"step {i} learned={learned} block {b0}: {r['iterations']} its, res {r['max_true_rel_residual']:.2e}")
         t0 = r["t0"]
         st = qd.trace_stats(ctx, np.concatenate(ts), t0)
         return st, its, worst
@@ -708,6 +726,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--prof-steps", type=int, default=2)
     ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS) + ["config4", "config5"])
+    ap.add_argument("--small", action="store_true",
+                    help="config5: the learned-vs-plain comparison on the 16^3 x 32 lattice")
     ap.add_argument("--fixed-coarse", type=int, default=0,
                     help="> 0: level-1 GCR of a three-level hierarchy runs exactly this many iterations")
     args = ap.parse_args()

@@ -157,6 +157,9 @@ def _traffic(workload, kind):
 def _setup(qd, ctx, U):
     g = qd.Gauge(ctx, WL["dims"], U)
     mg = qd.Multigrid(ctx, g, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"], **WL.get("mg_kw", {})))
+    if WL.get("learned"):
+        WL["smoother_judge"] = qd.smoother_train(mg, nsamples=8, solve_tol=1e-6, mr_steps=WL["learned"])
+        qd.smoother_enable(mg, True, WL["learned"])
     d = qd.Deflation(ctx, g, mg, WL["m0"], 0.0,
                      qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
                                     solve_tol=1e-10, maxit=60))
@@ -444,7 +447,10 @@ def run_ours(args):
                        "l2": "working set > L2 (GCR basis 2 x 16 x 50 MB per batch)",
                        "setup_s": round(setup_s, 3), "outer_iterations": iters,
                        "max_true_rel_residual": worst,
-                       "estimate": [results[-1]["estimate"].real, results[-1]["stderr"]]},
+                       "estimate": [results[-1]["estimate"].real, results[-1]["stderr"]],
+                       "mg_overrides": WL.get("mg_kw", {}),
+                       "learned_smoother": ({"mr_steps": WL["learned"], "judge": WL.get("smoother_judge")}
+                                            if WL.get("learned") else None)},
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "fp64_path": fp64, "stencil": stencil, "cpu_baseline": cpu,
         }
@@ -756,6 +762,9 @@ def main():
                     help="only the Wilson stencil alone on 16^3 x 32 (a profiling target)")
     ap.add_argument("--small", action="store_true",
                     help="config5: the learned-vs-plain comparison on the 16^3 x 32 lattice")
+    ap.add_argument("--smoother-steps", type=int, default=0, help="> 0: MR post-smoothing steps (default 4)")
+    ap.add_argument("--learned", type=int, default=0,
+                    help="> 0: train the learned smoother and use it with this many MR steps after it")
     ap.add_argument("--fixed-coarse", type=int, default=0,
                     help="> 0: level-1 GCR of a three-level hierarchy runs exactly this many iterations")
     args = ap.parse_args()
@@ -775,6 +784,10 @@ def main():
     WL.update(WORKLOADS[args.workload] if args.workload != "config2" else dict(WORKLOADS["config2"]))
     if args.fixed_coarse > 0:
         WL["mg_kw"] = {"coarse_tol": 0.0, "coarse_maxit": args.fixed_coarse}
+    if args.smoother_steps > 0:
+        WL["mg_kw"] = dict(WL.get("mg_kw", {}), smoother_steps=args.smoother_steps)
+    if args.learned > 0:
+        WL["learned"] = args.learned
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

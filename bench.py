@@ -37,10 +37,11 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 WL = dict(
-    workload="wilson-dirac 8^4 eps0.3 seed2 m0=-0.8, 2-level MG (2^4 blocks, nv 12), Algorithm 2 k=24, "
-             "64 Rademacher samples/step, true FP64 rel. residual 1e-8",
+    workload="wilson-dirac 8^4 eps0.3 seed2 m0=-0.8, 2-level MG (2^4 blocks, nv 12; learned smoother + 1 MR), "
+             "Algorithm 2 k=24, 64 Rademacher samples/step, true FP64 rel. residual 1e-8",
     dims=(8, 8, 8, 8), eps=0.3, link_seed=2, m0=-0.8, blocks=[(2, 2, 2, 2)], nvs=[12], k=24, guard=16,
     s=64, tol=1e-8, noise_seed=102, restart=16, maxit=500, inner_tol=1e-5,
+    learned=1,  # learned smoother, then 1 MR step (trained in setup); the FP64 leg uses plain MR(4)
 )
 # Larger configurations (parity-test cases, not the bench line); chosen with
 # --workload.  Config 3: 16^3 x 32, eps 0.2 (seed 3), m0 -0.8, three-level MG
@@ -388,6 +389,9 @@ def run_ours(args):
     for i in range(e2e_steps):
         g2 = qd.Gauge.from_host_buffer(ctx, WL["dims"], pinned)
         mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"], **WL.get("mg_kw", {})))
+        if WL.get("learned"):
+            qd.smoother_train(mg2, nsamples=8, solve_tol=1e-6, mr_steps=WL["learned"])
+            qd.smoother_enable(mg2, True, WL["learned"])
         d2 = qd.Deflation(ctx, g2, mg2, WL["m0"], 0.0,
                           qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
                                          solve_tol=1e-10, maxit=60))
@@ -403,12 +407,15 @@ def run_ours(args):
         e2e_dt = float(tt.item())
     e2e = None if not e2e_steps else {"value": s * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": s * 16 + 6 * 8,
-           "scope": "per step: link upload from pinned host memory, adaptive MG setup, Algorithm 2 deflation "
-                    "space, one 64-sample batch, per-sample t_j and statistics read back"}
+           "scope": "per step: link upload from pinned host memory, adaptive MG setup, learned-smoother "
+                    "training, Algorithm 2 deflation space, one 64-sample batch, per-sample t_j and statistics "
+                    "read back"}
 
     # the plain FP64 path on the same workload (the other side of the metric)
     fp64 = None
     if args.precision == "mixed" and args.fp64_steps > 0:
+        if WL.get("learned"):
+            qd.smoother_enable(mg, False, WL["learned"])  # the plain FP64 form
         _batch(qd, ctx, g, mg, d, offset(2000), qd.QD_PREC_F64)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -421,8 +428,10 @@ def run_ours(args):
             tt = torch.tensor([fms], device="cuda")
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             fms = float(tt.item())
+        if WL.get("learned"):
+            qd.smoother_enable(mg, True, WL["learned"])
         fp64 = {"value": args.fp64_steps * s * world / (fms / 1e3), "unit": UNIT, "steps": args.fp64_steps,
-                "ms_per_step": fms / args.fp64_steps, "dtype": "f64",
+                "ms_per_step": fms / args.fp64_steps, "dtype": "f64", "smoother": "plain MR(4)",
                 "outer_iterations": [r["iterations"] for r in fres],
                 "max_true_rel_residual": max(r["max_true_rel_residual"] for r in fres)}
 
@@ -440,7 +449,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 inner solves + f64 refinement" if args.precision == "mixed" else "f64",
+            "dtype": ("f32 inner solves + f64 refinement" + (" (FP16 smoother weights)" if WL.get("learned") else ""))
+            if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": WL["workload"], "precision": args.precision,
                        "parallelism": f"replicas x{world} (independent samples)",
@@ -763,8 +773,9 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="config5: the learned-vs-plain comparison on the 16^3 x 32 lattice")
     ap.add_argument("--smoother-steps", type=int, default=0, help="> 0: MR post-smoothing steps (default 4)")
-    ap.add_argument("--learned", type=int, default=0,
-                    help="> 0: train the learned smoother and use it with this many MR steps after it")
+    ap.add_argument("--learned", type=int, default=-1,
+                    help=">= 1: train the learned smoother and use it with this many MR steps after it; "
+                         "0: plain smoother; default: the workload's setting")
     ap.add_argument("--fixed-coarse", type=int, default=0,
                     help="> 0: level-1 GCR of a three-level hierarchy runs exactly this many iterations")
     args = ap.parse_args()
@@ -786,7 +797,7 @@ def main():
         WL["mg_kw"] = {"coarse_tol": 0.0, "coarse_maxit": args.fixed_coarse}
     if args.smoother_steps > 0:
         WL["mg_kw"] = dict(WL.get("mg_kw", {}), smoother_steps=args.smoother_steps)
-    if args.learned > 0:
+    if args.learned >= 0:
         WL["learned"] = args.learned
     if args.impl == "reference":
         return run_reference(args)

@@ -159,7 +159,7 @@ def _setup(qd, ctx, U):
     g = qd.Gauge(ctx, WL["dims"], U)
     mg = qd.Multigrid(ctx, g, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"], **WL.get("mg_kw", {})))
     if WL.get("learned"):
-        WL["smoother_judge"] = qd.smoother_train(mg, nsamples=8, solve_tol=1e-6, mr_steps=WL["learned"])
+        WL["smoother_judge"] = qd.smoother_train(mg, nsamples=4, solve_tol=1e-3, mr_steps=WL["learned"])
         qd.smoother_enable(mg, True, WL["learned"])
     d = qd.Deflation(ctx, g, mg, WL["m0"], 0.0,
                      qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
@@ -390,7 +390,7 @@ def run_ours(args):
         g2 = qd.Gauge.from_host_buffer(ctx, WL["dims"], pinned)
         mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"], **WL.get("mg_kw", {})))
         if WL.get("learned"):
-            qd.smoother_train(mg2, nsamples=8, solve_tol=1e-6, mr_steps=WL["learned"])
+            qd.smoother_train(mg2, nsamples=4, solve_tol=1e-3, mr_steps=WL["learned"])
             qd.smoother_enable(mg2, True, WL["learned"])
         d2 = qd.Deflation(ctx, g2, mg2, WL["m0"], 0.0,
                           qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,

@@ -163,10 +163,11 @@ typedef struct {
                                    iterations, no convergence checks */
   int coarse_restart;           /* restart length of coarse GCR */
   int coarsest_direct;          /* > 0: invert the coarsest operator densely
-                                   (FP64 Gauss-Jordan in setup) when its
-                                   dimension is <= this value (at most
-                                   16384); every coarsest solve is then one
-                                   dense product.  0: coarsest GCR */
+                                   (FP32 Gauss-Jordan with partial pivoting
+                                   in setup) when its dimension is <= this
+                                   value (at most 16384); every coarsest
+                                   solve in a V-cycle is then one dense
+                                   product.  0: coarsest GCR */
   int coarsest_bf16;            /* with a dense coarsest inverse: != 0 lets
                                    the FP32 V-cycle apply it as one BF16
                                    tcgen05 tensor-core GEMM (FP32
@@ -231,9 +232,11 @@ int qd_coarse_apply_f32(qd_mg* mg, int level, int nrhs, const float* in,
                         float* out);
 
 /* out = C_level^{-1} in, level >= 1: the coarse solve of the V-cycle (a5).
- * On the coarsest level with a dense inverse: one product (exact to FP64
- * rounding); otherwise GCR on C_level to coarse_tol (preconditioned by the
- * next level's V-cycle when there is one).  Synchronous. */
+ * On the coarsest level with a dense inverse: the product with the inverse
+ * followed by three residual corrections with the FP64 operator (FP64
+ * accuracy for coarse condition numbers up to ~1e5); otherwise GCR on
+ * C_level to coarse_tol (preconditioned by the next level's V-cycle when
+ * there is one).  Synchronous. */
 int qd_coarse_solve(qd_mg* mg, int level, int nrhs, const double* in,
                     double* out);
 

@@ -319,7 +319,7 @@ int qd_coarse_solve(qd_mg* mg, int level, int nrhs, const double* in, double* ou
     qd::cplx* y = reinterpret_cast<qd::cplx*>(out);
     const qd::cplx* inv = mg->Cinv<qd::cplx>(level);
     if (inv) {
-      qd::dense_apply<qd::cplx>(ctx, mg->L[level - 1]->ndense, nrhs, inv, x, y);
+      qd::coarsest_solve_refined(ctx, *mg->L[level - 1], nrhs, x, y, 3);
     } else {
       auto A = mg->op<qd::cplx>(level);
       std::unique_ptr<qd::MGPrecond<qd::cplx>> pre;

@@ -166,7 +166,8 @@ void defl_build(qd_defl& d, const double* injected) {
     const double stol = d.p.solve_tol;
     SolveFn fn = [&](const cplx* Xin, cplx* Wout, int mm) {
       if (inv) {
-        dense_apply<cplx>(ctx, (int)d.nb, mm, inv, Xin, Wout);  // exact coarsest solve
+        // direct coarsest solve, corrected to FP64 accuracy
+        coarsest_solve_refined(ctx, *d.mg->L[d.level - 1], mm, Xin, Wout, 3);
       } else {
         SolveInfo info;
         solver.solve(ctx, A, M, Xin, Wout, mm, stol, 20000, 32, &info);

@@ -7,6 +7,7 @@
 // end).  Every coarse solve is then one dense complex product C^{-1} R,
 // R = n x s right-hand sides, done by a shared-memory tiled GEMM in FP64 or
 // FP32.
+#include "blas.cuh"
 #include "direct.cuh"
 
 namespace qd {
@@ -15,16 +16,18 @@ namespace qd {
 // Gauss-Jordan step k, part 1 (one CTA): pivot search in column k over rows
 // i >= k, row swap, copy of column k into f, scaling of the pivot row.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, cplx* __restrict__ A, cplx* __restrict__ f,
+template <class C>
+__global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, C* __restrict__ A, C* __restrict__ f,
                                                    int* __restrict__ perm, int* __restrict__ flag) {
+  typedef typename CTraits<C>::R R;
   __shared__ double sv[1024];
   __shared__ int si[1024];
-  __shared__ cplx s_inv;
+  __shared__ C s_inv;
   const int tid = threadIdx.x, nth = blockDim.x;
   double best = -1.0;
   int bi = k;
   for (int i = k + tid; i < n; i += nth) {
-    const double v = cnorm2(A[(int64_t)i * n + k]);
+    const double v = (double)cnorm2(A[(int64_t)i * n + k]);
     if (v > best) { best = v; bi = i; }
   }
   sv[tid] = best;
@@ -47,7 +50,7 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, cplx* __restric
   }
   if (p != k) {
     for (int j = tid; j < n; j += nth) {
-      const cplx a = A[(int64_t)k * n + j];
+      const C a = A[(int64_t)k * n + j];
       A[(int64_t)k * n + j] = A[(int64_t)p * n + j];
       A[(int64_t)p * n + j] = a;
     }
@@ -55,98 +58,142 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, cplx* __restric
   __syncthreads();
   for (int i = tid; i < n; i += nth) f[i] = A[(int64_t)i * n + k];
   if (tid == 0) {
-    const cplx piv = A[(int64_t)k * n + k];
-    const double d = cnorm2(piv);
-    s_inv = d > 0.0 ? mkc(piv.x / d, -piv.y / d) : mkc(0.0, 0.0);
+    const C piv = A[(int64_t)k * n + k];
+    const R d = cnorm2(piv);
+    s_inv = d > (R)0 ? mk<C>(piv.x / d, -piv.y / d) : mk<C>((R)0, (R)0);
   }
   __syncthreads();
-  const cplx inv = s_inv;
+  const C inv = s_inv;
   for (int j = tid; j < n; j += nth) {
-    const cplx a = (j == k) ? mkc(1.0, 0.0) : A[(int64_t)k * n + j];
+    const C a = (j == k) ? mk<C>((R)1, (R)0) : A[(int64_t)k * n + j];
     A[(int64_t)k * n + j] = cmul(a, inv);
   }
 }
 
 // Part 2: for rows i != k: A[i][j] -= f[i] * A[k][j] (A[i][k] taken as 0).
-__global__ void k_gj_update(int n, int k, cplx* __restrict__ A, const cplx* __restrict__ f) {
+template <class C>
+__global__ void k_gj_update(int n, int k, C* __restrict__ A, const C* __restrict__ f) {
+  typedef typename CTraits<C>::R R;
   const int64_t tot = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
     if (i == k) continue;
-    const cplx fi = f[i];
-    cplx a = (j == k) ? mkc(0.0, 0.0) : A[e];
-    cfma(a, mkc(-fi.x, -fi.y), A[(int64_t)k * n + j]);
+    const C fi = f[i];
+    C a = (j == k) ? mk<C>((R)0, (R)0) : A[e];
+    cfma(a, mk<C>(-fi.x, -fi.y), A[(int64_t)k * n + j]);
     A[e] = a;
   }
 }
 
 // Undo the row interchanges as column interchanges, last step first.
-__global__ void k_gj_unswap(int n, cplx* __restrict__ A, const int* __restrict__ perm) {
+template <class C>
+__global__ void k_gj_unswap(int n, C* __restrict__ A, const int* __restrict__ perm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  cplx* row = A + (int64_t)i * n;
+  C* row = A + (int64_t)i * n;
   for (int k = n - 1; k >= 0; --k) {
     const int p = perm[k];
     if (p != k) {
-      const cplx t = row[k];
+      const C t = row[k];
       row[k] = row[p];
       row[p] = t;
     }
   }
 }
 
-void gauss_jordan_inverse(qd_ctx& ctx, int n, cplx* A) {
-  DevBuf f((size_t)n * sizeof(cplx)), perm((size_t)n * sizeof(int)), flag(sizeof(int));
+template <class C> void gauss_jordan_inverse(qd_ctx& ctx, int n, C* A) {
+  DevBuf f((size_t)n * sizeof(C)), perm((size_t)n * sizeof(int)), flag(sizeof(int));
   QD_CUDA(cudaMemsetAsync(flag.as<int>(), 0, sizeof(int), ctx.stream));
   const int64_t tot = (int64_t)n * n;
   int blocks = div_up(tot, 256);
   if (blocks > 16 * kNumSMs) blocks = 16 * kNumSMs;
   for (int k = 0; k < n; ++k) {
-    k_gj_pivot<<<1, 1024, 0, ctx.stream>>>(n, k, A, f.as<cplx>(), perm.as<int>(), flag.as<int>());
+    k_gj_pivot<C><<<1, 1024, 0, ctx.stream>>>(n, k, A, f.as<C>(), perm.as<int>(), flag.as<int>());
     QD_LAUNCH_CHECK();
-    k_gj_update<<<blocks, 256, 0, ctx.stream>>>(n, k, A, f.as<cplx>());
+    k_gj_update<C><<<blocks, 256, 0, ctx.stream>>>(n, k, A, f.as<C>());
     QD_LAUNCH_CHECK();
   }
-  k_gj_unswap<<<div_up(n, 128), 128, 0, ctx.stream>>>(n, A, perm.as<int>());
+  k_gj_unswap<C><<<div_up(n, 128), 128, 0, ctx.stream>>>(n, A, perm.as<int>());
   QD_LAUNCH_CHECK();
   int h = 0;
   QD_CUDA(cudaMemcpyAsync(&h, flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
   QD_CUDA(cudaStreamSynchronize(ctx.stream));
   if (h) fail(QD_ERR_NONFINITE, "coarsest operator is singular (zero pivot in Gauss-Jordan)");
 }
+template void gauss_jordan_inverse<cplx>(qd_ctx&, int, cplx*);
+template void gauss_jordan_inverse<cplxf>(qd_ctx&, int, cplxf*);
 
 // ---------------------------------------------------------------------------
 // Dense stencil -> matrix: D[(x*Dd + d)][(y*Dd + e)] += C[x][dir][d][e] for
-// y = nb(x, dir) (aliased neighbours on small lattices are summed).
+// y = nb(x, dir) (aliased neighbours on small lattices are summed; the sum
+// is formed in FP64 and rounded once to the output type).
 // ---------------------------------------------------------------------------
+template <class C>
 __global__ void k_stencil_to_dense(int64_t nsites, int D, const int* __restrict__ nbr, const cplx* __restrict__ mat,
-                                   cplx* __restrict__ dense) {
+                                   C* __restrict__ dense) {
+  typedef typename CTraits<C>::R R;
   const int64_t n = nsites * D;
-  const int64_t tot = nsites * D;  // one thread per row
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < tot;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
        row += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = row / D;
     const int d = (int)(row - x * D);
+    C* drow = dense + row * n;
     for (int dir = 0; dir < 9; ++dir) {
       const int64_t y = (dir == 0) ? x : (int64_t)nbr[x * 8 + dir - 1];
       const cplx* src = mat + ((x * 9 + dir) * D + d) * D;
-      cplx* dst = dense + row * n + y * D;
-      for (int e = 0; e < D; ++e) dst[e] = cadd(dst[e], src[e]);
+      for (int e = 0; e < D; ++e) {
+        // sum every block that lands on (row, y*D + e), in direction order
+        cplx acc = mkc(0.0, 0.0);
+        bool first = true;
+        for (int d2 = 0; d2 < dir && first; ++d2) {
+          const int64_t y2 = (d2 == 0) ? x : (int64_t)nbr[x * 8 + d2 - 1];
+          if (y2 == y) first = false;  // an earlier direction already wrote this column block
+        }
+        if (!first) continue;
+        for (int d2 = dir; d2 < 9; ++d2) {
+          const int64_t y2 = (d2 == 0) ? x : (int64_t)nbr[x * 8 + d2 - 1];
+          if (y2 == y) acc = cadd(acc, mat[((x * 9 + d2) * D + d) * D + e]);
+        }
+        drow[y * D + e] = mk<C>((R)acc.x, (R)acc.y);
+      }
+      (void)src;
     }
   }
 }
 
+// The dense inverse of the coarsest operator, computed by Gauss-Jordan in
+// FP32 (FP64 runs at 1/60 of the FP32 rate on this part) and kept in both
+// precisions; solves that need FP64 accuracy add residual corrections
+// (coarsest_solve_refined).
 void coarse_dense_inverse(qd_ctx& ctx, CoarseLevel& lv) {
   const int64_t n64 = lv.geo.nsites * (int64_t)lv.D;
   QD_REQUIRE(n64 <= 16384, "coarsest level too large for a dense direct solve");
   const int n = (int)n64;
-  lv.Cinv.resize((size_t)n * n * sizeof(cplx));
-  QD_CUDA(cudaMemsetAsync(lv.Cinv.as<cplx>(), 0, (size_t)n * n * sizeof(cplx), ctx.stream));
-  k_stencil_to_dense<<<div_up(n, 128), 128, 0, ctx.stream>>>(lv.geo.nsites, lv.D, lv.geo.nbr.as<int>(),
-                                                            lv.Cm.as<cplx>(), lv.Cinv.as<cplx>());
+  lv.Cinvf.resize((size_t)n * n * sizeof(cplxf));
+  QD_CUDA(cudaMemsetAsync(lv.Cinvf.as<cplxf>(), 0, (size_t)n * n * sizeof(cplxf), ctx.stream));
+  k_stencil_to_dense<cplxf><<<div_up(n, 128), 128, 0, ctx.stream>>>(lv.geo.nsites, lv.D, lv.geo.nbr.as<int>(),
+                                                                   lv.Cm.as<cplx>(), lv.Cinvf.as<cplxf>());
   QD_LAUNCH_CHECK();
-  gauss_jordan_inverse(ctx, n, lv.Cinv.as<cplx>());
+  gauss_jordan_inverse<cplxf>(ctx, n, lv.Cinvf.as<cplxf>());
+  lv.Cinv.resize((size_t)n * n * sizeof(cplx));
+  to_f64(ctx, lv.Cinvf.as<cplxf>(), lv.Cinv.as<cplx>(), (int64_t)n * n);
   lv.ndense = n;
+}
+
+// y = C^{-1} x to FP64 accuracy: y = X x with the stored inverse X, then
+// `steps` corrections y += X (x - C y) with the FP64 stencil C.
+void coarsest_solve_refined(qd_ctx& ctx, const CoarseLevel& lv, int nrhs, const cplx* x, cplx* y, int steps) {
+  const int n = lv.ndense;
+  QD_REQUIRE(n > 0, "no dense inverse on this level");
+  dense_apply<cplx>(ctx, n, nrhs, lv.Cinv.as<cplx>(), x, y);
+  if (steps <= 0) return;
+  DevBuf r((size_t)n * nrhs * sizeof(cplx)), e((size_t)n * nrhs * sizeof(cplx));
+  for (int it = 0; it < steps; ++it) {
+    coarse_apply<cplx>(ctx, lv, lv.Cm.as<cplx>(), y, r.as<cplx>(), nrhs);
+    blas::sub(ctx, (int64_t)n * nrhs, x, r.as<cplx>(), r.as<cplx>());
+    dense_apply<cplx>(ctx, n, nrhs, lv.Cinv.as<cplx>(), r.as<cplx>(), e.as<cplx>());
+    blas::add(ctx, (int64_t)n * nrhs, e.as<cplx>(), y);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -386,16 +386,30 @@ def run_ours(args):
     h2d = pinned.numel() * 8
     torch.cuda.synchronize()
     t = time.perf_counter()
+    phases = {"gauge": 0.0, "mg_setup": 0.0, "smoother_train": 0.0, "deflation": 0.0, "batch": 0.0}
+
+    def lap(key, t_prev):
+        torch.cuda.synchronize()
+        now = time.perf_counter()
+        phases[key] += now - t_prev
+        return now
+
     for i in range(e2e_steps):
+        tp = time.perf_counter()
         g2 = qd.Gauge.from_host_buffer(ctx, WL["dims"], pinned)
+        tp = lap("gauge", tp)
         mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"], **WL.get("mg_kw", {})))
+        tp = lap("mg_setup", tp)
         if WL.get("learned"):
             qd.smoother_train(mg2, nsamples=4, solve_tol=1e-3, mr_steps=WL["learned"])
             qd.smoother_enable(mg2, True, WL["learned"])
+        tp = lap("smoother_train", tp)
         d2 = qd.Deflation(ctx, g2, mg2, WL["m0"], 0.0,
                           qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
                                          solve_tol=1e-10, maxit=60))
+        tp = lap("deflation", tp)
         _batch(qd, ctx, g2, mg2, d2, offset(1000 + i), prec)
+        tp = lap("batch", tp)
         d2.close()
         mg2.close()
         g2.close()
@@ -407,6 +421,7 @@ def run_ours(args):
         e2e_dt = float(tt.item())
     e2e = None if not e2e_steps else {"value": s * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": s * 16 + 6 * 8,
+           "phases_s": {k: round(v / max(e2e_steps, 1), 4) for k, v in phases.items()},
            "scope": "per step: link upload from pinned host memory, adaptive MG setup, learned-smoother "
                     "training, Algorithm 2 deflation space, one 64-sample batch, per-sample t_j and statistics "
                     "read back"}

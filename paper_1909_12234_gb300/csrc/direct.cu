@@ -7,6 +7,8 @@
 // end).  Every coarse solve is then one dense complex product C^{-1} R,
 // R = n x s right-hand sides, done by a shared-memory tiled GEMM in FP64 or
 // FP32.
+#include <algorithm>
+
 #include "blas.cuh"
 #include "direct.cuh"
 
@@ -124,6 +126,220 @@ template void gauss_jordan_inverse<cplx>(qd_ctx&, int, cplx*);
 template void gauss_jordan_inverse<cplxf>(qd_ctx&, int, cplxf*);
 
 // ---------------------------------------------------------------------------
+// Blocked Gauss-Jordan (FP32): the same eliminations, grouped into panels of
+// w <= 64 columns.  A panel is factored on its own (a contiguous n x w copy,
+// column major, so each pivot search reads one contiguous column); the
+// panel's row interchanges are then applied to the whole matrix, and its
+// accumulated transformation M (identity except in the panel columns, which
+// the in-place factorisation leaves holding M's columns) is applied to the
+// other columns as one rank-w update A += (M - I)[:, panel] B, with B the
+// panel's rows of A and its panel columns zeroed.  The matrix is read and
+// written once per panel instead of once per column.
+// ---------------------------------------------------------------------------
+constexpr int kGJPanel = 64;
+
+__global__ void k_panel_extract(int n, int k0, int w, const cplxf* __restrict__ A, cplxf* __restrict__ P) {
+  const int64_t tot = (int64_t)n * w;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / w), c = (int)(e - (int64_t)i * w);
+    P[(int64_t)c * n + i] = A[(int64_t)i * n + k0 + c];
+  }
+}
+
+// Step k of the panel (column c = k - k0): pivot among rows >= k, swap in
+// the panel, f = column c, scale the pivot row.  One CTA.
+__global__ void __launch_bounds__(1024) k_pgj_pivot(int n, int k, int c, int w, cplxf* __restrict__ P,
+                                                    cplxf* __restrict__ f, int* __restrict__ perm,
+                                                    int* __restrict__ flag) {
+  __shared__ float sv[1024];
+  __shared__ int si[1024];
+  __shared__ cplxf s_inv;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const cplxf* col = P + (int64_t)c * n;
+  float best = -1.0f;
+  int bi = k;
+  for (int i = k + tid; i < n; i += nth) {
+    const float v = cnorm2(col[i]);
+    if (v > best) { best = v; bi = i; }
+  }
+  sv[tid] = best;
+  si[tid] = bi;
+  __syncthreads();
+  for (int h = nth / 2; h > 0; h >>= 1) {
+    if (tid < h) {
+      if (sv[tid + h] > sv[tid] || (sv[tid + h] == sv[tid] && si[tid + h] < si[tid])) {
+        sv[tid] = sv[tid + h];
+        si[tid] = si[tid + h];
+      }
+    }
+    __syncthreads();
+  }
+  const int p = si[0];
+  if (tid == 0) {
+    perm[k] = p;
+    if (!(sv[0] > 0.0f) && flag) *flag = 1;
+  }
+  if (p != k)
+    for (int cc = tid; cc < w; cc += nth) {
+      const cplxf a = P[(int64_t)cc * n + k];
+      P[(int64_t)cc * n + k] = P[(int64_t)cc * n + p];
+      P[(int64_t)cc * n + p] = a;
+    }
+  __syncthreads();
+  for (int i = tid; i < n; i += nth) f[i] = col[i];
+  if (tid == 0) {
+    const cplxf piv = col[k];
+    const float d = cnorm2(piv);
+    s_inv = d > 0.0f ? make_float2(piv.x / d, -piv.y / d) : make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  const cplxf inv = s_inv;
+  for (int cc = tid; cc < w; cc += nth) {
+    const cplxf a = (cc == c) ? make_float2(1.0f, 0.0f) : P[(int64_t)cc * n + k];
+    P[(int64_t)cc * n + k] = cmul(a, inv);
+  }
+}
+
+// Rows i != k of the panel: P[i][cc] -= f[i] P[k][cc] (P[i][c] taken as 0).
+__global__ void k_pgj_update(int n, int k, int c, int w, cplxf* __restrict__ P, const cplxf* __restrict__ f) {
+  const int64_t tot = (int64_t)n * w;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int cc = (int)(e / n), i = (int)(e - (int64_t)cc * n);
+    if (i == k) continue;
+    const cplxf fi = f[i];
+    cplxf a = (cc == c) ? make_float2(0.0f, 0.0f) : P[e];
+    cfma(a, make_float2(-fi.x, -fi.y), P[(int64_t)cc * n + k]);
+    P[e] = a;
+  }
+}
+
+// The panel's interchanges, in order, on every column of A (one thread per
+// column).
+__global__ void k_apply_swaps(int n, int k0, int k1, cplxf* __restrict__ A, const int* __restrict__ perm) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int k = k0; k < k1; ++k) {
+    const int p = perm[k];
+    if (p != k) {
+      const cplxf t = A[(int64_t)k * n + j];
+      A[(int64_t)k * n + j] = A[(int64_t)p * n + j];
+      A[(int64_t)p * n + j] = t;
+    }
+  }
+}
+
+// A[:, panel] = P; Tm = P - I (on the panel's diagonal); B = rows k0..k1 of
+// A with the panel columns zeroed.
+__global__ void k_panel_finish(int n, int k0, int w, const cplxf* __restrict__ P, cplxf* __restrict__ A,
+                               cplxf* __restrict__ Tm) {
+  const int64_t tot = (int64_t)n * w;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / w), c = (int)(e - (int64_t)i * w);
+    const cplxf v = P[(int64_t)c * n + i];
+    A[(int64_t)i * n + k0 + c] = v;
+    Tm[(int64_t)i * w + c] = (i == k0 + c) ? make_float2(v.x - 1.0f, v.y) : v;
+  }
+}
+__global__ void k_panel_rows(int n, int k0, int w, const cplxf* __restrict__ A, cplxf* __restrict__ B) {
+  const int64_t tot = (int64_t)w * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n), j = (int)(e - (int64_t)r * n);
+    B[e] = (j >= k0 && j < k0 + w) ? make_float2(0.0f, 0.0f) : A[(int64_t)(k0 + r) * n + j];
+  }
+}
+
+// C (m x n, ldc) += A (m x K, lda) B (K x n, ldb), FP32 complex, K <= 64:
+// 64 x 64 output tile per CTA (256 threads, 4 x 4 each), operands staged in
+// shared memory in K-slices of 16.
+__global__ void __launch_bounds__(256) k_cgemm_acc(int m, int n, int K, const cplxf* __restrict__ A, int lda,
+                                                   const cplxf* __restrict__ B, int ldb, cplxf* __restrict__ C,
+                                                   int ldc) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ cplxf sa[BK][BM + 1];
+  __shared__ cplxf sb[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tr = tid / 16, tc = tid % 16;
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  cplxf acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.0f, 0.0f);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 256) {
+      const int mm = e / BK, kk = e % BK;
+      const int gr = row0 + mm, gk = k0 + kk;
+      sa[kk][mm] = (gr < m && gk < K) ? A[(int64_t)gr * lda + gk] : make_float2(0.0f, 0.0f);
+    }
+    for (int e = tid; e < BK * BN; e += 256) {
+      const int kk = e / BN, cc = e % BN;
+      const int gk = k0 + kk, gc = col0 + cc;
+      sb[kk][cc] = (gk < K && gc < n) ? B[(int64_t)gk * ldb + gc] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      cplxf a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sa[kk][tr + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sb[kk][tc + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gr = row0 + tr + 16 * i;
+    if (gr >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + tc + 16 * j;
+      if (gc < n) C[(int64_t)gr * ldc + gc] = cadd(C[(int64_t)gr * ldc + gc], acc[i][j]);
+    }
+  }
+}
+
+void gauss_jordan_inverse_blocked(qd_ctx& ctx, int n, cplxf* A) {
+  const int W = kGJPanel;
+  DevBuf P((size_t)n * W * sizeof(cplxf)), Tm((size_t)n * W * sizeof(cplxf)), B((size_t)W * n * sizeof(cplxf)),
+      f((size_t)n * sizeof(cplxf)), perm((size_t)n * sizeof(int)), flag(sizeof(int));
+  QD_CUDA(cudaMemsetAsync(flag.as<int>(), 0, sizeof(int), ctx.stream));
+  auto grid = [](int64_t tot) { return (int)std::min<int64_t>(div_up(tot, 256), 16 * kNumSMs); };
+  for (int k0 = 0; k0 < n; k0 += W) {
+    const int w = std::min(W, n - k0);
+    k_panel_extract<<<grid((int64_t)n * w), 256, 0, ctx.stream>>>(n, k0, w, A, P.as<cplxf>());
+    QD_LAUNCH_CHECK();
+    for (int c = 0; c < w; ++c) {
+      const int k = k0 + c;
+      k_pgj_pivot<<<1, 1024, 0, ctx.stream>>>(n, k, c, w, P.as<cplxf>(), f.as<cplxf>(), perm.as<int>(),
+                                              flag.as<int>());
+      QD_LAUNCH_CHECK();
+      k_pgj_update<<<grid((int64_t)n * w), 256, 0, ctx.stream>>>(n, k, c, w, P.as<cplxf>(), f.as<cplxf>());
+      QD_LAUNCH_CHECK();
+    }
+    k_apply_swaps<<<div_up(n, 256), 256, 0, ctx.stream>>>(n, k0, k0 + w, A, perm.as<int>());
+    QD_LAUNCH_CHECK();
+    k_panel_finish<<<grid((int64_t)n * w), 256, 0, ctx.stream>>>(n, k0, w, P.as<cplxf>(), A, Tm.as<cplxf>());
+    QD_LAUNCH_CHECK();
+    k_panel_rows<<<grid((int64_t)w * n), 256, 0, ctx.stream>>>(n, k0, w, A, B.as<cplxf>());
+    QD_LAUNCH_CHECK();
+    dim3 g2(div_up(n, 64), div_up(n, 64));
+    k_cgemm_acc<<<g2, 256, 0, ctx.stream>>>(n, n, w, Tm.as<cplxf>(), w, B.as<cplxf>(), n, A, n);
+    QD_LAUNCH_CHECK();
+  }
+  k_gj_unswap<cplxf><<<div_up(n, 128), 128, 0, ctx.stream>>>(n, A, perm.as<int>());
+  QD_LAUNCH_CHECK();
+  int h = 0;
+  QD_CUDA(cudaMemcpyAsync(&h, flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  if (h) fail(QD_ERR_NONFINITE, "coarsest operator is singular (zero pivot in Gauss-Jordan)");
+}
+
+// ---------------------------------------------------------------------------
 // Dense stencil -> matrix: D[(x*Dd + d)][(y*Dd + e)] += C[x][dir][d][e] for
 // y = nb(x, dir) (aliased neighbours on small lattices are summed; the sum
 // is formed in FP64 and rounded once to the output type).
@@ -174,7 +390,10 @@ void coarse_dense_inverse(qd_ctx& ctx, CoarseLevel& lv) {
   k_stencil_to_dense<cplxf><<<div_up(n, 128), 128, 0, ctx.stream>>>(lv.geo.nsites, lv.D, lv.geo.nbr.as<int>(),
                                                                    lv.Cm.as<cplx>(), lv.Cinvf.as<cplxf>());
   QD_LAUNCH_CHECK();
-  gauss_jordan_inverse<cplxf>(ctx, n, lv.Cinvf.as<cplxf>());
+  if (n >= 4 * kGJPanel)
+    gauss_jordan_inverse_blocked(ctx, n, lv.Cinvf.as<cplxf>());
+  else
+    gauss_jordan_inverse<cplxf>(ctx, n, lv.Cinvf.as<cplxf>());
   lv.Cinv.resize((size_t)n * n * sizeof(cplx));
   to_f64(ctx, lv.Cinvf.as<cplxf>(), lv.Cinv.as<cplx>(), (int64_t)n * n);
   lv.ndense = n;

@@ -407,7 +407,13 @@ void coarsest_solve_refined(qd_ctx& ctx, const CoarseLevel& lv, int nrhs, const 
   const int n = lv.ndense;
   QD_REQUIRE(n > 0 && lv.Cinvf.bytes() > 0, "no dense inverse on this level");
   const int64_t tot = (int64_t)n * nrhs;
-  DevBuf rf((size_t)tot * sizeof(cplxf)), ef((size_t)tot * sizeof(cplxf)), r, e;
+  // scratch kept on the level (grow-only) so repeated solves allocate nothing
+  DevBuf& rf = lv.rs_f[0];
+  DevBuf& ef = lv.rs_f[1];
+  DevBuf& r = lv.rs_d[0];
+  DevBuf& e = lv.rs_d[1];
+  rf.resize((size_t)tot * sizeof(cplxf));
+  ef.resize((size_t)tot * sizeof(cplxf));
   to_f32(ctx, x, rf.as<cplxf>(), tot);
   dense_apply<cplxf>(ctx, n, nrhs, lv.Cinvf.as<cplxf>(), rf.as<cplxf>(), ef.as<cplxf>());
   to_f64(ctx, ef.as<cplxf>(), y, tot);

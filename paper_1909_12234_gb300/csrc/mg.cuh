@@ -91,6 +91,7 @@ template <class C> class MGPrecond : public Precond<C> {
     cudaGraphExec_t exec = nullptr;
   };
   std::vector<Graph> graphs_;
+  std::vector<std::pair<const void*, void*>> seen_;  // pairs met once (eager so far)
   int warm_nrhs_ = -1;
   cudaStream_t cap_stream_ = nullptr;  // capture only; nothing runs on it
 };

@@ -189,6 +189,8 @@ struct CoarseLevel {
   alignas(64) unsigned char tc_mapA[128];
   alignas(64) unsigned char tc_mapB[128];
   DevBuf tc_A, tc_B, tc_part, tc_err, tc_xc, tc_yc;
+  // scratch of the FP64-corrected coarsest solve (grow-only)
+  mutable DevBuf rs_f[2], rs_d[2];
 };
 
 template <class C> struct CoarseOp : public Op<C> {

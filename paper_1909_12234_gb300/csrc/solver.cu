@@ -361,6 +361,7 @@ template <class C> MGPrecond<C>::~MGPrecond() {
 template <class C> void MGPrecond<C>::drop_graphs() {
   for (Graph& g : graphs_) cudaGraphExecDestroy(g.exec);
   graphs_.clear();
+  seen_.clear();
 }
 
 // No host synchronisation anywhere below this level: the next level has a
@@ -417,6 +418,17 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
     // first call at this size: eager, so that every buffer reaches its size
     body(ctx, r, z, nrhs);
     warm_nrhs_ = nrhs;
+    seen_.clear();
+    return;
+  }
+  // capture an (input, output) pair only when it comes back: one-shot
+  // solves (setup, training) run eagerly and pay no capture
+  bool again = false;
+  for (const auto& pr : seen_)
+    if (pr.first == r && pr.second == z) again = true;
+  if (!again) {
+    if (seen_.size() < 64) seen_.push_back({r, z});
+    body(ctx, r, z, nrhs);
     return;
   }
   // capture on a private stream (the caller's may be the legacy default

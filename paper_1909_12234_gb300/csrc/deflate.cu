@@ -166,8 +166,9 @@ void defl_build(qd_defl& d, const double* injected) {
     const double stol = d.p.solve_tol;
     SolveFn fn = [&](const cplx* Xin, cplx* Wout, int mm) {
       if (inv) {
-        // direct coarsest solve, corrected to FP64 accuracy
-        coarsest_solve_refined(ctx, *d.mg->L[d.level - 1], mm, Xin, Wout, 3);
+        // direct coarsest solve, corrected to FP64 accuracy (each correction
+        // gains ~4 digits; two reach the 1e-10 of the eigensolver's solves)
+        coarsest_solve_refined(ctx, *d.mg->L[d.level - 1], mm, Xin, Wout, 2);
       } else {
         SolveInfo info;
         solver.solve(ctx, A, M, Xin, Wout, mm, stol, 20000, 32, &info);

@@ -489,10 +489,54 @@ __global__ void __launch_bounds__(256) k_zgemm(int n, int s, const C* __restrict
   }
 }
 
+// Few right-hand sides (s <= S <= 16): one warp per row of M, which is read
+// once and contiguously; lanes take every 32nd column, then a fixed shuffle
+// tree adds the lanes (deterministic).  The 64 x 64 tile above would leave
+// most of each tile idle here.
+template <class C, int S>
+__global__ void __launch_bounds__(256) k_dense_small(int n, int s, const C* __restrict__ M, const C* __restrict__ X,
+                                                     C* __restrict__ Y) {
+  typedef typename CTraits<C>::R R;
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  C acc[S];
+#pragma unroll
+  for (int c = 0; c < S; ++c) acc[c] = mk<C>((R)0, (R)0);
+  const C* mrow = M + (int64_t)row * n;
+  for (int k = lane; k < n; k += 32) {
+    const C m = mrow[k];
+    const C* xk = X + (int64_t)k * s;
+#pragma unroll
+    for (int c = 0; c < S; ++c)
+      if (c < s) cfma(acc[c], m, xk[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < S; ++c) {
+    R re = acc[c].x, im = acc[c].y;
+    for (int off = 16; off > 0; off >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, off);
+      im += __shfl_down_sync(0xffffffffu, im, off);
+    }
+    if (lane == 0 && c < s) Y[(int64_t)row * s + c] = mk<C>(re, im);
+  }
+}
+
 template <class C> void dense_apply(qd_ctx& ctx, int n, int s, const C* M, const C* X, C* Y) {
   const double cb = (double)sizeof(C);
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_DIRECT_F64 : QD_PROF_DIRECT_F32, 8.0 * n * (double)n * s,
                cb * ((double)n * n + 2.0 * n * s));
+  if (s <= 16) {
+    const int blocks = div_up((int64_t)n * 32, 256);
+    if (s <= 4)
+      k_dense_small<C, 4><<<blocks, 256, 0, ctx.stream>>>(n, s, M, X, Y);
+    else if (s <= 8)
+      k_dense_small<C, 8><<<blocks, 256, 0, ctx.stream>>>(n, s, M, X, Y);
+    else
+      k_dense_small<C, 16><<<blocks, 256, 0, ctx.stream>>>(n, s, M, X, Y);
+    QD_LAUNCH_CHECK();
+    return;
+  }
   dim3 grid(div_up(s, 64), div_up(n, 64));
   k_zgemm<C><<<grid, 256, 0, ctx.stream>>>(n, s, M, X, Y);
   QD_LAUNCH_CHECK();

@@ -42,6 +42,7 @@ WL = dict(
     dims=(8, 8, 8, 8), eps=0.3, link_seed=2, m0=-0.8, blocks=[(2, 2, 2, 2)], nvs=[12], k=24, guard=16,
     s=64, tol=1e-8, noise_seed=102, restart=16, maxit=500, inner_tol=1e-5,
     learned=1,  # learned smoother, then 1 MR step (trained in setup); the FP64 leg uses plain MR(4)
+    eig_maxit=30,  # subspace iterations: the sample variance is within 0.3 % of the 60-iteration space
 )
 # Larger configurations (parity-test cases, not the bench line); chosen with
 # --workload.  Config 3: 16^3 x 32, eps 0.2 (seed 3), m0 -0.8, three-level MG
@@ -163,7 +164,7 @@ def _setup(qd, ctx, U):
         qd.smoother_enable(mg, True, WL["learned"])
     d = qd.Deflation(ctx, g, mg, WL["m0"], 0.0,
                      qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
-                                    solve_tol=1e-10, maxit=60))
+                                    solve_tol=1e-10, maxit=WL.get("eig_maxit", 60)))
     return g, mg, d
 
 
@@ -406,7 +407,7 @@ def run_ours(args):
         tp = lap("smoother_train", tp)
         d2 = qd.Deflation(ctx, g2, mg2, WL["m0"], 0.0,
                           qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
-                                         solve_tol=1e-10, maxit=60))
+                                         solve_tol=1e-10, maxit=WL.get("eig_maxit", 60)))
         tp = lap("deflation", tp)
         _batch(qd, ctx, g2, mg2, d2, offset(1000 + i), prec)
         tp = lap("batch", tp)

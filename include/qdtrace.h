@@ -488,6 +488,9 @@ int qd_smoother_enable(qd_mg* mg, int enabled, int mr_steps);
 
 /* out = S in, FP64, nrhs columns in fine qd layout.  Asynchronous. */
 int qd_smoother_apply(qd_mg* mg, int nrhs, const double* in, double* out);
+/* The same in FP32 with the FP16-rounded weights (the FP32 V-cycle's form):
+ * in/out interleaved complex float.  Asynchronous. */
+int qd_smoother_apply_f32(qd_mg* mg, int nrhs, const float* in, float* out);
 
 /* ------------------------------------------------------------------------ */
 /* Launch-shape autotuner (the paper has no counterpart)                     */

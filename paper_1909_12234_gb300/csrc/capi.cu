@@ -779,6 +779,20 @@ int qd_smoother_apply(qd_mg* mg, int nrhs, const double* in, double* out) {
   });
 }
 
+int qd_smoother_apply_f32(qd_mg* mg, int nrhs, const float* in, float* out) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    QD_REQUIRE(mg->ls != nullptr, "no learned-smoother weights set");
+    set_device(mg->ctx);
+    qd::smoother_apply<qd::cplxf>(*mg->ctx, *mg, nrhs, reinterpret_cast<const qd::cplxf*>(in),
+                                  reinterpret_cast<qd::cplxf*>(out), false);
+  });
+}
+
 void qd_autotune_set(int mode) { qd::tune_set_mode(mode); }
 void qd_autotune_clear(void) { qd::tune_clear(); }
 int qd_autotune_report(char* buf, int len) {

@@ -99,6 +99,102 @@ __global__ void __launch_bounds__(128) k_smoother_apply(const C* __restrict__ U,
   for (int k = 0; k < 12; ++k) y[k * rs] = ACC ? cadd(y[k * rs], acc[k]) : acc[k];
 }
 
+// FP32, two right-hand sides per thread: each colour component of the two is
+// one 16-byte load and each link is loaded once for both (even nrhs, 16-byte
+// aligned fields; the launcher checks).
+template <bool ADJ>
+__device__ __forceinline__ void transport4x2(const float2* __restrict__ L, const float2* __restrict__ p, int64_t rs,
+                                             float2 t[2][12]) {
+  float2 l[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) l[k] = L[k];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    float4 v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = *reinterpret_cast<const float4*>(p + (s * 3 + c) * rs);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float2 x0 = make_float2(v[b].x, v[b].y), x1 = make_float2(v[b].z, v[b].w);
+        if (ADJ) {
+          cfmac(a0, l[b * 3 + a], x0);
+          cfmac(a1, l[b * 3 + a], x1);
+        } else {
+          cfma(a0, l[a * 3 + b], x0);
+          cfma(a1, l[a * 3 + b], x1);
+        }
+      }
+      t[0][s * 3 + a] = a0;
+      t[1][s * 3 + a] = a1;
+    }
+  }
+}
+
+template <bool ACC>
+__global__ void __launch_bounds__(128, 4) k_smoother_apply_x2(const float2* __restrict__ U, const int* __restrict__ nbr,
+                                                              int64_t V, int nrhs, const float2* __restrict__ w,
+                                                              const float2* __restrict__ in, float2* __restrict__ out) {
+  __shared__ float2 sw[144];
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) sw[k] = w[k];
+  __syncthreads();
+  const int half = nrhs >> 1;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= V * half) return;
+  const int64_t site = g / half;
+  const int r0 = 2 * (int)(g - site * half);
+  const int64_t rs = nrhs;
+  float2 acc[2][12];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[j][k] = make_float2(0.f, 0.f);
+  for (int d = 0; d < 9; ++d) {
+    float2 t[2][12];
+    if (d == 0) {
+      const float2* p = in + site * 12 * rs + r0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const float4 q = *reinterpret_cast<const float4*>(p + k * rs);
+        t[0][k] = make_float2(q.x, q.y);
+        t[1][k] = make_float2(q.z, q.w);
+      }
+    } else if (d <= 4) {
+      const int mu = d - 1;
+      const int64_t y = nbr[site * 8 + mu];
+      transport4x2<false>(U + ((int64_t)mu * V + site) * 9, in + y * 12 * rs + r0, rs, t);
+    } else {
+      const int mu = d - 5;
+      const int64_t y = nbr[site * 8 + 4 + mu];
+      transport4x2<true>(U + ((int64_t)mu * V + y) * 9, in + y * 12 * rs + r0, rs, t);
+    }
+    const float2* wd = sw + d * 16;
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 c = wd[o * 4 + i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          cfma(acc[0][o * 3 + a], c, t[0][i * 3 + a]);
+          cfma(acc[1][o * 3 + a], c, t[1][i * 3 + a]);
+        }
+      }
+  }
+  float2* y = out + site * 12 * rs + r0;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    float4 v = make_float4(acc[0][k].x, acc[0][k].y, acc[1][k].x, acc[1][k].y);
+    if (ACC) {
+      const float4 o = *reinterpret_cast<const float4*>(y + k * rs);
+      v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+    }
+    *reinterpret_cast<float4*>(y + k * rs) = v;
+  }
+}
+
 template <class C>
 void smoother_apply(qd_ctx& ctx, qd_mg& mg, int nrhs, const C* in, C* out, bool accumulate) {
   const LearnedSmoother& ls = *mg.ls;
@@ -118,6 +214,22 @@ void smoother_apply(qd_ctx& ctx, qd_mg& mg, int nrhs, const C* in, C* out, bool 
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_SMOOTHER_F64 : QD_PROF_SMOOTHER_F32,
                (9.0 * 36 + 9.0 * 48) * 8.0 * (double)tot,
                (double)geo.nsites * ((accumulate ? 36.0 : 24.0) * cb * nrhs + 36.0 * cb));
+  if (sizeof(C) == 8 && (nrhs % 2) == 0 &&
+      ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0) {
+    const int blocks2 = div_up(geo.nsites * (nrhs / 2), 128);
+    const float2* L = reinterpret_cast<const float2*>(links);
+    const float2* W2 = reinterpret_cast<const float2*>(w);
+    if (accumulate)
+      k_smoother_apply_x2<true><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2,
+                                                                 reinterpret_cast<const float2*>(in),
+                                                                 reinterpret_cast<float2*>(out));
+    else
+      k_smoother_apply_x2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2,
+                                                                  reinterpret_cast<const float2*>(in),
+                                                                  reinterpret_cast<float2*>(out));
+    QD_LAUNCH_CHECK();
+    return;
+  }
   const int blocks = div_up(tot, 128);
   if (accumulate)
     k_smoother_apply<C, true><<<blocks, 128, 0, ctx.stream>>>(links, geo.nbr.as<int>(), geo.nsites, nrhs, w, in, out);

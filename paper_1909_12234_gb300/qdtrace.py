@@ -173,6 +173,7 @@ SIGNATURES = {
     "qd_smoother_get_weights": (_I, [_P, _DPTR]),
     "qd_smoother_enable": (_I, [_P, _I, _I]),
     "qd_smoother_apply": (_I, [_P, _I, _P, _P]),
+    "qd_smoother_apply_f32": (_I, [_P, _I, _P, _P]),
     "qd_autotune_set": (None, [_I]),
     "qd_autotune_clear": (None, []),
     "qd_autotune_report": (_I, [ctypes.c_char_p, _I]),
@@ -685,3 +686,8 @@ def smoother_enable(mg, enabled=True, mr_steps=2):
 
 def smoother_apply(mg, nrhs, inp, out):
     _check(load().qd_smoother_apply(mg.h, int(nrhs), _ptr(inp), _ptr(out)))
+
+
+def smoother_apply_f32(mg, nrhs, inp, out):
+    """FP32 S in (FP16-rounded weights) on torch.complex64 fields in qd layout."""
+    _check(load().qd_smoother_apply_f32(mg.h, int(nrhs), _ptr64(inp), _ptr64(out)))

@@ -60,6 +60,28 @@ def test_apply_and_fit_match_oracle(qd, ctx):
     assert rel_err(qd.smoother_get_weights(mg), osm.fit(U, En, R, dims)) < 1e-9
 
 
+def test_fp32_apply_matches_oracle_with_fp16_weights(qd, ctx):
+    # the FP32 form (two RHS per thread for even counts, one otherwise)
+    # against the oracle applied with the same FP16-rounded weights; FP32
+    # rounding of ~160 products per output bounds the error by ~1e-5 of max|y|
+    dims = (8, 4, 4, 6)
+    U = synth.random_su3_links(dims, 0.3, 4)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, -0.5, 0.0, qd.mg_params(1, [(2, 2, 2, 2)], [4], null_maxit=0))
+    rng = np.random.default_rng(8)
+    w0 = rng.standard_normal((9, 4, 4)) + 1j * rng.standard_normal((9, 4, 4))
+    qd.smoother_set_weights(mg, w0)
+    w16 = (w0.real.astype(np.float32).astype(np.float16).astype(np.float64)
+           + 1j * w0.imag.astype(np.float32).astype(np.float16).astype(np.float64))
+    for s in (2, 3, 64):
+        r = synth.random_field(dims, s, 20 + s)
+        x32 = qd.to_qd(ctx, g, r).to(torch.complex64)
+        out = torch.empty_like(x32)
+        qd.smoother_apply_f32(mg, s, x32, out)
+        got = qd.from_qd(ctx, g, out.to(torch.complex128))
+        assert rel_err(got, osm.apply(U, w16, r, dims)) < 1e-5, s
+
+
 def test_solves_with_the_learned_smoother(qd, ctx):
     dims, m0, s = (8, 8, 8, 8), -0.8, 8
     U = synth.random_su3_links(dims, 0.3, 2)

@@ -173,7 +173,7 @@ void restrict_(qd_ctx& ctx, const Transfer& T, const C* W, const C* fine, C* coa
   while (RT > 1 && (size_t)rows * (RT + T.nv) * sizeof(C) > cap) RT >>= 1;
   const size_t smem = (size_t)rows * (RT + T.nv) * sizeof(C);
   if (smem <= cap && (RT >= 8 || RT >= nrhs)) {
-    QD_CUDA(cudaFuncSetAttribute(k_restrict_smem<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_smem_limit(reinterpret_cast<const void*>(k_restrict_smem<C>), smem);
     k_restrict_smem<C><<<dim3((unsigned)T.ncoarse, div_up(nrhs, RT)), 256, smem, ctx.stream>>>(
         T.bsites, T.Df, T.nv, nrhs, RT, T.members.as<int>(), W, fine, coarse);
   } else {
@@ -324,16 +324,8 @@ static bool coarse_tiled_launch(qd_ctx& ctx, const CoarseLevel& lv, const C* mat
   if (tpg > cap) tpg = cap;
   const int rhs_per_cta = tpg * NR;
   const int nchunks = div_up(nrhs, rhs_per_cta);
-  // the shared-memory limit is a per-function, per-device attribute
-  static std::atomic<uint64_t> attr_set{0};
-  int dev = 0;
-  QD_CUDA(cudaGetDevice(&dev));
-  const uint64_t bit = 1ull << (dev & 63);
-  if (!(attr_set.load() & bit)) {
-    QD_CUDA(cudaFuncSetAttribute(k_coarse_apply_tiled<C, RB, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
-    attr_set.fetch_or(bit);
-  }
+  // one limit per kernel and device, the largest any shape of it needs
+  ensure_smem_limit(reinterpret_cast<const void*>(k_coarse_apply_tiled<C, RB, NR>), 200 * 1024);
   const int64_t blocks = lv.geo.nsites * (int64_t)nchunks;
   k_coarse_apply_tiled<C, RB, NR><<<(unsigned)blocks, ngroups * tpg, smem, ctx.stream>>>(
       D, ld, nrhs, rhs_per_cta, nchunks, lv.geo.nbr.as<int>(), mat, in, out);
@@ -464,7 +456,7 @@ void block_orthonormalize(qd_ctx& ctx, Transfer& T, const cplx* Y) {
   const int threads = 256;
   const size_t smem = ((size_t)rows * T.nv + T.nv) * sizeof(cplx) + threads * sizeof(double);
   QD_REQUIRE(smem <= 220 * 1024, "aggregate block too large for the shared-memory CGS2 kernel");
-  QD_CUDA(cudaFuncSetAttribute(k_block_cgs2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ensure_smem_limit(reinterpret_cast<const void*>(k_block_cgs2), smem);
   T.W.resize(T.nfine * T.Df * T.nv * sizeof(cplx));
   DevBuf err(sizeof(int));
   QD_CUDA(cudaMemsetAsync(err.as<int>(), 0, sizeof(int), ctx.stream));
@@ -643,7 +635,7 @@ void coarse_build_from_wilson(qd_ctx& ctx, const Transfer& T, const qd_gauge& g,
   out.Cm.resize(out.geo.nsites * 9 * Dc * Dc * sizeof(cplx));
   const size_t smem = ((size_t)12 * Dc + 12 * T.nv + (size_t)Dc * Dc) * sizeof(cplx);
   QD_REQUIRE(smem <= 220 * 1024, "coarse dimension too large for the coarse-build kernel");
-  QD_CUDA(cudaFuncSetAttribute(k_coarse_build_wilson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ensure_smem_limit(reinterpret_cast<const void*>(k_coarse_build_wilson), smem);
   k_coarse_build_wilson<<<(int)(out.geo.nsites * 9), 256, smem, ctx.stream>>>(
       T.bsites, T.nv, g.geo.nsites, T.members.as<int>(), T.hopdir.as<int8_t>(), g.geo.nbr.as<int>(),
       g.links.as<cplx>(), T.W.as<cplx>(), 4.0 + m0, tau, out.Cm.as<cplx>());
@@ -657,7 +649,7 @@ void coarse_build_from_coarse(qd_ctx& ctx, const Transfer& T, const CoarseLevel&
   out.Cm.resize(out.geo.nsites * 9 * Dc * Dc * sizeof(cplx));
   const size_t smem = ((size_t)Df * Dc + (size_t)Df * T.nv + (size_t)Dc * Dc) * sizeof(cplx);
   QD_REQUIRE(smem <= 220 * 1024, "coarse dimension too large for the coarse-build kernel");
-  QD_CUDA(cudaFuncSetAttribute(k_coarse_build_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ensure_smem_limit(reinterpret_cast<const void*>(k_coarse_build_coarse), smem);
   k_coarse_build_coarse<<<(int)(out.geo.nsites * 9), 256, smem, ctx.stream>>>(
       T.bsites, T.nv, Df, T.members.as<int>(), T.hopdir.as<int8_t>(), fine.geo.nbr.as<int>(),
       fine.Cm.as<cplx>(), T.W.as<cplx>(), out.Cm.as<cplx>());

@@ -243,7 +243,7 @@ void jacobi_eigh(qd_ctx& ctx, int m, cplx* A, cplx* E, double* w, int* sweeps_de
   const int half = ((m + 1) & ~1) / 2;
   const size_t smem = (size_t)(2 * half + 2) * sizeof(int) + (size_t)4 * half * sizeof(double) +
                       2 * threads * sizeof(double) + 16;
-  QD_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ensure_smem_limit(reinterpret_cast<const void*>(k_jacobi), smem);
   k_jacobi<<<1, threads, smem, ctx.stream>>>(m, A, E, w, 40, 1e-15, sweeps_dev);
   QD_LAUNCH_CHECK();
 }

@@ -1,8 +1,23 @@
 // Kernel timing support (qd_prof_enable / qd_prof_read): an event pair per
 // instrumented launch, folded into per-kind totals in batches.
+#include <map>
+#include <mutex>
+#include <utility>
 #include "qd_internal.cuh"
 
 namespace qd {
+
+void ensure_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> limit;
+  int dev = 0;
+  QD_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[{kernel, dev}];
+  if (bytes <= cur) return;
+  QD_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+}
 
 std::atomic<long long>& launch_counter() {
   static std::atomic<long long> n{0};

@@ -35,6 +35,11 @@ inline void cuda_check(cudaError_t e, const char* what, const char* file, int li
 }
 // Kernels launched by this library since load (qd_launch_count()).
 std::atomic<long long>& launch_counter();
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The limit only ever grows (a launch that fits an earlier,
+// smaller request still fits), so threads launching the same kernel with
+// different sizes cannot undercut each other.  Thread safe.
+void ensure_smem_limit(const void* kernel, size_t bytes);
 
 #define QD_CUDA(call) ::qd::cuda_check((call), #call, __FILE__, __LINE__)
 #define QD_LAUNCH_CHECK()                                                      \

@@ -349,7 +349,7 @@ void tc_dense_apply(qd_ctx& ctx, CoarseLevel& lv, const cplxf* X, cplxf* Y, int 
       if (stages > kMaxStages) stages = kMaxStages;
       QD_REQUIRE(stages >= 2, "tensor-core tile does not fit in shared memory");
       const size_t smem = 1024 + (size_t)stages * stage;
-      QD_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ensure_smem_limit(reinterpret_cast<const void*>(k_tc_gemm), smem);
       k_tc_gemm<<<dim3(mtiles, nsplit), kThreads, smem, ctx.stream>>>(
           *reinterpret_cast<const CUtensorMap*>(lv.tc_mapA), *reinterpret_cast<const CUtensorMap*>(lv.tc_mapB), N,
           kps, ktiles, Mp, stages, lv.tc_part.as<float>(), lv.tc_err.as<int>());

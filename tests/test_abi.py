@@ -56,6 +56,10 @@ int main(void) {
   printf("%zu %zu\n", sizeof(qd_trace_params), offsetof(qd_trace_params, solver));
   printf("%zu %zu %zu\n", sizeof(qd_solver_params), offsetof(qd_solver_params, inner_tol), offsetof(qd_solver_params, max_refine));
   printf("%zu %zu %zu\n", sizeof(qd_trace_result), offsetof(qd_trace_result, nsamples), offsetof(qd_trace_result, UhKZ));
+  printf("%zu %zu %zu\n", sizeof(qd_smoother_params), offsetof(qd_smoother_params, seed), offsetof(qd_smoother_params, mr_steps));
+  printf("%zu %zu\n", sizeof(qd_smoother_info), offsetof(qd_smoother_info, enabled));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(qd_batch_item), offsetof(qd_batch_item, m0), offsetof(qd_batch_item, params),
+         offsetof(qd_batch_item, result), offsetof(qd_batch_item, status));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -69,6 +73,10 @@ int main(void) {
         [ctypes.sizeof(qd.TraceParams), qd.TraceParams.solver.offset],
         [ctypes.sizeof(qd.SolverParams), qd.SolverParams.inner_tol.offset, qd.SolverParams.max_refine.offset],
         [ctypes.sizeof(qd.TraceResult), qd.TraceResult.nsamples.offset, qd.TraceResult.UhKZ.offset],
+        [ctypes.sizeof(qd.SmootherParams), qd.SmootherParams.seed.offset, qd.SmootherParams.mr_steps.offset],
+        [ctypes.sizeof(qd.SmootherInfo), qd.SmootherInfo.enabled.offset],
+        [ctypes.sizeof(qd.BatchItem), qd.BatchItem.m0.offset, qd.BatchItem.params.offset, qd.BatchItem.result.offset,
+         qd.BatchItem.status.offset],
     ]
     assert got == want
 
@@ -93,3 +101,15 @@ def test_defaults(library):
     sp = qd.solver_params()
     assert sp.tol == 1e-8 and sp.precision == qd.QD_PREC_F64 and sp.inner_tol == 1e-5
     assert p.coarsest_direct == 16384 and p.coarsest_bf16 == 1 and p.use_graphs == 1
+    sm = qd.smoother_params()
+    assert sm.nsamples == 8 and sm.solve_tol == 1e-6 and sm.seed == 4242 and sm.mr_steps == 2
+
+
+def test_autotune_table_host_side(library):
+    # no GPU work: an empty table reports nothing; the mode switch is host state
+    qd.autotune_clear()
+    assert qd.autotune_report() == {}
+    qd.autotune_set(0)
+    qd.autotune_set(1)
+    n = library.qd_autotune_report(None, 0)
+    assert n == 1  # the terminating NUL only

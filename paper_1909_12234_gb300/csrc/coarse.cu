@@ -5,7 +5,6 @@
 //   * prolongation W c and restriction W^H x (two-grid step 1);
 //   * the Galerkin coarse operator C = W^H A W as a 9-point block stencil,
 //     and its application.
-#include <atomic>
 #include <string>
 #include "tune.cuh"
 #include "qd_internal.cuh"

@@ -356,7 +356,6 @@ __global__ void k_stencil_to_dense(int64_t nsites, int D, const int* __restrict_
     C* drow = dense + row * n;
     for (int dir = 0; dir < 9; ++dir) {
       const int64_t y = (dir == 0) ? x : (int64_t)nbr[x * 8 + dir - 1];
-      const cplx* src = mat + ((x * 9 + dir) * D + d) * D;
       for (int e = 0; e < D; ++e) {
         // sum every block that lands on (row, y*D + e), in direction order
         cplx acc = mkc(0.0, 0.0);
@@ -372,7 +371,6 @@ __global__ void k_stencil_to_dense(int64_t nsites, int D, const int* __restrict_
         }
         drow[y * D + e] = mk<C>((R)acc.x, (R)acc.y);
       }
-      (void)src;
     }
   }
 }

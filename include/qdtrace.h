@@ -19,7 +19,13 @@
  *            has finished the call.  Opaque handles (qd_ctx, qd_gauge, qd_mg,
  *            qd_defl) are owned by the library and freed by *_destroy.
  *            The library allocates its own device work space on first use.
- * Numbers:   complex numbers are two doubles (re, im), FP64.
+ * Threads:   a qd_ctx, and the qd_gauge / qd_mg / qd_defl handles used with
+ *            it, serve one host thread at a time.  qd_hutchinson_batch runs
+ *            its own worker threads and streams internally.  Process-wide
+ *            state (the launch counter, the autotuner table, kernels'
+ *            shared-memory limits) is guarded for concurrent use.
+ * Numbers:   complex numbers are two doubles (re, im), FP64 (the *_f32
+ *            entry points take two floats).
  *
  * Lattice:   dims = {Lx, Ly, Lz, Lt}, periodic; Lx must be even.
  *            lexicographic site  lex = x + Lx*(y + Ly*(z + Lz*t));

@@ -16,8 +16,12 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 Vectors are flat complex128 arrays; ``op`` maps one vector to one vector.
 Each right-hand side is solved independently (no block Krylov).
 
-Pinned by: the true-residual stopping rule against dense solves
-(tests/test_oracle_krylov.py).
+Pinned by (tests/test_oracle_krylov.py): the true-residual stopping rule and
+the kappa * xi error bound against dense solves; for the minimal-residual
+iteration a first step computed by hand on diag(i, 2) (which fixes the
+conjugation in a), one-step convergence on c I, the orthogonality of every new
+residual to A r_k with ||r|| non-increasing and a the exact minimiser, the
+stopping rule, and the column form against single-column runs.
 """
 
 import numpy as np

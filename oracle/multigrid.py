@@ -27,10 +27,15 @@ Coarse dof order inside a coarse site: d = chirality * nv + j, chirality 0
 for gamma5 = +1, so gamma5^W = diag(+1 x nv, -1 x nv) per coarse site.
 A coarse vector is indexed lex_coarse_site * 2 nv + d.
 
-Pins: W^H W = I, gamma5 W = W gamma5^W, gamma5^W C Hermitian, the coarse
-dimension arithmetic of Table 2, Galerkin identity W^H A W e = W^H (A (W e))
-against dense matrices (tests/test_oracle_multigrid.py).  The quality of the
-setup (how well W captures low modes) is parity unpinned.
+Pins (tests/test_oracle_multigrid.py): W^H W = I, gamma5 W = W gamma5^W,
+gamma5^W C Hermitian, the coarse dimension arithmetic of Table 2, Galerkin
+identity W^H A W e = W^H (A (W e)) against dense matrices; the V-cycle equals
+the dense coarse-grid correction W C^{-1} W^H r without smoothing (and kills
+the restricted residual), equals A^{-1} r when W spans the whole space, moves
+along the corrected residual with the minimal-residual optimality when it
+smooths (two and three levels), and planted mistakes (smoothing r instead of
+r - A x, a wrong transfer order) fail these pins.  The quality of the setup
+(how well W captures low modes) is parity unpinned.
 """
 
 import numpy as np

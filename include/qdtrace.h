@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define QD_ABI_VERSION 1
+#define QD_ABI_VERSION 2
 #define QD_MAX_LEVELS 4 /* fine level + up to 3 coarse levels */
 
 typedef enum {
@@ -186,11 +186,17 @@ typedef struct {
                                    per (input, output, nrhs) as a CUDA graph
                                    and replayed; the result is the same as
                                    the eager launches.  Off while profiling */
+  int coarse_tc;                /* != 0: the FP32 V-cycle applies coarse
+                                   stencils with dof 8, 16, 24 or 32 on the
+                                   tcgen05 tensor cores (split-BF16 operands,
+                                   FP32 accumulate; qd_coarse_apply_tc); 0:
+                                   FP32 CUDA cores (qd_coarse_apply_f32) */
 } qd_mg_params;
 
 /* Fill `p` with this library's defaults (1 level, 2^4 blocks, nv 12,
  * 1e-2 / 200, 4 smoothing steps, coarse GCR to 0.1 / 256 / 16, direct
- * coarsest solve on). */
+ * coarsest solve on, BF16 tensor cores for the coarsest solve and the coarse
+ * stencils of the FP32 V-cycle, CUDA graphs on). */
 void qd_mg_params_default(qd_mg_params* p);
 
 /* Build the hierarchy for A(m0, tau).  Null-vector starts are complex
@@ -236,6 +242,21 @@ int qd_coarse_apply(qd_mg* mg, int level, int nrhs, const double* in,
  * Asynchronous. */
 int qd_coarse_apply_f32(qd_mg* mg, int level, int nrhs, const float* in,
                         float* out);
+
+/* The same stencil as a dense contraction on the tcgen05 tensor cores (the
+ * form the FP32 V-cycle uses with qd_mg_params.coarse_tc): per coarse site
+ * and chunk of <= 128 right-hand sides one real GEMM (M = right-hand sides,
+ * N = 2 dof, K = 9 x 2 dof).  Each operand is split into two BF16 terms
+ * (hi = bf16(v), lo = bf16(v - hi)) and the product formed as
+ * hi*hi + hi*lo + lo*hi with FP32 accumulation, so each output's error is
+ * about 3 * 2^-16 sum |C||in| (plain BF16, 2^-7, perturbs the small singular
+ * values of a near-critical coarse operator too much).  The level's dof must
+ * be 8, 16, 24 or 32, in/out 16-byte aligned interleaved complex float,
+ * nrhs even when above 128 (QD_ERR_INVALID otherwise).  A bounded wait that gives up is reported as QD_ERR_TIMEOUT by
+ * the next synchronising call on the hierarchy (qd_coarse_solve*, qd_solve,
+ * qd_hutchinson_trace).  Asynchronous. */
+int qd_coarse_apply_tc(qd_mg* mg, int level, int nrhs, const float* in,
+                       float* out);
 
 /* out = C_level^{-1} in, level >= 1: the coarse solve of the V-cycle (a5).
  * On the coarsest level with a dense inverse: the product with the inverse
@@ -347,27 +368,32 @@ int qd_defl_info(const qd_defl* defl, double* mu, double* lambda,
 /* out = (I - P) z on the fine level, nrhs columns, qd layout:
  *   kind 2: P = A W U Lambda^{-1} U^H gamma5^W W^H (K = gamma5 projector);
  *   kind 1: P = U U^H.
- * Uses the active rank.  Asynchronous. */
+ * Uses the active rank.  z and out must not overlap (QD_ERR_INVALID).
+ * Asynchronous. */
 int qd_deflate_project(qd_defl* defl, int nrhs, const double* z, double* out);
 
-/* The paper has no counterpart to this entry point; it serves callers that
- * must not have the library allocate device memory during a call.
- * qd_deflate_project allocates (and frees) small device buffers for U^H z
- * on every call; cudaMalloc and cudaFree synchronise the device and can fail
- * once an application has handed its memory to its own pool, so a
- * latency-critical loop, or a program that reserves all device memory up
- * front, cannot use it.  This variant computes the same Algorithm 1
- * projection, out = (I - U U^H) z with the active rank, but keeps its
- * scratch (the rank x nrhs coefficients and their partial sums) in one
- * fixed 8 MiB device array compiled into the library; it calls no
- * cudaMalloc, cudaFree or other allocating routine.
- *   - Algorithm 1 deflation (QD_DEFL_EIG_ORTHO) only; QD_ERR_INVALID
- *     otherwise, and when rank * nrhs > 262144 (the array's limit).
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot let the library allocate device memory during a call: an
+ * application that gives all device memory to its own pool up front (a
+ * cudaMalloc inside the call would then fail), or a latency-critical loop
+ * that must not pay for cudaMalloc and cudaFree (both can synchronise the
+ * device).  qd_deflate_project allocates and frees small device buffers for
+ * U^H z on every call; this variant computes the same result for a space of
+ * orthonormal eigenvectors (QD_DEFL_EIG_ORTHO) at its active rank,
+ *     out = (I - U U^H) z,
+ * but keeps its scratch (the rank x nrhs coefficients and their partial
+ * sums) in one fixed 8 MiB __device__ array compiled into the library.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine: qd_alloc_count()
+ * does not move across a call.
+ *   - QD_DEFL_EIG_ORTHO spaces only; QD_ERR_INVALID for other kinds, when
+ *     rank * nrhs > 262144 (the array's limit) and when z and out overlap.
  *   - The array exists once per device that loads the library and stays
- *     allocated until the process exits.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     allocated until the process exits.  qd_ctx_create takes it: with the
+ *     context's device current it looks up the array's device address
+ *     (cudaGetSymbolAddress, which also loads the module holding the array,
+ *     so that is when its 8 MiB are allocated) and loads the kernels this
+ *     call launches.  The call itself uses the address kept in the context
+ *     that `defl` was created with.
  *   - Every call on a device uses the same array and leaves the last call's
  *     values in it: calls whose GPU work overlaps (other streams, threads or
  *     contexts on the same device) race; issue them on one stream.
@@ -525,6 +551,10 @@ int qd_autotune_report(char* buf, int len);
  * contexts and threads). */
 long long qd_launch_count(void);
 
+/* Number of device allocations (cudaMalloc) this library has made since it
+ * was loaded (all contexts and threads). */
+long long qd_alloc_count(void);
+
 /* Kernel kinds: operator x precision. */
 enum {
   QD_PROF_WILSON_F64 = 0,   /* a2 stencil, FP64 */
@@ -544,7 +574,8 @@ enum {
   QD_PROF_UPDATE_F32 = 14,  /* FP32 fused GCR / minimal-residual updates */
   QD_PROF_SMOOTHER_F64 = 15,/* learned smoother S r, FP64 */
   QD_PROF_SMOOTHER_F32 = 16,/* learned smoother S r, FP32 (FP16 weights) */
-  QD_PROF_NKINDS = 17
+  QD_PROF_COARSE_TC = 17,   /* a4 coarse stencil on tcgen05 (split-BF16 operands) */
+  QD_PROF_NKINDS = 18
 };
 
 /* enable != 0: record a CUDA event pair on the context stream around every

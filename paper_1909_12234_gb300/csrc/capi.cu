@@ -7,6 +7,7 @@
 #include <thread>
 
 #include "blas.cuh"
+#include "coarse_tc.cuh"
 #include "defl.cuh"
 #include "direct.cuh"
 #include "tc_gemm.cuh"
@@ -39,6 +40,12 @@ template <class F> static int guarded(F&& f) {
 
 static void set_device(const qd_ctx* c) { QD_CUDA(cudaSetDevice(c->device)); }
 
+// Whether two byte ranges [a, a + bytes) and [b, b + bytes) share a byte.
+static bool overlaps(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
 extern "C" {
 
 int qd_abi_version(void) { return QD_ABI_VERSION; }
@@ -56,6 +63,9 @@ int qd_ctx_create(qd_ctx** ctx, int device, void* stream) {
     c->device = device;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     QD_CUDA(cudaMallocHost(&c->host_pinned, 64 * sizeof(int)));
+    // qd_deflate_project_static's array: loaded and looked up now, per
+    // context (a device reset between contexts moves it)
+    c->static_scratch = qd::static_scratch_resolve();
     *ctx = c.release();
   });
 }
@@ -192,6 +202,7 @@ void qd_mg_params_default(qd_mg_params* p) {
   p->coarsest_direct = 16384;
   p->coarsest_bf16 = 1;
   p->use_graphs = 1;
+  p->coarse_tc = 1;
 }
 
 void qd_solver_params_default(qd_solver_params* p) {
@@ -300,8 +311,28 @@ int qd_coarse_apply_f32(qd_mg* mg, int level, int nrhs, const float* in, float* 
     QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     QD_REQUIRE(in != out, "in and out must not overlap");
     set_device(mg->ctx);
-    auto op = mg->op<qd::cplxf>(level);
-    op->apply(*mg->ctx, reinterpret_cast<const qd::cplxf*>(in), reinterpret_cast<qd::cplxf*>(out), nrhs);
+    mg->op<qd::cplxf>(level);  // makes the FP32 copy of the stencil
+    const qd::CoarseLevel& lv = *mg->L[level - 1];
+    qd::coarse_apply<qd::cplxf>(*mg->ctx, lv, lv.Cmf.as<qd::cplxf>(), reinterpret_cast<const qd::cplxf*>(in),
+                                reinterpret_cast<qd::cplxf*>(out), nrhs);
+  });
+}
+
+int qd_coarse_apply_tc(qd_mg* mg, int level, int nrhs, const float* in, float* out) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(level >= 1 && level <= mg->nlevels, "coarse level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE((const void*)in != (void*)out, "in and out must not overlap");
+    set_device(mg->ctx);
+    qd::CoarseLevel& lv = *mg->L[level - 1];
+    QD_REQUIRE(qd::coarse_tc_supported(lv, in, out, nrhs),
+               "tensor-core coarse stencil needs dof 8, 16, 24 or 32, 16-byte aligned fields and an even nrhs "
+               "above 128");
+    qd::coarse_apply_tc(*mg->ctx, lv, reinterpret_cast<const qd::cplxf*>(in), reinterpret_cast<qd::cplxf*>(out),
+                        nrhs);
   });
 }
 
@@ -462,7 +493,8 @@ int qd_deflate_project(qd_defl* defl, int nrhs, const double* z, double* out) {
     NONNULL(z);
     NONNULL(out);
     QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
-    QD_REQUIRE(z != out, "z and out must not overlap");
+    QD_REQUIRE(!overlaps(z, out, (size_t)defl->gauge->geo.nsites * 12 * nrhs * sizeof(qd::cplx)),
+               "z and out must not overlap");
     set_device(defl->ctx);
     qd::defl_project(*defl->ctx, *defl, nrhs, reinterpret_cast<const qd::cplx*>(z), reinterpret_cast<qd::cplx*>(out));
   });
@@ -474,7 +506,8 @@ int qd_deflate_project_static(qd_defl* defl, int nrhs, const double* z, double* 
     NONNULL(z);
     NONNULL(out);
     QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
-    QD_REQUIRE(z != out, "z and out must not overlap");
+    QD_REQUIRE(!overlaps(z, out, (size_t)defl->gauge->geo.nsites * 12 * nrhs * sizeof(qd::cplx)),
+               "z and out must not overlap");
     set_device(defl->ctx);
     qd::defl_project_static(*defl, nrhs, reinterpret_cast<const qd::cplx*>(z), reinterpret_cast<qd::cplx*>(out));
   });
@@ -806,6 +839,8 @@ int qd_autotune_report(char* buf, int len) {
 }
 
 long long qd_launch_count(void) { return qd::launch_counter().load(); }
+
+long long qd_alloc_count(void) { return qd::alloc_counter().load(); }
 
 int qd_prof_enable(qd_ctx* ctx, int enable) {
   return guarded([&] {

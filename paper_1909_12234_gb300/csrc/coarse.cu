@@ -6,8 +6,9 @@
 //   * the Galerkin coarse operator C = W^H A W as a 9-point block stencil,
 //     and its application.
 #include <string>
-#include "tune.cuh"
+#include "coarse_tc.cuh"
 #include "qd_internal.cuh"
+#include "tune.cuh"
 
 namespace qd {
 
@@ -374,6 +375,10 @@ void CoarseOp<cplx>::apply(qd_ctx& ctx, const cplx* in, cplx* out, int nrhs) con
 }
 template <>
 void CoarseOp<cplxf>::apply(qd_ctx& ctx, const cplxf* in, cplxf* out, int nrhs) const {
+  if (lv->use_tc && in != out && coarse_tc_supported(*lv, in, out, nrhs)) {
+    coarse_apply_tc(ctx, const_cast<CoarseLevel&>(*lv), in, out, nrhs);
+    return;
+  }
   coarse_apply<cplxf>(ctx, *lv, mat, in, out, nrhs);
 }
 

@@ -48,8 +48,10 @@ void defl_set_rank(qd_defl& d, int r);
 // Launches go to ctx (the caller's stream), not to the context d was built on.
 void defl_project(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* out);
 void defl_coeffs(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* M1, cplx* M2);
-// Algorithm 1 projection with scratch in a fixed device array (noalloc.cu).
+// (I - U U^H) z with scratch in a fixed device array (noalloc.cu), and the
+// address of that array on the current device (resolved at context creation).
 void defl_project_static(qd_defl& d, int s, const cplx* z, cplx* out);
+void* static_scratch_resolve();
 void blockmul_identity_cols(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int r, cplx* Y);
 void copy_leading_block(qd_ctx& ctx, int k, int r, const cplx* G, cplx* Gr);
 void sum_over_lambda(qd_ctx& ctx, int r, const cplx* dv, const double* lam, cplx* out);

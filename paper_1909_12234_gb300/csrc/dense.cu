@@ -92,6 +92,19 @@ bool blockdot_into(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int ma, const
 
 // Y[i][b] = alpha sum_a X[i][a] S[a][b] + beta Y[i][b]
 __global__ void k_blockmul(int64_t n, const cplx* __restrict__ X, int ldx, int ma, const cplx* __restrict__ S,
+                           int lds, int mb, cplx* __restrict__ Y, int ldy, double alpha, double beta);
+
+// Load the kernels of blockdot_into and blockmul on the current device now
+// (with lazy module loading a kernel is otherwise loaded, and its module's
+// memory taken, at its first launch).
+void preload_projection_kernels() {
+  cudaFuncAttributes a;
+  QD_CUDA(cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(k_blockdot)));
+  QD_CUDA(cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(k_chunk_sum)));
+  QD_CUDA(cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(k_blockmul)));
+}
+
+__global__ void k_blockmul(int64_t n, const cplx* __restrict__ X, int ldx, int ma, const cplx* __restrict__ S,
                            int lds, int mb, cplx* __restrict__ Y, int ldy, double alpha, double beta) {
   const int64_t tot = n * mb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;

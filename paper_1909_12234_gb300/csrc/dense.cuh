@@ -12,6 +12,8 @@ void blockdot(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int ma, const cplx
 // allocates nothing; false if the space is too small.
 bool blockdot_into(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int ma, const cplx* Y, int ldy, int mb,
                    cplx* G, cplx* partials, int64_t cap);
+// Load blockdot_into's and blockmul's kernels on the current device.
+void preload_projection_kernels();
 // Y = alpha X S + beta Y; X: n x ma, S: ma x mb (row stride lds), Y: n x mb.
 void blockmul(qd_ctx& ctx, int64_t n, const cplx* X, int ldx, int ma, const cplx* S, int lds, int mb,
               cplx* Y, int ldy, double alpha, double beta);

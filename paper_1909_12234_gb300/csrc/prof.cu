@@ -24,6 +24,11 @@ std::atomic<long long>& launch_counter() {
   return n;
 }
 
+std::atomic<long long>& alloc_counter() {
+  static std::atomic<long long> n{0};
+  return n;
+}
+
 static cudaEvent_t take_event(qd_ctx& c) {
   if (c.prof_pool.empty()) {
     cudaEvent_t e;

@@ -35,6 +35,9 @@ inline void cuda_check(cudaError_t e, const char* what, const char* file, int li
 }
 // Kernels launched by this library since load (qd_launch_count()).
 std::atomic<long long>& launch_counter();
+// Device allocations (cudaMalloc) this library has made since load
+// (qd_alloc_count()).
+std::atomic<long long>& alloc_counter();
 // Raise a kernel's dynamic shared-memory limit on the current device to at
 // least `bytes`.  The limit only ever grows (a launch that fits an earlier,
 // smaller request still fits), so threads launching the same kernel with
@@ -72,6 +75,7 @@ class DevBuf {
     release();
     if (bytes == 0) return;
     QD_CUDA(cudaMalloc(&p_, bytes));
+    alloc_counter().fetch_add(1, std::memory_order_relaxed);
     n_ = bytes;
   }
   void release() {

@@ -31,6 +31,7 @@ struct qd_ctx {
   qd::DevBuf red_partials;  // reduction partial sums (double2)
   qd::DevBuf small;         // small device scratch (per-RHS scalars)
   int* host_pinned = nullptr;  // 64 pinned ints for flag read-back
+  void* static_scratch = nullptr;  // device address of the fixed scratch array (noalloc.cu)
   std::shared_ptr<void> cache;  // solver work spaces reused across calls
 };
 
@@ -180,6 +181,9 @@ struct CoarseLevel {
   int D = 0;          // dofs per site
   DevBuf Cm;          // cplx  [nsites][9][D][D]; dir 0 self, 1+mu: +mu, 5+mu: -mu
   DevBuf Cmf;         // cplxf copy
+  bool use_tc = false;      // FP32 V-cycle applies the stencil on tensor cores
+  mutable DevBuf Cmb;       // uint32 [nsites][9][D][D]: (re, im) BF16 pairs
+  mutable DevBuf ctc_err;   // int: bounded-wait error of the tensor-core stencil
   int ndense = 0;     // > 0: Cinv holds the dense inverse (coarsest level)
   DevBuf Cinv;        // cplx  [n][n], n = nsites * D
   DevBuf Cinvf;       // cplxf copy

@@ -4,6 +4,7 @@
 // Sec. 4), chirality split + blocking + per-block CGS2 -> W, then the
 // Galerkin coarse operator W^H A W.
 #include "blas.cuh"
+#include "coarse_tc.cuh"
 #include "direct.cuh"
 #include "mg.cuh"
 #include "tc_gemm.cuh"
@@ -64,6 +65,11 @@ void mg_build(qd_mg& mg, const double* injected_null) {
       tc_prepare(ctx, last);
       last.tc = true;
     }
+  }
+  // tensor-core coarse stencils for the FP32 V-cycle where the shape allows
+  for (auto& lv : mg.L) {
+    lv->use_tc = p.coarse_tc != 0 && (lv->D == 8 || lv->D == 16 || lv->D == 24 || lv->D == 32);
+    if (lv->use_tc) coarse_tc_prepare(ctx, *lv);
   }
   mg.pre64.reset(new MGPrecond<cplx>(&mg, 0));
   mg.pre32.reset(new MGPrecond<cplxf>(&mg, 0));

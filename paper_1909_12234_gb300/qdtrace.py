@@ -57,7 +57,8 @@ class MGParams(ctypes.Structure):
                 ("coarse_restart", ctypes.c_int),
                 ("coarsest_direct", ctypes.c_int),
                 ("coarsest_bf16", ctypes.c_int),
-                ("use_graphs", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int),
+                ("coarse_tc", ctypes.c_int)]
 
 
 class SolverParams(ctypes.Structure):
@@ -154,6 +155,7 @@ SIGNATURES = {
     "qd_restrict": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_apply": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_apply_f32": (_I, [_P, _I, _I, _P, _P]),
+    "qd_coarse_apply_tc": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_solver_params_default": (None, [ctypes.POINTER(SolverParams)]),
@@ -182,6 +184,7 @@ SIGNATURES = {
                                  ctypes.POINTER(TraceResult)]),
     "qd_trace_stats": (_I, [_P, _I, _P, _DPTR, ctypes.POINTER(TraceResult)]),
     "qd_launch_count": (ctypes.c_longlong, []),
+    "qd_alloc_count": (ctypes.c_longlong, []),
     "qd_prof_enable": (_I, [_P, _I]),
     "qd_prof_read": (_I, [_P, _I, _I64PTR, _DPTR, _DPTR, _DPTR, _I]),
 }
@@ -189,7 +192,7 @@ SIGNATURES = {
 PROF_KINDS = {"wilson_f64": 0, "wilson_f32": 1, "coarse_f64": 2, "coarse_f32": 3, "prolong_f64": 4,
               "prolong_f32": 5, "restrict_f64": 6, "restrict_f32": 7, "direct_f64": 8, "direct_f32": 9, "direct_bf16": 10,
               "blas_f64": 11, "dots_f32": 12, "axpy_f32": 13, "update_f32": 14, "smoother_f64": 15,
-              "smoother_f32": 16}
+              "smoother_f32": 16, "coarse_tc": 17}
 
 _lib = None
 
@@ -419,6 +422,10 @@ def coarse_apply_f32(mg, level, nrhs, inp, out):
     _check(load().qd_coarse_apply_f32(mg.h, int(level), int(nrhs), _ptr64(inp), _ptr64(out)))
 
 
+def coarse_apply_tc(mg, level, nrhs, inp, out):
+    _check(load().qd_coarse_apply_tc(mg.h, int(level), int(nrhs), _ptr64(inp), _ptr64(out)))
+
+
 def coarse_solve_f32(mg, level, nrhs, inp, out):
     _check(load().qd_coarse_solve_f32(mg.h, int(level), int(nrhs), _ptr64(inp), _ptr64(out)))
 
@@ -485,8 +492,9 @@ class Deflation:
         _check(load().qd_deflate_project(self.h, int(nrhs), _ptr(z), _ptr(out)))
 
     def project_static(self, nrhs, z, out):
-        """Algorithm 1 projection with the library's fixed device scratch
-        (no device allocation during the call); see qdtrace.h."""
+        """out = (I - U U^H) z for an orthonormal-eigenvector space, with the
+        library's fixed device scratch (no device allocation during the
+        call); see qdtrace.h."""
         _check(load().qd_deflate_project_static(self.h, int(nrhs), _ptr(z), _ptr(out)))
 
     def coeffs(self, nrhs, z):
@@ -525,6 +533,11 @@ def trace_stats(ctx, t, t0=0j):
 def launch_count():
     """Kernels launched by libqdtrace since it was loaded."""
     return int(load().qd_launch_count())
+
+
+def alloc_count():
+    """Device allocations (cudaMalloc) libqdtrace has made since it was loaded."""
+    return int(load().qd_alloc_count())
 
 
 def prof_enable(ctx, on):

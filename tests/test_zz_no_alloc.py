@@ -1,7 +1,10 @@
-"""qd_deflate_project_static: the Algorithm 1 projection for callers that
-must not have the library allocate device memory during a call (it keeps its
-scratch in a fixed device array).  Its output must equal qd_deflate_project's
-on consecutive calls, whether this file runs alone or after the others."""
+"""qd_deflate_project_static: out = (I - U U^H) z for an orthonormal
+eigenvector space, for callers that cannot let the library allocate device
+memory during a call (an application that gave all device memory to its own
+pool, or a loop that must not pay cudaMalloc / cudaFree).  It keeps its
+scratch in a fixed device array.  Its output must equal qd_deflate_project's
+on consecutive calls, and no call may allocate (qd_alloc_count stays put),
+whether this file runs alone or after the others."""
 import numpy as np
 import pytest
 
@@ -38,8 +41,11 @@ def test_static_scratch_projection_matches_allocating_one(qd):
         ref = torch.empty_like(z)
         out = torch.full_like(z, complex("nan"))
         d.project(s, z, ref)
+        torch.cuda.synchronize()
+        n_alloc = qd.alloc_count()
         d.project_static(s, z, out)
         torch.cuda.synchronize()
+        assert qd.alloc_count() == n_alloc, "the static projection allocated device memory"
         assert rel_err(out.cpu().numpy(), ref.cpu().numpy()) < 1e-12, call
     # a smaller active rank reuses the same array
     d.set_rank(7)
@@ -77,3 +83,12 @@ def test_static_scratch_rejects_oversize_and_oblique(qd):
     with pytest.raises(qd.QDError) as e:
         d2.project_static(1, z1, torch.empty_like(z1))
     assert e.value.code == qd.QD_ERR_INVALID
+    # partially overlapping input and output ranges are rejected, not corrupted
+    buf = torch.zeros((2 * g.V * 12 * 2,), dtype=torch.complex128, device="cuda:0")
+    zz, oo = buf[: g.V * 12 * 2], buf[g.V * 12: g.V * 12 * 3]
+    for fn in (d.project_static, d.project):
+        with pytest.raises(qd.QDError) as e:
+            fn(2, zz, oo)
+        assert e.value.code == qd.QD_ERR_INVALID
+    for o in (d2, mg, d, g, ctx):
+        o.close()

@@ -1,24 +1,36 @@
 """Benchmark: deflated Hutchinson samples/s at true relative residual 1e-8.
 
-Workload (the estimator configuration that fits one GPU): Wilson-Dirac
-operator on an 8^4 periodic lattice (N = 49,152), random SU(3) links
-exp(i 0.3 H) (seed 2), m0 = -0.8; two-level multigrid with 2^4 aggregates
-and 12 null vectors per chirality (24 coarse dofs per aggregate); Algorithm 2
-deflation of rank 24; 64 real Rademacher samples per step solved together,
-solves to ||b - A x|| <= 1e-8 ||b|| measured on the FP64 residual.  The
-default path is mixed precision (FP32 flexible GCR and V-cycle inside FP64
-residual refinement); the plain FP64 path is timed in the same run
-("fp64_path").
+Default workload (the mixed-precision estimator configuration of the
+metric): Wilson-Dirac operator on a 16^3 x 32 periodic lattice
+(N = 1,572,864), random SU(3) links exp(i 0.2 H) (seed 3), m0 = -0.8;
+three-level multigrid (2^4 then 2^4 aggregates, 12 and 16 null vectors per
+chirality; level-1 GCR of 6 iterations, two minimal-residual smoothing steps
+on the coarse levels, dense coarsest inverse applied on tensor cores);
+Algorithm 2 deflation of rank 24 on the coarsest level; 128 real Rademacher
+samples per step solved together, each to ||b - A x|| <= 1e-8 ||b|| on the
+FP64 residual.  The path: FP32 flexible GCR and FP32 V-cycle (learned
+smoother + 1 MR step on the fine level, tensor-core coarse stencil) inside
+FP64 residual refinement.  The plain FP64 form (FP64 GCR and V-cycle, plain
+minimal-residual smoother) is timed on the same lattice ("fp64_path").
 
 A step = one batch through the whole sample path: Rademacher noise (a1),
 deflation projection (a8, with the Wilson and transfer kernels), the
-multigrid-preconditioned GCR solves (a2-a6) and the trace statistics (a9).
-The adaptive setup and the deflation space (a7, a10) are built once before
-timing and reported as setup_s; the end-to-end number repeats them per step.
+multigrid-preconditioned solves (a2-a6) and the trace statistics (a9).  The
+adaptive setup, the smoother training and the deflation space (a7, a10) are
+built once before timing and reported as setup_s; the end-to-end number
+repeats them every step.
+
+Errors against the FP64 oracle ("errors"): the true residual of
+mixed-precision solutions recomputed with the oracle's operator; and, on the
+unit-link twin of the workload (same lattice and path, links = 1), the
+estimate against the oracle's closed-form tr A^{-1} in standard errors and
+the undeflated sample variance against the oracle's closed-form exact
+variance, with the variance reduction from deflation.
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun (N > 1) each rank takes its own sample range (replicas: the
-samples are independent) and only the timing is reduced (max over ranks).
+samples are independent); the per-sample values are gathered on the host and
+rank 0 reports the whole run's estimate.
 """
 
 import argparse
@@ -36,26 +48,28 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-WL = dict(
+# Config 3: 16^3 x 32, eps 0.2 (seed 3), m0 -0.8, three levels, 128 samples
+# per step, mixed precision with the learned smoother (the metric's form).
+CONFIG3 = dict(
+    workload="wilson-dirac 16^3x32 eps0.2 seed3 m0=-0.8, 3-level MG (2^4, 2^4; nv 12, 16; level-1 GCR 6 its; "
+             "coarse MR 2), Algorithm 2 k=24 on the coarsest level, 128 Rademacher samples/step, learned smoother "
+             "+ 1 MR, FP32 inner solves with FP64 refinement to true rel. residual 1e-8",
+    dims=(16, 16, 16, 32), eps=0.2, link_seed=3, m0=-0.8, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16],
+    k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=16, maxit=500, inner_tol=1e-5,
+    mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6, "coarse_smoother_steps": 2},
+    learned=1, eig_maxit=30, fp64_samples=16,
+)
+# Config 2: 8^4 lattice (the two-level workload of round one), kept for
+# comparison with earlier numbers.
+CONFIG2 = dict(
     workload="wilson-dirac 8^4 eps0.3 seed2 m0=-0.8, 2-level MG (2^4 blocks, nv 12; learned smoother + 1 MR), "
              "Algorithm 2 k=24, 64 Rademacher samples/step, true FP64 rel. residual 1e-8",
     dims=(8, 8, 8, 8), eps=0.3, link_seed=2, m0=-0.8, blocks=[(2, 2, 2, 2)], nvs=[12], k=24, guard=16,
-    s=64, tol=1e-8, noise_seed=102, restart=16, maxit=500, inner_tol=1e-5,
-    learned=1,  # learned smoother, then 1 MR step (trained in setup); the FP64 leg uses plain MR(4)
-    eig_maxit=30,  # subspace iterations: the sample variance is within 0.3 % of the 60-iteration space
+    s=64, tol=1e-8, noise_seed=102, restart=16, maxit=500, inner_tol=1e-5, learned=1, eig_maxit=30,
+    fp64_samples=64,
 )
-# Larger configurations (parity-test cases, not the bench line); chosen with
-# --workload.  Config 3: 16^3 x 32, eps 0.2 (seed 3), m0 -0.8, three-level MG
-# (2^4 then 2^4, nv 12 then 16), Algorithm 2, 128 samples, mixed precision.
-WORKLOADS = {
-    "config2": dict(WL),
-    "config3": dict(
-        workload="wilson-dirac 16^3x32 eps0.2 seed3 m0=-0.8, 3-level MG (2^4, 2^4; nv 12, 16), Algorithm 2 "
-                 "k=24 (level-1 GCR 6 its), 128 Rademacher samples/step, true FP64 rel. residual 1e-8",
-        dims=(16, 16, 16, 32), eps=0.2, link_seed=3, m0=-0.8, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16],
-        k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=16, maxit=500, inner_tol=1e-5,
-        mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6}),
-}
+WORKLOADS = {"config3": CONFIG3, "config2": CONFIG2}
+WL = dict(CONFIG3)
 # Config 4: an uneven batch solved concurrently (qd_hutchinson_batch):
 # (lattice, m0, samples) = (8^4, -0.6, 16), (12^4, -0.75, 48), (16^4, -0.8,
 # 96); eps 0.2 links (seeds 4, 5, 6), three-level MG (2^4, 2^4; nv 12, 16)
@@ -75,6 +89,10 @@ UNIT = "samples/s"
 # Recipe peaks (MEASURED_PEAKS.json holds HBM and bf16; FP64 is the recipe's
 # nominal 1.25 TFLOP/s, matching the 1.20 TFLOP/s an FMA-chain probe measured).
 FP64_PEAK_TFLOPS = 1.25
+# Outer GCR iterations per sample of the plain FP64 path on the config-3
+# workload (the fp64_path leg measures 49-50); the oracle arm's time per
+# iteration is scaled by it when the run itself has no FP64 leg.
+FP64_ITERS_CONFIG3 = 50
 
 
 def _peaks():
@@ -156,76 +174,104 @@ def _traffic(workload, kind):
     return None
 
 
-def _setup(qd, ctx, U):
-    g = qd.Gauge(ctx, WL["dims"], U)
-    mg = qd.Multigrid(ctx, g, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"], **WL.get("mg_kw", {})))
-    if WL.get("learned"):
-        WL["smoother_judge"] = qd.smoother_train(mg, nsamples=4, solve_tol=1e-3, mr_steps=WL["learned"])
-        qd.smoother_enable(mg, True, WL["learned"])
-    d = qd.Deflation(ctx, g, mg, WL["m0"], 0.0,
-                     qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
-                                    solve_tol=1e-10, maxit=WL.get("eig_maxit", 60)))
-    return g, mg, d
+def _mg_params(qd, wl=None):
+    wl = WL if wl is None else wl
+    return qd.mg_params(len(wl["blocks"]), wl["blocks"], wl["nvs"], **wl.get("mg_kw", {}))
 
 
-def _batch(qd, ctx, g, mg, d, offset, precision):
-    return qd.hutchinson_trace(ctx, g, mg, d, WL["m0"], 0.0, seed=WL["noise_seed"], sample_offset=offset,
-                               nsamples=WL["s"], tol=WL["tol"], maxit=WL["maxit"], restart=WL["restart"],
-                               precision=precision, inner_tol=WL["inner_tol"], max_refine=10)
+def _setup(qd, ctx, U, wl=None):
+    """Gauge, hierarchy, learned smoother, deflation space for the workload."""
+    wl = WL if wl is None else wl
+    g = qd.Gauge(ctx, wl["dims"], U)
+    mg = qd.Multigrid(ctx, g, wl["m0"], 0.0, _mg_params(qd, wl))
+    judge = None
+    if wl.get("learned"):
+        judge = qd.smoother_train(mg, nsamples=4, solve_tol=1e-3, mr_steps=wl["learned"])
+        qd.smoother_enable(mg, True, wl["learned"])
+    d = qd.Deflation(ctx, g, mg, wl["m0"], 0.0,
+                     qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, wl["k"], guard=wl["guard"], eig_tol=1e-6,
+                                    solve_tol=1e-10, maxit=wl.get("eig_maxit", 60)))
+    return g, mg, d, judge
 
 
-def cpu_baseline(samples=2):
-    """The FP64 oracle on this host's cores: setup untimed, `samples` solves timed."""
-    from oracle import deflation as odefl
-    from oracle import estimator
+def _batch(qd, ctx, g, mg, d, offset, precision, nsamples=None, wl=None):
+    wl = WL if wl is None else wl
+    return qd.hutchinson_trace(ctx, g, mg, d, wl["m0"], 0.0, seed=wl["noise_seed"], sample_offset=offset,
+                               nsamples=wl["s"] if nsamples is None else nsamples, tol=wl["tol"], maxit=wl["maxit"],
+                               restart=wl["restart"], precision=precision, inner_tol=wl["inner_tol"], max_refine=10)
+
+
+def _oracle_iteration_seconds(dims, eps, link_seed, m0, blocks, nvs, mg_kw, noise_seed, iters=1):
+    """Seconds of one outer V-cycle-preconditioned FP64 GCR iteration of the
+    oracle on the workload's lattice (the same operator sizes, transfers and
+    V-cycle shape as the plain FP64 path: fine MR(4), coarse MR steps and
+    fixed coarse GCR iterations as the workload sets them).  The oracle's
+    null-vector iteration is capped at 2 steps: its setup (single-threaded
+    sparse products, ~15 min at 16^3 x 32 for 200 steps) is untimed and the
+    per-iteration cost does not depend on the null vectors' quality."""
+    from oracle import krylov, philox
     from oracle import multigrid as omg
     from paper_1909_12234_gb300 import synth
-    U = synth.random_su3_links(WL["dims"], WL["eps"], WL["link_seed"])
-    H = omg.setup(U, WL["m0"], WL["dims"], WL["blocks"], WL["nvs"], seed=7)
-    alg = odefl.Alg2(odefl.Composite(H.transfers), H.matrices[-1], WL["k"])
+    U = synth.random_su3_links(dims, eps, link_seed)
+    H = omg.setup(U, m0, dims, blocks, nvs, seed=7, null_maxit=2, smoother_steps=4,
+                  coarse_tol=mg_kw.get("coarse_tol", 0.1), coarse_maxit=mg_kw.get("coarse_maxit", 256),
+                  coarse_smoother_steps=mg_kw.get("coarse_smoother_steps"))
     lev = H.levels[0]
+    z = philox.rademacher(lev.n, noise_seed, range(1)).astype(np.complex128)[:, 0]
     t = time.perf_counter()
-    estimator.hutchinson(lev.matvec, lev.n, WL["noise_seed"], range(samples), WL["tol"],
-                         project=lambda z: alg.project(lev.matvec, z), t0=alg.t0,
-                         precond=lambda r: H.vcycle(0, r), restart=WL["restart"])
-    dt = time.perf_counter() - t
-    return {"value": samples / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{samples} samples of the workload (oracle setup untimed); numpy/scipy FP64, sparse "
-                      f"ops single-threaded, BLAS threads up to cores"}
+    krylov.gcr(lev.matvec, z, 0.0, maxit=iters, restart=16, precond=lambda r: H.vcycle(0, r))
+    return (time.perf_counter() - t) / iters
+
+
+def cpu_baseline(iters_per_sample):
+    """The FP64 oracle on this host's cores, on a bounded sample of the
+    workload: one outer iteration of one sample, scaled to samples/s by the
+    outer iterations a sample of the plain FP64 algorithm takes."""
+    kw = {k: WL[k] for k in ("dims", "eps", "link_seed", "m0", "blocks", "nvs", "noise_seed")}
+    sec = _oracle_iteration_seconds(mg_kw=WL.get("mg_kw", {}), **kw)
+    return {"value": 1.0 / (sec * iters_per_sample), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one outer V-cycle-preconditioned FP64 GCR iteration of one sample on the workload lattice "
+                      f"({sec:.1f} s, oracle setup untimed, null-vector steps capped at 2), times "
+                      f"{iters_per_sample} iterations per sample (the plain FP64 path's count); numpy/scipy FP64, "
+                      f"sparse products single-threaded"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from oracle import deflation as odefl
-    from oracle import estimator
+    kw = {k: WL[k] for k in ("dims", "eps", "link_seed", "m0", "blocks", "nvs", "noise_seed")}
+    iters_per_sample = FP64_ITERS_CONFIG3 if WL["dims"] == CONFIG3["dims"] else 28
+    from oracle import krylov, philox
     from oracle import multigrid as omg
     from paper_1909_12234_gb300 import synth
     U = synth.random_su3_links(WL["dims"], WL["eps"], WL["link_seed"])
-    H = omg.setup(U, WL["m0"], WL["dims"], WL["blocks"], WL["nvs"], seed=7)
-    alg = odefl.Alg2(odefl.Composite(H.transfers), H.matrices[-1], WL["k"])
+    mg_kw = WL.get("mg_kw", {})
+    H = omg.setup(U, WL["m0"], WL["dims"], WL["blocks"], WL["nvs"], seed=7, null_maxit=2, smoother_steps=4,
+                  coarse_tol=mg_kw.get("coarse_tol", 0.1), coarse_maxit=mg_kw.get("coarse_maxit", 256),
+                  coarse_smoother_steps=mg_kw.get("coarse_smoother_steps"))
     lev = H.levels[0]
-    per_step = 1
+    Z = philox.rademacher(lev.n, WL["noise_seed"], range(args.warmup + args.steps)).astype(np.complex128)
 
-    def step(i):
-        estimator.hutchinson(lev.matvec, lev.n, WL["noise_seed"], range(i * per_step, (i + 1) * per_step),
-                             WL["tol"], project=lambda z: alg.project(lev.matvec, z), t0=alg.t0,
-                             precond=lambda r: H.vcycle(0, r), restart=WL["restart"])
+    def step(i):  # one outer iteration of sample i
+        krylov.gcr(lev.matvec, Z[:, i], 0.0, maxit=1, restart=16, precond=lambda r: H.vcycle(0, r))
 
     for i in range(args.warmup):
         step(i)
     t = time.perf_counter()
     for i in range(args.steps):
         step(args.warmup + i)
-    dt = time.perf_counter() - t
-    value = args.steps * per_step / dt
+    dt = (time.perf_counter() - t) / args.steps
+    value = 1.0 / (dt * iters_per_sample)
+    sample = (f"each step one outer V-cycle-preconditioned FP64 GCR iteration of one sample ({dt:.1f} s); "
+              f"samples/s = 1 / (seconds per iteration x {iters_per_sample} iterations per sample of the plain "
+              f"FP64 algorithm); oracle setup untimed with null-vector steps capped at 2")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt * iters_per_sample,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WL["workload"] + f"; reference step = {per_step} sample (the oracle smooths with plain MR)"},
+            "data": "synthetic", "config": {"workload": WL["workload"] + "; reference = the FP64 oracle (numpy/scipy)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{per_step} sample per step (oracle setup untimed)"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -267,8 +313,68 @@ def stencil_roofline(qd, ctx, reps=20):
     return out
 
 
+def errors_against_oracle(qd, ctx, U, g, mg, d):
+    """Errors of the GPU path against the FP64 oracle (see the module docstring)."""
+    import torch
+    from oracle import lattice, wilson
+    from paper_1909_12234_gb300 import synth
+    out = {}
+    dims, m0, tol = WL["dims"], WL["m0"], WL["tol"]
+    # (1) mixed-precision solutions of two deflated samples: true residual
+    # with the oracle's (matrix-free) operator, and the FP64 path's solution
+    ncol = 2
+    z = torch.empty((g.V, 12, ncol), dtype=torch.complex128, device=f"cuda:{ctx.device}")
+    qd.rademacher(ctx, g, WL["noise_seed"], 10 ** 6, ncol, z)
+    b = torch.empty_like(z)
+    d.project(ncol, z, b)
+    xm, x64 = torch.empty_like(b), torch.empty_like(b)
+    qd.solve(ctx, g, mg, m0, 0.0, ncol, b, xm, tol, maxit=WL["maxit"], precision=qd.QD_PREC_MIXED,
+             inner_tol=WL["inner_tol"], max_refine=10)
+    qd.solve(ctx, g, mg, m0, 0.0, ncol, b, x64, tol, maxit=WL["maxit"])
+    torch.cuda.synchronize()
+    eo = lattice.eo_index(dims)
+    bl = b.cpu().numpy()[eo].reshape(-1, 4, 3, ncol)
+    res = {}
+    for name, x in (("mixed", xm), ("fp64", x64)):
+        xl = x.cpu().numpy()[eo].reshape(-1, 4, 3, ncol)
+        r = bl - wilson.dirac_apply(U, xl, m0, dims)
+        res[name] = (np.linalg.norm(r.reshape(-1, ncol), axis=0) / np.linalg.norm(bl.reshape(-1, ncol), axis=0))
+    dx = (torch.linalg.vector_norm(xm - x64, dim=(0, 1)) / torch.linalg.vector_norm(x64, dim=(0, 1))).cpu().numpy()
+    out["solution"] = {"samples": ncol, "tol": tol,
+                       "oracle_true_rel_residual_mixed": float(res["mixed"].max()),
+                       "oracle_true_rel_residual_fp64": float(res["fp64"].max()),
+                       "rel_diff_mixed_vs_fp64": float(dx.max()),
+                       "scope": "two deflated samples of the workload, GPU solutions, residual b - A x computed by "
+                                "the oracle's operator on the host"}
+    # (2) the unit-link twin: same lattice, hierarchy, smoother, deflation and
+    # precisions, links = 1; exact trace and variance from the oracle
+    Ut = synth.random_su3_links(dims, 0.0, 0, unit=True)
+    gt, mgt, dt, _ = _setup(qd, ctx, Ut)
+    s = WL["s"]
+    _batch(qd, ctx, gt, mgt, dt, 0, qd.QD_PREC_MIXED)  # warm-up (graphs)
+    rd = _batch(qd, ctx, gt, mgt, dt, 0, qd.QD_PREC_MIXED)
+    ru = _batch(qd, ctx, gt, mgt, None, 0, qd.QD_PREC_MIXED)
+    exact = wilson.free_field_trace_inverse(dims, m0)
+    var_exact = wilson.free_field_variance_real_rademacher(dims, m0)
+    out["unit_link_twin"] = {
+        "samples": s, "exact_trace": exact, "estimate": rd["estimate"].real, "stderr": rd["stderr"],
+        "deviation_in_stderr": (rd["estimate"].real - exact) / rd["stderr"],
+        "undeflated_estimate": ru["estimate"].real, "undeflated_stderr": ru["stderr"],
+        "undeflated_deviation_in_stderr": (ru["estimate"].real - exact) / ru["stderr"],
+        "undeflated_var": ru["var"], "undeflated_var_jackknife_err": ru["var_jackknife_err"],
+        "oracle_exact_undeflated_var": var_exact,
+        "undeflated_var_over_exact": ru["var"] / var_exact,
+        "deflated_var": rd["var"], "variance_reduction": ru["var"] / rd["var"],
+        "max_true_rel_residual": max(rd["max_true_rel_residual"], ru["max_true_rel_residual"]),
+        "scope": "exact tr A^-1 and exact Var of the undeflated estimator: oracle closed forms (free field)"}
+    for o in (dt, mgt, gt):
+        o.close()
+    return out
+
+
 def run_ours(args):
     import torch
+    from paper_1909_12234_gb300 import parallel
     from paper_1909_12234_gb300 import qdtrace as qd
     from paper_1909_12234_gb300 import synth
 
@@ -288,12 +394,10 @@ def run_ours(args):
     U = synth.random_su3_links(WL["dims"], WL["eps"], WL["link_seed"])
     torch.cuda.synchronize()
     t = time.perf_counter()
-    g, mg, d = _setup(qd, ctx, U)
+    g, mg, d, judge = _setup(qd, ctx, U)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t
     s = WL["s"]
-
-    from paper_1909_12234_gb300 import parallel
 
     def offset(i):
         return parallel.sample_offset(rank, world, s, i)
@@ -325,6 +429,11 @@ def run_ours(args):
         tt = torch.tensor([ms_total], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms_total = float(tt.item())
+    # the whole run's per-sample values (all ranks), statistics on rank 0
+    t_local = np.concatenate([r["t"] for r in results])
+    idx_local = np.concatenate([np.arange(s) + offset(args.warmup + i) for i in range(args.steps)])
+    t_all = parallel.gather_samples(t_local, idx_local)[1] if dist else t_local
+    run_stats = qd.trace_stats(ctx, t_all, results[-1]["t0"]) if rank == 0 else None
 
     # per-kernel device time: separate steps with the library's CUDA-event
     # profiling on (graph replay is off while profiling, so these steps run
@@ -352,9 +461,8 @@ def run_ours(args):
     if pt["ms"] <= 0.0:  # no profiled steps
         pt = {"ms": float("nan"), "flops": float("nan"), "bytes": float("nan"), "launches": 0}
     peaks = _peaks()
-    if top in ("direct_f32", "coarse_f32"):
-        # dense contractions on FP32 CUDA cores (the multi-RHS coarse stencil
-        # does 8 * 9 * D^2 flops per site and right-hand side)
+    if top in ("direct_f32", "coarse_f32", "smoother_f32"):
+        # FP32 CUDA-core contractions
         fp32_peak = 70.0  # FMA-chain probe (2 flops per FMA), 152 SMs at ~2 GHz
         achieved = pt["flops"] / (pt["ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -373,17 +481,19 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": top, "launches": pt["launches"],
                 "ms_per_launch": pt["ms"] / max(pt["launches"], 1),
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+                "peak_source": "measured (burst copy)" if "hbm_gbs" in peaks else "fallback"}
     roof["traffic"] = _traffic(args.workload, top)
     kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                   "share_of_step": round(v["ms"] / ms_prof, 4)} for k, v in prof.items() if v["launches"]}
+                   "share_of_step": round(v["ms"] / ms_prof, 4),
+                   "alg_gbs": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None,
+                   "alg_tflops": round(v["flops"] / (v["ms"] / 1e3) / 1e12, 2) if v["ms"] > 0 else None}
+               for k, v in prof.items() if v["launches"]}
     kernels["_profiled_steps"] = {"steps": args.prof_steps, "ms_per_step": round(ms_prof / max(args.prof_steps, 1), 3)}
 
     # end to end through the public API: links from pinned host memory,
     # setup, one batch, results read back, per step
     e2e_steps = args.e2e_steps
-    canon = np.ascontiguousarray(np.transpose(U, (1, 0, 2, 3)))
-    pinned = torch.from_numpy(canon.view(np.float64).reshape(-1)).pin_memory()
+    pinned = torch.from_numpy(synth.links_to_canonical(U).view(np.float64).reshape(-1)).pin_memory()
     h2d = pinned.numel() * 8
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -399,7 +509,7 @@ def run_ours(args):
         tp = time.perf_counter()
         g2 = qd.Gauge.from_host_buffer(ctx, WL["dims"], pinned)
         tp = lap("gauge", tp)
-        mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, qd.mg_params(len(WL["blocks"]), WL["blocks"], WL["nvs"], **WL.get("mg_kw", {})))
+        mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, _mg_params(qd))
         tp = lap("mg_setup", tp)
         if WL.get("learned"):
             qd.smoother_train(mg2, nsamples=4, solve_tol=1e-3, mr_steps=WL["learned"])
@@ -423,20 +533,23 @@ def run_ours(args):
     e2e = None if not e2e_steps else {"value": s * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": s * 16 + 6 * 8,
            "phases_s": {k: round(v / max(e2e_steps, 1), 4) for k, v in phases.items()},
-           "scope": "per step: link upload from pinned host memory, adaptive MG setup, learned-smoother "
-                    "training, Algorithm 2 deflation space, one 64-sample batch, per-sample t_j and statistics "
-                    "read back"}
+           "scope": f"per step: link upload from pinned host memory, adaptive MG setup, learned-smoother "
+                    f"training, Algorithm 2 deflation space, one {s}-sample batch, per-sample t_j and statistics "
+                    f"read back"}
 
-    # the plain FP64 path on the same workload (the other side of the metric)
+    # the plain FP64 path on the same workload (the other side of the
+    # metric), on a block of fp64_samples samples per step
     fp64 = None
     if args.precision == "mixed" and args.fp64_steps > 0:
+        sf = WL.get("fp64_samples", s)
         if WL.get("learned"):
             qd.smoother_enable(mg, False, WL["learned"])  # the plain FP64 form
-        _batch(qd, ctx, g, mg, d, offset(2000), qd.QD_PREC_F64)
+        _batch(qd, ctx, g, mg, d, offset(2000), qd.QD_PREC_F64, nsamples=sf)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        fres = [_batch(qd, ctx, g, mg, d, offset(2001 + i), qd.QD_PREC_F64) for i in range(args.fp64_steps)]
+        fres = [_batch(qd, ctx, g, mg, d, offset(2001 + i), qd.QD_PREC_F64, nsamples=sf)
+                for i in range(args.fp64_steps)]
         f1.record(stream)
         torch.cuda.synchronize()
         fms = f0.elapsed_time(f1)
@@ -446,17 +559,24 @@ def run_ours(args):
             fms = float(tt.item())
         if WL.get("learned"):
             qd.smoother_enable(mg, True, WL["learned"])
-        fp64 = {"value": args.fp64_steps * s * world / (fms / 1e3), "unit": UNIT, "steps": args.fp64_steps,
-                "ms_per_step": fms / args.fp64_steps, "dtype": "f64", "smoother": "plain MR(4)",
+        fp64 = {"value": args.fp64_steps * sf * world / (fms / 1e3), "unit": UNIT, "steps": args.fp64_steps,
+                "samples_per_step": sf, "ms_per_step": fms / args.fp64_steps, "dtype": "f64",
+                "smoother": "plain MR (4 fine, coarse as the workload)",
                 "outer_iterations": [r["iterations"] for r in fres],
-                "max_true_rel_residual": max(r["max_true_rel_residual"] for r in fres)}
+                "max_true_rel_residual": max(r["max_true_rel_residual"] for r in fres),
+                "mixed_over_fp64": value / (args.fp64_steps * sf * world / (fms / 1e3))}
+
+    errors = None
+    if rank == 0 and not args.no_errors:
+        errors = errors_against_oracle(qd, ctx, U, g, mg, d)
 
     stencil = stencil_roofline(qd, ctx) if rank == 0 else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
+        its = max(fp64["outer_iterations"]) if fp64 else FP64_ITERS_CONFIG3
         try:
-            cpu = cpu_baseline(samples=args.cpu_samples)
+            cpu = cpu_baseline(its)
         except Exception as exc:  # report, never hide the GPU line
             cpu = {"value": None, "unit": UNIT, "error": repr(exc)}
 
@@ -470,13 +590,15 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WL["workload"], "precision": args.precision,
                        "parallelism": f"replicas x{world} (independent samples)",
-                       "l2": "working set > L2 (GCR basis 2 x 16 x 50 MB per batch)",
+                       "l2": "working set > L2 (fine fields 1.6 GB each)",
                        "setup_s": round(setup_s, 3), "outer_iterations": iters,
                        "max_true_rel_residual": worst,
-                       "estimate": [results[-1]["estimate"].real, results[-1]["stderr"]],
+                       "estimate": [run_stats["estimate"].real, run_stats["stderr"]],
+                       "estimate_samples": int(run_stats["s"]),
                        "mg_overrides": WL.get("mg_kw", {}),
-                       "learned_smoother": ({"mr_steps": WL["learned"], "judge": WL.get("smoother_judge")}
+                       "learned_smoother": ({"mr_steps": WL["learned"], "judge": judge}
                                             if WL.get("learned") else None)},
+            "errors": errors,
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "fp64_path": fp64, "stencil": stencil, "cpu_baseline": cpu,
         }
@@ -778,17 +900,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-samples", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-errors", action="store_true", help="skip the errors-against-the-oracle leg")
     ap.add_argument("--prof-steps", type=int, default=2)
-    ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS) + ["config4", "config5"])
+    ap.add_argument("--workload", default="config3", choices=sorted(WORKLOADS) + ["config4", "config5"])
     ap.add_argument("--stencil-only", action="store_true",
                     help="only the Wilson stencil alone on 16^3 x 32 (a profiling target)")
     ap.add_argument("--small", action="store_true",
                     help="config5: the learned-vs-plain comparison on the 16^3 x 32 lattice")
     ap.add_argument("--smoother-steps", type=int, default=0, help="> 0: MR post-smoothing steps (default 4)")
+    ap.add_argument("--coarse-smoother-steps", type=int, default=-1,
+                    help=">= 0: MR post-smoothing steps on the coarse levels (default: as the fine level)")
     ap.add_argument("--learned", type=int, default=-1,
                     help=">= 1: train the learned smoother and use it with this many MR steps after it; "
                          "0: plain smoother; default: the workload's setting")
@@ -808,11 +932,13 @@ def main():
             return 0
         return run_batch(args) if args.workload == "config4" else run_learned(args)
     WL.clear()
-    WL.update(WORKLOADS[args.workload] if args.workload != "config2" else dict(WORKLOADS["config2"]))
+    WL.update(WORKLOADS[args.workload])
     if args.fixed_coarse > 0:
-        WL["mg_kw"] = {"coarse_tol": 0.0, "coarse_maxit": args.fixed_coarse}
+        WL["mg_kw"] = dict(WL.get("mg_kw", {}), coarse_tol=0.0, coarse_maxit=args.fixed_coarse)
     if args.smoother_steps > 0:
         WL["mg_kw"] = dict(WL.get("mg_kw", {}), smoother_steps=args.smoother_steps)
+    if args.coarse_smoother_steps >= 0:
+        WL["mg_kw"] = dict(WL.get("mg_kw", {}), coarse_smoother_steps=args.coarse_smoother_steps)
     if args.learned >= 0:
         WL["learned"] = args.learned
     if args.impl == "reference":

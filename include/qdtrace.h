@@ -191,6 +191,9 @@ typedef struct {
                                    tcgen05 tensor cores (split-BF16 operands,
                                    FP32 accumulate; qd_coarse_apply_tc); 0:
                                    FP32 CUDA cores (qd_coarse_apply_f32) */
+  int coarse_smoother_steps;    /* minimal-residual post-smoothing steps of
+                                   the V-cycles on coarse levels; < 0: the
+                                   same as smoother_steps */
 } qd_mg_params;
 
 /* Fill `p` with this library's defaults (1 level, 2^4 blocks, nv 12,

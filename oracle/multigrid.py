@@ -185,11 +185,13 @@ class Hierarchy:
     """Levels 0..L-1, transfers 0..L-2 and coarse matrices 1..L-1."""
 
     def __init__(self, levels, transfers, matrices, smoother_steps=4,
-                 coarse_tol=0.1, coarse_maxit=256, restart=16):
+                 coarse_tol=0.1, coarse_maxit=256, restart=16, coarse_smoother_steps=None):
         self.levels = levels
         self.transfers = transfers
         self.matrices = matrices
         self.nu = smoother_steps
+        # smoothing steps of the V-cycles on coarse levels (default: the same)
+        self.nu_coarse = smoother_steps if coarse_smoother_steps is None else coarse_smoother_steps
         self.coarse_tol = coarse_tol
         self.coarse_maxit = coarse_maxit
         self.restart = restart
@@ -204,7 +206,8 @@ class Hierarchy:
         ec, _, _ = krylov.gcr(self.levels[nxt].matvec, rc, self.coarse_tol,
                               maxit=self.coarse_maxit, restart=self.restart, precond=pre)
         x = T.prolong(ec)
-        e, _, _ = krylov.minres_steps(A.matvec, r - A.matvec(x), self.nu)
+        nu = self.nu if lvl == 0 else self.nu_coarse
+        e, _, _ = krylov.minres_steps(A.matvec, r - A.matvec(x), nu)
         return x + e
 
 

@@ -156,3 +156,30 @@ def free_field_trace_inverse(dims, m0):
     M = m0 + sum(1 - np.cos(k) for k in ks)
     S2 = sum(np.sin(k) ** 2 for k in ks)
     return float(np.sum(12.0 * M / (M * M + S2)))
+
+
+def free_field_variance_real_rademacher(dims, m0):
+    """E|t - tr A^{-1}|^2 of one real Rademacher sample t = z^T A^{-1} z, unit links.
+
+    The variance is 2||S||_F^2 - 2 sum_i |S_ii|^2 with S = (B + B^T)/2,
+    B = A^{-1} (see ``dense.exact_variance_real_rademacher``).  With unit links
+    B is translation invariant, B(x, y) = G(x - y), and Parseval turns
+    ||S||_F^2 into sum_p ||F(p)||_F^2 with F(p) = (A(p)^{-1} + A(-p)^{-T}) / 2,
+    A(p)^{-1} = (M - i sum_mu s_mu gamma_mu) / (M^2 + S^2) (s_mu = sin p_mu,
+    S^2 = sum s_mu^2), times the colour identity.  In the chiral basis gamma_1
+    and gamma_3 are antisymmetric and gamma_2, gamma_4 symmetric, so
+    F(p) = (M - i (s_1 gamma_1 + s_3 gamma_3)) / (M^2 + S^2) and
+    ||F(p)||_F^2 = 12 (M^2 + s_1^2 + s_3^2) / (M^2 + S^2)^2.  The diagonal of
+    S is that of G(0), 12 V entries g0 = (1/V) sum_p M / (M^2 + S^2) (the
+    gammas have zero diagonal).
+    """
+    ks = np.meshgrid(*[2 * np.pi * np.arange(L) / L for L in dims], indexing="ij")
+    M = m0 + sum(1 - np.cos(k) for k in ks)
+    s = [np.sin(k) for k in ks]
+    S2 = sum(x ** 2 for x in s)
+    den = M * M + S2
+    V = int(np.prod(dims))
+    frob = np.sum(12.0 * (M * M + s[0] ** 2 + s[2] ** 2) / den ** 2)
+    g0 = np.sum(M / den) / V
+    return float(2.0 * frob - 2.0 * 12 * V * g0 * g0)
+

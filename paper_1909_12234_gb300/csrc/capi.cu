@@ -203,6 +203,7 @@ void qd_mg_params_default(qd_mg_params* p) {
   p->coarsest_bf16 = 1;
   p->use_graphs = 1;
   p->coarse_tc = 1;
+  p->coarse_smoother_steps = -1;
 }
 
 void qd_solver_params_default(qd_solver_params* p) {

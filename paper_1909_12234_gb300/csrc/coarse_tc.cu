@@ -33,8 +33,11 @@
 // the CTA records an error, stops, drains its copies and MMAs and frees TMEM.
 #include <cuda_bf16.h>
 
+#include <string>
+
 #include "coarse_tc.cuh"
 #include "ptx.cuh"
+#include "tune.cuh"
 
 namespace qd {
 
@@ -323,17 +326,18 @@ __global__ void k_build_cb(int64_t nblk, int DD, const cplx* __restrict__ C, uin
   }
 }
 
+// Launch with NS staging slots and as many operand stages as fit (at most
+// kMaxNA); false (nothing launched) when fewer than two operand stages fit.
 template <int D>
-void launch(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int s, int* err) {
+bool launch(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int s, int* err, int NS) {
   const int nchunks = (s + 127) / 128;
   const int w = s < 128 ? s : 128;
   const uint32_t b_tile = (uint32_t)((4 * D * 128 + 1023) / 1024 * 1024);
   const uint32_t stage = (uint32_t)(((size_t)D * w * 8 + (size_t)2 * D * D * 4 + 1023) / 1024 * 1024);
   const size_t budget = 220 * 1024;
-  int NS = 2;
+  if (NS > kMaxNS || 1024 + (size_t)NS * stage + 2 * (2 * kATile + b_tile) > budget) return false;
   int NA = (int)((budget - 1024 - (size_t)NS * stage) / (2 * kATile + b_tile));
   if (NA > kMaxNA) NA = kMaxNA;
-  QD_REQUIRE(NA >= 2, "tensor-core coarse stencil: operand tiles do not fit in shared memory");
   const size_t smem = 1024 + (size_t)NA * (2 * kATile + b_tile) + (size_t)NS * stage;
   ensure_smem_limit(reinterpret_cast<const void*>(k_coarse_tc<D>), smem);
   const int64_t items = lv.geo.nsites * (int64_t)nchunks;
@@ -343,6 +347,7 @@ void launch(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int
                                                         reinterpret_cast<const float2*>(in),
                                                         reinterpret_cast<float2*>(out), err);
   QD_LAUNCH_CHECK();
+  return true;
 }
 
 }  // namespace
@@ -380,12 +385,24 @@ void coarse_apply_tc(qd_ctx& ctx, CoarseLevel& lv, const cplxf* in, cplxf* out, 
   ProfScope ps(ctx, QD_PROF_COARSE_TC, 72.0 * D * D * (double)lv.geo.nsites * s,
                (double)lv.geo.nsites * (9.0 * D * D * 8.0 + 2.0 * D * 8.0 * s));
   int* err = lv.ctc_err.as<int>();
-  switch (lv.D) {
-    case 8: launch<8>(ctx, lv, in, out, s, err); break;
-    case 16: launch<16>(ctx, lv, in, out, s, err); break;
-    case 24: launch<24>(ctx, lv, in, out, s, err); break;
-    default: launch<32>(ctx, lv, in, out, s, err); break;
-  }
+  // candidates: 2, 3 or 4 staging slots (deeper prefetch against fewer
+  // operand stages); every candidate computes the same sums in the same order
+  auto go = [&](int c) -> bool {
+    const int NS = 2 + c;
+    switch (lv.D) {
+      case 8: return launch<8>(ctx, lv, in, out, s, err, NS);
+      case 16: return launch<16>(ctx, lv, in, out, s, err, NS);
+      case 24: return launch<24>(ctx, lv, in, out, s, err, NS);
+      default: return launch<32>(ctx, lv, in, out, s, err, NS);
+    }
+  };
+  const std::string key = "coarse_tc D" + std::to_string(lv.D) + " sites" + std::to_string(lv.geo.nsites) + " rhs" +
+                          std::to_string(s);
+  const int c = tune_pick(ctx, key, 3, go);
+  if (c >= 0 && go(c)) return;
+  for (int d = 0; d < 3; ++d)
+    if (go(d)) return;
+  fail(QD_ERR_INVALID, "tensor-core coarse stencil: operand tiles do not fit in shared memory");
 }
 
 int coarse_tc_error(qd_ctx& ctx, const CoarseLevel& lv) {

@@ -31,6 +31,7 @@ template <class C> class GCR {
   void ensure(int64_t n, int nrhs, int m);
   DevBuf P_, Q_, r_, t_;
   DevBuf sc_;   // cplx per-RHS scalars
+  DevBuf tab_;  // cplx coefficient tables of the fused one-pass form
   DevBuf act_;  // int [nrhs + 1]: active flags, then the count of active
   int64_t cap_n_ = -1;
   int cap_rhs_ = -1, cap_m_ = -1;

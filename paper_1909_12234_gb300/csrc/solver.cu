@@ -139,6 +139,160 @@ __global__ void k_set_active(int nrhs, const cplx* __restrict__ rn2, const cplx*
   if (a) atomicAdd(count, 1);
 }
 
+// ---------------------------------------------------------------------------
+// One-pass (classical) Gram-Schmidt GCR with a deferred solution update, for
+// FP32 fields.  The preconditioned directions Pt_i = M r are never rewritten:
+// P_i = Pt_i - sum_{k<i} beta_ik P_k is kept implicit, Q_i = A Pt_i is
+// orthogonalised in place (unnormalised, nu_i = <Q_i, Q_i>), and the solution
+// x += sum_i a_i P_i = sum_k d_k Pt_k is formed once per cycle with
+// d_k = a_k - sum_{i>k} beta_ik d_i.  Per iteration this reads the basis once
+// for the projections and once for the update, instead of also updating P
+// and rewriting q, p, x every iteration.
+// ---------------------------------------------------------------------------
+constexpr int kMaxMdot = 16;
+
+// partials[(blk*K + k)*nrhs + c] = sum over this block's rows of conj(Q_k) y
+// for k < K <= 16, reading y once.
+__global__ void k_mdot_f32(int K, int64_t n, int nrhs, const float2* __restrict__ Q, int64_t qs,
+                           const float2* __restrict__ y, cplx* __restrict__ partials) {
+  __shared__ float2 sm[kMaxMdot][blas::kThreads];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c = blockIdx.y * blockDim.x + tx;
+  float2 acc[kMaxMdot];
+#pragma unroll
+  for (int k = 0; k < kMaxMdot; ++k) acc[k] = make_float2(0.f, 0.f);
+  if (c < nrhs) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.y + ty; i < n; i += (int64_t)gridDim.x * blockDim.y) {
+      const int64_t e = i * nrhs + c;
+      const float2 yv = y[e];
+#pragma unroll
+      for (int k = 0; k < kMaxMdot; ++k)
+        if (k < K) cfmac(acc[k], Q[k * qs + e], yv);
+    }
+  }
+  const int t = ty * blockDim.x + tx;
+#pragma unroll
+  for (int k = 0; k < kMaxMdot; ++k)
+    if (k < K) sm[k][t] = acc[k];
+  __syncthreads();
+  for (int h = blockDim.y / 2; h > 0; h >>= 1) {
+    if (ty < h) {
+#pragma unroll
+      for (int k = 0; k < kMaxMdot; ++k)
+        if (k < K) sm[k][t] = cadd(sm[k][t], sm[k][t + h * blockDim.x]);
+    }
+    __syncthreads();
+  }
+  if (ty == 0 && c < nrhs)
+    for (int k = 0; k < K; ++k)
+      partials[((int64_t)blockIdx.x * K + k) * nrhs + c] = mkc((double)sm[k][tx].x, (double)sm[k][tx].y);
+}
+
+// Q_i -= sum_{k<i} (beta'_k / nu_k) Q_k for active columns, with the partial
+// sums of <Q_i, Q_i> and <Q_i, r> (two values per column).  The coefficients
+// are recorded in btab[k][c] (0 for inactive columns).
+__global__ void k_orth_f32(int i, int64_t n, int nrhs, float2* __restrict__ Q, int64_t qs,
+                           const float2* __restrict__ r, const cplx* __restrict__ braw,
+                           const cplx* __restrict__ ngtab, const int* __restrict__ active,
+                           cplx* __restrict__ btab, cplx* __restrict__ partials) {
+  __shared__ double smr[2][blas::kThreads];
+  __shared__ double smi[blas::kThreads];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c = blockIdx.y * blockDim.x + tx;
+  const bool act = c < nrhs && active[c];
+  float2 coef[kMaxMdot];
+#pragma unroll
+  for (int k = 0; k < kMaxMdot; ++k) {
+    coef[k] = make_float2(0.f, 0.f);
+    if (act && k < i) {
+      const double nu = ngtab[(int64_t)(2 * k) * nrhs + c].x;
+      const cplx b = braw[(int64_t)k * nrhs + c];
+      if (nu > 0.0) coef[k] = make_float2((float)(b.x / nu), (float)(b.y / nu));
+    }
+  }
+  if (blockIdx.x == 0 && ty == 0 && c < nrhs)
+    for (int k = 0; k < i; ++k) btab[(int64_t)k * nrhs + c] = mkc((double)coef[k].x, (double)coef[k].y);
+  float nn = 0.f;
+  float2 nr = make_float2(0.f, 0.f);
+  float2* Qi = Q + (int64_t)i * qs;
+  if (act) {
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.y + ty; row < n; row += (int64_t)gridDim.x * blockDim.y) {
+      const int64_t e = row * nrhs + c;
+      float2 q = Qi[e];
+#pragma unroll
+      for (int k = 0; k < kMaxMdot; ++k)
+        if (k < i) cfma(q, make_float2(-coef[k].x, -coef[k].y), Q[k * qs + e]);
+      Qi[e] = q;
+      nn += cnorm2(q);
+      cfmac(nr, q, r[e]);
+    }
+  }
+  const int t = ty * blockDim.x + tx;
+  smr[0][t] = (double)nn;
+  smr[1][t] = (double)nr.x;
+  smi[t] = (double)nr.y;
+  __syncthreads();
+  for (int h = blockDim.y / 2; h > 0; h >>= 1) {
+    if (ty < h) {
+      smr[0][t] += smr[0][t + h * blockDim.x];
+      smr[1][t] += smr[1][t + h * blockDim.x];
+      smi[t] += smi[t + h * blockDim.x];
+    }
+    __syncthreads();
+  }
+  if (ty == 0 && c < nrhs) {
+    partials[((int64_t)blockIdx.x * 2 + 0) * nrhs + c] = mkc(smr[0][tx], 0.0);
+    partials[((int64_t)blockIdx.x * 2 + 1) * nrhs + c] = mkc(smr[1][tx], smi[tx]);
+  }
+}
+
+// a = <Q_i, r> / <Q_i, Q_i>; r -= a Q_i for active columns (a recorded in
+// atab[c], 0 for inactive ones), with the partial sums of |r|^2.
+__global__ void k_rupd_f32(int64_t n, int nrhs, const float2* __restrict__ Qi, float2* __restrict__ r,
+                           const cplx* __restrict__ ng, const int* __restrict__ active, cplx* __restrict__ atab,
+                           cplx* __restrict__ partials) {
+  const int col = blockIdx.y * blockDim.x + threadIdx.x;
+  float acc = 0.f;
+  const bool act = col < nrhs && active[col];
+  double ar = 0.0, ai = 0.0;
+  if (act) {
+    const double nu = ng[col].x;
+    const cplx g = ng[nrhs + col];
+    if (nu > 0.0) {
+      ar = g.x / nu;
+      ai = g.y / nu;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.y == 0 && col < nrhs) atab[col] = mkc(ar, ai);
+  if (act) {
+    const float2 na = make_float2((float)(-ar), (float)(-ai));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < n; i += (int64_t)gridDim.x * blockDim.y) {
+      const int64_t e = i * nrhs + col;
+      float2 rv = r[e];
+      cfma(rv, na, Qi[e]);
+      r[e] = rv;
+      acc += cnorm2(rv);
+    }
+  }
+  rows_reduce((double)acc, partials, nrhs);
+}
+
+// Per column: d_{m-1} = a_{m-1}, d_k = a_k - sum_{i>k} beta_ik d_i; writes
+// coef[k][c] = -d_k (multi_axpy subtracts).
+__global__ void k_backsub(int m, int nrhs, const cplx* __restrict__ atab, const cplx* __restrict__ btab,
+                          cplx* __restrict__ coef) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrhs) return;
+  cplx d[kMaxMdot];
+  for (int k = m - 1; k >= 0; --k) {
+    cplx v = atab[(int64_t)k * nrhs + c];
+    for (int i = k + 1; i < m; ++i)
+      cfma(v, cscale(-1.0, btab[((int64_t)i * kMaxMdot + k) * nrhs + c]), d[i]);
+    d[k] = v;
+    coef[(int64_t)k * nrhs + c] = mkc(-v.x, -v.y);
+  }
+}
+
 static void read_flags(qd_ctx& ctx, const int* dev, int n, int* host) {
   QD_CUDA(cudaMemcpyAsync(ctx.host_pinned, dev, n * sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
   QD_CUDA(cudaStreamSynchronize(ctx.stream));
@@ -149,7 +303,7 @@ static void read_flags(qd_ctx& ctx, const int* dev, int n, int* host) {
 // GCR
 // ---------------------------------------------------------------------------
 template <class C> void GCR<C>::buffers(std::vector<const void*>& v) const {
-  for (const DevBuf* b : {&P_, &Q_, &r_, &t_, &sc_, &act_}) v.push_back(b->as<void>());
+  for (const DevBuf* b : {&P_, &Q_, &r_, &t_, &sc_, &act_, &tab_}) v.push_back(b->as<void>());
 }
 
 template <class C> void GCR<C>::ensure(int64_t n, int nrhs, int m) {
@@ -176,6 +330,14 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
   const int64_t n = A.n();
   const int64_t tot = n * nrhs;
   ensure(n, nrhs, restart);
+  // FP32 with one Gram-Schmidt pass: the fused form with a deferred update
+  const bool fused = orth_passes == 1 && sizeof(C) == sizeof(cplxf) && restart <= kMaxMdot;
+  tab_.resize((size_t)(2 * kMaxMdot + kMaxMdot * kMaxMdot + 3 * kMaxMdot) * nrhs * sizeof(cplx));
+  cplx* ngtab = tab_.as<cplx>();                          // [m][2][nrhs]: nu_i, gamma_i
+  cplx* btab = ngtab + (int64_t)2 * kMaxMdot * nrhs;      // [m][16][nrhs]: beta_ik
+  cplx* atab = btab + (int64_t)kMaxMdot * kMaxMdot * nrhs;  // [m][nrhs]: a_i
+  cplx* coefx = atab + (int64_t)kMaxMdot * nrhs;           // [m][nrhs]: -d_k
+  cplx* braw = coefx + (int64_t)kMaxMdot * nrhs;           // [m][nrhs]: <Q_k, Q_i>
   C* P = P_.as<C>();
   C* Q = Q_.as<C>();
   C* r = r_.as<C>();
@@ -211,6 +373,70 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
       read_flags(ctx, flags, 2, hflags);
       if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
       if (hflags[0] == 0 || its >= maxit) break;
+    }
+    if (fused) {
+      // one-pass Gram-Schmidt, deferred solution update (see k_orth_f32)
+      float2* Pf = reinterpret_cast<float2*>(P);
+      float2* Qf = reinterpret_cast<float2*>(Q);
+      float2* rf = reinterpret_cast<float2*>(r);
+      int mi = 0;
+      for (int i = 0; i < restart; ++i) {
+        C* Pi = P + i * tot;
+        C* Qi = Q + i * tot;
+        if (M)
+          M->apply(ctx, r, Pi, nrhs);
+        else
+          blas::copy(ctx, tot, r, Pi);
+        A.apply(ctx, Pi, Qi, nrhs);
+        if (i > 0) {
+          {
+            ProfScope ps(ctx, QD_PROF_DOTS_F32, 8.0 * i * n * nrhs, 8.0 * (i + 1.0) * n * nrhs);
+            k_mdot_f32<<<sw.grid, sw.block, 0, ctx.stream>>>(i, n, nrhs, Qf, tot, Qf + i * tot,
+                                                              ctx.red_partials.as<cplx>());
+            QD_LAUNCH_CHECK();
+          }
+          blas::k_dots_final<<<div_up(i * nrhs, 8), 256, 0, ctx.stream>>>(i, nrhs, sw.grid.x, ctx.red_partials.as<cplx>(),
+                                                                    braw);
+          QD_LAUNCH_CHECK();
+        }
+        {
+          ProfScope ps(ctx, QD_PROF_AXPY_F32, 8.0 * (i + 2.0) * n * nrhs, 8.0 * (i + 3.0) * n * nrhs);
+          k_orth_f32<<<sw.grid, sw.block, 0, ctx.stream>>>(i, n, nrhs, Qf, tot, rf, braw, ngtab, act,
+                                                            btab + (int64_t)i * kMaxMdot * nrhs,
+                                                            ctx.red_partials.as<cplx>());
+          QD_LAUNCH_CHECK();
+        }
+        blas::k_dots_final<<<div_up(2 * nrhs, 8), 256, 0, ctx.stream>>>(2, nrhs, sw.grid.x, ctx.red_partials.as<cplx>(),
+                                                                  ngtab + (int64_t)2 * i * nrhs);
+        QD_LAUNCH_CHECK();
+        {
+          ProfScope ps(ctx, QD_PROF_UPDATE_F32, 8.0 * n * nrhs, 8.0 * 3.0 * n * nrhs);
+          k_rupd_f32<<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, Qf + i * tot, rf, ngtab + (int64_t)2 * i * nrhs, act,
+                                                            atab + (int64_t)i * nrhs, ctx.red_partials.as<cplx>());
+          QD_LAUNCH_CHECK();
+        }
+        QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
+        k_resid_final<<<div_up(nrhs, 8), 256, 0, ctx.stream>>>(nrhs, sw.grid.x, ctx.red_partials.as<cplx>(), rn2,
+                                                              bn2, tol2, act, flags, flags + 1, iters);
+        QD_LAUNCH_CHECK();
+        ++its;
+        ++mi;
+        if (check) {
+          read_flags(ctx, flags, 2, hflags);
+          if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
+          if (hflags[0] == 0) break;
+        }
+        if (its >= maxit) break;
+      }
+      // x += sum_k d_k Pt_k
+      k_backsub<<<div_up(nrhs, 128), 128, 0, ctx.stream>>>(mi, nrhs, atab, btab, coefx);
+      QD_LAUNCH_CHECK();
+      blas::multi_axpy(ctx, mi, n, nrhs, coefx, nullptr, P, tot, x);
+      (void)Pf;
+      if (!check && its >= maxit) break;
+      A.residual(ctx, b, x, r, nrhs);
+      blas::dots(ctx, 1, n, nrhs, r, 0, r, 0, rn2);
+      continue;
     }
     for (int i = 0; i < restart; ++i) {
       C* Pi = P + i * tot;
@@ -351,6 +577,9 @@ template void mr_steps<cplxf>(qd_ctx&, const Op<cplxf>&, const cplxf*, cplxf*, b
 template <class C>
 MGPrecond<C>::MGPrecond(qd_mg* mg, int level) : mg_(mg), level_(level) {
   if (level + 1 < mg->nlevels) next_.reset(new MGPrecond<C>(mg, level + 1));
+  // FP32 coarse GCR: one Gram-Schmidt pass in the fused form (a handful of
+  // iterations of a preconditioner lose little orthogonality); FP64 keeps two
+  if (sizeof(C) == sizeof(cplxf)) coarse_.orth_passes = 1;
 }
 
 template <class C> MGPrecond<C>::~MGPrecond() {
@@ -534,7 +763,8 @@ template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, int nr
     }
     return;
   }
-  const int nu = mg_->p.smoother_steps;
+  const int nu = (level_ > 0 && mg_->p.coarse_smoother_steps >= 0) ? mg_->p.coarse_smoother_steps
+                                                                    : mg_->p.smoother_steps;
   if (nu > 0) {
     Af->residual(ctx, r, z, res_.as<C>(), nrhs);
     mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, nu, scratch_);

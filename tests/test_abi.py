@@ -49,8 +49,9 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "qdtrace.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol),
-         offsetof(qd_mg_params, coarsest_direct), offsetof(qd_mg_params, use_graphs), offsetof(qd_mg_params, coarse_tc));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol),
+         offsetof(qd_mg_params, coarsest_direct), offsetof(qd_mg_params, use_graphs), offsetof(qd_mg_params, coarse_tc),
+         offsetof(qd_mg_params, coarse_smoother_steps));
   printf("%zu %zu\n", sizeof(qd_solve_stats), offsetof(qd_solve_stats, true_rel_residual));
   printf("%zu %zu\n", sizeof(qd_defl_params), offsetof(qd_defl_params, seed));
   printf("%zu %zu\n", sizeof(qd_trace_params), offsetof(qd_trace_params, solver));
@@ -67,7 +68,7 @@ int main(void) {
     got = [list(map(int, l.split())) for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines()]
     want = [
         [ctypes.sizeof(qd.MGParams), qd.MGParams.null_tol.offset, qd.MGParams.coarsest_direct.offset,
-         qd.MGParams.use_graphs.offset, qd.MGParams.coarse_tc.offset],
+         qd.MGParams.use_graphs.offset, qd.MGParams.coarse_tc.offset, qd.MGParams.coarse_smoother_steps.offset],
         [ctypes.sizeof(qd.SolveStats), qd.SolveStats.true_rel_residual.offset],
         [ctypes.sizeof(qd.DeflParams), qd.DeflParams.seed.offset],
         [ctypes.sizeof(qd.TraceParams), qd.TraceParams.solver.offset],

@@ -198,3 +198,72 @@ def test_config3_three_level_mixed_precision(qd, ctx):
     # t_j = z_j^H x_j for those samples
     zl = host(z)[eo].reshape(-1, 2)
     assert np.allclose(np.einsum("ij,ij->j", zl.conj(), xl.reshape(-1, 2)), res["t"][:2], rtol=1e-5)
+
+
+def test_bench_path_8x4_against_oracle(qd, ctx):
+    # The estimator workload's exact GPU path at 8^4 (eps 0.3, m0 -0.8,
+    # two-level MG 2^4 / nv 12, Algorithm 2 with k = 24, xi = 1e-8): mixed
+    # precision (FP32 GCR + FP32 V-cycle inside FP64 refinement), the learned
+    # smoother with one MR step, captured V-cycle graphs, tensor-core coarsest
+    # solve; compared per sample with the oracle on the same noise.  Both sides
+    # use the oracle's null vectors (minimal residual to 1e-2 / 200 steps) and
+    # its Algorithm 2 basis, so W, C and P are the same; the learned smoother
+    # and the precisions only change how the solves get to xi.
+    #
+    # Bound: t_gpu - t_exact = z^H (x - A^{-1} b) = -(A^{-H} z)^H r with r the
+    # GPU's final residual, so |t_gpu - t_exact| <= ||A^{-H} z|| ||r||.  The
+    # oracle solves A y = gamma5 z to 1e-11: gamma5 A gamma5 = A^H gives
+    # ||A^{-H} z|| = ||y|| and z^H A^{-1} z = y^H gamma5 z, and the deflated
+    # t_exact = z^H A^{-1} z - (W^H z)^H U Lambda^{-1} U^H gamma5^W (W^H z)
+    # (the scalar form of Algorithm 2, exact for any z).
+    from oracle import krylov
+    dims, m0, k, s, xi = (8, 8, 8, 8), -0.8, 24, 6, 1e-8
+    U = synth.random_su3_links(dims, 0.3, 2)
+    lev0 = omg.fine_level(U, m0, dims)
+    Y, _ = omg.null_vectors(lev0, 12, 7, 1e-2, 200)
+    H = omg.setup(U, m0, dims, [(2, 2, 2, 2)], [12], seed=7, injected_null=[Y])
+    alg = odefl.Alg2(H.transfers[0], H.matrices[0], k)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(1, [(2, 2, 2, 2)], [12], seed=7),
+                      injected_null=qd.to_qd(ctx, g, Y.reshape(g.V, 4, 3, 12)))
+    qd.smoother_train(mg, nsamples=4, solve_tol=1e-3, mr_steps=1)
+    qd.smoother_enable(mg, True, 1)
+    d = qd.Deflation(ctx, g, mg, m0, 0.0, qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, k),
+                     injected_basis=torch.from_numpy(np.ascontiguousarray(alg.Ubar)).to("cuda:0"))
+    kw = dict(seed=102, sample_offset=0, nsamples=s, tol=xi, maxit=500, restart=16,
+              precision=qd.QD_PREC_MIXED, inner_tol=1e-5, max_refine=10)
+    runs = [qd.hutchinson_trace(ctx, g, mg, d, m0, 0.0, **kw) for _ in range(3)]  # eager, capture, replay
+    res0 = qd.hutchinson_trace(ctx, g, mg, None, m0, 0.0, **kw)
+    for r in runs + [res0]:
+        assert r["status"] == qd.QD_OK and r["max_true_rel_residual"] <= xi
+    assert abs(runs[-1]["t0"] - alg.t0) <= 1e-9 * abs(alg.t0)
+    # oracle, per sample
+    Z = philox.rademacher(lev0.n, 102, range(s)).astype(complex)
+    g5 = np.tile(np.repeat([1.0, -1.0], 6), g.V)
+    ZhV, UhKZ = alg.coeffs(Z)
+    corr = alg.correction(ZhV, UhKZ, k)
+    B = alg.project(lev0.matvec, Z)
+    t_u, t_d, bound_u, bound_d = [], [], [], []
+    for j in range(s):
+        y, _, rel = krylov.gcr(lev0.matvec, g5 * Z[:, j], 1e-11, restart=16, precond=lambda v: H.vcycle(0, v))
+        assert rel <= 1e-11
+        tu = np.vdot(y, g5 * Z[:, j])
+        t_u.append(tu)
+        t_d.append(tu - corr[j])
+        ny, nz = np.linalg.norm(y), np.linalg.norm(Z[:, j])
+        slack = 1e-10 * ny * nz  # the oracle's own 1e-11 solve
+        bound_u.append(ny * xi * nz + slack)
+        bound_d.append(ny * xi * np.linalg.norm(B[:, j]) + slack)
+    t_u, t_d = np.array(t_u), np.array(t_d)
+    for r in runs:
+        assert np.all(np.abs(r["t"] - t_d) <= bound_d), (np.abs(r["t"] - t_d) / bound_d).max()
+    assert np.all(np.abs(res0["t"] - t_u) <= bound_u), (np.abs(res0["t"] - t_u) / bound_u).max()
+    # the oracle's statistics of the same samples, and the variance reduction
+    ref_d = estimator.statistics(t_d, alg.t0)
+    ref_u = estimator.statistics(t_u)
+    assert abs(runs[-1]["estimate"] - ref_d["estimate"]) <= max(bound_d) + 1e-9 * abs(alg.t0)
+    ratio_gpu = res0["var"] / runs[-1]["var"]
+    ratio_orc = ref_u["var"] / ref_d["var"]
+    assert abs(ratio_gpu - ratio_orc) <= 1e-3 * ratio_orc, (ratio_gpu, ratio_orc)
+    for o in (d, mg, g):
+        o.close()

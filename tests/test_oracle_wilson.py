@@ -94,6 +94,27 @@ def test_free_field_trace_inverse_dense():
     assert abs(tr - wilson.free_field_trace_inverse(dims, -0.4)) < 1e-10 * abs(tr)
 
 
+@pytest.mark.parametrize("dims,m0", [((4, 2, 2, 2), -0.4), ((2, 4, 2, 4), -0.8), ((4, 4, 2, 2), 0.3)])
+def test_free_field_variance_closed_form_against_dense(dims, m0):
+    # the closed form against the dense exact variance of the same A^{-1}
+    # (itself pinned by enumeration of all sign vectors)
+    from oracle import dense
+    U = synth.random_su3_links(dims, 0.0, 0, unit=True)
+    B = np.linalg.inv(wilson.dirac_sparse(U, m0, dims).toarray())
+    ref = dense.exact_variance_real_rademacher(B)
+    got = wilson.free_field_variance_real_rademacher(dims, m0)
+    assert abs(got - ref) < 1e-10 * ref
+    # a wrong basis reading (gamma_2 instead of gamma_3 antisymmetric) fails
+    ks = np.meshgrid(*[2 * np.pi * np.arange(L) / L for L in dims], indexing="ij")
+    M = m0 + sum(1 - np.cos(k) for k in ks)
+    sn = [np.sin(k) for k in ks]
+    den = M * M + sum(x ** 2 for x in sn)
+    V = int(np.prod(dims))
+    bad = 2 * np.sum(12.0 * (M * M + sn[0] ** 2 + sn[1] ** 2) / den ** 2) - 24 * V * (np.sum(M / den) / V) ** 2
+    if not np.allclose(sn[1] ** 2, sn[2] ** 2):
+        assert abs(bad - ref) > 1e-6 * ref
+
+
 def test_gauge_covariance():
     dims = (4, 4, 2, 2)
     U = synth.random_su3_links(dims, 0.3, 6)

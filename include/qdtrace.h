@@ -187,10 +187,12 @@ typedef struct {
                                    and replayed; the result is the same as
                                    the eager launches.  Off while profiling */
   int coarse_tc;                /* != 0: the FP32 V-cycle applies coarse
-                                   stencils with dof 8, 16, 24 or 32 on the
+                                   stencils with dof 8, 16, 24 or 32
+                                   (qd_coarse_apply_tc) and restrictions with
+                                   fine dof 12, 16, 24 or 32 and coarse dof
+                                   16, 24 or 32 (qd_restrict_tc) on the
                                    tcgen05 tensor cores (split-BF16 operands,
-                                   FP32 accumulate; qd_coarse_apply_tc); 0:
-                                   FP32 CUDA cores (qd_coarse_apply_f32) */
+                                   FP32 accumulate); 0: FP32 CUDA cores */
   int coarse_smoother_steps;    /* minimal-residual post-smoothing steps of
                                    the V-cycles on coarse levels; < 0: the
                                    same as smoother_steps */
@@ -230,6 +232,17 @@ int qd_prolongate(qd_mg* mg, int level, int nrhs, const double* coarse,
 /* coarse (level l+1) = W_l^H fine (level l).  Asynchronous. */
 int qd_restrict(qd_mg* mg, int level, int nrhs, const double* fine,
                 double* coarse);
+
+/* coarse (level l+1) = W_l^H fine (level l) in FP32 on the tcgen05 tensor
+ * cores (the form the FP32 V-cycle uses with qd_mg_params.coarse_tc): per
+ * aggregate and chunk of <= 128 right-hand sides one real GEMM over the
+ * aggregate's fine sites, each operand split into two BF16 terms
+ * (hi = bf16(v), lo = bf16(v - hi)), products hi*hi + hi*lo + lo*hi with FP32
+ * accumulation (error about 3 * 2^-16 sum |W||fine| per output).  Needs fine
+ * dof 12, 16, 24 or 32, coarse dof 16, 24 or 32, 16-byte aligned interleaved
+ * complex float fields, nrhs even above 128 (QD_ERR_INVALID otherwise).
+ * Timeouts as qd_coarse_apply_tc.  Asynchronous. */
+int qd_restrict_tc(qd_mg* mg, int level, int nrhs, const float* fine, float* coarse);
 
 /* ------------------------------------------------------------------------ */
 /* a4: coarse operator C_l = W^H A W (Sec. 2, "V^H A V")                     */
@@ -578,7 +591,8 @@ enum {
   QD_PROF_SMOOTHER_F64 = 15,/* learned smoother S r, FP64 */
   QD_PROF_SMOOTHER_F32 = 16,/* learned smoother S r, FP32 (FP16 weights) */
   QD_PROF_COARSE_TC = 17,   /* a4 coarse stencil on tcgen05 (split-BF16 operands) */
-  QD_PROF_NKINDS = 18
+  QD_PROF_RESTRICT_TC = 18, /* a3 W^H x on tcgen05 (split-BF16 operands) */
+  QD_PROF_NKINDS = 19
 };
 
 /* enable != 0: record a CUDA event pair on the context stream around every

@@ -8,6 +8,7 @@
 
 #include "blas.cuh"
 #include "coarse_tc.cuh"
+#include "restrict_tc.cuh"
 #include "defl.cuh"
 #include "direct.cuh"
 #include "tc_gemm.cuh"
@@ -285,6 +286,22 @@ int qd_restrict(qd_mg* mg, int level, int nrhs, const double* fine, double* coar
     const qd::Transfer& T = *mg->T[level];
     qd::restrict_<qd::cplx>(*mg->ctx, T, T.W.as<qd::cplx>(), reinterpret_cast<const qd::cplx*>(fine),
                             reinterpret_cast<qd::cplx*>(coarse), nrhs);
+  });
+}
+
+int qd_restrict_tc(qd_mg* mg, int level, int nrhs, const float* fine, float* coarse) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(fine);
+    NONNULL(coarse);
+    QD_REQUIRE(level >= 0 && level < mg->nlevels, "level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    set_device(mg->ctx);
+    qd::Transfer& T = *mg->T[level];
+    QD_REQUIRE(qd::restrict_tc_supported(T, fine, coarse, nrhs),
+               "tensor-core restriction needs fine dof 12, 16, 24 or 32, coarse dof 16, 24 or 32, 16-byte aligned "
+               "fields and an even nrhs above 128");
+    qd::restrict_tc(*mg->ctx, T, reinterpret_cast<const qd::cplxf*>(fine), reinterpret_cast<qd::cplxf*>(coarse), nrhs);
   });
 }
 

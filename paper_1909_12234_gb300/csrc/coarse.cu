@@ -7,6 +7,7 @@
 //     and its application.
 #include <string>
 #include "coarse_tc.cuh"
+#include "restrict_tc.cuh"
 #include "qd_internal.cuh"
 #include "tune.cuh"
 
@@ -160,6 +161,11 @@ void prolongate(qd_ctx& ctx, const Transfer& T, const C* W, const C* coarse, C* 
 
 template <class C>
 void restrict_(qd_ctx& ctx, const Transfer& T, const C* W, const C* fine, C* coarse, int nrhs) {
+  if (sizeof(C) == sizeof(cplxf) && T.use_tc && W == T.Wf.as<C>() && restrict_tc_supported(T, fine, coarse, nrhs)) {
+    restrict_tc(ctx, const_cast<Transfer&>(T), reinterpret_cast<const cplxf*>(fine), reinterpret_cast<cplxf*>(coarse),
+                nrhs);
+    return;
+  }
   const int64_t tot = T.ncoarse * T.Dc * nrhs;
   const double cb = (double)sizeof(C);
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_RESTRICT_F64 : QD_PROF_RESTRICT_F32,

@@ -173,6 +173,9 @@ struct Transfer {
   DevBuf hopdir;      // int8  [nfine][8]: coarse stencil direction of each hop
   DevBuf W;           // cplx  [nfine][Df][nv]
   DevBuf Wf;          // cplxf copy
+  bool use_tc = false;     // FP32 V-cycle restricts on tensor cores
+  mutable DevBuf Wtc;      // uint32 [nfine][2][Df][nv]: split-BF16 (hi, lo) W
+  mutable DevBuf rtc_err;  // int: bounded-wait error of the tensor-core restriction
   std::vector<int> null_steps;
 };
 
@@ -184,6 +187,7 @@ struct CoarseLevel {
   bool use_tc = false;      // FP32 V-cycle applies the stencil on tensor cores
   mutable DevBuf Cmb;       // uint32 [nsites][9][D][D]: (re, im) BF16 pairs
   mutable DevBuf ctc_err;   // int: bounded-wait error of the tensor-core stencil
+  mutable DevBuf sten_src;  // int32 [nsites][9]: the site, then its 8 neighbours
   int ndense = 0;     // > 0: Cinv holds the dense inverse (coarsest level)
   DevBuf Cinv;        // cplx  [n][n], n = nsites * D
   DevBuf Cinvf;       // cplxf copy

@@ -5,6 +5,7 @@
 // Galerkin coarse operator W^H A W.
 #include "blas.cuh"
 #include "coarse_tc.cuh"
+#include "restrict_tc.cuh"
 #include "direct.cuh"
 #include "mg.cuh"
 #include "tc_gemm.cuh"
@@ -70,6 +71,11 @@ void mg_build(qd_mg& mg, const double* injected_null) {
   for (auto& lv : mg.L) {
     lv->use_tc = p.coarse_tc != 0 && (lv->D == 8 || lv->D == 16 || lv->D == 24 || lv->D == 32);
     if (lv->use_tc) coarse_tc_prepare(ctx, *lv);
+  }
+  for (auto& t : mg.T) {
+    t->use_tc = p.coarse_tc != 0 && (t->Df == 12 || t->Df == 16 || t->Df == 24 || t->Df == 32) &&
+                (t->Dc == 16 || t->Dc == 24 || t->Dc == 32);
+    if (t->use_tc) restrict_tc_prepare(ctx, *t);
   }
   mg.pre64.reset(new MGPrecond<cplx>(&mg, 0));
   mg.pre32.reset(new MGPrecond<cplxf>(&mg, 0));

@@ -152,38 +152,38 @@ __global__ void k_set_active(int nrhs, const cplx* __restrict__ rn2, const cplx*
 constexpr int kMaxMdot = 16;
 
 // partials[(blk*K + k)*nrhs + c] = sum over this block's rows of conj(Q_k) y
-// for k < K <= 16, reading y once.
-__global__ void k_mdot_f32(int K, int64_t n, int nrhs, const float2* __restrict__ Q, int64_t qs,
+// for k < K <= 16, reading y once (K a template argument so that the
+// accumulators stay in registers).
+template <int K>
+__global__ void k_mdot_f32(int64_t n, int nrhs, const float2* __restrict__ Q, int64_t qs,
                            const float2* __restrict__ y, cplx* __restrict__ partials) {
-  __shared__ float2 sm[kMaxMdot][blas::kThreads];
+  __shared__ float2 sm[K][blas::kThreads];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int c = blockIdx.y * blockDim.x + tx;
-  float2 acc[kMaxMdot];
+  float2 acc[K];
 #pragma unroll
-  for (int k = 0; k < kMaxMdot; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < K; ++k) acc[k] = make_float2(0.f, 0.f);
   if (c < nrhs) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.y + ty; i < n; i += (int64_t)gridDim.x * blockDim.y) {
       const int64_t e = i * nrhs + c;
       const float2 yv = y[e];
 #pragma unroll
-      for (int k = 0; k < kMaxMdot; ++k)
-        if (k < K) cfmac(acc[k], Q[k * qs + e], yv);
+      for (int k = 0; k < K; ++k) cfmac(acc[k], Q[k * qs + e], yv);
     }
   }
   const int t = ty * blockDim.x + tx;
 #pragma unroll
-  for (int k = 0; k < kMaxMdot; ++k)
-    if (k < K) sm[k][t] = acc[k];
+  for (int k = 0; k < K; ++k) sm[k][t] = acc[k];
   __syncthreads();
   for (int h = blockDim.y / 2; h > 0; h >>= 1) {
     if (ty < h) {
 #pragma unroll
-      for (int k = 0; k < kMaxMdot; ++k)
-        if (k < K) sm[k][t] = cadd(sm[k][t], sm[k][t + h * blockDim.x]);
+      for (int k = 0; k < K; ++k) sm[k][t] = cadd(sm[k][t], sm[k][t + h * blockDim.x]);
     }
     __syncthreads();
   }
   if (ty == 0 && c < nrhs)
+#pragma unroll
     for (int k = 0; k < K; ++k)
       partials[((int64_t)blockIdx.x * K + k) * nrhs + c] = mkc((double)sm[k][tx].x, (double)sm[k][tx].y);
 }
@@ -191,27 +191,30 @@ __global__ void k_mdot_f32(int K, int64_t n, int nrhs, const float2* __restrict_
 // Q_i -= sum_{k<i} (beta'_k / nu_k) Q_k for active columns, with the partial
 // sums of <Q_i, Q_i> and <Q_i, r> (two values per column).  The coefficients
 // are recorded in btab[k][c] (0 for inactive columns).
-__global__ void k_orth_f32(int i, int64_t n, int nrhs, float2* __restrict__ Q, int64_t qs,
+template <int I>
+__global__ void k_orth_f32(int64_t n, int nrhs, float2* __restrict__ Q, int64_t qs,
                            const float2* __restrict__ r, const cplx* __restrict__ braw,
                            const cplx* __restrict__ ngtab, const int* __restrict__ active,
                            cplx* __restrict__ btab, cplx* __restrict__ partials) {
+  constexpr int i = I;
   __shared__ double smr[2][blas::kThreads];
   __shared__ double smi[blas::kThreads];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int c = blockIdx.y * blockDim.x + tx;
   const bool act = c < nrhs && active[c];
-  float2 coef[kMaxMdot];
+  float2 coef[I > 0 ? I : 1];
 #pragma unroll
-  for (int k = 0; k < kMaxMdot; ++k) {
+  for (int k = 0; k < I; ++k) {
     coef[k] = make_float2(0.f, 0.f);
-    if (act && k < i) {
+    if (act) {
       const double nu = ngtab[(int64_t)(2 * k) * nrhs + c].x;
       const cplx b = braw[(int64_t)k * nrhs + c];
       if (nu > 0.0) coef[k] = make_float2((float)(b.x / nu), (float)(b.y / nu));
     }
   }
   if (blockIdx.x == 0 && ty == 0 && c < nrhs)
-    for (int k = 0; k < i; ++k) btab[(int64_t)k * nrhs + c] = mkc((double)coef[k].x, (double)coef[k].y);
+#pragma unroll
+    for (int k = 0; k < I; ++k) btab[(int64_t)k * nrhs + c] = mkc((double)coef[k].x, (double)coef[k].y);
   float nn = 0.f;
   float2 nr = make_float2(0.f, 0.f);
   float2* Qi = Q + (int64_t)i * qs;
@@ -220,8 +223,7 @@ __global__ void k_orth_f32(int i, int64_t n, int nrhs, float2* __restrict__ Q, i
       const int64_t e = row * nrhs + c;
       float2 q = Qi[e];
 #pragma unroll
-      for (int k = 0; k < kMaxMdot; ++k)
-        if (k < i) cfma(q, make_float2(-coef[k].x, -coef[k].y), Q[k * qs + e]);
+      for (int k = 0; k < I; ++k) cfma(q, make_float2(-coef[k].x, -coef[k].y), Q[k * qs + e]);
       Qi[e] = q;
       nn += cnorm2(q);
       cfmac(nr, q, r[e]);
@@ -290,6 +292,31 @@ __global__ void k_backsub(int m, int nrhs, const cplx* __restrict__ atab, const 
       cfma(v, cscale(-1.0, btab[((int64_t)i * kMaxMdot + k) * nrhs + c]), d[i]);
     d[k] = v;
     coef[(int64_t)k * nrhs + c] = mkc(-v.x, -v.y);
+  }
+}
+
+// Launch k_mdot_f32<K> / k_orth_f32<I> for a run-time count (1..16 / 0..15).
+template <int K>
+static void launch_mdot(int k, dim3 g, dim3 b, cudaStream_t st, int64_t n, int nrhs, const float2* Q, int64_t qs,
+                        const float2* y, cplx* partials) {
+  if constexpr (K <= kMaxMdot) {
+    if (k == K) {
+      k_mdot_f32<K><<<g, b, 0, st>>>(n, nrhs, Q, qs, y, partials);
+      return;
+    }
+    launch_mdot<K + 1>(k, g, b, st, n, nrhs, Q, qs, y, partials);
+  }
+}
+template <int I>
+static void launch_orth(int i, dim3 g, dim3 b, cudaStream_t st, int64_t n, int nrhs, float2* Q, int64_t qs,
+                        const float2* r, const cplx* braw, const cplx* ngtab, const int* active, cplx* btab,
+                        cplx* partials) {
+  if constexpr (I < kMaxMdot) {
+    if (i == I) {
+      k_orth_f32<I><<<g, b, 0, st>>>(n, nrhs, Q, qs, r, braw, ngtab, active, btab, partials);
+      return;
+    }
+    launch_orth<I + 1>(i, g, b, st, n, nrhs, Q, qs, r, braw, ngtab, active, btab, partials);
   }
 }
 
@@ -391,8 +418,8 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
         if (i > 0) {
           {
             ProfScope ps(ctx, QD_PROF_DOTS_F32, 8.0 * i * n * nrhs, 8.0 * (i + 1.0) * n * nrhs);
-            k_mdot_f32<<<sw.grid, sw.block, 0, ctx.stream>>>(i, n, nrhs, Qf, tot, Qf + i * tot,
-                                                              ctx.red_partials.as<cplx>());
+            launch_mdot<1>(i, sw.grid, sw.block, ctx.stream, n, nrhs, Qf, tot, Qf + i * tot,
+                           ctx.red_partials.as<cplx>());
             QD_LAUNCH_CHECK();
           }
           blas::k_dots_final<<<div_up(i * nrhs, 8), 256, 0, ctx.stream>>>(i, nrhs, sw.grid.x, ctx.red_partials.as<cplx>(),
@@ -401,9 +428,8 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
         }
         {
           ProfScope ps(ctx, QD_PROF_AXPY_F32, 8.0 * (i + 2.0) * n * nrhs, 8.0 * (i + 3.0) * n * nrhs);
-          k_orth_f32<<<sw.grid, sw.block, 0, ctx.stream>>>(i, n, nrhs, Qf, tot, rf, braw, ngtab, act,
-                                                            btab + (int64_t)i * kMaxMdot * nrhs,
-                                                            ctx.red_partials.as<cplx>());
+          launch_orth<0>(i, sw.grid, sw.block, ctx.stream, n, nrhs, Qf, tot, rf, braw, ngtab, act,
+                         btab + (int64_t)i * kMaxMdot * nrhs, ctx.red_partials.as<cplx>());
           QD_LAUNCH_CHECK();
         }
         blas::k_dots_final<<<div_up(2 * nrhs, 8), 256, 0, ctx.stream>>>(2, nrhs, sw.grid.x, ctx.red_partials.as<cplx>(),

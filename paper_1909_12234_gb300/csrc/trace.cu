@@ -3,6 +3,7 @@
 // and 2: t0 + (1/s) sum_j z_j^H A^{-1}_xi (I - P) z_j).
 #include "blas.cuh"
 #include "coarse_tc.cuh"
+#include "restrict_tc.cuh"
 #include "defl.cuh"
 #include "tc_gemm.cuh"
 
@@ -106,12 +107,18 @@ static void solve_mixed(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, do
     const int e = tc_error(ctx, *mg->L.back());
     if (e) fail(QD_ERR_TIMEOUT, "tensor-core coarsest solve: bounded wait timed out (code " + std::to_string(e) + ")");
   }
-  if (mg)
+  if (mg) {
     for (auto& lv : mg->L)
       if (lv->use_tc) {
         const int e = coarse_tc_error(ctx, *lv);
         if (e) fail(QD_ERR_TIMEOUT, "tensor-core coarse stencil: bounded wait timed out (code " + std::to_string(e) + ")");
       }
+    for (auto& t : mg->T)
+      if (t->use_tc) {
+        const int e = restrict_tc_error(ctx, *t);
+        if (e) fail(QD_ERR_TIMEOUT, "tensor-core restriction: bounded wait timed out (code " + std::to_string(e) + ")");
+      }
+  }
   std::vector<cplx> hb(s), hr(s);
   QD_CUDA(cudaMemcpyAsync(hb.data(), bn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
   QD_CUDA(cudaMemcpyAsync(hr.data(), rn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));

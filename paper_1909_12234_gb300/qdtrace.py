@@ -157,6 +157,7 @@ SIGNATURES = {
     "qd_coarse_apply": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_apply_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_apply_tc": (_I, [_P, _I, _I, _P, _P]),
+    "qd_restrict_tc": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_solver_params_default": (None, [ctypes.POINTER(SolverParams)]),
@@ -193,7 +194,7 @@ SIGNATURES = {
 PROF_KINDS = {"wilson_f64": 0, "wilson_f32": 1, "coarse_f64": 2, "coarse_f32": 3, "prolong_f64": 4,
               "prolong_f32": 5, "restrict_f64": 6, "restrict_f32": 7, "direct_f64": 8, "direct_f32": 9, "direct_bf16": 10,
               "blas_f64": 11, "dots_f32": 12, "axpy_f32": 13, "update_f32": 14, "smoother_f64": 15,
-              "smoother_f32": 16, "coarse_tc": 17}
+              "smoother_f32": 16, "coarse_tc": 17, "restrict_tc": 18}
 
 _lib = None
 
@@ -425,6 +426,10 @@ def coarse_apply_f32(mg, level, nrhs, inp, out):
 
 def coarse_apply_tc(mg, level, nrhs, inp, out):
     _check(load().qd_coarse_apply_tc(mg.h, int(level), int(nrhs), _ptr64(inp), _ptr64(out)))
+
+
+def restrict_tc(mg, level, nrhs, fine, coarse):
+    _check(load().qd_restrict_tc(mg.h, int(level), int(nrhs), _ptr64(fine), _ptr64(coarse)))
 
 
 def coarse_solve_f32(mg, level, nrhs, inp, out):

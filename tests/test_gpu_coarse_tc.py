@@ -170,3 +170,48 @@ def test_mixed_solve_with_tensor_core_coarse_stencil(qd, ctx):
     # comparable iteration counts
     assert out[1] <= 1.2 * out[0] + 2, out
     g.close()
+
+
+@pytest.mark.parametrize("dims,m0,blocks,nvs", CASES)
+def test_tensor_core_restriction(qd, ctx, dims, m0, blocks, nvs):
+    # coarse = W^H fine with split-BF16 operands against the oracle's
+    # restriction; bound as above with S = P(W)^T P(fine) (the sum of
+    # magnitudes of the products of one output) and 2 x (sites per
+    # aggregate) x (2 Df / 16) MMA steps
+    U = synth.random_su3_links(dims, 0.3, 2)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(len(blocks), blocks, nvs, null_maxit=0, seed=5))
+    H = omg.setup(U, m0, dims, blocks, nvs, seed=5, null_maxit=0)
+    rng = np.random.default_rng(8)
+    u = U_BF16
+    for l, T in enumerate(H.transfers):
+        Df, Dc, n, nc = T.level.dof, 2 * T.nv, T.level.n, T.nc
+        supported = Df in (12, 16, 24, 32) and Dc in (16, 24, 32)
+        PW = sp.csr_matrix(_abs_parts(T.matrix()))
+        steps = 2 * int(np.prod(T.block)) * ((2 * Df + 15) // 16)
+        for s in (1, 3, 64, 128, 130):
+            f = (rng.standard_normal((n, s)) + 1j * rng.standard_normal((n, s))).astype(np.complex64)
+            if l == 0:
+                fd = qd.to_qd(ctx, g, f.astype(np.complex128).reshape(g.V, 4, 3, s)).to(torch.complex64)
+            else:
+                fd = torch.from_numpy(np.ascontiguousarray(f)).to("cuda:0")
+            out = torch.full((nc, s), float("nan"), dtype=torch.complex64, device="cuda:0")
+            if not supported:
+                with pytest.raises(qd.QDError) as ei:
+                    qd.restrict_tc(mg, l, s, fd, out)
+                assert ei.value.code == qd.QD_ERR_INVALID
+                break
+            qd.restrict_tc(mg, l, s, fd, out)
+            got = host(out).astype(np.complex128)
+            f64 = f.astype(np.complex128)
+            ref = T.restrict(f64)
+            S = PW.T @ _abs_parts(f64)
+            tol = (3 * u ** 2 + 3 * u ** 3 + 2.0 ** -23 + (steps + 1) * 2.0 ** -22) * S
+            err_re, err_im = np.abs(got.real - ref.real), np.abs(got.imag - ref.imag)
+            assert np.all(err_re <= tol) and np.all(err_im <= tol), (l, s, float(max((err_re / tol).max(),
+                                                                                   (err_im / tol).max())))
+            out2 = torch.empty_like(out)
+            qd.restrict_tc(mg, l, s, fd, out2)
+            assert torch.equal(out, out2)
+    for o in (mg, g):
+        o.close()

@@ -893,6 +893,99 @@ def run_batch(args):
     return 0
 
 
+# Algorithm 1 against Algorithm 2 on the 8^4 lattice (Sec. 2.2, Sec. 4.1):
+# the a-posteriori variance of the deflated estimator as a function of the
+# rank, from one set of undeflated solves, with jackknife errors, and the
+# sines of the angles between the Algorithm 1 vectors and range(W) (Fig. 3).
+DEFL_CMP = dict(
+    workload="deflation comparison: wilson-dirac 8^4 eps0.3 seed2 m0=-0.8, 2-level MG (2^4, nv 12); Algorithm 1 "
+             "(24 smallest eigenvectors of A gamma5, GPU eigensolver with MG solves) vs Algorithm 2 (24 coarse "
+             "eigenvectors); a-posteriori variance vs rank from 64 undeflated samples solved to 1e-8",
+    dims=(8, 8, 8, 8), eps=0.3, link_seed=2, m0=-0.8, blocks=[(2, 2, 2, 2)], nvs=[12], k=24, guard=16, s=64,
+    tol=1e-8, noise_seed=102, ranks=[0, 2, 4, 8, 12, 16, 20, 24],
+)
+
+
+def run_deflation_compare(args):
+    import torch
+    from paper_1909_12234_gb300 import qdtrace as qd
+    from paper_1909_12234_gb300 import synth
+    C = DEFL_CMP
+    qd.load()
+    ctx = qd.Context(0)
+    U = synth.random_su3_links(C["dims"], C["eps"], C["link_seed"])
+    g = qd.Gauge(ctx, C["dims"], U)
+    mg = qd.Multigrid(ctx, g, C["m0"], 0.0, qd.mg_params(1, C["blocks"], C["nvs"]))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    d2 = qd.Deflation(ctx, g, mg, C["m0"], 0.0, qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, C["k"], guard=C["guard"],
+                                                               eig_tol=1e-6, solve_tol=1e-10, maxit=60))
+    torch.cuda.synchronize()
+    t_alg2 = time.perf_counter() - t
+    t = time.perf_counter()
+    d1 = qd.Deflation(ctx, g, mg, C["m0"], 0.0, qd.defl_params(qd.QD_DEFL_EIG_ORTHO, C["k"], guard=C["guard"],
+                                                               eig_tol=1e-6, solve_tol=1e-10, maxit=60))
+    torch.cuda.synchronize()
+    t_alg1 = time.perf_counter() - t
+    s, k = C["s"], C["k"]
+    res0 = qd.hutchinson_trace(ctx, g, mg, None, C["m0"], 0.0, seed=C["noise_seed"], sample_offset=0, nsamples=s,
+                               tol=C["tol"], maxit=500, precision=qd.QD_PREC_MIXED, inner_tol=1e-5, max_refine=10)
+    z = torch.empty((g.V, 12, s), dtype=torch.complex128, device="cuda:0")
+    qd.rademacher(ctx, g, C["noise_seed"], 0, s, z)
+    zhv1, uhz1 = d1.coeffs(s, z)
+    zhv2, uhkz2 = d2.coeffs(s, z)
+    G = d2.gram()
+    rows = []
+    for r in C["ranks"]:
+        row = {"rank": r}
+        for name, d in (("alg1", d1), ("alg2", d2)):
+            if r == 0:
+                tr, t0 = res0["t"], 0j
+            else:
+                t0 = d.set_rank(r)
+                if name == "alg1":
+                    corr = np.einsum("ji,ij->j", zhv1[:, :r], uhz1[:r])
+                else:
+                    corr = np.einsum("ji,ij->j", zhv2[:, :r], np.linalg.solve(G[:r, :r], uhkz2[:r]))
+                tr = res0["t"] - corr
+            st = qd.trace_stats(ctx, tr, t0)
+            row[name] = {"estimate": st["estimate"].real, "stderr": st["stderr"], "var": st["var"],
+                         "var_jackknife_err": st["var_jackknife_err"], "t0": t0.real}
+        rows.append(row)
+    # check the a-posteriori values against real deflated runs at full rank
+    check = {}
+    for name, d in (("alg1", d1), ("alg2", d2)):
+        d.set_rank(k)
+        rr = qd.hutchinson_trace(ctx, g, mg, d, C["m0"], 0.0, seed=C["noise_seed"], sample_offset=0, nsamples=s,
+                                 tol=C["tol"], maxit=500, precision=qd.QD_PREC_MIXED, inner_tol=1e-5, max_refine=10)
+        if name == "alg1":
+            post = res0["t"] - np.einsum("ji,ij->j", zhv1, uhz1)
+        else:
+            post = res0["t"] - np.einsum("ji,ij->j", zhv2, np.linalg.solve(G, uhkz2))
+        check[name] = {"max_abs_diff_posteriori_vs_run": float(np.abs(post - rr["t"]).max()),
+                       "max_abs_t": float(np.abs(rr["t"]).max()), "var_run": rr["var"]}
+    # Fig. 3 (right): sin of the angle between each Algorithm 1 vector and range(W)
+    V = torch.empty((g.V, 12, k), dtype=torch.complex128, device="cuda:0")
+    d1.basis(V)
+    sines = qd.mg_subspace_sines(mg, 1, V)
+    mu1, _, its1 = d1.info()
+    mu2, _, its2 = d2.info()
+    tau, nrs = d1.shift_info()
+    line = {"analysis": "deflation rank sweep (Algorithm 1 vs Algorithm 2)", "workload": C["workload"],
+            "build_s": {"alg1": round(t_alg1, 3), "alg2": round(t_alg2, 3)},
+            "eigensolver": {"alg1_iterations": its1, "alg2_iterations": its2, "alg1_shift": tau,
+                            "alg1_restarts": nrs, "alg1_mu": [round(float(x), 6) for x in mu1],
+                            "alg2_mu": [round(float(x), 6) for x in mu2]},
+            "undeflated": {"estimate": res0["estimate"].real, "var": res0["var"],
+                           "var_jackknife_err": res0["var_jackknife_err"]},
+            "rank_sweep": rows, "check_full_rank": check,
+            "sin_angle_alg1_vectors_to_W": [round(float(x), 5) for x in sines]}
+    print(json.dumps(line))
+    for o in (d1, d2, mg, g, ctx):
+        o.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -905,7 +998,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-errors", action="store_true", help="skip the errors-against-the-oracle leg")
     ap.add_argument("--prof-steps", type=int, default=2)
-    ap.add_argument("--workload", default="config3", choices=sorted(WORKLOADS) + ["config4", "config5"])
+    ap.add_argument("--workload", default="config3",
+                    choices=sorted(WORKLOADS) + ["config4", "config5", "deflation"])
     ap.add_argument("--stencil-only", action="store_true",
                     help="only the Wilson stencil alone on 16^3 x 32 (a profiling target)")
     ap.add_argument("--small", action="store_true",
@@ -926,10 +1020,12 @@ def main():
         print(json.dumps({"stencil": stencil_roofline(qd, ctx)}))
         ctx.close()
         return 0
-    if args.workload in ("config4", "config5"):
+    if args.workload in ("config4", "config5", "deflation"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-lattice workload"}))
             return 0
+        if args.workload == "deflation":
+            return run_deflation_compare(args)
         return run_batch(args) if args.workload == "config4" else run_learned(args)
     WL.clear()
     WL.update(WORKLOADS[args.workload])

@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define QD_ABI_VERSION 2
+#define QD_ABI_VERSION 3
 #define QD_MAX_LEVELS 4 /* fine level + up to 3 coarse levels */
 
 typedef enum {
@@ -310,6 +310,12 @@ typedef struct {
   int precision;     /* QD_PREC_* */
   double inner_tol;  /* QD_PREC_MIXED: relative tolerance of each FP32 solve */
   int max_refine;    /* QD_PREC_MIXED: cap on refinement steps */
+  int stag_window;   /* > 0: stagnation test (Sec. 3.2, the inverter that
+                        "stagnates at an error level well above xi"): every
+                        stag_window iterations, a column whose residual fell
+                        by less than 10 % since the previous check stops the
+                        solve with QD_ERR_NOT_CONVERGED and
+                        qd_solve_stats.stagnated = 1; 0: off */
 } qd_solver_params;
 
 void qd_solver_params_default(qd_solver_params* p);
@@ -320,6 +326,7 @@ typedef struct {
   double max_true_rel_residual;  /* max over columns of ||b-Ax||/||b|| */
   int* iters_per_rhs;            /* optional host [nrhs] */
   double* true_rel_residual;     /* optional host [nrhs] */
+  int stagnated;                 /* 1: stopped by the stagnation test */
 } qd_solve_stats;
 
 /* Solve A(m0, tau) x = b for nrhs columns.  QD_PREC_F64: flexible
@@ -351,6 +358,23 @@ typedef struct {
   double solve_tol;  /* xi of the inner solves H^{-1} */
   int maxit;         /* subspace iterations cap */
   uint64_t seed;     /* starting block: Philox random starts, this key */
+  /* Sec. 3.2, eigensolver tuning (kind 1, whose eigensolver runs inexact
+   * multigrid solves with the fine operator): when an inner solve
+   * stagnates (stag_window iterations without a 10 % residual drop) or
+   * fails to converge, the multigrid inverter is rebuilt for the shifted
+   * operator A + i tau_eig gamma5 and the eigensolver restarts, with
+   * tau_eig = tau_restart at the first restart and 4x larger at each next
+   * one, at most max_restarts times.  (A gamma5 + i tau)^{-1} has the
+   * eigenvectors of A gamma5, so the space deflates the unshifted A; the
+   * Rayleigh-Ritz step then works on the Hermitian Y^H Y of
+   * Y = (A gamma5 + i tau)^{-1} X (eigenvalues 1/(lambda^2 + tau^2)), and
+   * lambda = Re 1/mu from the Rayleigh quotient mu of Y. */
+  double tau_restart;  /* first shift (0.1) */
+  int max_restarts;    /* (3) */
+  int stag_window;     /* inner-solve stagnation window (100); 0: off */
+  int solve_restart;   /* restart length of the inner GCR (32) */
+  int fail_first;      /* test hook: report the first fail_first attempts
+                          as stagnated without solving (0) */
 } qd_defl_params;
 
 void qd_defl_params_default(qd_defl_params* p);
@@ -375,6 +399,20 @@ int qd_defl_set_rank(qd_defl* defl, int rank, double* t0);
  * the active rank (rank, nullable), iterations taken (nullable). */
 int qd_defl_info(const qd_defl* defl, double* mu, double* lambda,
                  int* iterations);
+
+/* The eigensolver's shift after its restarts (0 without one) and the number
+ * of restarts it took (Sec. 3.2; qd_defl_params.tau_restart). */
+int qd_defl_shift_info(const qd_defl* defl, double* tau_eig, int* restarts);
+
+/* Kind 2: G = U_bar^H gamma5^W C U_bar (host, k x k complex, row major),
+ * the matrix whose leading r x r block gives the rank-r correction of
+ * qd_deflate_coeffs (Sec. 2.2).  QD_ERR_INVALID for kind 1 (G = I). */
+int qd_defl_gram(const qd_defl* defl, double* G);
+
+/* Copy the k basis vectors (kind 1: U on the fine level; kind 2: U_bar on
+ * the coarsest level), qd layout with nrhs = k, to the caller's device
+ * buffer `out`.  Asynchronous. */
+int qd_defl_basis(const qd_defl* defl, double* out);
 
 /* ------------------------------------------------------------------------ */
 /* a8: deflation projection (Algorithm 1 step 3, Algorithm 2 step 5,         */
@@ -417,11 +455,26 @@ int qd_deflate_project(qd_defl* defl, int nrhs, const double* z, double* out);
 int qd_deflate_project_static(qd_defl* defl, int nrhs, const double* z,
                               double* out);
 
-/* Sec. 2.2 matrices for an a-posteriori rank sweep (kind 2 only), host
- * outputs, row-major complex: ZhV [nrhs][k] = Z^H W U_bar and
- * UhKZ [k][nrhs] = U_bar^H gamma5^W W^H Z.  Synchronous. */
+/* Sec. 2.2 matrices for an a-posteriori rank sweep, host outputs,
+ * row-major complex, over all k columns of the space:
+ *   kind 2: ZhV [nrhs][k] = Z^H W U_bar, UhKZ [k][nrhs] = U_bar^H gamma5^W
+ *           W^H Z; the rank-r correction of sample j is
+ *           ZhV[j][:r] G_r^{-1} UhKZ[:r][j], G = U_bar^H gamma5^W C U_bar;
+ *   kind 1: ZhV [nrhs][k] = Z^H A^{-1}_xi U (the solves of Algorithm 1,
+ *           step 2), UhKZ [k][nrhs] = U^H Z (K = I); the rank-r correction
+ *           is sum_{i<r} ZhV[j][i] UhKZ[i][j].
+ * With qd_defl_set_rank's t0 at rank r, t0 + mean_j (t_j - correction_j)
+ * is the rank-r estimate from undeflated t_j = z_j^H A^{-1}_xi z_j.
+ * Synchronous. */
 int qd_deflate_coeffs(qd_defl* defl, int nrhs, const double* z, double* ZhV,
                       double* UhKZ);
+
+/* Sec. 4.1 (Fig. 3, right): sin of the angle between each of the k columns
+ * v_i of V (fine level, qd layout, device, k columns) and the range of the
+ * composite prolongator W = W_0 ... W_{depth-1} (orthonormal):
+ * sin_out[i] = ||v_i - W W^H v_i|| / ||v_i|| (host array of k doubles).
+ * depth in [1, nlevels].  Synchronous. */
+int qd_mg_subspace_sines(qd_mg* mg, int depth, int k, const double* V, double* sin_out);
 
 /* ------------------------------------------------------------------------ */
 /* a9: deflated Hutchinson estimator (Eq. 1; Algorithms 1 and 2)             */
@@ -432,6 +485,13 @@ typedef struct {
   int64_t sample_offset;  /* first global sample index */
   int nsamples;           /* s, solved together as one multi-RHS batch */
   qd_solver_params solver;/* xi = solver.tol and the solve's settings */
+  int dilution;           /* 0: none (H = I); 12: spin-colour dilution, the
+                             probing basis H of Algorithms 1 and 2 with its 12
+                             spin-colour vectors: every sample z_j becomes the
+                             12 vectors z_jh (entries of z_j with 3 spin +
+                             colour = h) and t_j = sum_h z_jh^H A^{-1}_xi
+                             (I - P) z_jh, 12 s right-hand sides solved
+                             together */
 } qd_trace_params;
 
 typedef struct {
@@ -452,8 +512,10 @@ typedef struct {
 
 /* One batch of the deflated estimator: z_j = Rademacher(seed, offset + j),
  * b_j = (I - P) z_j (defl nullable: P = 0), x_j = A^{-1}_xi b_j by qd_solve
- * with mg (nullable), t_j = z_j^H x_j; statistics accumulated on the device
- * with compensated FP64 sums in a fixed order.  Synchronous.  Returns
+ * with mg (nullable), t_j = z_j^H x_j (with dilution: the sum over the 12
+ * spin-colour parts of z_j); statistics accumulated on the device with
+ * compensated FP64 sums in a fixed order.  ZhV / UhKZ (kind 1 or 2) are not
+ * available with dilution (QD_ERR_INVALID).  Synchronous.  Returns
  * QD_ERR_NOT_CONVERGED (result filled) if any solve missed tol. */
 int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg,
                         qd_defl* defl, double m0, double tau,

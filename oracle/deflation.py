@@ -149,17 +149,38 @@ class Alg1:
     def __init__(self, U, A_matvec, xi, restart=16, precond=None, maxit=100000):
         self.U = np.asarray(U, dtype=np.complex128)
         self.k = self.U.shape[1]
-        # step 2: t0 = sum_i u_i^H A^{-1}_xi u_i
-        t0 = 0.0
+        # step 2: t0 = sum_i u_i^H A^{-1}_xi u_i, keeping Y = A^{-1}_xi U
+        self.Y = np.empty_like(self.U)
         for i in range(self.k):
-            y, _, _ = krylov.gcr(A_matvec, self.U[:, i], xi, maxit=maxit,
-                                 restart=restart, precond=precond)
-            t0 += np.vdot(self.U[:, i], y)
-        self.t0 = complex(t0)
+            self.Y[:, i], _, _ = krylov.gcr(A_matvec, self.U[:, i], xi, maxit=maxit,
+                                            restart=restart, precond=precond)
+        self.d = np.einsum("ni,ni->i", self.U.conj(), self.Y)
+        self.t0 = complex(np.sum(self.d))
 
     def project(self, z):
         """(I - U U^H) z."""
         return z - self.U @ (self.U.conj().T @ z)
+
+    def coeffs(self, z):
+        """(z_j^H A^{-1}_xi u_i (s x k), u_i^H z_j (k x s)): with them the
+        deflated value of a rank-r space is, for every sample,
+        z^H A^{-1}(I - U_r U_r^H) z = z^H A^{-1} z - sum_{i<r} (z^H A^{-1} u_i)(u_i^H z)."""
+        return (z.conj().T @ self.Y), (self.U.conj().T @ z)
+
+    def correction(self, ZhAU, UhZ, r):
+        return np.einsum("ji,ij->j", ZhAU[:, :r], UhZ[:r])
+
+    def t0_rank(self, r):
+        return complex(np.sum(self.d[:r]))
+
+
+def subspace_sines(T, V):
+    """sin of the angle between each column v of V and the range of the
+    (orthonormal) prolongator W of T (a Transfer or a Composite):
+    ||v - W W^H v|| / ||v|| (Sec. 4.1, Fig. 3 right)."""
+    V = np.asarray(V, dtype=np.complex128)
+    R = V - T.prolong(T.restrict(V))
+    return np.linalg.norm(R, axis=0) / np.linalg.norm(V, axis=0)
 
 
 def fine_eigvecs_dense(A, g5, k):

@@ -74,3 +74,31 @@ def brute_force_variances(B):
     ts = np.asarray(ts)
     mean = ts.mean()
     return mean, float(np.mean(np.abs(ts - mean) ** 2)), float(np.var(ts.real))
+
+
+def exact_variance_real_rademacher_diluted(B, classes, s=1):
+    """E|t - tr B|^2 of the diluted estimator t = sum_h z_h^T B z_h, where z is
+    real +-1 noise and z_h keeps the entries of class h (spin-colour
+    dilution: class = dof mod 12).  Only products z_i z_j of one class
+    survive, so the variance is sum_{i<j, same class} |B_ij + B_ji|^2."""
+    c = np.asarray(classes)
+    M = c[:, None] == c[None, :]
+    S = 0.5 * (B + B.T)
+    return (2.0 / s) * (np.sum(np.abs(S[M]) ** 2) - np.sum(np.abs(np.diag(S)) ** 2))
+
+
+def brute_force_diluted_variance(B, classes):
+    """Enumerate all sign vectors: E|t - mean|^2 of t = sum_h z_h^T B z_h."""
+    n = B.shape[0]
+    c = np.asarray(classes)
+    ts = []
+    for signs in itertools.product((1.0, -1.0), repeat=n):
+        z = np.asarray(signs)
+        t = 0.0
+        for h in np.unique(c):
+            zh = np.where(c == h, z, 0.0)
+            t = t + zh @ B @ zh
+        ts.append(t)
+    ts = np.asarray(ts)
+    return float(np.mean(np.abs(ts - ts.mean()) ** 2))
+

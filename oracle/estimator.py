@@ -72,21 +72,38 @@ def statistics(t, t0=0.0):
     }
 
 
+def dilute(z, nclass=12):
+    """Spin-colour dilution (the probing basis H of Algorithms 1 and 2 with
+    its 12 spin-colour vectors): z_h keeps the entries of z whose dof
+    (12 lex + 3 spin + colour) is h modulo 12.  Returns (n, nclass)."""
+    z = np.asarray(z)
+    cls = np.arange(z.shape[0]) % nclass
+    return np.stack([np.where(cls == h, z, 0) for h in range(nclass)], axis=1)
+
+
 def hutchinson(A_matvec, ndof, seed, samples, xi, project=None, t0=0.0,
-               precond=None, restart=16, maxit=100000):
+               precond=None, restart=16, maxit=100000, dilution=False):
     """Per-sample t_j = z_j^H A^{-1}_xi (project(z_j)) and their statistics.
 
-    ``project`` is (I - P) of Algorithm 1 or 2, or None (plain Eq. 1).
+    ``project`` is (I - P) of Algorithm 1 or 2, or None (plain Eq. 1).  With
+    ``dilution`` every sample is t_j = sum_h z_jh^H A^{-1}_xi project(z_jh)
+    over the 12 spin-colour parts z_jh of z_j (t(... odot H H^H) of
+    Algorithms 1 and 2 with H the spin-colour basis).
     Returns (t (s,), stats dict, per-sample (iterations, true rel residual)).
     """
     Z = philox.rademacher(ndof, seed, samples)
     ts, info = [], []
     for j in range(Z.shape[1]):
         z = Z[:, j].astype(np.complex128)
-        b = z if project is None else project(z)
-        x, its, rel = krylov.gcr(A_matvec, b, xi, maxit=maxit, restart=restart,
-                                 precond=precond)
-        ts.append(np.vdot(z, x))
-        info.append((its, rel))
+        parts = dilute(z).T if dilution else [z]
+        tj, its_j, rel_j = 0j, 0, 0.0
+        for zh in parts:
+            b = zh if project is None else project(zh)
+            x, its, rel = krylov.gcr(A_matvec, b, xi, maxit=maxit, restart=restart,
+                                     precond=precond)
+            tj += np.vdot(zh, x)
+            its_j, rel_j = max(its_j, its), max(rel_j, rel)
+        ts.append(tj)
+        info.append((its_j, rel_j))
     t = np.asarray(ts)
     return t, statistics(t, t0), info

@@ -429,6 +429,7 @@ int qd_solve(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, double m0, double ta
         for (int c = 0; c < nrhs; ++c) stats->iters_per_rhs[c] = info.iters[c];
       if (stats->true_rel_residual)
         for (int c = 0; c < nrhs; ++c) stats->true_rel_residual[c] = info.true_rel[c];
+      stats->stagnated = info.stagnated ? 1 : 0;
     }
     not_conv = info.converged < nrhs;
   });
@@ -449,6 +450,11 @@ void qd_defl_params_default(qd_defl_params* p) {
   p->solve_tol = 1e-10;
   p->maxit = 50;
   p->seed = 12345;
+  p->tau_restart = 0.1;
+  p->max_restarts = 3;
+  p->stag_window = 100;
+  p->solve_restart = 32;
+  p->fail_first = 0;
 }
 
 int qd_defl_create(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, double m0, double tau, const qd_defl_params* params,
@@ -502,6 +508,35 @@ int qd_defl_info(const qd_defl* defl, double* mu, double* lambda, int* iteration
       QD_CUDA(cudaMemcpy(lambda, defl->lam.as<double>(), defl->rank * sizeof(double), cudaMemcpyDeviceToHost));
     }
     if (iterations) *iterations = defl->iterations;
+  });
+}
+
+int qd_defl_shift_info(const qd_defl* defl, double* tau_eig, int* restarts) {
+  return guarded([&] {
+    NONNULL(defl);
+    if (tau_eig) *tau_eig = defl->tau_eig;
+    if (restarts) *restarts = defl->restarts;
+  });
+}
+
+int qd_defl_gram(const qd_defl* defl, double* G) {
+  return guarded([&] {
+    NONNULL(defl);
+    NONNULL(G);
+    QD_REQUIRE(defl->kind == QD_DEFL_MG_OBLIQUE, "the Gram matrix G is defined for Algorithm 2 (Algorithm 1: G = I)");
+    set_device(defl->ctx);
+    const int k = defl->p.k;
+    QD_CUDA(cudaMemcpy(G, defl->G.as<qd::cplx>(), (size_t)k * k * sizeof(qd::cplx), cudaMemcpyDeviceToHost));
+  });
+}
+
+int qd_defl_basis(const qd_defl* defl, double* out) {
+  return guarded([&] {
+    NONNULL(defl);
+    NONNULL(out);
+    set_device(defl->ctx);
+    QD_CUDA(cudaMemcpyAsync(out, defl->Ubar.as<qd::cplx>(), (size_t)defl->nb * defl->p.k * sizeof(qd::cplx),
+                            cudaMemcpyDeviceToDevice, defl->ctx->stream));
   });
 }
 
@@ -562,6 +597,18 @@ int qd_deflate_coeffs(qd_defl* defl, int nrhs, const double* z, double* ZhV, dou
   });
 }
 
+int qd_mg_subspace_sines(qd_mg* mg, int depth, int k, const double* V, double* sin_out) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(V);
+    NONNULL(sin_out);
+    QD_REQUIRE(depth >= 1 && depth <= mg->nlevels, "depth must be in [1, nlevels]");
+    QD_REQUIRE(k >= 1, "k must be >= 1");
+    set_device(mg->ctx);
+    qd::mg_subspace_sines(*mg->ctx, *mg, depth, k, reinterpret_cast<const qd::cplx*>(V), sin_out);
+  });
+}
+
 // Host outputs of one estimator call (shared by the single and batched forms).
 static void fill_trace_result(qd_trace_result* result, const qd_defl* defl, const qd::TraceOut& out,
                               const std::vector<qd::cplx>& M1, const std::vector<qd::cplx>& M2, int s, bool coeffs) {
@@ -606,10 +653,12 @@ static bool run_trace(qd_ctx& ctx, const qd_gauge& gauge, qd_mg* mg, qd_defl* de
   QD_REQUIRE(params.nsamples >= 1, "nsamples must be >= 1");
   qd::TraceOut out;
   std::vector<qd::cplx> M1, M2;
-  const bool coeffs = defl && defl->kind == QD_DEFL_MG_OBLIQUE && (result->ZhV || result->UhKZ);
+  const bool coeffs = defl && (result->ZhV || result->UhKZ);
+  QD_REQUIRE(!(coeffs && params.dilution), "a-posteriori coefficients are not available with dilution");
+  QD_REQUIRE(params.dilution == 0 || params.dilution == 12, "dilution must be 0 or 12");
   qd::hutchinson(ctx, gauge, mg, defl, m0, tau, params, coeffs, out, &M1, &M2);
   fill_trace_result(result, defl, out, M1, M2, params.nsamples, coeffs);
-  return out.info.converged >= params.nsamples;
+  return out.info.converged >= (params.dilution == 12 ? 12 : 1) * params.nsamples;
 }
 
 int qd_hutchinson_trace(qd_ctx* ctx, const qd_gauge* gauge, qd_mg* mg, qd_defl* defl, double m0, double tau,

@@ -35,6 +35,9 @@ struct qd_defl {
   qd::DevBuf lam;        // rank doubles (Algorithm 2)
   qd::DevBuf t0buf;      // one complex on device
   double t0[2] = {0.0, 0.0};
+  double tau_eig = 0.0;  // eigensolver shift after restarts (Sec. 3.2)
+  int restarts = 0;
+  std::unique_ptr<qd_mg> mg_shift;  // multigrid inverter of A + i tau_eig gamma5
   qd::cplx* t0_dev() {
     t0buf.resize(sizeof(qd::cplx));
     return t0buf.as<qd::cplx>();
@@ -57,6 +60,8 @@ void copy_leading_block(qd_ctx& ctx, int k, int r, const cplx* G, cplx* Gr);
 void sum_over_lambda(qd_ctx& ctx, int r, const cplx* dv, const double* lam, cplx* out);
 void trace_stats(qd_ctx& ctx, int s, const cplx* t, double* out_dev, double* loo_dev);
 void mg_build(qd_mg& mg, const double* injected_null);
+// sin of the angle between each of the k columns of V and range(W_0 ... W_{L-1})
+void mg_subspace_sines(qd_ctx& ctx, qd_mg& mg, int L, int k, const cplx* V, double* out);
 
 // Drivers (trace.cu).
 void solve(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, double tau, int s, const cplx* b, cplx* x,

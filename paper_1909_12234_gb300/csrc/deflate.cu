@@ -61,18 +61,25 @@ __global__ void k_reciprocal(int m, const double* __restrict__ in, double* __res
 // extra solve:
 //   Y = H^{-1} X;  T = X^H Y = S diag(nu) S^H;  order by |1/nu| ascending;
 //   residual_i = ||Y s_i - nu_i X s_i|| / |nu_i|;  X <- orth(Y S).
-// X (n x m, ld m) out: Ritz vectors; theta (host, m) out: 1/nu.
+// With a shift (Op = A + i tau gamma5, tau = tau_s != 0) H is the normal
+// A gamma5 + i tau; then T = Y^H Y = X^H (H_h^2 + tau^2)^{-1} X is the
+// Hermitian matrix used (H_h = A gamma5, same eigenvectors, eigenvalues
+// 1/(lambda^2 + tau^2) largest for the smallest |lambda|), mu_i = x_i^H Y s_i
+// is the complex Rayleigh quotient, residual_i = ||Y s_i - mu_i x_i|| / |mu_i|
+// and lambda_i = Re 1/mu_i.
+// X (n x m, ld m) out: Ritz vectors; theta (host, m) out: eigenvalues of H_h.
 // `solve(X, W, m)` must return W ~= Op^{-1} X for m columns.
 typedef std::function<void(const cplx*, cplx*, int)> SolveFn;
 
 static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, const SolveFn& solve, const LevelGeom& geo, int m, int k,
                          double eig_tol, int maxit, uint64_t seed, cplx* X, std::vector<double>& theta,
-                         int& iters_out) {
+                         int& iters_out, double tau_s = 0.0) {
   const int64_t n = A.n();
   const int dof = A.dof();
   const size_t blk = (size_t)n * m * sizeof(cplx);
   DevBuf Yb(blk), Zb(blk), Tb(blk), small, eig((size_t)(3 * m * m + 4) * sizeof(cplx) + 6 * m * sizeof(double)),
       resid(m * sizeof(cplx)), iv((m + 8) * sizeof(int));
+  DevBuf Rb(tau_s != 0.0 ? blk : 0), cm(tau_s != 0.0 ? (size_t)3 * m * sizeof(cplx) : 0);
   cplx* Y = Yb.as<cplx>();
   cplx* Z = Zb.as<cplx>();
   cplx* Tm = Tb.as<cplx>();
@@ -91,7 +98,10 @@ static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, const SolveFn& solve, c
     // Y = H^{-1} X = gamma5 Op^{-1} X
     solve(X, Tm, m);
     blas::gamma5(ctx, geo.nsites, dof, m, Tm, Y);
-    blockdot(ctx, n, X, m, m, Y, m, m, Tmat);
+    if (tau_s != 0.0)
+      blockdot(ctx, n, Y, m, m, Y, m, m, Tmat);  // Y^H Y
+    else
+      blockdot(ctx, n, X, m, m, Y, m, m, Tmat);  // X^H Y
     hermitize(ctx, m, Tmat);
     jacobi_eigh(ctx, m, Tmat, S, nu, nullptr);
     k_reciprocal<<<div_up(m, 128), 128, 0, ctx.stream>>>(m, nu, mu);
@@ -101,13 +111,38 @@ static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, const SolveFn& solve, c
     QD_LAUNCH_CHECK();
     blockmul(ctx, n, X, m, m, Ss, m, m, Tm, m, 1.0, 0.0);  // Ritz vectors X S
     blockmul(ctx, n, Y, m, m, Ss, m, m, Z, m, 1.0, 0.0);   // H^{-1} X S
-    eig_residuals(ctx, n, m, Z, Tm, nus, resid.as<cplx>());
     std::vector<cplx> hr(m);
     std::vector<double> hnu(m);
-    QD_CUDA(cudaMemcpyAsync(hr.data(), resid.as<cplx>(), m * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
-    QD_CUDA(cudaMemcpyAsync(theta.data(), mus, m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
-    QD_CUDA(cudaMemcpyAsync(hnu.data(), nus, m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
-    QD_CUDA(cudaStreamSynchronize(ctx.stream));
+    if (tau_s != 0.0) {
+      // complex Rayleigh quotients mu_i = x_i^H (H^{-1} x_i) and the
+      // residuals ||H^{-1} x_i - mu_i x_i||
+      cplx* muc = cm.as<cplx>();
+      cplx* negmu = muc + m;
+      cplx* ones = negmu + m;
+      blas::dots(ctx, 1, n, m, Tm, 0, Z, 0, muc);
+      std::vector<cplx> hmu(m), hneg(m), hone(m, mkc(1.0, 0.0));
+      QD_CUDA(cudaMemcpyAsync(hmu.data(), muc, m * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+      QD_CUDA(cudaStreamSynchronize(ctx.stream));
+      for (int i = 0; i < m; ++i) {
+        hneg[i] = mkc(-hmu[i].x, -hmu[i].y);
+        const double a2 = hmu[i].x * hmu[i].x + hmu[i].y * hmu[i].y;
+        hnu[i] = std::sqrt(a2);
+        theta[i] = a2 > 0.0 ? hmu[i].x / a2 : 0.0;  // Re 1/mu
+      }
+      QD_CUDA(cudaMemcpyAsync(negmu, hneg.data(), m * sizeof(cplx), cudaMemcpyHostToDevice, ctx.stream));
+      QD_CUDA(cudaMemcpyAsync(ones, hone.data(), m * sizeof(cplx), cudaMemcpyHostToDevice, ctx.stream));
+      blas::copy(ctx, (int64_t)n * m, Z, Rb.as<cplx>());
+      blas::axpby(ctx, n, m, negmu, Tm, ones, Rb.as<cplx>());
+      blas::dots(ctx, 1, n, m, Rb.as<cplx>(), 0, Rb.as<cplx>(), 0, resid.as<cplx>());
+      QD_CUDA(cudaMemcpyAsync(hr.data(), resid.as<cplx>(), m * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+      QD_CUDA(cudaStreamSynchronize(ctx.stream));
+    } else {
+      eig_residuals(ctx, n, m, Z, Tm, nus, resid.as<cplx>());
+      QD_CUDA(cudaMemcpyAsync(hr.data(), resid.as<cplx>(), m * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+      QD_CUDA(cudaMemcpyAsync(theta.data(), mus, m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+      QD_CUDA(cudaMemcpyAsync(hnu.data(), nus, m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+      QD_CUDA(cudaStreamSynchronize(ctx.stream));
+    }
     double worst = 0.0;
     for (int i = 0; i < k; ++i) {
       const double rel = std::sqrt(hr[i].x) / (std::fabs(hnu[i]) > 0 ? std::fabs(hnu[i]) : 1.0);
@@ -123,6 +158,10 @@ static void subspace_eig(qd_ctx& ctx, const Op<cplx>& A, const SolveFn& solve, c
   }
   iters_out = it;
 }
+
+// Raised by the eigensolver's inner solves when the inverter stagnates or
+// misses its tolerance (Sec. 3.2).
+struct InverterStagnated {};
 
 // ---------------------------------------------------------------------------
 void defl_build(qd_defl& d, const double* injected) {
@@ -157,25 +196,64 @@ void defl_build(qd_defl& d, const double* injected) {
     int m = k + (d.p.guard > 0 ? d.p.guard : 0);
     if (m > d.nb) m = (int)d.nb;
     DevBuf X((size_t)d.nb * m * sizeof(cplx));
-    Precond<cplx>* M = nullptr;
-    std::unique_ptr<MGPrecond<cplx>> pre;
-    if (d.level == 0 && d.mg) M = d.mg->pre64.get();  // the coarsest level has no coarser one
     const cplx* inv = d.level >= 1 ? d.mg->Cinv<cplx>(d.level) : nullptr;
-    GCR<cplx> solver;
-    const Op<cplx>& A = *op;
     const double stol = d.p.solve_tol;
-    SolveFn fn = [&](const cplx* Xin, cplx* Wout, int mm) {
-      if (inv) {
-        // direct coarsest solve, corrected to FP64 accuracy (each correction
-        // gains ~4 digits; two reach the 1e-10 of the eigensolver's solves)
-        coarsest_solve_refined(ctx, *d.mg->L[d.level - 1], mm, Xin, Wout, 2);
-      } else {
-        SolveInfo info;
-        solver.solve(ctx, A, M, Xin, Wout, mm, stol, 20000, 32, &info);
-      }
-    };
+    const int srestart = d.p.solve_restart > 0 ? d.p.solve_restart : 32;
     std::vector<double> theta;
-    subspace_eig(ctx, *op, fn, geo, m, k, d.p.eig_tol, d.p.maxit, d.p.seed, X.as<cplx>(), theta, d.iterations);
+    d.tau_eig = 0.0;
+    d.restarts = 0;
+    for (int attempt = 0;; ++attempt) {
+      // the eigensolver's operator: A + i (tau + tau_eig) gamma5 and its
+      // multigrid inverter (rebuilt for the shift after a restart)
+      std::unique_ptr<Op<cplx>> opx;
+      Precond<cplx>* M = nullptr;
+      if (d.level == 0) {
+        opx.reset(new WilsonOp<cplx>(d.gauge, d.gauge->links.as<cplx>(), d.m0, d.tau + d.tau_eig, false));
+        if (d.tau_eig != 0.0 && d.mg_shift) M = d.mg_shift->pre64.get();
+        else if (d.tau_eig == 0.0 && d.mg) M = d.mg->pre64.get();
+      }
+      const Op<cplx>& A = d.level == 0 ? *opx : *op;
+      GCR<cplx> solver;
+      solver.stag_window = d.p.stag_window;
+      bool first = true;
+      SolveFn fn = [&](const cplx* Xin, cplx* Wout, int mm) {
+        if (inv) {
+          // direct coarsest solve, corrected to FP64 accuracy (each correction
+          // gains ~4 digits; two reach the 1e-10 of the eigensolver's solves)
+          coarsest_solve_refined(ctx, *d.mg->L[d.level - 1], mm, Xin, Wout, 2);
+          return;
+        }
+        if (first && attempt < d.p.fail_first) throw InverterStagnated();  // test hook
+        first = false;
+        SolveInfo info;
+        solver.solve(ctx, A, M, Xin, Wout, mm, stol, 20000, srestart, &info);
+        if (info.stagnated || info.converged < mm) throw InverterStagnated();
+      };
+      try {
+        subspace_eig(ctx, A, fn, geo, m, k, d.p.eig_tol, d.p.maxit, d.p.seed, X.as<cplx>(), theta, d.iterations,
+                     d.level == 0 ? d.tau_eig : 0.0);
+        break;
+      } catch (const InverterStagnated&) {
+        if (d.level != 0 || attempt >= d.p.max_restarts)
+          fail(QD_ERR_NOT_CONVERGED, "eigensolver: the inverter stagnated (restarts " + std::to_string(attempt) +
+                                         ", shift " + std::to_string(d.tau_eig) + ")");
+        // Sec. 3.2: rebuild the multigrid inverter with a larger shift and
+        // restart the eigensolver
+        d.tau_eig = d.tau_eig > 0.0 ? 4.0 * d.tau_eig : d.p.tau_restart;
+        ++d.restarts;
+        d.mg_shift.reset();
+        if (d.mg) {
+          std::unique_ptr<qd_mg> ms(new qd_mg());
+          ms->ctx = d.mg->ctx;
+          ms->gauge = d.gauge;
+          ms->m0 = d.m0;
+          ms->tau = d.tau + d.tau_eig;
+          ms->p = d.mg->p;
+          mg_build(*ms, nullptr);
+          d.mg_shift = std::move(ms);
+        }
+      }
+    }
     for (int i = 0; i < k; ++i) d.mu[i] = theta[i];
     // U_bar = first k columns of X (ld m -> ld k)
     blockmul_identity_cols(ctx, d.nb, X.as<cplx>(), m, k, d.Ubar.as<cplx>());
@@ -291,16 +369,40 @@ void defl_project(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* out) {
   }
 }
 
-// Sec. 2.2 matrices (kind 2): M1 = U_bar^H W^H Z (k x s), M2 = U_bar^H g5 W^H Z.
+// Sec. 2.2 matrices: kind 2: M1 = U_bar^H W^H Z (k x s), M2 = U_bar^H g5 W^H Z;
+// kind 1: M1 = (A^{-1}_xi U)^H Z, M2 = U^H Z.
 void defl_coeffs(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* M1, cplx* M2) {
-  QD_REQUIRE(d.kind == QD_DEFL_MG_OBLIQUE, "a-posteriori coefficients are defined for Algorithm 2");
   const int k = d.p.k;
+  if (d.kind == QD_DEFL_EIG_ORTHO) {
+    blockdot(ctx, d.nb, d.AinvU.as<cplx>(), k, k, z, s, s, M1);
+    blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, z, s, s, M2);
+    return;
+  }
   const LevelGeom& cg = d.mg->geom(d.level);
   DevBuf c((size_t)d.nb * s * sizeof(cplx)), gc((size_t)d.nb * s * sizeof(cplx));
   restrict_chain(ctx, d, s, z, c.as<cplx>());
   blas::gamma5(ctx, cg.nsites, d.mg->dof(d.level), s, c.as<cplx>(), gc.as<cplx>());
   blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, c.as<cplx>(), s, s, M1);
   blockdot(ctx, d.nb, d.Ubar.as<cplx>(), k, k, gc.as<cplx>(), s, s, M2);
+}
+
+// sin of the angle between each column of V and range(W), W = W_0 ... W_{L-1}
+void mg_subspace_sines(qd_ctx& ctx, qd_mg& mg, int L, int k, const cplx* V, double* out) {
+  const int64_t nf = mg.gauge->geo.nsites * 12;
+  qd_defl tmp;  // only the chain fields are used
+  tmp.mg = &mg;
+  tmp.level = L;
+  const int64_t nc = mg.geom(L).nsites * (int64_t)mg.dof(L);
+  DevBuf c((size_t)nc * k * sizeof(cplx)), f((size_t)nf * k * sizeof(cplx)), nn((size_t)2 * k * sizeof(cplx));
+  restrict_chain(ctx, tmp, k, V, c.as<cplx>());
+  prolong_chain(ctx, tmp, k, c.as<cplx>(), f.as<cplx>());
+  blas::sub(ctx, nf * k, V, f.as<cplx>(), f.as<cplx>());  // v - W W^H v
+  blas::dots(ctx, 1, nf, k, f.as<cplx>(), 0, f.as<cplx>(), 0, nn.as<cplx>());
+  blas::dots(ctx, 1, nf, k, V, 0, V, 0, nn.as<cplx>() + k);
+  std::vector<cplx> h(2 * k);
+  QD_CUDA(cudaMemcpyAsync(h.data(), nn.as<cplx>(), 2 * k * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  for (int i = 0; i < k; ++i) out[i] = h[k + i].x > 0.0 ? std::sqrt(h[i].x / h[k + i].x) : 0.0;
 }
 
 // ---------------------------------------------------------------------------

@@ -9,6 +9,7 @@ namespace qd {
 struct SolveInfo {
   int iterations = 0;
   int converged = 0;
+  bool stagnated = false;  // stopped by the stagnation test (GCR::stag_window)
   double max_rel = 0.0;
   std::vector<int> iters;
   std::vector<double> true_rel;
@@ -19,6 +20,12 @@ template <class C> class GCR {
  public:
   // Gram-Schmidt passes per iteration (2 = CGS2; 1 = classical, one pass).
   int orth_passes = 2;
+  // > 0 (with a tolerance > 0): every stag_window iterations compare each
+  // active column's residual with its value stag_window iterations before;
+  // if one fell by less than the factor stag_ratio the solve stops with
+  // SolveInfo::stagnated (the inverter stagnating, Sec. 3.2).
+  int stag_window = 0;
+  double stag_ratio = 0.9;
   // x = A^{-1} b to ||b - A x|| <= tol ||b|| per column (x overwritten,
   // zero initial guess).  M (nullable) is a right preconditioner that may
   // change between calls.  `quiet` skips per-column statistics.

@@ -391,6 +391,23 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
   // tol <= 0: exactly maxit iterations and no host synchronisation (columns
   // with a zero residual are masked on the device)
   const bool check = tol > 0.0;
+  // stagnation test: residual norms of the active columns every stag_window
+  // iterations against the previous snapshot
+  bool stag = false;
+  std::vector<cplx> snap, now(nrhs);
+  std::vector<int> hact(nrhs);
+  auto stagnating = [&]() -> bool {
+    if (!check || stag_window <= 0 || its == 0 || its % stag_window != 0) return false;
+    QD_CUDA(cudaMemcpyAsync(now.data(), rn2, nrhs * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaMemcpyAsync(hact.data(), act, nrhs * sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaStreamSynchronize(ctx.stream));
+    bool st = false;
+    if (!snap.empty())
+      for (int c = 0; c < nrhs; ++c)
+        if (hact[c] && now[c].x > stag_ratio * stag_ratio * snap[c].x) st = true;
+    snap = now;
+    return st;
+  };
   while (true) {
     if (!check && its >= maxit) break;
     QD_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx.stream));
@@ -451,6 +468,10 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
           read_flags(ctx, flags, 2, hflags);
           if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
           if (hflags[0] == 0) break;
+          if (stagnating()) {
+            stag = true;
+            break;
+          }
         }
         if (its >= maxit) break;
       }
@@ -462,6 +483,7 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
       if (!check && its >= maxit) break;
       A.residual(ctx, b, x, r, nrhs);
       blas::dots(ctx, 1, n, nrhs, r, 0, r, 0, rn2);
+      if (stag) break;
       continue;
     }
     for (int i = 0; i < restart; ++i) {
@@ -494,6 +516,10 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
         read_flags(ctx, flags, 2, hflags);
         if (hflags[1]) fail(QD_ERR_NONFINITE, "non-finite residual in GCR");
         if (hflags[0] == 0) break;
+        if (stagnating()) {
+          stag = true;
+          break;
+        }
       }
       if (its >= maxit) break;
     }
@@ -501,8 +527,10 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
     // true residual r = b - A x
     A.residual(ctx, b, x, r, nrhs);
     blas::dots(ctx, 1, n, nrhs, r, 0, r, 0, rn2);
+    if (stag) break;
   }
   if (info) {
+    info->stagnated = stag;
     std::vector<cplx> hb(nrhs), hr(nrhs);
     info->iters.assign(nrhs, 0);
     QD_CUDA(cudaMemcpyAsync(hb.data(), bn2, nrhs * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));

@@ -95,13 +95,16 @@ static void solve_mixed(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, do
     const double itol = std::min(0.5, std::max(p.inner_tol, need));
     SolveInfo in;
     sc.gcr32.orth_passes = 1;
+    sc.gcr32.stag_window = p.stag_window;
     sc.gcr32.solve(ctx, A32, mg ? mg->pre32.get() : nullptr, rf, ef, s, itol, p.maxit, p.restart, &in);
+    if (in.stagnated) info.stagnated = true;
     inner_total += in.iterations;
     for (int c = 0; c < s; ++c) iters[c] += in.iters[c];
     k_axpy_from_f32<<<blas::grid_1d(tot), 256, 0, ctx.stream>>>(n, s, ef, sout, x);
     QD_LAUNCH_CHECK();
     A64.residual(ctx, b, x, r, s);
     blas::dots(ctx, 1, n, s, r, 0, r, 0, rn2);
+    if (info.stagnated) break;
   }
   if (mg && mg->L.back()->tc) {
     const int e = tc_error(ctx, *mg->L.back());
@@ -152,7 +155,30 @@ void solve(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, double tau, int
   QD_REQUIRE(p.precision == QD_PREC_F64, "unknown precision");
   WilsonOp<cplx> A(&g, g.links.as<cplx>(), m0, tau, false);
   SolverCache& sc = cache(ctx);
+  sc.gcr64.stag_window = p.stag_window;
   sc.gcr64.solve(ctx, A, mg ? mg->pre64.get() : nullptr, b, x, s, p.tol, p.maxit, p.restart, &info);
+}
+
+// Spin-colour dilution: column 12 j + h of Zd is column j of Z restricted to
+// the components a = 3 spin + colour equal to h (layout (site, a, column)).
+__global__ void k_dilute(int64_t nsites, int s, const cplx* __restrict__ Z, cplx* __restrict__ Zd) {
+  const int64_t tot = nsites * 12 * (int64_t)s * 12;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(e % (12 * s));
+    const int64_t sa = e / (12 * s);
+    const int a = (int)(sa % 12);
+    const int j = col / 12, h = col - 12 * j;
+    Zd[e] = (a == h) ? Z[sa * s + j] : mkc(0.0, 0.0);
+  }
+}
+
+// t[j] = sum_h td[12 j + h] in order h = 0..11
+__global__ void k_sum_dilution(int s, const cplx* __restrict__ td, cplx* __restrict__ t) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s) return;
+  cplx acc = mkc(0.0, 0.0);
+  for (int h = 0; h < 12; ++h) acc = cadd(acc, td[12 * j + h]);
+  t[j] = acc;
 }
 
 void hutchinson(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, qd_defl* d, double m0, double tau,
@@ -161,34 +187,50 @@ void hutchinson(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, qd_defl* d, double m0
   const int s = p.nsamples;
   QD_REQUIRE(s >= 1, "nsamples must be >= 1");
   if (d) QD_REQUIRE(d->gauge == &g && d->m0 == m0 && d->tau == tau, "deflation space built for another operator");
+  const bool dil = p.dilution == 12;
+  const int nc = dil ? 12 * s : s;  // right-hand sides solved
   const int64_t n = g.geo.nsites * 12;
   SolverCache& sc = cache(ctx);
-  const size_t vb = (size_t)n * s * sizeof(cplx);
+  const size_t vb = (size_t)n * nc * sizeof(cplx);
   sc.Z.resize(vb);
   sc.B.resize(vb);
   sc.X.resize(vb);
-  sc.tdev.resize((size_t)s * sizeof(cplx));
+  sc.tdev.resize((size_t)nc * sizeof(cplx));
   sc.stats.resize(8 * sizeof(double));
   sc.loo.resize((size_t)s * sizeof(double));
   cplx* Z = sc.Z.as<cplx>();
   cplx* B = sc.B.as<cplx>();
   cplx* X = sc.X.as<cplx>();
-  // a1: noise
-  rademacher_fill(ctx, g.geo, p.seed, p.sample_offset, s, Z);
+  // a1: noise (diluted: the s samples are made in B, then split into Z)
+  if (dil) {
+    rademacher_fill(ctx, g.geo, p.seed, p.sample_offset, s, B);
+    k_dilute<<<blas::grid_1d(n * nc), 256, 0, ctx.stream>>>(g.geo.nsites, s, B, Z);
+    QD_LAUNCH_CHECK();
+  } else {
+    rademacher_fill(ctx, g.geo, p.seed, p.sample_offset, s, Z);
+  }
   // a8: deflated right-hand sides
   if (d)
-    defl_project(ctx, *d, s, Z, B);
+    defl_project(ctx, *d, nc, Z, B);
   else
-    blas::copy(ctx, n * s, Z, B);
+    blas::copy(ctx, n * nc, Z, B);
   // a5/a6: solves
-  solve(ctx, g, mg, m0, tau, s, B, X, p.solver, out.info);
-  // a9: t_j = z_j^H x_j, statistics
-  blas::dots(ctx, 1, n, s, Z, 0, X, 0, sc.tdev.as<cplx>());
+  solve(ctx, g, mg, m0, tau, nc, B, X, p.solver, out.info);
+  // a9: t_j = z_j^H x_j (summed over the diluted parts), statistics
+  if (dil) {
+    DevBuf td((size_t)nc * sizeof(cplx));
+    blas::dots(ctx, 1, n, nc, Z, 0, X, 0, td.as<cplx>());
+    k_sum_dilution<<<div_up(s, 128), 128, 0, ctx.stream>>>(s, td.as<cplx>(), sc.tdev.as<cplx>());
+    QD_LAUNCH_CHECK();
+    QD_CUDA(cudaStreamSynchronize(ctx.stream));  // td goes out of scope
+  } else {
+    blas::dots(ctx, 1, n, s, Z, 0, X, 0, sc.tdev.as<cplx>());
+  }
   trace_stats(ctx, s, sc.tdev.as<cplx>(), sc.stats.as<double>(), sc.loo.as<double>());
   out.t.resize(s);
   QD_CUDA(cudaMemcpyAsync(out.stats, sc.stats.as<double>(), 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
   QD_CUDA(cudaMemcpyAsync(out.t.data(), sc.tdev.as<cplx>(), s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
-  if (want_coeffs && d && d->kind == QD_DEFL_MG_OBLIQUE) {
+  if (want_coeffs && d && !dil) {
     const int k = d->p.k;
     DevBuf m1((size_t)k * s * sizeof(cplx)), m2((size_t)k * s * sizeof(cplx));
     defl_coeffs(ctx, *d, s, Z, m1.as<cplx>(), m2.as<cplx>());

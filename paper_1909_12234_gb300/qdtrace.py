@@ -68,7 +68,8 @@ class SolverParams(ctypes.Structure):
                 ("restart", ctypes.c_int),
                 ("precision", ctypes.c_int),
                 ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int)]
+                ("max_refine", ctypes.c_int),
+                ("stag_window", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -76,7 +77,8 @@ class SolveStats(ctypes.Structure):
                 ("converged", ctypes.c_int),
                 ("max_true_rel_residual", ctypes.c_double),
                 ("iters_per_rhs", ctypes.POINTER(ctypes.c_int)),
-                ("true_rel_residual", ctypes.POINTER(ctypes.c_double))]
+                ("true_rel_residual", ctypes.POINTER(ctypes.c_double)),
+                ("stagnated", ctypes.c_int)]
 
 
 class DeflParams(ctypes.Structure):
@@ -86,14 +88,20 @@ class DeflParams(ctypes.Structure):
                 ("eig_tol", ctypes.c_double),
                 ("solve_tol", ctypes.c_double),
                 ("maxit", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64),
+                ("tau_restart", ctypes.c_double),
+                ("max_restarts", ctypes.c_int),
+                ("stag_window", ctypes.c_int),
+                ("solve_restart", ctypes.c_int),
+                ("fail_first", ctypes.c_int)]
 
 
 class TraceParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64),
                 ("sample_offset", ctypes.c_int64),
                 ("nsamples", ctypes.c_int),
-                ("solver", SolverParams)]
+                ("solver", SolverParams),
+                ("dilution", ctypes.c_int)]
 
 
 class TraceResult(ctypes.Structure):
@@ -167,6 +175,9 @@ SIGNATURES = {
     "qd_defl_destroy": (_I, [_P]),
     "qd_defl_set_rank": (_I, [_P, _I, _DPTR]),
     "qd_defl_info": (_I, [_P, _DPTR, _DPTR, _IPTR]),
+    "qd_defl_shift_info": (_I, [_P, _DPTR, _IPTR]),
+    "qd_defl_gram": (_I, [_P, _DPTR]),
+    "qd_defl_basis": (_I, [_P, _P]),
     "qd_deflate_project": (_I, [_P, _I, _P, _P]),
     "qd_deflate_project_static": (_I, [_P, _I, _P, _P]),
     "qd_deflate_coeffs": (_I, [_P, _I, _P, _DPTR, _DPTR]),
@@ -182,6 +193,7 @@ SIGNATURES = {
     "qd_autotune_clear": (None, []),
     "qd_autotune_report": (_I, [ctypes.c_char_p, _I]),
     "qd_hutchinson_batch": (_I, [_P, _I, ctypes.POINTER(BatchItem), _I]),
+    "qd_mg_subspace_sines": (_I, [_P, _I, _I, _P, _DPTR]),
     "qd_hutchinson_trace": (_I, [_P, _P, _P, _P, _D, _D, ctypes.POINTER(TraceParams),
                                  ctypes.POINTER(TraceResult)]),
     "qd_trace_stats": (_I, [_P, _I, _P, _DPTR, ctypes.POINTER(TraceResult)]),
@@ -404,6 +416,15 @@ def restrict(mg, level, nrhs, fine, coarse):
     _check(load().qd_restrict(mg.h, int(level), int(nrhs), _ptr(fine), _ptr(coarse)))
 
 
+def mg_subspace_sines(mg, depth, V):
+    """sin of the angle between each column of V (fine qd layout, complex128
+    CUDA tensor (V, 12, k)) and the range of W_0 ... W_{depth-1}."""
+    k = int(V.shape[-1])
+    out = np.zeros(k)
+    _check(load().qd_mg_subspace_sines(mg.h, int(depth), k, _ptr(V), out.ctypes.data_as(_DPTR)))
+    return out
+
+
 def coarse_apply(mg, level, nrhs, inp, out):
     _check(load().qd_coarse_apply(mg.h, int(level), int(nrhs), _ptr(inp), _ptr(out)))
 
@@ -450,11 +471,12 @@ def solve(ctx, gauge, mg, m0, tau, nrhs, b, x, tol, maxit=10000, restart=16, all
     """Returns (status, iterations, per-column iterations, per-column true residual)."""
     it = (ctypes.c_int * nrhs)()
     rel = (ctypes.c_double * nrhs)()
-    st = SolveStats(0, 0, 0.0, it, rel)
+    st = SolveStats(0, 0, 0.0, it, rel, 0)
     p = solver_params(tol, maxit, restart, precision, **kw)
     rc = load().qd_solve(ctx.h, gauge.h, mg.h if mg is not None else None, float(m0), float(tau), int(nrhs),
                          _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(st))
     _check(rc, allow=(QD_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    solve.last_stagnated = bool(st.stagnated)
     return rc, st.iterations, list(it), list(rel)
 
 
@@ -493,6 +515,24 @@ class Deflation:
         its = ctypes.c_int()
         _check(load().qd_defl_info(self.h, mu, lam, ctypes.byref(its)))
         return np.array(mu[:]), np.array(lam[:self.rank]), its.value
+
+    def shift_info(self):
+        """(eigensolver shift tau_eig after its restarts, number of restarts)."""
+        tau = ctypes.c_double()
+        n = ctypes.c_int()
+        _check(load().qd_defl_shift_info(self.h, ctypes.byref(tau), ctypes.byref(n)))
+        return tau.value, n.value
+
+    def gram(self):
+        """Algorithm 2: G = U_bar^H gamma5^W C U_bar (k x k)."""
+        k = self.params.k
+        G = np.zeros((k, k, 2))
+        _check(load().qd_defl_gram(self.h, G.ctypes.data_as(_DPTR)))
+        return G[..., 0] + 1j * G[..., 1]
+
+    def basis(self, out):
+        """Copy the k basis vectors into the complex128 CUDA tensor `out`."""
+        _check(load().qd_defl_basis(self.h, _ptr(out)))
 
     def project(self, nrhs, z, out):
         _check(load().qd_deflate_project(self.h, int(nrhs), _ptr(z), _ptr(out)))
@@ -594,9 +634,11 @@ class _TraceOut:
 
 def hutchinson_trace(ctx, gauge, mg, defl, m0, tau, seed, sample_offset, nsamples, tol, maxit=10000,
                      restart=16, want_samples=True, want_coeffs=False, allow_not_converged=False,
-                     precision=QD_PREC_F64, **kw):
-    """One multi-RHS batch of the deflated estimator; returns a dict."""
-    p = TraceParams(int(seed), int(sample_offset), int(nsamples), solver_params(tol, maxit, restart, precision, **kw))
+                     precision=QD_PREC_F64, dilution=0, **kw):
+    """One multi-RHS batch of the deflated estimator; returns a dict.
+    dilution=12: spin-colour dilution (12 solves per sample)."""
+    p = TraceParams(int(seed), int(sample_offset), int(nsamples), solver_params(tol, maxit, restart, precision, **kw),
+                    int(dilution))
     o = _TraceOut(defl, nsamples, want_samples, want_coeffs)
     rc = load().qd_hutchinson_trace(ctx.h, gauge.h, mg.h if mg is not None else None,
                                     defl.h if defl is not None else None, float(m0), float(tau),

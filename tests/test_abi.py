@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(library):
 
 
 def test_abi_version(library):
-    assert library.qd_abi_version() == 2
+    assert library.qd_abi_version() == 3
 
 
 def test_struct_layouts_match_c(tmp_path):
@@ -52,10 +52,14 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol),
          offsetof(qd_mg_params, coarsest_direct), offsetof(qd_mg_params, use_graphs), offsetof(qd_mg_params, coarse_tc),
          offsetof(qd_mg_params, coarse_smoother_steps));
-  printf("%zu %zu\n", sizeof(qd_solve_stats), offsetof(qd_solve_stats, true_rel_residual));
-  printf("%zu %zu\n", sizeof(qd_defl_params), offsetof(qd_defl_params, seed));
-  printf("%zu %zu\n", sizeof(qd_trace_params), offsetof(qd_trace_params, solver));
-  printf("%zu %zu %zu\n", sizeof(qd_solver_params), offsetof(qd_solver_params, inner_tol), offsetof(qd_solver_params, max_refine));
+  printf("%zu %zu %zu\n", sizeof(qd_solve_stats), offsetof(qd_solve_stats, true_rel_residual),
+         offsetof(qd_solve_stats, stagnated));
+  printf("%zu %zu %zu %zu\n", sizeof(qd_defl_params), offsetof(qd_defl_params, seed),
+         offsetof(qd_defl_params, tau_restart), offsetof(qd_defl_params, fail_first));
+  printf("%zu %zu %zu\n", sizeof(qd_trace_params), offsetof(qd_trace_params, solver),
+         offsetof(qd_trace_params, dilution));
+  printf("%zu %zu %zu %zu\n", sizeof(qd_solver_params), offsetof(qd_solver_params, inner_tol),
+         offsetof(qd_solver_params, max_refine), offsetof(qd_solver_params, stag_window));
   printf("%zu %zu %zu\n", sizeof(qd_trace_result), offsetof(qd_trace_result, nsamples), offsetof(qd_trace_result, UhKZ));
   printf("%zu %zu %zu\n", sizeof(qd_smoother_params), offsetof(qd_smoother_params, seed), offsetof(qd_smoother_params, mr_steps));
   printf("%zu %zu\n", sizeof(qd_smoother_info), offsetof(qd_smoother_info, enabled));
@@ -69,10 +73,12 @@ int main(void) {
     want = [
         [ctypes.sizeof(qd.MGParams), qd.MGParams.null_tol.offset, qd.MGParams.coarsest_direct.offset,
          qd.MGParams.use_graphs.offset, qd.MGParams.coarse_tc.offset, qd.MGParams.coarse_smoother_steps.offset],
-        [ctypes.sizeof(qd.SolveStats), qd.SolveStats.true_rel_residual.offset],
-        [ctypes.sizeof(qd.DeflParams), qd.DeflParams.seed.offset],
-        [ctypes.sizeof(qd.TraceParams), qd.TraceParams.solver.offset],
-        [ctypes.sizeof(qd.SolverParams), qd.SolverParams.inner_tol.offset, qd.SolverParams.max_refine.offset],
+        [ctypes.sizeof(qd.SolveStats), qd.SolveStats.true_rel_residual.offset, qd.SolveStats.stagnated.offset],
+        [ctypes.sizeof(qd.DeflParams), qd.DeflParams.seed.offset, qd.DeflParams.tau_restart.offset,
+         qd.DeflParams.fail_first.offset],
+        [ctypes.sizeof(qd.TraceParams), qd.TraceParams.solver.offset, qd.TraceParams.dilution.offset],
+        [ctypes.sizeof(qd.SolverParams), qd.SolverParams.inner_tol.offset, qd.SolverParams.max_refine.offset,
+         qd.SolverParams.stag_window.offset],
         [ctypes.sizeof(qd.TraceResult), qd.TraceResult.nsamples.offset, qd.TraceResult.UhKZ.offset],
         [ctypes.sizeof(qd.SmootherParams), qd.SmootherParams.seed.offset, qd.SmootherParams.mr_steps.offset],
         [ctypes.sizeof(qd.SmootherInfo), qd.SmootherInfo.enabled.offset],

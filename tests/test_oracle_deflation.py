@@ -118,3 +118,45 @@ def test_alg2_three_level_composite(setup):
     assert abs(alg.t0 + np.trace(B) - np.trace(Ainv)) < 1e-9 * abs(np.trace(Ainv))
     Z = np.sign(rng.standard_normal((3072, 3))) + 0j
     assert np.allclose(alg.project(H.levels[0].matvec, Z), Z - P @ Z, atol=1e-10)
+
+
+def test_alg1_rank_sweep_coefficients(setup):
+    # z^H A^{-1}(I - U_r U_r^H) z from the stored s x k and k x s matrices
+    # equals the vector form for every r, and t0 at rank r is the partial sum
+    A, Ainv, G5 = setup["A"], setup["Ainv"], setup["G5"]
+    _, Ue = deflation.fine_eigvecs_dense(A, G5, 12)
+    lev = setup["H"].levels[0]
+    a1 = deflation.Alg1(Ue, lev.matvec, 1e-12)
+    rng = np.random.default_rng(5)
+    Z = np.sign(rng.standard_normal((A.shape[0], 4))) + 0j
+    ZhAU, UhZ = a1.coeffs(Z)
+    t_und = np.einsum("ij,ij->j", Z.conj(), Ainv @ Z)
+    for r in (1, 5, 12):
+        Ur = Ue[:, :r]
+        vec = np.einsum("ij,ij->j", Z.conj(), Ainv @ (Z - Ur @ (Ur.conj().T @ Z)))
+        assert np.allclose(t_und - a1.correction(ZhAU, UhZ, r), vec, rtol=1e-9)
+        assert abs(a1.t0_rank(r) - np.trace(Ur.conj().T @ Ainv @ Ur)) < 1e-9 * abs(a1.t0_rank(r))
+
+
+def test_subspace_sines(setup):
+    # columns of W: angle 0; vectors orthogonal to range(W): sin 1; random:
+    # the dense projector's value
+    T = setup["H"].transfers[0]
+    W = T.matrix().toarray()
+    s0 = deflation.subspace_sines(T, W[:, :5])
+    assert np.all(s0 < 1e-12)
+    rng = np.random.default_rng(6)
+    V = rng.standard_normal((W.shape[0], 3)) + 1j * rng.standard_normal((W.shape[0], 3))
+    Vperp = V - W @ (W.conj().T @ V)
+    assert np.allclose(deflation.subspace_sines(T, Vperp), 1.0, atol=1e-12)
+    ref = np.linalg.norm(V - W @ (W.conj().T @ V), axis=0) / np.linalg.norm(V, axis=0)
+    assert np.allclose(deflation.subspace_sines(T, V), ref, rtol=1e-12)
+    # and for the composite prolongator of a three-level hierarchy
+    dims = (4, 4, 4, 4)
+    U = synth.random_su3_links(dims, 0.3, 1)
+    H3 = multigrid.setup(U, -0.4, dims, [(2, 2, 2, 2), (2, 2, 1, 1)], [6, 4], seed=11, null_maxit=10)
+    Cp = deflation.Composite(H3.transfers)
+    Wc = Cp.matrix().toarray()
+    V = rng.standard_normal((Wc.shape[0], 2)) + 0j
+    ref = np.linalg.norm(V - Wc @ (Wc.conj().T @ V), axis=0) / np.linalg.norm(V, axis=0)
+    assert np.allclose(deflation.subspace_sines(Cp, V), ref, rtol=1e-12)

@@ -51,9 +51,12 @@ template <class C>
 void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int nrhs, int nsteps,
               double tol, C* rbuf, C* qbuf, int* steps_dev, DevBuf& scratch);
 // nsteps minimal-residual steps on A e = res, accumulated into x; res is
-// updated in place (smoother: no checks, no host synchronisation).
+// updated in place (smoother: no checks, no host synchronisation).  With
+// rin and Az given (res = rin - A x on entry), the last step also writes
+// Az = rin - res = A x.
 template <class C>
-void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int nsteps, DevBuf& scratch);
+void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int nsteps, DevBuf& scratch,
+               const C* rin = nullptr, C* Az = nullptr);
 
 }  // namespace qd
 
@@ -73,6 +76,7 @@ template <class C> class MGPrecond : public Precond<C> {
   MGPrecond& operator=(const MGPrecond&) = delete;
   ~MGPrecond();
   void apply(qd_ctx& ctx, const C* r, C* z, int nrhs) override;
+  bool apply_az(qd_ctx& ctx, const Op<C>& A, const C* r, C* z, C* Az, int nrhs) override;
   void buffers(std::vector<const void*>& v) const;
   bool sync_free() const;
   // z = W C^{-1} W^H r only (no smoothing).
@@ -80,7 +84,9 @@ template <class C> class MGPrecond : public Precond<C> {
 
  private:
   void ensure_buffers(int nrhs);
-  void body(qd_ctx& ctx, const C* r, C* z, int nrhs);
+  void run(qd_ctx& ctx, const C* r, C* z, C* Az, int nrhs);
+  void body(qd_ctx& ctx, const C* r, C* z, C* Az, int nrhs);
+  bool ends_on_residual() const;
   void drop_graphs();
   qd_mg* mg_;
   int level_;
@@ -93,13 +99,19 @@ template <class C> class MGPrecond : public Precond<C> {
   struct Graph {
     const void* r = nullptr;
     void* z = nullptr;
+    void* Az = nullptr;
     int nrhs = 0;
     std::vector<const void*> ptrs;
     long long kernels = 0;
     cudaGraphExec_t exec = nullptr;
   };
   std::vector<Graph> graphs_;
-  std::vector<std::pair<const void*, void*>> seen_;  // pairs met once (eager so far)
+  struct Seen {
+    const void* r;
+    void* z;
+    void* Az;
+  };
+  std::vector<Seen> seen_;  // (input, outputs) met once (eager so far)
   int warm_nrhs_ = -1;
   cudaStream_t cap_stream_ = nullptr;  // capture only; nothing runs on it
 };

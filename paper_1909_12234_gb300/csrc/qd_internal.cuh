@@ -106,11 +106,22 @@ template <class C> struct Op {
   virtual void apply(qd_ctx& ctx, const C* in, C* out, int nrhs) const = 0;
   // r = b - A x; r must not alias x.  Default: apply into r, then subtract.
   virtual void residual(qd_ctx& ctx, const C* b, const C* x, C* r, int nrhs) const;
+  // True when o is the same operator (same data, parameters and form).
+  virtual bool same(const Op<C>& o) const { return false; }
 };
 
 template <class C> struct Precond {
   virtual ~Precond() {}
   virtual void apply(qd_ctx& ctx, const C* r, C* z, int nrhs) = 0;
+  // z = M r and, when M ends on a residual of A (minimal-residual smoothing
+  // keeps res = r - A z), also Az = A z = r - res without a product with A;
+  // returns false with Az untouched when it cannot.
+  virtual bool apply_az(qd_ctx& ctx, const Op<C>& A, const C* r, C* z, C* Az, int nrhs) {
+    (void)A;
+    (void)Az;
+    apply(ctx, r, z, nrhs);
+    return false;
+  }
 };
 
 }  // namespace qd
@@ -140,6 +151,10 @@ template <class C> struct WilsonOp : public Op<C> {
   int dof() const override { return 12; }
   void apply(qd_ctx& ctx, const C* in, C* out, int nrhs) const override;
   void residual(qd_ctx& ctx, const C* b, const C* x, C* r, int nrhs) const override;
+  bool same(const Op<C>& o) const override {
+    const WilsonOp<C>* w = dynamic_cast<const WilsonOp<C>*>(&o);
+    return w && w->g == g && w->links == links && w->m0 == m0 && w->tau == tau && w->dagger == dagger;
+  }
 };
 
 // Launchers (wilson.cu).  b != nullptr: out = b - A in (fused residual).
@@ -188,6 +203,7 @@ struct CoarseLevel {
   mutable DevBuf Cmb;       // uint32 [nsites][9][D][D]: (re, im) BF16 pairs
   mutable DevBuf ctc_err;   // int: bounded-wait error of the tensor-core stencil
   mutable DevBuf sten_src;  // int32 [nsites][9]: the site, then its 8 neighbours
+  mutable DevBuf ctc_tiles; // split-BF16 operand tiles of the stencil's input (grow-only)
   int ndense = 0;     // > 0: Cinv holds the dense inverse (coarsest level)
   DevBuf Cinv;        // cplx  [n][n], n = nsites * D
   DevBuf Cinvf;       // cplxf copy
@@ -208,6 +224,10 @@ template <class C> struct CoarseOp : public Op<C> {
   int64_t nsites() const override { return lv->geo.nsites; }
   int dof() const override { return lv->D; }
   void apply(qd_ctx& ctx, const C* in, C* out, int nrhs) const override;
+  bool same(const Op<C>& o) const override {
+    const CoarseOp<C>* c = dynamic_cast<const CoarseOp<C>*>(&o);
+    return c && c->lv == lv && c->mat == mat;
+  }
 };
 
 // Launchers (coarse.cu).

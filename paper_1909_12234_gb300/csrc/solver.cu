@@ -71,7 +71,8 @@ __global__ void k_gcr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
 template <class C>
 __global__ void k_mr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
                             const int* __restrict__ active, C* __restrict__ q, C* __restrict__ x,
-                            C* __restrict__ r, cplx* __restrict__ partials) {
+                            C* __restrict__ r, cplx* __restrict__ partials, const C* __restrict__ rin = nullptr,
+                            C* __restrict__ Az = nullptr) {
   typedef typename CTraits<C>::R R;
   const int col = blockIdx.y * blockDim.x + threadIdx.x;
   R acc = 0;
@@ -89,6 +90,11 @@ __global__ void k_mr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
       cfma(rv, na, qv);
       x[e] = xv;
       r[e] = rv;
+      if (Az) {
+        // A x = rin - res once res is the residual of x
+        const C bv = rin[e];
+        Az[e] = mk<C>(bv.x - rv.x, bv.y - rv.y);
+      }
       acc += cnorm2(rv);
     }
   }
@@ -427,11 +433,12 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
       for (int i = 0; i < restart; ++i) {
         C* Pi = P + i * tot;
         C* Qi = Q + i * tot;
+        bool have_q = false;
         if (M)
-          M->apply(ctx, r, Pi, nrhs);
+          have_q = M->apply_az(ctx, A, r, Pi, Qi, nrhs);
         else
           blas::copy(ctx, tot, r, Pi);
-        A.apply(ctx, Pi, Qi, nrhs);
+        if (!have_q) A.apply(ctx, Pi, Qi, nrhs);
         if (i > 0) {
           {
             ProfScope ps(ctx, QD_PROF_DOTS_F32, 8.0 * i * n * nrhs, 8.0 * (i + 1.0) * n * nrhs);
@@ -489,11 +496,12 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
     for (int i = 0; i < restart; ++i) {
       C* Pi = P + i * tot;
       C* Qi = Q + i * tot;
+      bool have_q = false;
       if (M)
-        M->apply(ctx, r, Pi, nrhs);
+        have_q = M->apply_az(ctx, A, r, Pi, Qi, nrhs);
       else
         blas::copy(ctx, tot, r, Pi);
-      A.apply(ctx, Pi, Qi, nrhs);
+      if (!have_q) A.apply(ctx, Pi, Qi, nrhs);
       for (int pass = 0; pass < orth_passes && i > 0; ++pass) {
         blas::dots(ctx, i, n, nrhs, Q, tot, Qi, 0, beta);
         blas::multi_axpy(ctx, i, n, nrhs, beta, act, Q, tot, Qi, P, Pi);
@@ -603,7 +611,8 @@ void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int
 // nsteps minimal-residual steps on A e = res that add to x and update res
 // in place (no convergence checks, no host synchronisation).
 template <class C>
-void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int nsteps, DevBuf& scratch) {
+void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int nsteps, DevBuf& scratch,
+               const C* rin, C* Az) {
   const int64_t n = A.n();
   scratch.resize((size_t)2 * nrhs * sizeof(cplx));
   cplx* s2 = scratch.as<cplx>();
@@ -611,14 +620,18 @@ void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int ns
   for (int k = 0; k < nsteps; ++k) {
     A.apply(ctx, res, q, nrhs);
     blas::dots_qq_qr(ctx, n, nrhs, q, res, s2);
+    const bool last_az = Az && k == nsteps - 1;
     ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_UPDATE_F32, 8.0 * n * nrhs,
-                 (double)sizeof(C) * 5.0 * n * nrhs);
-    k_mr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, nullptr, q, x, res, nullptr);
+                 (double)sizeof(C) * (last_az ? 7.0 : 5.0) * n * nrhs);
+    k_mr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, nullptr, q, x, res, nullptr,
+                                                         last_az ? rin : nullptr, last_az ? Az : nullptr);
     QD_LAUNCH_CHECK();
   }
 }
-template void mr_smooth<cplx>(qd_ctx&, const Op<cplx>&, cplx*, cplx*, cplx*, int, int, DevBuf&);
-template void mr_smooth<cplxf>(qd_ctx&, const Op<cplxf>&, cplxf*, cplxf*, cplxf*, int, int, DevBuf&);
+template void mr_smooth<cplx>(qd_ctx&, const Op<cplx>&, cplx*, cplx*, cplx*, int, int, DevBuf&, const cplx*,
+                              cplx*);
+template void mr_smooth<cplxf>(qd_ctx&, const Op<cplxf>&, cplxf*, cplxf*, cplxf*, int, int, DevBuf&,
+                               const cplxf*, cplxf*);
 
 template void mr_steps<cplx>(qd_ctx&, const Op<cplx>&, const cplx*, cplx*, bool, int, int, double, cplx*,
                              cplx*, int*, DevBuf&);
@@ -663,14 +676,38 @@ template <class C> void MGPrecond<C>::buffers(std::vector<const void*>& v) const
   for (const DevBuf* b : {&rc_, &ec_, &t_, &res_, &q_, &d_, &scratch_}) v.push_back(b->as<void>());
   coarse_.buffers(v);
   const CoarseLevel& cl = *mg_->L[level_];
-  for (const DevBuf* b : {&cl.tc_xc, &cl.tc_yc, &cl.tc_B, &cl.tc_part, &cl.tc_err, &cl.Cinvf, &cl.Cmf})
+  for (const DevBuf* b : std::initializer_list<const DevBuf*>{&cl.tc_xc, &cl.tc_yc, &cl.tc_B, &cl.tc_part, &cl.tc_err,
+                                                                &cl.Cinvf, &cl.Cmf, &cl.Cmb, &cl.ctc_err, &cl.sten_src,
+                                                                &cl.ctc_tiles})
     v.push_back(b->as<void>());
+  const Transfer& tr = *mg_->T[level_];
+  for (const DevBuf* b : std::initializer_list<const DevBuf*>{&tr.Wf, &tr.Wtc, &tr.rtc_err}) v.push_back(b->as<void>());
   if (next_) next_->buffers(v);
 }
 
-template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int nrhs) {
+// The V-cycle ends on minimal-residual smoothing, whose residual gives A z.
+template <class C> bool MGPrecond<C>::ends_on_residual() const {
+  const LearnedSmoother* ls = level_ == 0 ? mg_->ls.get() : nullptr;
+  if (ls && ls->enabled) return ls->mr_steps > 0;
+  const int nu = (level_ > 0 && mg_->p.coarse_smoother_steps >= 0) ? mg_->p.coarse_smoother_steps
+                                                                    : mg_->p.smoother_steps;
+  return nu > 0;
+}
+
+template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int nrhs) { run(ctx, r, z, nullptr, nrhs); }
+
+template <class C> bool MGPrecond<C>::apply_az(qd_ctx& ctx, const Op<C>& A, const C* r, C* z, C* Az, int nrhs) {
+  if (!Az || !ends_on_residual() || !A.same(*mg_->op<C>(level_))) {
+    run(ctx, r, z, nullptr, nrhs);
+    return false;
+  }
+  run(ctx, r, z, Az, nrhs);
+  return true;
+}
+
+template <class C> void MGPrecond<C>::run(qd_ctx& ctx, const C* r, C* z, C* Az, int nrhs) {
   if (level_ != 0 || !mg_->p.use_graphs || ctx.prof || !sync_free()) {
-    body(ctx, r, z, nrhs);
+    body(ctx, r, z, Az, nrhs);
     return;
   }
   std::vector<const void*> cur;
@@ -691,7 +728,7 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
     warm_nrhs_ = -1;
   }
   for (Graph& g : graphs_) {
-    if (g.r == r && g.z == z) {
+    if (g.r == r && g.z == z && g.Az == Az) {
       QD_CUDA(cudaGraphLaunch(g.exec, ctx.stream));
       launch_counter().fetch_add(g.kernels, std::memory_order_relaxed);
       return;
@@ -699,7 +736,7 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
   }
   if (warm_nrhs_ != nrhs) {
     // first call at this size: eager, so that every buffer reaches its size
-    body(ctx, r, z, nrhs);
+    body(ctx, r, z, Az, nrhs);
     warm_nrhs_ = nrhs;
     seen_.clear();
     return;
@@ -707,11 +744,11 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
   // capture an (input, output) pair only when it comes back: one-shot
   // solves (setup, training) run eagerly and pay no capture
   bool again = false;
-  for (const auto& pr : seen_)
-    if (pr.first == r && pr.second == z) again = true;
+  for (const Seen& sn : seen_)
+    if (sn.r == r && sn.z == z && sn.Az == Az) again = true;
   if (!again) {
-    if (seen_.size() < 64) seen_.push_back({r, z});
-    body(ctx, r, z, nrhs);
+    if (seen_.size() < 64) seen_.push_back({r, z, Az});
+    body(ctx, r, z, Az, nrhs);
     return;
   }
   // capture on a private stream (the caller's may be the legacy default
@@ -728,7 +765,7 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
     QD_CUDA(ce);
   }
   try {
-    body(ctx, r, z, nrhs);
+    body(ctx, r, z, Az, nrhs);
   } catch (...) {
     cudaStreamEndCapture(cap_stream_, &graph);
     if (graph) cudaGraphDestroy(graph);
@@ -754,6 +791,7 @@ template <class C> void MGPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int n
   Graph g;
   g.r = r;
   g.z = z;
+  g.Az = Az;
   g.nrhs = nrhs;
   g.ptrs = cur;
   g.kernels = kernels;
@@ -800,7 +838,7 @@ template <class C> void MGPrecond<C>::coarse_correction(qd_ctx& ctx, const C* r,
   prolongate<C>(ctx, T, W, ec_.as<C>(), z, nrhs);
 }
 
-template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, int nrhs) {
+template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, C* Az, int nrhs) {
   coarse_correction(ctx, r, z, nrhs);
   // smoothing: z += M^{-1} (r - A z).  Plain: M^{-1} = minimal-residual
   // steps from 0, which update z in place with the residual res = r - A z.
@@ -813,7 +851,7 @@ template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, int nr
     smoother_apply<C>(ctx, *mg_, nrhs, res_.as<C>(), z, true);
     if (ls->mr_steps > 0) {
       Af->residual(ctx, r, z, res_.as<C>(), nrhs);
-      mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, ls->mr_steps, scratch_);
+      mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, ls->mr_steps, scratch_, r, Az);
     }
     return;
   }
@@ -821,7 +859,7 @@ template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, int nr
                                                                     : mg_->p.smoother_steps;
   if (nu > 0) {
     Af->residual(ctx, r, z, res_.as<C>(), nrhs);
-    mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, nu, scratch_);
+    mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, nu, scratch_, r, Az);
   }
 }
 

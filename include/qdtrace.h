@@ -232,6 +232,12 @@ int qd_prolongate(qd_mg* mg, int level, int nrhs, const double* coarse,
 /* coarse (level l+1) = W_l^H fine (level l).  Asynchronous. */
 int qd_restrict(qd_mg* mg, int level, int nrhs, const double* fine,
                 double* coarse);
+/* fine = W_l coarse in FP32, the kernel of the FP32 V-cycle: W rounded to
+ * FP32, FP32 products summed over the nv vectors of the component's
+ * chirality in index order.  coarse and fine: FP32 complex (re, im) device
+ * fields, layouts as qd_prolongate.  Asynchronous. */
+int qd_prolongate_f32(qd_mg* mg, int level, int nrhs, const float* coarse,
+                      float* fine);
 
 /* coarse (level l+1) = W_l^H fine (level l) in FP32 on the tcgen05 tensor
  * cores (the form the FP32 V-cycle uses with qd_mg_params.coarse_tc): per
@@ -615,6 +621,13 @@ int qd_smoother_apply_f32(qd_mg* mg, int nrhs, const float* in, float* out);
 void qd_autotune_set(int mode);
 /* Clear the stored choices. */
 void qd_autotune_clear(void);
+/* Testing aid: candidate k >= 0 of every tunable kernel where k applies
+ * (the default where it does not), nothing timed or stored; -1 (initial)
+ * returns to the mode above.  Process-wide.  Lets a test compare every
+ * launch shape of a kernel (coarse stencil on tensor cores: 0-3 input split
+ * into operand tiles first, at most 8/4/3/2 operand slots; 4-6 input
+ * converted in the kernel, 2/3/4 staging slots). */
+void qd_autotune_force(int candidate);
 /* The table as text, one line per shape key: the key, the chosen candidate,
  * then each candidate's best time in ms (-1: not applicable).  Writes at most
  * len bytes (NUL-terminated) to buf (nullable) and returns the full length

@@ -48,7 +48,7 @@ namespace blocktc {
 
 using namespace ptx;
 
-enum { kStencil = 0, kRestrict = 1 };
+enum { kStencil = 0, kRestrict = 1, kStencilSplit = 2 };
 
 constexpr int kThreads = 512;
 constexpr int kMaxNS = 4;  // staging ring depth
@@ -76,6 +76,51 @@ __device__ __forceinline__ bool mbar_wait_drain(uint32_t a, uint32_t parity) {
   while (!mbar_try(a, parity))
     if (gtimer() - t0 > kTimeoutNs) return false;
   return true;
+}
+
+// B tile of one input block from its compact split-BF16 coefficients sw
+// (hi block, then lo): for output row d the complex coefficients b[d][e] of
+// y[d] = sum_e b[d][e] in[e], as rows d (Re b, -Im b) and DOUT + d
+// (Im b, Re b) of B_hi (rows 0..2 DOUT) and of B_lo (2 DOUT..4 DOUT), K-major
+// with 128-byte swizzle; K chunks past DIN/4 that the MMAs read are zero.
+template <int DIN, int DOUT, int MODE>
+__device__ __forceinline__ void build_b_tile(int ct, int nct, const uint32_t* sw, unsigned char* bt) {
+  constexpr int KSTEPS = (2 * DIN + 15) / 16;
+  constexpr int KCH = 2 * KSTEPS;
+  constexpr int NV = DOUT / 2;
+  for (int idx = ct; idx < 2 * DOUT * KCH; idx += nct) {
+    const int part = idx / (DOUT * KCH);  // 0: hi, 1: lo
+    const int rem = idx - part * (DOUT * KCH);
+    const int d = rem / KCH, c = rem - d * KCH;
+    uint4 re = make_uint4(0u, 0u, 0u, 0u), im = re;
+    if (c < DIN / 4) {
+      uint32_t bw[4];
+      if (MODE != kRestrict) {
+        // b = C_dir[d][e], stored (Re, Im)
+        const uint4 cv = *reinterpret_cast<const uint4*>(sw + part * DOUT * DIN + d * DIN + 4 * c);
+        bw[0] = cv.x; bw[1] = cv.y; bw[2] = cv.z; bw[3] = cv.w;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) bw[i] ^= 0x80000000u;  // (Re b, -Im b)
+      } else {
+        // b = conj(W[e][j]) on the output's chirality, 0 across:
+        // (Re b, -Im b) = (Re W, Im W) as stored
+        const int jv = d % NV, cout = d / NV;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = 4 * c + i;
+          bw[i] = (e / (DIN / 2) == cout) ? sw[part * DIN * NV + e * NV + jv] : 0u;
+        }
+      }
+      re = make_uint4(bw[0], bw[1], bw[2], bw[3]);
+      // (Im b, Re b) from (Re b, -Im b): swap halves, negate the low one
+      im.x = __byte_perm(bw[0], 0, 0x1032) ^ 0x00008000u;
+      im.y = __byte_perm(bw[1], 0, 0x1032) ^ 0x00008000u;
+      im.z = __byte_perm(bw[2], 0, 0x1032) ^ 0x00008000u;
+      im.w = __byte_perm(bw[3], 0, 0x1032) ^ 0x00008000u;
+    }
+    *reinterpret_cast<uint4*>(bt + sw128_offset(part * 2 * DOUT + d, 8 * c)) = re;
+    *reinterpret_cast<uint4*>(bt + sw128_offset(part * 2 * DOUT + DOUT + d, 8 * c)) = im;
+  }
 }
 
 template <int DIN, int DOUT, int MODE>
@@ -289,42 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             *reinterpret_cast<uint4*>(at + kATile + off) = l;
           }
         }
-        // B: for output row d the complex coefficients b[d][e] of
-        // y[d] = sum_e b[d][e] in[e], as rows d (Re b, -Im b) and DOUT + d
-        // (Im b, Re b) of B_hi (rows 0..2 DOUT) and of B_lo (2 DOUT..4 DOUT)
-        for (int idx = ct; idx < 2 * DOUT * KCH; idx += 256) {
-          const int part = idx / (DOUT * KCH);  // 0: hi, 1: lo
-          const int rem = idx - part * (DOUT * KCH);
-          const int d = rem / KCH, c = rem - d * KCH;
-          uint4 re = make_uint4(0u, 0u, 0u, 0u), im = re;
-          if (c < DIN / 4) {
-            uint32_t bw[4];
-            if (MODE == kStencil) {
-              // b = C_dir[d][e], stored (Re, Im)
-              const uint4 cv = *reinterpret_cast<const uint4*>(sw + part * DOUT * DIN + d * DIN + 4 * c);
-              bw[0] = cv.x; bw[1] = cv.y; bw[2] = cv.z; bw[3] = cv.w;
-#pragma unroll
-              for (int i = 0; i < 4; ++i) bw[i] ^= 0x80000000u;  // (Re b, -Im b)
-            } else {
-              // b = conj(W[e][j]) on the output's chirality, 0 across:
-              // (Re b, -Im b) = (Re W, Im W) as stored
-              const int jv = d % NV, cout = d / NV;
-#pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                const int e = 4 * c + i;
-                bw[i] = (e / (DIN / 2) == cout) ? sw[part * DIN * NV + e * NV + jv] : 0u;
-              }
-            }
-            re = make_uint4(bw[0], bw[1], bw[2], bw[3]);
-            // (Im b, Re b) from (Re b, -Im b): swap halves, negate the low one
-            im.x = __byte_perm(bw[0], 0, 0x1032) ^ 0x00008000u;
-            im.y = __byte_perm(bw[1], 0, 0x1032) ^ 0x00008000u;
-            im.z = __byte_perm(bw[2], 0, 0x1032) ^ 0x00008000u;
-            im.w = __byte_perm(bw[3], 0, 0x1032) ^ 0x00008000u;
-          }
-          *reinterpret_cast<uint4*>(bt + sw128_offset(part * 2 * DOUT + d, 8 * c)) = re;
-          *reinterpret_cast<uint4*>(bt + sw128_offset(part * 2 * DOUT + DOUT + d, 8 * c)) = im;
-        }
+        build_b_tile<DIN, DOUT, MODE>(ct, 256, sw, bt);
         fence_proxy_async_smem();
         mbar_arrive(smem_u32(&afull[as]));
         mbar_arrive(smem_u32(&sempty[ss]));
@@ -341,6 +351,278 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Stencil from pre-split input tiles.
+//
+// A coarse field is read by nine output sites, so converting each staged
+// block to BF16 inside the stencil converts every value nine times.  Here
+// k_split_tiles converts the field once into the operand tiles the MMAs read
+// (split BF16, K-major, 32-byte swizzle): for site x and chunk of 128
+// right-hand sides, part p (hi, lo) and K step k (complex components
+// 8k..8k+7, re/im interleaved) one 4 KB region of 128 rows x 32 B, row r =
+// column r of the chunk.  The same number of bytes as the FP32 field.  The
+// stencil kernel then bulk-copies a neighbour's tile straight into an operand
+// slot; its converter warps only build the B tiles from the coefficients.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSplitRegion = 4096;  // 128 rows x 32 B
+
+template <int DIN>
+__host__ __device__ constexpr uint32_t split_tile_bytes() {
+  return 2u * (uint32_t)((2 * DIN + 15) / 16) * kSplitRegion;
+}
+
+template <int DIN>
+__global__ void __launch_bounds__(256) k_split_tiles(int64_t nsites, int s, int nchunks, const float2* __restrict__ in,
+                                                    unsigned char* __restrict__ tiles) {
+  constexpr int KSTEPS = (2 * DIN + 15) / 16;
+  const int64_t tot = nsites * nchunks * KSTEPS * 128;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t & 127);
+    int64_t u = t >> 7;
+    const int k = (int)(u % KSTEPS);
+    u /= KSTEPS;
+    const int ch = (int)(u % nchunks);
+    const int64_t x = u / nchunks;
+    const int rr = ch * 128 + r;
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int e = 8 * k + i;
+      float2 v = make_float2(0.f, 0.f);
+      if (e < DIN && rr < s) v = in[(x * DIN + e) * (int64_t)s + rr];
+      split_bf16x2(v.x, v.y, hi[i], lo[i]);
+    }
+    unsigned char* tb = tiles + (size_t)(x * nchunks + ch) * split_tile_bytes<DIN>();
+    unsigned char* ph = tb + (size_t)k * kSplitRegion;
+    unsigned char* pl = tb + (size_t)(KSTEPS + k) * kSplitRegion;
+    *reinterpret_cast<uint4*>(ph + sw32_offset(r, 0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(ph + sw32_offset(r, 1)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+    *reinterpret_cast<uint4*>(pl + sw32_offset(r, 0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4*>(pl + sw32_offset(r, 1)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+  }
+}
+
+// y(x) = sum_dir C_dir(x) in(nb(x, dir)) from pre-split tiles.  One
+// persistent CTA per SM; each operand slot holds one direction's A tile
+// (bulk-copied), its compact coefficients (bulk-copied) and its B tile
+// (built by the converter warps).  Roles as in k_block_tc; barriers per
+// slot: full (copies landed), bready (B tile built), empty (MMAs done).
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_stencil_tc_split(int64_t nout, int s, int nchunks, int NA, uint32_t slot_bytes, uint32_t b_tile,
+                       const int* __restrict__ src, const uint32_t* __restrict__ Bsrc,
+                       const unsigned char* __restrict__ tiles, float2* __restrict__ out, int* __restrict__ err) {
+  constexpr int NSTEP = 9;
+  constexpr int KSTEPS = (2 * D + 15) / 16;
+  constexpr int NCOL = 2 * D;
+  constexpr uint32_t kTile = split_tile_bytes<D>();
+  constexpr uint32_t kBWords = 2u * D * D;
+  constexpr uint32_t kCBytes = kBWords * 4u;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kMaxNA], bready[kMaxNA], empty[kMaxNA];
+  __shared__ __align__(8) uint64_t accf[2], acce[2], drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // slot layout: A tile (kTile), B tile (b_tile), coefficients (kCBytes)
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - smem_u32(smem_raw));
+  const uint32_t b_off = kTile, c_off = kTile + b_tile;
+  const int64_t total = nout * (int64_t)nchunks;
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int i = 0; i < NA; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&bready[i]), 256);
+      mbar_init(smem_u32(&empty[i]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf[b]), 1);
+      mbar_init(smem_u32(&acce[b]), 128);
+    }
+    mbar_init(smem_u32(&drain), 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(smem_u32(&tmem_base), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- bulk-copy producer ----
+      int last_use[kMaxNA];
+      for (int i = 0; i < kMaxNA; ++i) last_use[i] = -1;
+      int64_t q = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
+        const int64_t x = it / nchunks;
+        const int ch = (int)(it - x * nchunks);
+        for (int j = 0; j < NSTEP; ++j, ++q) {
+          const int as = (int)(q % NA), ua = (int)(q / NA);
+          if (ua > 0 && !mbar_wait(smem_u32(&empty[as]), (uint32_t)(ua - 1) & 1u, &abort_flag)) {
+            atomicExch(err, 21);
+            abort_flag = 1;
+            ok = false;
+            break;
+          }
+          const int64_t nb = src[x * NSTEP + j];
+          const uint32_t slot = base + (uint32_t)as * slot_bytes;
+          const uint32_t bar = smem_u32(&full[as]);
+          mbar_expect_tx(bar, kTile + kCBytes);
+          bulk_g2s(slot, tiles + (size_t)(nb * nchunks + ch) * kTile, kTile, bar);
+          bulk_g2s(slot + c_off, Bsrc + (x * NSTEP + j) * (int64_t)kBWords, kCBytes, bar);
+          last_use[as] = ua;
+        }
+      }
+      // copies still in flight land before the CTA may exit
+      for (int i = 0; i < NA; ++i)
+        if (last_use[i] >= 0 && !mbar_wait_drain(smem_u32(&full[i]), (uint32_t)last_use[i] & 1u)) atomicExch(err, 22);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      const uint32_t idesc2 = idesc_bf16(128, 2 * NCOL);  // A_hi x [B_hi; B_lo]
+      const uint32_t idesc1 = idesc_bf16(128, NCOL);      // A_lo x B_hi
+      int64_t q = 0;
+      int li = 0;
+      bool issued = false, ok = true;
+      for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x, ++li) {
+        const int b = li & 1, ub = li >> 1;
+        if (ub > 0 && !mbar_wait(smem_u32(&acce[b]), (uint32_t)(ub - 1) & 1u, &abort_flag)) {
+          atomicExch(err, 23);
+          abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)b * kAccStride;
+        for (int j = 0; j < NSTEP; ++j, ++q) {
+          const int as = (int)(q % NA), ua = (int)(q / NA);
+          if (!mbar_wait(smem_u32(&full[as]), (uint32_t)ua & 1u, &abort_flag) ||
+              !mbar_wait(smem_u32(&bready[as]), (uint32_t)ua & 1u, &abort_flag)) {
+            atomicExch(err, 24);
+            abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t at = base + (uint32_t)as * slot_bytes;
+          const uint32_t bt = at + b_off;
+#pragma unroll
+          for (int k = 0; k < KSTEPS; ++k) {
+            const uint64_t bdesc = sdesc_sw128(bt + (uint32_t)k * 32u);
+            mma_bf16(acc, sdesc_sw32(at + (uint32_t)k * kSplitRegion), bdesc, idesc2, (j > 0 || k > 0) ? 1u : 0u);
+            mma_bf16(acc, sdesc_sw32(at + (uint32_t)(KSTEPS + k) * kSplitRegion), bdesc, idesc1, 1u);
+          }
+          mma_commit(smem_u32(&empty[as]));
+          issued = true;
+        }
+        if (ok) mma_commit(smem_u32(&accf[b]));
+      }
+      if (issued) {
+        mma_commit(smem_u32(&drain));
+        if (!mbar_wait_drain(smem_u32(&drain), 0)) atomicExch(err, 25);
+      }
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ---- epilogue: TMEM -> y ----
+    const int ew = warp - 4;
+    const int r = ew * 32 + lane;
+    int li = 0;
+    for (int64_t it = blockIdx.x; it < total; it += gridDim.x, ++li) {
+      const int64_t x = it / nchunks;
+      const int r0 = (int)(it - x * nchunks) * 128;
+      const int w = min(128, s - r0);
+      const int b = li & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf[b]), (uint32_t)(li >> 1) & 1u, &abort_flag));
+      if (!ok) {
+        if (lane == 0) atomicExch(err, 26);
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      float v[NCOL];
+      const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)b * kAccStride;
+#pragma unroll
+      for (int c0 = 0; c0 < NCOL; c0 += 16) {
+        uint32_t u0[16], u1[16];
+        tmem_ld16(taddr + (uint32_t)c0, u0);
+        tmem_ld16(taddr + (uint32_t)(NCOL + c0), u1);
+        tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[c0 + i] = __uint_as_float(u0[i]) + __uint_as_float(u1[i]);
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&acce[b]));
+      if (r < w) {
+        float2* o = out + x * D * (int64_t)s + r0 + r;
+#pragma unroll
+        for (int d = 0; d < D; ++d) o[(int64_t)d * s] = make_float2(v[d], v[D + d]);
+      }
+    }
+  } else if (warp >= 8) {
+    // ---- converters: compact coefficients -> B tiles ----
+    const int ct = tid - 256;
+    int64_t q = 0;
+    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+      bool ok = true;
+      for (int j = 0; j < NSTEP; ++j, ++q) {
+        const int as = (int)(q % NA), ua = (int)(q / NA);
+        if (!mbar_wait(smem_u32(&full[as]), (uint32_t)ua & 1u, &abort_flag)) {
+          atomicExch(err, 27);
+          abort_flag = 1;
+          ok = false;
+          break;
+        }
+        unsigned char* slot = gbase + (size_t)as * slot_bytes;
+        build_b_tile<D, D, kStencilSplit>(ct, 256, reinterpret_cast<const uint32_t*>(slot + c_off), slot + b_off);
+        fence_proxy_async_smem();
+        mbar_arrive(smem_u32(&bready[as]));
+      }
+      if (!ok) break;
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    __syncwarp();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// Split `in` (nsites x D x s, FP32) into `tiles` and apply the stencil from
+// them; false (nothing launched) when fewer than two operand slots fit.
+template <int D>
+bool launch_split(qd_ctx& ctx, int64_t nout, const int* src, const uint32_t* Bsrc, const cplxf* in, unsigned char* tiles,
+                  cplxf* out, int s, int* err, int NA_max) {
+  constexpr uint32_t kTile = split_tile_bytes<D>();
+  constexpr int KSTEPS = (2 * D + 15) / 16;
+  const int nchunks = (s + 127) / 128;
+  const uint32_t b_tile = (uint32_t)((4 * D * 128 + 1023) / 1024 * 1024);
+  const uint32_t c_bytes = (uint32_t)((2u * D * D * 4u + 1023) / 1024 * 1024);
+  const uint32_t slot = kTile + b_tile + c_bytes;
+  const size_t budget = 220 * 1024;
+  int NA = (int)((budget - 1024) / slot);
+  if (NA > NA_max) NA = NA_max;
+  if (NA > kMaxNA) NA = kMaxNA;
+  if (NA < 2) return false;
+  const int64_t st = nout * nchunks * KSTEPS * 128;
+  const int sgrid = (int)(div_up(st, 256) < 16 * kNumSMs ? div_up(st, 256) : 16 * kNumSMs);
+  k_split_tiles<D><<<sgrid, 256, 0, ctx.stream>>>(nout, s, nchunks, reinterpret_cast<const float2*>(in), tiles);
+  QD_LAUNCH_CHECK();
+  const size_t smem = 1024 + (size_t)NA * slot;
+  ensure_smem_limit(reinterpret_cast<const void*>(k_stencil_tc_split<D>), smem);
+  const int64_t items = nout * (int64_t)nchunks;
+  const int grid = (int)(items < kNumSMs ? items : kNumSMs);
+  k_stencil_tc_split<D><<<grid, kThreads, smem, ctx.stream>>>(nout, s, nchunks, NA, slot, b_tile, src, Bsrc, tiles,
+                                                              reinterpret_cast<float2*>(out), err);
+  QD_LAUNCH_CHECK();
+  return true;
+}
 
 // Launch k_block_tc with NS staging slots and as many operand stages as fit
 // (at most kMaxNA); false (nothing launched) when fewer than two fit.

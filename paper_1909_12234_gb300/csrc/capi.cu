@@ -275,6 +275,20 @@ int qd_prolongate(qd_mg* mg, int level, int nrhs, const double* coarse, double* 
   });
 }
 
+int qd_prolongate_f32(qd_mg* mg, int level, int nrhs, const float* coarse, float* fine) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(coarse);
+    NONNULL(fine);
+    QD_REQUIRE(level >= 0 && level < mg->nlevels, "level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    set_device(mg->ctx);
+    const qd::cplxf* W = mg->W<qd::cplxf>(level);
+    qd::prolongate<qd::cplxf>(*mg->ctx, *mg->T[level], W, reinterpret_cast<const qd::cplxf*>(coarse),
+                              reinterpret_cast<qd::cplxf*>(fine), nrhs);
+  });
+}
+
 int qd_restrict(qd_mg* mg, int level, int nrhs, const double* fine, double* coarse) {
   return guarded([&] {
     NONNULL(mg);
@@ -895,6 +909,7 @@ int qd_smoother_apply_f32(qd_mg* mg, int nrhs, const float* in, float* out) {
 
 void qd_autotune_set(int mode) { qd::tune_set_mode(mode); }
 void qd_autotune_clear(void) { qd::tune_clear(); }
+void qd_autotune_force(int candidate) { qd::tune_force(candidate); }
 int qd_autotune_report(char* buf, int len) {
   const std::string r = qd::tune_report();
   if (buf && len > 0) {

@@ -78,6 +78,50 @@ __global__ void k_prolong(int64_t nfine, int Df, int nv, int nrhs, const int* __
   }
 }
 
+// FP32 form with the aggregate's values in registers: thread (s, rp) holds
+// coarse[agg(s)][c nv + j][2rp, 2rp + 1] for one chirality c at a time and
+// forms fine[s][a][2rp, 2rp + 1] for the Df/2 components a of that
+// chirality; W[s][a][.] is the same for every thread of a site (broadcast
+// loads of two entries at a time).  Same products in the same order as
+// k_prolong, so the results are identical.
+template <int NV>
+__global__ void __launch_bounds__(256) k_prolong_f32x2(int64_t nfine, int Df, int nrhs2, const int* __restrict__ agg_of,
+                                                      const float4* __restrict__ W, const float4* __restrict__ coarse,
+                                                      float4* __restrict__ fine) {
+  const int64_t tot = nfine * nrhs2;
+  const int half = Df / 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int rp = (int)(e % nrhs2);
+    const int64_t s = e / nrhs2;
+    const int64_t x = agg_of[s];
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      float4 cv[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) cv[j] = coarse[(x * 2 * NV + c * NV + j) * nrhs2 + rp];
+#pragma unroll 1
+      for (int a = c * half; a < (c + 1) * half; ++a) {
+        const float4* w = W + (s * Df + a) * (NV / 2);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < NV / 2; ++jj) {
+          const float4 wv = __ldg(w + jj);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float wr = h ? wv.z : wv.x, wi = h ? wv.w : wv.y;
+            const float4 v = cv[2 * jj + h];
+            acc.x = fmaf(wr, v.x, fmaf(-wi, v.y, acc.x));
+            acc.y = fmaf(wr, v.y, fmaf(wi, v.x, acc.y));
+            acc.z = fmaf(wr, v.z, fmaf(-wi, v.w, acc.z));
+            acc.w = fmaf(wr, v.w, fmaf(wi, v.z, acc.w));
+          }
+        }
+        fine[(s * Df + a) * nrhs2 + rp] = acc;
+      }
+    }
+  }
+}
+
 // Restriction: coarse[x][c nv + j][r] = sum_{s in x, a in c} conj(W[s][a][j]) fine[s][a][r]
 template <class C>
 __global__ void k_restrict(int64_t ncoarse, int bsites, int Df, int nv, int nrhs,
@@ -154,6 +198,24 @@ void prolongate(qd_ctx& ctx, const Transfer& T, const C* W, const C* coarse, C* 
   const double cb = (double)sizeof(C);
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_PROLONG_F64 : QD_PROF_PROLONG_F32, 8.0 * T.nv * (double)tot,
                cb * ((double)T.nfine * T.Df * T.nv + (double)tot + (double)T.ncoarse * T.Dc * nrhs));
+  const bool al16 = ((reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(coarse) |
+                      reinterpret_cast<uintptr_t>(fine)) & 15) == 0;
+  if (sizeof(C) == sizeof(cplxf) && nrhs % 2 == 0 && al16 && (T.nv == 8 || T.nv == 12 || T.nv == 16)) {
+    const int64_t t2 = T.nfine * (nrhs / 2);
+    const int grid = (int)(div_up(t2, 256) < 16 * kNumSMs ? div_up(t2, 256) : 16 * kNumSMs);
+    const int nr2 = nrhs / 2;
+    const int* ag = T.agg_of.as<int>();
+    const float4* w4 = reinterpret_cast<const float4*>(W);
+    const float4* c4 = reinterpret_cast<const float4*>(coarse);
+    float4* f4 = reinterpret_cast<float4*>(fine);
+    switch (T.nv) {
+      case 8: k_prolong_f32x2<8><<<grid, 256, 0, ctx.stream>>>(T.nfine, T.Df, nr2, ag, w4, c4, f4); break;
+      case 12: k_prolong_f32x2<12><<<grid, 256, 0, ctx.stream>>>(T.nfine, T.Df, nr2, ag, w4, c4, f4); break;
+      default: k_prolong_f32x2<16><<<grid, 256, 0, ctx.stream>>>(T.nfine, T.Df, nr2, ag, w4, c4, f4); break;
+    }
+    QD_LAUNCH_CHECK();
+    return;
+  }
   k_prolong<C><<<div_up(tot, 256) < 32 * kNumSMs ? div_up(tot, 256) : 32 * kNumSMs, 256, 0, ctx.stream>>>(
       T.nfine, T.Df, T.nv, nrhs, T.agg_of.as<int>(), W, coarse, fine);
   QD_LAUNCH_CHECK();

@@ -12,6 +12,8 @@ namespace qd {
 
 namespace {
 
+constexpr int kCoarseTcCandidates = 7;
+
 // Compact split-BF16 copy of the stencil: for block (x, dir) of D x D
 // entries, Cb[(x*9 + dir)][0][d][e] = hi and [1][d][e] = lo of (Re, Im) C,
 // each pair one 32-bit word (real part in the low half).
@@ -30,6 +32,14 @@ template <int D>
 bool launch(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int s, int* err, int NS) {
   return blocktc::launch<D, D, blocktc::kStencil>(ctx, lv.geo.nsites, 9, lv.sten_src.as<int>(),
                                                   lv.Cmb.as<uint32_t>(), in, out, s, err, NS);
+}
+
+template <int D>
+bool launch_split(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int s, int* err, int NA) {
+  const size_t need = (size_t)lv.geo.nsites * ((s + 127) / 128) * blocktc::split_tile_bytes<D>();
+  if (lv.ctc_tiles.bytes() < need) lv.ctc_tiles.resize(need);
+  return blocktc::launch_split<D>(ctx, lv.geo.nsites, lv.sten_src.as<int>(), lv.Cmb.as<uint32_t>(), in,
+                                  lv.ctc_tiles.as<unsigned char>(), out, s, err, NA);
 }
 
 }  // namespace
@@ -72,22 +82,35 @@ void coarse_apply_tc(qd_ctx& ctx, CoarseLevel& lv, const cplxf* in, cplxf* out, 
   ProfScope ps(ctx, QD_PROF_COARSE_TC, 72.0 * D * D * (double)lv.geo.nsites * s,
                (double)lv.geo.nsites * (9.0 * D * D * 8.0 + 2.0 * D * 8.0 * s));
   int* err = lv.ctc_err.as<int>();
-  // candidates: 2, 3 or 4 staging slots (deeper prefetch against fewer
-  // operand stages); every candidate computes the same sums in the same order
+  // candidates 0-3: the input split once into operand tiles first
+  // (k_split_tiles), at most 8, 4, 3 or 2 operand slots; 4-6: the input
+  // blocks converted inside the kernel with 2, 3 or 4 staging slots.  Every
+  // candidate forms the same BF16 operands and issues the same MMAs in the
+  // same order.
   auto go = [&](int c) -> bool {
-    const int NS = 2 + c;
+    if (c >= 4) {
+      const int NS = c - 2;
+      switch (lv.D) {
+        case 8: return launch<8>(ctx, lv, in, out, s, err, NS);
+        case 16: return launch<16>(ctx, lv, in, out, s, err, NS);
+        case 24: return launch<24>(ctx, lv, in, out, s, err, NS);
+        default: return launch<32>(ctx, lv, in, out, s, err, NS);
+      }
+    }
+    static const int kNA[4] = {8, 4, 3, 2};
+    const int NA = kNA[c];
     switch (lv.D) {
-      case 8: return launch<8>(ctx, lv, in, out, s, err, NS);
-      case 16: return launch<16>(ctx, lv, in, out, s, err, NS);
-      case 24: return launch<24>(ctx, lv, in, out, s, err, NS);
-      default: return launch<32>(ctx, lv, in, out, s, err, NS);
+      case 8: return launch_split<8>(ctx, lv, in, out, s, err, NA);
+      case 16: return launch_split<16>(ctx, lv, in, out, s, err, NA);
+      case 24: return launch_split<24>(ctx, lv, in, out, s, err, NA);
+      default: return launch_split<32>(ctx, lv, in, out, s, err, NA);
     }
   };
   const std::string key = "coarse_tc D" + std::to_string(lv.D) + " sites" + std::to_string(lv.geo.nsites) + " rhs" +
                           std::to_string(s);
-  const int c = tune_pick(ctx, key, 3, go);
+  const int c = tune_pick(ctx, key, kCoarseTcCandidates, go);
   if (c >= 0 && go(c)) return;
-  for (int d = 0; d < 3; ++d)
+  for (int d = 0; d < kCoarseTcCandidates; ++d)
     if (go(d)) return;
   fail(QD_ERR_INVALID, "tensor-core coarse stencil: operand tiles do not fit in shared memory");
 }

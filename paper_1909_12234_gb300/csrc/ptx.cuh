@@ -77,6 +77,22 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
   d |= (uint64_t)2 << 61;            // 128-byte swizzle
   return d;
 }
+// Shared-memory matrix descriptor: K-major operand, 32-byte swizzle (rows
+// of 32 B = one K step of 16 BF16 elements), 8-row core groups 256 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;           // leading byte offset (unused: one atom along K)
+  d |= (uint64_t)(256 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;           // descriptor version
+  d |= (uint64_t)6 << 61;           // 32-byte swizzle
+  return d;
+}
+// Byte offset of 16-byte half `half` of row `row` in a K-major 32-byte-swizzled
+// tile (256-byte aligned base): the halves of rows with bit 2 set trade places.
+__host__ __device__ __forceinline__ uint32_t sw32_offset(int row, int half) {
+  return (uint32_t)((row >> 3) * 256 + (row & 7) * 32 + (((half ^ (row >> 2)) & 1) << 4));
+}
 // Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);

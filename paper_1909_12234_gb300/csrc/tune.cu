@@ -22,6 +22,7 @@ std::map<std::string, Entry>& table() {
   return t;
 }
 std::atomic<int> g_mode{1};
+std::atomic<int> g_force{-1};
 
 bool capturing(cudaStream_t s) {
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
@@ -32,6 +33,7 @@ bool capturing(cudaStream_t s) {
 }  // namespace
 
 void tune_set_mode(int mode) { g_mode.store(mode ? 1 : 0); }
+void tune_force(int candidate) { g_force.store(candidate >= 0 ? candidate : -1); }
 int tune_mode() { return g_mode.load(); }
 
 void tune_clear() {
@@ -51,6 +53,8 @@ std::string tune_report() {
 }
 
 int tune_pick(qd_ctx& ctx, const std::string& key, int ncand, const std::function<bool(int)>& launch) {
+  const int forced = g_force.load();
+  if (forced >= 0) return forced < ncand ? forced : -1;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = table().find(key);

@@ -25,6 +25,9 @@ int tune_pick(qd_ctx& ctx, const std::string& key, int ncand, const std::functio
 
 // 0: defaults only; 1: tune on first use (the library's default).
 void tune_set_mode(int mode);
+// >= 0: tune_pick returns this candidate (when < ncand) without timing;
+// -1: normal selection.
+void tune_force(int candidate);
 int tune_mode();
 // The table as text, one line per key: key, chosen candidate, then the
 // measured time (ms) of every candidate (-1: not applicable).

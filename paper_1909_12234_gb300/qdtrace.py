@@ -166,6 +166,7 @@ SIGNATURES = {
     "qd_coarse_apply_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_apply_tc": (_I, [_P, _I, _I, _P, _P]),
     "qd_restrict_tc": (_I, [_P, _I, _I, _P, _P]),
+    "qd_prolongate_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_solver_params_default": (None, [ctypes.POINTER(SolverParams)]),
@@ -191,6 +192,7 @@ SIGNATURES = {
     "qd_smoother_apply_f32": (_I, [_P, _I, _P, _P]),
     "qd_autotune_set": (None, [_I]),
     "qd_autotune_clear": (None, []),
+    "qd_autotune_force": (None, [_I]),
     "qd_autotune_report": (_I, [ctypes.c_char_p, _I]),
     "qd_hutchinson_batch": (_I, [_P, _I, ctypes.POINTER(BatchItem), _I]),
     "qd_mg_subspace_sines": (_I, [_P, _I, _I, _P, _DPTR]),
@@ -449,6 +451,10 @@ def coarse_apply_tc(mg, level, nrhs, inp, out):
     _check(load().qd_coarse_apply_tc(mg.h, int(level), int(nrhs), _ptr64(inp), _ptr64(out)))
 
 
+def prolongate_f32(mg, level, nrhs, coarse, fine):
+    _check(load().qd_prolongate_f32(mg.h, int(level), int(nrhs), _ptr64(coarse), _ptr64(fine)))
+
+
 def restrict_tc(mg, level, nrhs, fine, coarse):
     _check(load().qd_restrict_tc(mg.h, int(level), int(nrhs), _ptr64(fine), _ptr64(coarse)))
 
@@ -684,6 +690,11 @@ def autotune_set(mode):
 
 def autotune_clear():
     load().qd_autotune_clear()
+
+
+def autotune_force(candidate):
+    """Candidate k of every tunable kernel where it applies; -1: normal."""
+    load().qd_autotune_force(int(candidate))
 
 
 def autotune_report():

@@ -33,6 +33,7 @@ from gpu_util import dev, host, need_gpu, torch
 pytestmark = pytest.mark.gpu
 
 U_BF16 = 2.0 ** -8
+N_TC_CANDIDATES = 7  # launch shapes of the tensor-core stencil
 
 
 @pytest.fixture(scope="module")
@@ -126,6 +127,17 @@ def test_tensor_core_coarse_stencil(qd, ctx, dims, m0, blocks, nvs):
             out2 = torch.empty_like(xd)
             qd.coarse_apply_tc(mg, l + 1, s, xd, out2)
             assert torch.equal(out, out2)
+            # every launch shape (input split into operand tiles first, or
+            # converted inside the kernel; operand/staging ring depths) forms
+            # the same operands and MMAs: the same bits
+            try:
+                for cand in range(N_TC_CANDIDATES):
+                    qd.autotune_force(cand)
+                    out3 = torch.full_like(xd, float("nan"))
+                    qd.coarse_apply_tc(mg, l + 1, s, xd, out3)
+                    assert torch.equal(out, out3), (l, s, cand)
+            finally:
+                qd.autotune_force(-1)
     for o in (mg, g):
         o.close()
 

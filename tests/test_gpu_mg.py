@@ -96,6 +96,33 @@ def test_coarse_stencil_fp64_fp32_rhs_counts(qd, ctx, dims, m0, blocks, nvs):
             assert rel_err(host(o32).astype(np.complex128).reshape(nc, s), ref) < 5e-5, (l, s)
 
 
+@pytest.mark.parametrize("dims,m0,blocks,nvs", CASES + [((8, 8, 8, 8), -0.8, [(2, 2, 2, 2), (2, 2, 2, 2)], [12, 16]),
+                                                        ((4, 4, 4, 8), -0.6, [(2, 2, 2, 2), (1, 1, 2, 2)], [8, 8])])
+def test_prolongation_fp32(qd, ctx, dims, m0, blocks, nvs):
+    # the FP32 prolongation of the V-cycle (register-blocked two-column form
+    # for even counts, scalar form for odd ones) against the oracle's W c:
+    # nv FP32 complex products per output plus the rounding of W and c, so
+    # |error| <= 4 (nv + 2) 2^-24 (|W| |c|) elementwise
+    U, g, mg, H = _build(qd, ctx, dims, m0, blocks, nvs)
+    rng = np.random.default_rng(11)
+    for l, T in enumerate(H.transfers):
+        Wabs = T.matrix().copy()
+        Wabs.data = np.abs(Wabs.data)
+        for s in (1, 2, 3, 64, 130):
+            c = rng.standard_normal((T.nc, s)) + 1j * rng.standard_normal((T.nc, s))
+            c32 = dev(c).to(torch.complex64)
+            c_r = host(c32).astype(np.complex128)  # the rounded input both sides use
+            ref = T.prolong(c_r)
+            fine = torch.empty((T.level.n * s,), dtype=torch.complex64, device="cuda:0")
+            qd.prolongate_f32(mg, l, s, c32, fine)
+            got = host(fine).astype(np.complex128)
+            if l == 0:
+                got = qd.from_qd(ctx, g, torch.from_numpy(got).to("cuda:0").reshape(g.V, 12, s))
+            got = np.asarray(got).reshape(T.level.n, s)
+            bound = 4 * (T.nv + 2) * 2.0 ** -24 * (Wabs @ np.abs(c_r)) + 1e-30
+            assert np.all(np.abs(got - ref) <= bound), (l, s, np.max(np.abs(got - ref) / bound))
+
+
 def test_null_vector_iteration(qd, ctx):
     # the full adaptive setup (MR on A y = 0 to 1e-2 / 200 steps): the same
     # step counts per vector as the oracle, an orthonormal chiral W, and a

@@ -53,9 +53,9 @@ import numpy as np  # noqa: E402
 CONFIG3 = dict(
     workload="wilson-dirac 16^3x32 eps0.2 seed3 m0=-0.8, 3-level MG (2^4, 2^4; nv 12, 16; level-1 GCR 6 its; "
              "coarse MR 2), Algorithm 2 k=24 on the coarsest level, 128 Rademacher samples/step, learned smoother "
-             "+ 1 MR, FP32 inner solves with FP64 refinement to true rel. residual 1e-8",
+             "+ 1 MR, FP32 GCR(8) inner solves with FP64 refinement to true rel. residual 1e-8",
     dims=(16, 16, 16, 32), eps=0.2, link_seed=3, m0=-0.8, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16],
-    k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=16, maxit=500, inner_tol=1e-5,
+    k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=8, maxit=500, inner_tol=1e-5,
     mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6, "coarse_smoother_steps": 2},
     learned=1, eig_maxit=30, fp64_samples=16,
 )
@@ -198,7 +198,8 @@ def _batch(qd, ctx, g, mg, d, offset, precision, nsamples=None, wl=None):
     wl = WL if wl is None else wl
     return qd.hutchinson_trace(ctx, g, mg, d, wl["m0"], 0.0, seed=wl["noise_seed"], sample_offset=offset,
                                nsamples=wl["s"] if nsamples is None else nsamples, tol=wl["tol"], maxit=wl["maxit"],
-                               restart=wl["restart"], precision=precision, inner_tol=wl["inner_tol"], max_refine=10)
+                               restart=wl["restart"], precision=precision, inner_tol=wl["inner_tol"], max_refine=10,
+                               **({"schur": wl["schur"]} if wl.get("schur") else {}))
 
 
 def _oracle_iteration_seconds(dims, eps, link_seed, m0, blocks, nvs, mg_kw, noise_seed, iters=1):
@@ -310,6 +311,61 @@ def stencil_roofline(qd, ctx, reps=20):
                      "tflops": 1368.0 * V * nrhs / (ms / 1e3) / 1e12}
         del x, y
     g.close()
+    return out
+
+
+def kernel_only(qd, ctx, names, reps=20):
+    """Hot kernels alone on the shapes of the 16^3 x 32 workload (a profiling
+    target): the FP32 V-cycle's level-1 stencil on tensor cores (8192 sites,
+    D = 24, split pass included), the restriction fine -> level 1 on tensor
+    cores, the FP32 prolongation level 1 -> fine and level 2 -> level 1, and
+    the FP32 Wilson stencil; 128 right-hand sides.  The hierarchy takes
+    random blocked vectors (no null-vector iteration: the kernels' cost does
+    not depend on W) and no dense coarsest inverse.  Algorithmic bytes as in
+    the bench's per-kernel table; every field is larger than L2 except the
+    level-2 field."""
+    import torch
+    from paper_1909_12234_gb300 import synth
+    dims, s = (16, 16, 16, 32), 128
+    U = synth.random_su3_links(dims, 0.2, 3)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, -0.8, 0.0, qd.mg_params(2, [(2, 2, 2, 2), (2, 2, 2, 2)], [12, 16], null_maxit=0,
+                                                       seed=5, coarsest_direct=0))
+    dev = f"cuda:{ctx.device}"
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    V = g.V
+    n1, n2 = 8192 * 24, 512 * 32
+    x0 = torch.randn((V * 12, s), dtype=torch.complex64, device=dev)
+    y0 = torch.empty_like(x0)
+    x1 = torch.randn((n1, s), dtype=torch.complex64, device=dev)
+    y1 = torch.empty_like(x1)
+    x2 = torch.randn((n2, s), dtype=torch.complex64, device=dev)
+    cases = {
+        "coarse_tc": (lambda: qd.coarse_apply_tc(mg, 1, s, x1, y1), 8192 * (9 * 24 * 24 * 8.0 + 2 * 24 * 8.0 * s)),
+        "restrict_tc": (lambda: qd.restrict_tc(mg, 0, s, x0, x1),
+                        8.0 * (V * 12 * 12 + V * 12 * s + 8192 * 24 * s)),
+        "prolong_l1": (lambda: qd.prolongate_f32(mg, 0, s, x1, y0), 8.0 * (V * 12 * 12 + V * 12 * s + n1 * s)),
+        "prolong_l2": (lambda: qd.prolongate_f32(mg, 1, s, x2, y1), 8.0 * (8192 * 24 * 16 + n1 * s + n2 * s)),
+        "wilson_f32": (lambda: qd.dirac_apply_f32(ctx, g, -0.8, 0.0, False, s, x0, y0), V * (24.0 * 8 * s + 36.0 * 8)),
+    }
+    out = {"lattice": "16^3x32", "nrhs": s, "peak_gbs": hbm}
+    for name in names:
+        fn, nbytes = cases[name]
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(reps):
+            fn()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out[name] = {"ms_per_launch": ms, "alg_bytes": nbytes, "achieved_gbs": gbs, "frac": gbs / hbm}
+    out["autotune"] = qd.autotune_report()
+    for o in (mg, g):
+        o.close()
     return out
 
 
@@ -1012,7 +1068,31 @@ def main():
                          "0: plain smoother; default: the workload's setting")
     ap.add_argument("--fixed-coarse", type=int, default=0,
                     help="> 0: level-1 GCR of a three-level hierarchy runs exactly this many iterations")
+    ap.add_argument("--restart", type=int, default=0, help="> 0: restart length of the fine-level GCR")
+    ap.add_argument("--inner-tol", type=float, default=0.0, help="> 0: tolerance of the FP32 inner solves")
+    ap.add_argument("--schur", type=int, default=-1,
+                    help="1: even-odd fine solves (GCR on the odd-site Schur complement); 0: full lattice; "
+                         "default: the workload's setting")
+    ap.add_argument("--kernel", default="",
+                    help="comma-separated hot kernels timed alone on the 16^3 x 32 shapes (a profiling target): "
+                         "coarse_tc, restrict_tc, prolong_l1, prolong_l2, wilson_f32; 'all' for every one")
+    ap.add_argument("--reps", type=int, default=20, help="launches timed per kernel with --kernel")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="launch shapes fixed at their defaults (nothing timed by the autotuner)")
     args = ap.parse_args()
+    if args.no_tune:
+        from paper_1909_12234_gb300 import qdtrace as qd
+        qd.load()
+        qd.autotune_set(0)
+    if args.kernel:
+        from paper_1909_12234_gb300 import qdtrace as qd
+        qd.load()
+        ctx = qd.Context(0)
+        names = (["coarse_tc", "restrict_tc", "prolong_l1", "prolong_l2", "wilson_f32"] if args.kernel == "all"
+                 else args.kernel.split(","))
+        print(json.dumps({"kernels_alone": kernel_only(qd, ctx, names, args.reps)}))
+        ctx.close()
+        return 0
     if args.stencil_only:
         from paper_1909_12234_gb300 import qdtrace as qd
         qd.load()
@@ -1037,6 +1117,12 @@ def main():
         WL["mg_kw"] = dict(WL.get("mg_kw", {}), coarse_smoother_steps=args.coarse_smoother_steps)
     if args.learned >= 0:
         WL["learned"] = args.learned
+    if args.restart > 0:
+        WL["restart"] = args.restart
+    if args.inner_tol > 0:
+        WL["inner_tol"] = args.inner_tol
+    if args.schur >= 0:
+        WL["schur"] = args.schur
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

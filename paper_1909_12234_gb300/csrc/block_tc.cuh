@@ -70,6 +70,16 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uin
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+// Source indices the producer loads one item ahead.
+constexpr int kPrefetch = 16;
+__device__ __forceinline__ void prefetch_src(const int* __restrict__ src, int nstep, int nchunks, int64_t total,
+                                             int64_t item, int pre[kPrefetch]) {
+  const bool valid = item < total;
+  const int64_t x = valid ? item / nchunks : 0;
+#pragma unroll
+  for (int j = 0; j < kPrefetch; ++j) pre[j] = (valid && j < nstep) ? src[x * nstep + j] : 0;
+}
+
 // Wait that ignores the abort flag (used to drain work already in flight).
 __device__ __forceinline__ bool mbar_wait_drain(uint32_t a, uint32_t parity) {
   const uint64_t t0 = gtimer();
@@ -138,6 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t kCBytes = kBWords * 4u;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t sfull[kMaxNS], sempty[kMaxNS], afull[kMaxNA], aempty[kMaxNA];
+  __shared__ int s_src[kPrefetch];  // the producer's source indices of the current item
   __shared__ __align__(8) uint64_t accf[2], acce[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
@@ -177,11 +188,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int i = 0; i < kMaxNS; ++i) last_use[i] = -1;
       int64_t q = 0;
       bool ok = true;
+      // the first kPrefetch source indices of the next item are loaded while
+      // the current item's copies are issued (no memory round trip per step)
+      int pre[kPrefetch];
+      prefetch_src(src, nstep, nchunks, total, (int64_t)blockIdx.x, pre);
       for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
         const int64_t x = it / nchunks;
         const int r0 = (int)(it - x * nchunks) * 128;
         const int w = min(128, s - r0);
         const uint32_t vbytes = (uint32_t)DIN * w * 8u;
+#pragma unroll
+        for (int j = 0; j < kPrefetch; ++j) s_src[j] = pre[j];
+        prefetch_src(src, nstep, nchunks, total, it + gridDim.x, pre);
         for (int j = 0; j < nstep; ++j, ++q) {
           const int ss = (int)(q % NS);
           const int us = (int)(q / NS);
@@ -191,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const int64_t nb = src[x * nstep + j];
+          const int64_t nb = j < kPrefetch ? s_src[j] : src[x * nstep + j];
           const uint32_t dst = base + s_off + (uint32_t)ss * stage_bytes;
           const uint32_t bar = smem_u32(&sfull[ss]);
           mbar_expect_tx(bar, vbytes + kCBytes);
@@ -421,6 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t kCBytes = kBWords * 4u;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kMaxNA], bready[kMaxNA], empty[kMaxNA];
+  __shared__ int s_src[kPrefetch];  // the producer's source indices of the current item
   __shared__ __align__(8) uint64_t accf[2], acce[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
@@ -457,9 +476,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int i = 0; i < kMaxNA; ++i) last_use[i] = -1;
       int64_t q = 0;
       bool ok = true;
+      // the next item's nine source indices load while this item's copies go out
+      int pre[kPrefetch];
+      prefetch_src(src, NSTEP, nchunks, total, (int64_t)blockIdx.x, pre);
       for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
         const int64_t x = it / nchunks;
         const int ch = (int)(it - x * nchunks);
+#pragma unroll
+        for (int j = 0; j < NSTEP; ++j) s_src[j] = pre[j];
+        prefetch_src(src, NSTEP, nchunks, total, it + gridDim.x, pre);
         for (int j = 0; j < NSTEP; ++j, ++q) {
           const int as = (int)(q % NA), ua = (int)(q / NA);
           if (ua > 0 && !mbar_wait(smem_u32(&empty[as]), (uint32_t)(ua - 1) & 1u, &abort_flag)) {
@@ -468,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const int64_t nb = src[x * NSTEP + j];
+          const int64_t nb = s_src[j];
           const uint32_t slot = base + (uint32_t)as * slot_bytes;
           const uint32_t bar = smem_u32(&full[as]);
           mbar_expect_tx(bar, kTile + kCBytes);

@@ -78,45 +78,62 @@ __global__ void k_prolong(int64_t nfine, int Df, int nv, int nrhs, const int* __
   }
 }
 
-// FP32 form with the aggregate's values in registers: thread (s, rp) holds
-// coarse[agg(s)][c nv + j][2rp, 2rp + 1] for one chirality c at a time and
-// forms fine[s][a][2rp, 2rp + 1] for the Df/2 components a of that
-// chirality; W[s][a][.] is the same for every thread of a site (broadcast
-// loads of two entries at a time).  Same products in the same order as
-// k_prolong, so the results are identical.
+// FP32 form.  Fine sites are taken aggregate by aggregate (through the
+// member table), so that the 2 nv coarse values of an aggregate are read
+// from memory once and then hit in cache for its other fine sites.  A block
+// covers spb fine sites x tps threads: W[s][.][.] of its sites is staged in
+// shared memory (broadcast reads), and thread (site, rp) holds
+// coarse[agg][c nv + j][2rp, 2rp + 1] of one chirality c at a time in
+// registers and forms fine[s][a][2rp, 2rp + 1] for the Df/2 components a of
+// that chirality.  Same products in the same order as k_prolong, so the
+// results are identical.
 template <int NV>
-__global__ void __launch_bounds__(256) k_prolong_f32x2(int64_t nfine, int Df, int nrhs2, const int* __restrict__ agg_of,
-                                                      const float4* __restrict__ W, const float4* __restrict__ coarse,
-                                                      float4* __restrict__ fine) {
-  const int64_t tot = nfine * nrhs2;
+__global__ void __launch_bounds__(256) k_prolong_f32x2(int nsites, int bsites, int Df, int nrhs2, int tps, int spb,
+                                                      const int* __restrict__ members, const float4* __restrict__ W,
+                                                      const float4* __restrict__ coarse, float4* __restrict__ fine) {
+  extern __shared__ float4 wsm[];  // [spb][Df][NV / 2]
   const int half = Df / 2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int rp = (int)(e % nrhs2);
-    const int64_t s = e / nrhs2;
-    const int64_t x = agg_of[s];
+  const int wrow = Df * (NV / 2);  // float4 per site
+  const int li = threadIdx.x / tps, lane = threadIdx.x - li * tps;
+  for (int q0 = blockIdx.x * spb; q0 < nsites; q0 += gridDim.x * spb) {
+    __syncthreads();  // the previous sites' W is no longer read
+    for (int e = threadIdx.x; e < spb * wrow; e += blockDim.x) {
+      const int i = e / wrow, k = e - i * wrow;
+      if (q0 + i < nsites) wsm[e] = __ldg(W + (size_t)members[q0 + i] * wrow + k);
+    }
+    __syncthreads();
+    const int q = q0 + li;
+    if (li >= spb || q >= nsites) continue;
+    const int s = members[q];
+    const int x = q / bsites;
+    const float4* ws = wsm + li * wrow;
+    for (int rp = lane; rp < nrhs2; rp += tps) {
 #pragma unroll 1
-    for (int c = 0; c < 2; ++c) {
-      float4 cv[NV];
+      for (int c = 0; c < 2; ++c) {
+        float4 cv[NV];
+        const float4* cb = coarse + ((size_t)x * 2 * NV + (size_t)c * NV) * nrhs2 + rp;
 #pragma unroll
-      for (int j = 0; j < NV; ++j) cv[j] = coarse[(x * 2 * NV + c * NV + j) * nrhs2 + rp];
-#pragma unroll 1
-      for (int a = c * half; a < (c + 1) * half; ++a) {
-        const float4* w = W + (s * Df + a) * (NV / 2);
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < NV; ++j) cv[j] = cb[(size_t)j * nrhs2];
+        float4* fo = fine + ((size_t)s * Df + (size_t)c * half) * nrhs2 + rp;
+#pragma unroll 2
+        for (int a = 0; a < half; ++a) {
+          const float4* w = ws + (c * half + a) * (NV / 2);
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int jj = 0; jj < NV / 2; ++jj) {
-          const float4 wv = __ldg(w + jj);
+          for (int jj = 0; jj < NV / 2; ++jj) {
+            const float4 wv = w[jj];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const float wr = h ? wv.z : wv.x, wi = h ? wv.w : wv.y;
-            const float4 v = cv[2 * jj + h];
-            acc.x = fmaf(wr, v.x, fmaf(-wi, v.y, acc.x));
-            acc.y = fmaf(wr, v.y, fmaf(wi, v.x, acc.y));
-            acc.z = fmaf(wr, v.z, fmaf(-wi, v.w, acc.z));
-            acc.w = fmaf(wr, v.w, fmaf(wi, v.z, acc.w));
+            for (int h = 0; h < 2; ++h) {
+              const float wr = h ? wv.z : wv.x, wi = h ? wv.w : wv.y;
+              const float4 v = cv[2 * jj + h];
+              acc.x = fmaf(wr, v.x, fmaf(-wi, v.y, acc.x));
+              acc.y = fmaf(wr, v.y, fmaf(wi, v.x, acc.y));
+              acc.z = fmaf(wr, v.z, fmaf(-wi, v.w, acc.z));
+              acc.w = fmaf(wr, v.w, fmaf(wi, v.z, acc.w));
+            }
           }
+          fo[(size_t)a * nrhs2] = acc;
         }
-        fine[(s * Df + a) * nrhs2 + rp] = acc;
       }
     }
   }
@@ -200,18 +217,30 @@ void prolongate(qd_ctx& ctx, const Transfer& T, const C* W, const C* coarse, C* 
                cb * ((double)T.nfine * T.Df * T.nv + (double)tot + (double)T.ncoarse * T.Dc * nrhs));
   const bool al16 = ((reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(coarse) |
                       reinterpret_cast<uintptr_t>(fine)) & 15) == 0;
-  if (sizeof(C) == sizeof(cplxf) && nrhs % 2 == 0 && al16 && (T.nv == 8 || T.nv == 12 || T.nv == 16)) {
-    const int64_t t2 = T.nfine * (nrhs / 2);
-    const int grid = (int)(div_up(t2, 256) < 16 * kNumSMs ? div_up(t2, 256) : 16 * kNumSMs);
+  if (sizeof(C) == sizeof(cplxf) && nrhs % 2 == 0 && al16 && (T.nv == 8 || T.nv == 12 || T.nv == 16) &&
+      T.nfine * T.Df * (int64_t)nrhs < ((int64_t)1 << 31)) {
     const int nr2 = nrhs / 2;
-    const int* ag = T.agg_of.as<int>();
+    const int tps = nr2 < 256 ? nr2 : 256;
+    const int spb = 256 / tps;
+    const int nsites = (int)T.nfine;
+    const int blocks = (int)std::min<int64_t>(div_up(nsites, spb), 16 * kNumSMs);
+    const size_t smem = (size_t)spb * T.Df * (T.nv / 2) * sizeof(float4);
+    const int* mem = T.members.as<int>();
     const float4* w4 = reinterpret_cast<const float4*>(W);
     const float4* c4 = reinterpret_cast<const float4*>(coarse);
     float4* f4 = reinterpret_cast<float4*>(fine);
     switch (T.nv) {
-      case 8: k_prolong_f32x2<8><<<grid, 256, 0, ctx.stream>>>(T.nfine, T.Df, nr2, ag, w4, c4, f4); break;
-      case 12: k_prolong_f32x2<12><<<grid, 256, 0, ctx.stream>>>(T.nfine, T.Df, nr2, ag, w4, c4, f4); break;
-      default: k_prolong_f32x2<16><<<grid, 256, 0, ctx.stream>>>(T.nfine, T.Df, nr2, ag, w4, c4, f4); break;
+      case 8:
+        k_prolong_f32x2<8><<<blocks, spb * tps, smem, ctx.stream>>>(nsites, T.bsites, T.Df, nr2, tps, spb, mem, w4, c4, f4);
+        break;
+      case 12:
+        k_prolong_f32x2<12><<<blocks, spb * tps, smem, ctx.stream>>>(nsites, T.bsites, T.Df, nr2, tps, spb, mem, w4, c4,
+                                                                     f4);
+        break;
+      default:
+        k_prolong_f32x2<16><<<blocks, spb * tps, smem, ctx.stream>>>(nsites, T.bsites, T.Df, nr2, tps, spb, mem, w4, c4,
+                                                                     f4);
+        break;
     }
     QD_LAUNCH_CHECK();
     return;

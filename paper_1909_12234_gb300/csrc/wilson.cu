@@ -268,18 +268,25 @@ __device__ __forceinline__ void hop2_dir(const float2* __restrict__ U, const int
 }
 
 // (128, 4): at most 128 registers, four blocks per SM; the output is written
-// with evict-first stores so that it does not push neighbour spinors out of L2
+// with evict-first stores so that it does not push neighbour spinors out of L2.
+// The right-hand sides are swept in chunks of 2 rc2 columns, chunk-major: the
+// lattice is traversed once per chunk, so that the spinors a traversal keeps
+// in flight between a site and its farthest neighbour in visiting order take
+// less L2 (a chunk of 2 rc2 = nrhs is the plain order).
 template <bool DAG, bool RESID>
 __global__ void __launch_bounds__(128, 4) k_wilson_f32x2(const float2* __restrict__ U, const int* __restrict__ nbr,
-                                                      const int* __restrict__ visit, int64_t V, int nrhs,
+                                                      const int* __restrict__ visit, int64_t V, int nrhs, int rc2,
                                                       float mass, float tau,
                                                       const float2* __restrict__ in, float2* __restrict__ out,
                                                       const float2* __restrict__ b) {
   const int half = nrhs >> 1;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= V * half) return;
-  const int64_t slot = g / half;
-  const int r0 = 2 * (int)(g - slot * half);
+  const int64_t per_chunk = V * rc2;
+  const int ch = (int)(g / per_chunk);
+  const int64_t rem = g - ch * per_chunk;
+  const int64_t slot = rem / rc2;
+  const int r0 = 2 * (ch * rc2 + (int)(rem - slot * rc2));
   const int64_t site = visit[slot];
   const int64_t rs = nrhs;
   int nb8[8];
@@ -334,13 +341,17 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
   const int* nb = geo.nbr.as<int>();
   const int* vis = geo.visit.as<int>();
   const double mass = 4.0 + m0;
-  // candidate 0: two right-hand sides per thread (FP32, even nrhs, 16-byte
-  // aligned fields); candidate 1: one per thread.  The FP32 choice is tuned.
-  auto launch_x2 = [&]() -> bool {
+  // candidates 0, 2, 3: two right-hand sides per thread (FP32, even nrhs,
+  // 16-byte aligned fields), the columns swept whole, in chunks of 64 or in
+  // chunks of 32; candidate 1: one per thread.  The FP32 choice is tuned.
+  auto launch_x2 = [&](int rc) -> bool {
     if (!(sizeof(C) == 8 && (nrhs % 2) == 0 &&
           ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(b)) &
            15) == 0))
       return false;
+    if (rc <= 0) rc = nrhs;
+    if (rc > nrhs || nrhs % rc != 0 || rc % 2 != 0) return false;
+    const int rc2 = rc / 2;
     const int64_t tot2 = geo.nsites * (nrhs / 2);
     const int blocks2 = div_up(tot2, threads);
     const float2* L = reinterpret_cast<const float2*>(links);
@@ -350,16 +361,18 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
     const float fm = (float)mass, ft = (float)tau;
     if (b) {
       if (dagger)
-        k_wilson_f32x2<true, true><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, fm, ft, xin, yout, bb);
+        k_wilson_f32x2<true, true><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin, yout,
+                                                                        bb);
       else
-        k_wilson_f32x2<false, true><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, fm, ft, xin, yout, bb);
+        k_wilson_f32x2<false, true><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin,
+                                                                         yout, bb);
     } else {
       if (dagger)
-        k_wilson_f32x2<true, false><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, fm, ft, xin, yout,
-                                                                         nullptr);
+        k_wilson_f32x2<true, false><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin,
+                                                                         yout, nullptr);
       else
-        k_wilson_f32x2<false, false><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, fm, ft, xin, yout,
-                                                                          nullptr);
+        k_wilson_f32x2<false, false><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin,
+                                                                          yout, nullptr);
     }
     QD_LAUNCH_CHECK();
     return true;
@@ -385,13 +398,20 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
     launch_x1();
     return;
   }
-  auto launch = [&](int c) -> bool { return c == 0 ? launch_x2() : launch_x1(); };
+  auto launch = [&](int c) -> bool {
+    switch (c) {
+      case 0: return launch_x2(0);
+      case 1: return launch_x1();
+      case 2: return nrhs > 64 && launch_x2(64);
+      default: return nrhs > 32 && launch_x2(32);
+    }
+  };
   // the residual form writes out = b - A in: out-of-place, safe to repeat
   const std::string key = std::string("wilson f32 sites") + std::to_string(geo.nsites) + " rhs" +
                           std::to_string(nrhs) + (b ? " resid" : "") + (dagger ? " dag" : "");
-  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 2, launch);
+  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 4, launch);
   if (c >= 0 && launch(c)) return;
-  if (!launch_x2()) launch_x1();
+  if (!launch_x2(0)) launch_x1();
 }
 
 template void wilson_apply<cplx>(qd_ctx&, const LevelGeom&, const cplx*, double, double, bool,

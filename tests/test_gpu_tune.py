@@ -61,3 +61,30 @@ def test_autotuned_shapes_match_defaults(qd, ctx):
             assert rel_err(outs[(1, "w")], outs[(0, "w")]) < 1e-6
     finally:
         qd.autotune_set(1)
+
+
+def test_wilson_f32_launch_shapes(qd, ctx):
+    # the FP32 Wilson stencil's shapes: two columns per thread swept whole
+    # (0), in chunks of 64 (2) or of 32 columns (3) -- the same arithmetic per
+    # element, so the same bits -- and one column per thread (1), which
+    # agrees to FP32 rounding; A and A^H
+    dims = (8, 8, 8, 8)
+    U = synth.random_su3_links(dims, 0.3, 2)
+    g = qd.Gauge(ctx, dims, U)
+    try:
+        for s in (128, 96, 64, 130, 6):
+            xf = torch.randn((g.V, 12, s), dtype=torch.complex64, device="cuda:0",
+                             generator=torch.Generator("cuda:0").manual_seed(s))
+            for dag in (False, True):
+                outs = {}
+                for cand in range(4):
+                    qd.autotune_force(cand)
+                    yf = torch.full_like(xf, float("nan"))
+                    qd.dirac_apply_f32(ctx, g, -0.8, 0.1, dag, s, xf, yf)
+                    outs[cand] = yf
+                for cand in (2, 3):
+                    assert torch.equal(outs[0], outs[cand]), (s, dag, cand)
+                assert rel_err(host(outs[1]), host(outs[0])) < 1e-6, (s, dag)
+    finally:
+        qd.autotune_force(-1)
+    g.close()

@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define QD_ABI_VERSION 3
+#define QD_ABI_VERSION 4
 #define QD_MAX_LEVELS 4 /* fine level + up to 3 coarse levels */
 
 typedef enum {
@@ -149,6 +149,19 @@ int qd_dirac_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau,
  * qd_dirac_apply.  Asynchronous. */
 int qd_dirac_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau,
                        int dagger, int nrhs, const float* in, float* out);
+
+/* out = S in with S = A_oo - A_oe A_ee^{-1} A_eo, the Schur complement of A
+ * on the odd sites (the even-odd solves of Sec. 4; qd_solver_params.schur).
+ * in/out: half fields of the odd sites, (site - V/2, 12, nrhs) for the odd
+ * half of the qd layout (sites V/2 .. V-1).  in and out must not overlap.
+ * Returns after the stream has finished the product. */
+int qd_dirac_schur_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0,
+                         double tau, int nrhs, const double* in, double* out);
+/* The same in FP32 (interleaved complex float, links as
+ * qd_dirac_apply_f32). */
+int qd_dirac_schur_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0,
+                             double tau, int nrhs, const float* in,
+                             float* out);
 
 /* ------------------------------------------------------------------------ */
 /* a10: adaptive multigrid setup (Sec. 2 "adaptive setup" and "blocking";    */
@@ -322,6 +335,14 @@ typedef struct {
                         by less than 10 % since the previous check stops the
                         solve with QD_ERR_NOT_CONVERGED and
                         qd_solve_stats.stagnated = 1; 0: off */
+  int schur;         /* 1: even-odd solve (Sec. 4, the even-odd
+                        preconditioned fine solves): GCR on the odd-site
+                        Schur complement S = A_oo - A_oe A_ee^{-1} A_eo,
+                        preconditioned by the odd block of the V-cycle, then
+                        x_e = A_ee^{-1} (b_e - A_eo x_o); with QD_PREC_MIXED
+                        each FP32 correction is solved this way.  The
+                        tolerance still applies to the full FP64 residual.
+                        0 (default): GCR on A itself */
 } qd_solver_params;
 
 void qd_solver_params_default(qd_solver_params* p);

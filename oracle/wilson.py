@@ -21,7 +21,9 @@ so gamma5 = gamma1 gamma2 gamma3 gamma4 = diag(1, 1, -1, -1).
 Pinned by: the Clifford algebra and gamma5 (test), gamma5 A gamma5 = A^H,
 the adjoint identity <y, A x> = <A^H y, x>, the free-field plane-wave
 spectrum M(p) +- i sqrt(sum sin^2 p) and gauge covariance
-(``tests/test_oracle_wilson.py``).
+(``tests/test_oracle_wilson.py``).  The odd-site Schur complement is pinned
+by eliminating the even sites through the matrix-free operator and by the
+block-inverse identity (A^{-1})_oo = S^{-1}.
 """
 
 import numpy as np
@@ -128,6 +130,28 @@ def dirac_sparse(U, m0, dims, tau=0.0):
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(N, N))
     return A.tocsr()  # duplicate entries are summed
+
+
+def schur_odd_sparse(U, m0, dims, tau=0.0):
+    """The Schur complement of A on the odd sites (even-odd solves, Sec. 4).
+
+    With the dofs split by site parity (sum of coordinates even / odd),
+    S = A_oo - A_oe A_ee^{-1} A_eo.  Every hop joins sites of opposite
+    parity, so A_ee is block diagonal (one 12 x 12 block per even site,
+    (4 + m0) 1 + i tau gamma5) and is inverted block by block.  Rows and
+    columns of S run over the odd sites in lexicographic order, dof
+    12 k + 3 spin + colour for the k-th odd site.  Returns (S, odd_sites).
+    """
+    A = dirac_sparse(U, m0, dims, tau)
+    par = lattice.parity(dims)
+    ev, od = np.flatnonzero(par == 0), np.flatnonzero(par == 1)
+    E = (12 * ev[:, None] + np.arange(12)[None, :]).ravel()
+    O = (12 * od[:, None] + np.arange(12)[None, :]).ravel()
+    Aee = A[E][:, E].tocsr()
+    blocks = [np.linalg.inv(Aee[12 * k:12 * k + 12, 12 * k:12 * k + 12].toarray()) for k in range(len(ev))]
+    Aee_inv = sp.block_diag(blocks, format="csr")
+    S = A[O][:, O] - A[O][:, E] @ Aee_inv @ A[E][:, O]
+    return S.tocsr(), od
 
 
 def free_field_eigenvalues(dims, m0):

@@ -185,6 +185,40 @@ int qd_dirac_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau, int 
   });
 }
 
+int qd_dirac_schur_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau, int nrhs, const double* in,
+                         double* out) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    QD_REQUIRE(std::isfinite(m0) && std::isfinite(tau), "m0 and tau must be finite");
+    set_device(ctx);
+    qd::SchurOp<qd::cplx> S(gauge, gauge->links.as<qd::cplx>(), m0, tau);
+    S.apply(*ctx, reinterpret_cast<const qd::cplx*>(in), reinterpret_cast<qd::cplx*>(out), nrhs);
+    QD_CUDA(cudaStreamSynchronize(ctx->stream));  // S's scratch is released on return
+  });
+}
+
+int qd_dirac_schur_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau, int nrhs, const float* in,
+                             float* out) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(in);
+    NONNULL(out);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE(in != out, "in and out must not overlap");
+    QD_REQUIRE(std::isfinite(m0) && std::isfinite(tau), "m0 and tau must be finite");
+    set_device(ctx);
+    qd::SchurOp<qd::cplxf> S(gauge, gauge->links_f32(), m0, tau);
+    S.apply(*ctx, reinterpret_cast<const qd::cplxf*>(in), reinterpret_cast<qd::cplxf*>(out), nrhs);
+    QD_CUDA(cudaStreamSynchronize(ctx->stream));  // S's scratch is released on return
+  });
+}
+
 void qd_mg_params_default(qd_mg_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
@@ -216,6 +250,7 @@ void qd_solver_params_default(qd_solver_params* p) {
   p->precision = QD_PREC_F64;
   p->inner_tol = 1e-5;
   p->max_refine = 10;
+  p->schur = 0;
 }
 
 int qd_mg_setup(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau, const qd_mg_params* params,

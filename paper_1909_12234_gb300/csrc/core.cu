@@ -68,6 +68,16 @@ void LevelGeom::build(const int d[4], bool even_odd) {
   for (int64_t k = 0; k < V; ++k) h_visit[k] = key[k].second;
   visit.resize(V * sizeof(int));
   QD_CUDA(cudaMemcpy(visit.as<int>(), h_visit.data(), V * sizeof(int), cudaMemcpyHostToDevice));
+  if (eo) {
+    for (int par = 0; par < 2; ++par) {
+      std::vector<int> vp;
+      vp.reserve(V / 2);
+      for (int64_t k = 0; k < V; ++k)
+        if ((h_visit[k] >= V / 2) == (par == 1)) vp.push_back(h_visit[k]);
+      visit_par[par].resize(vp.size() * sizeof(int));
+      QD_CUDA(cudaMemcpy(visit_par[par].as<int>(), vp.data(), vp.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+  }
   nbr.resize(V * 8 * sizeof(int));
   lex_of_site.resize(V * sizeof(int));
   site_of_lex.resize(V * sizeof(int));

@@ -9,6 +9,12 @@ namespace qd {
 struct SolverCache {
   GCR<cplx> gcr64;
   GCR<cplxf> gcr32;
+  // even-odd (Schur complement) fine solves
+  GCR<cplx> gcr64s;
+  GCR<cplxf> gcr32s;
+  SchurPrecond<cplx> spre64;
+  SchurPrecond<cplxf> spre32;
+  DevBuf sch64, sch32;
   DevBuf Z, B, X, tdev, stats, loo;
   DevBuf mr, mt, mrf, mef, mscal;  // mixed-precision refinement
 };

@@ -116,6 +116,45 @@ template <class C> class MGPrecond : public Precond<C> {
   cudaStream_t cap_stream_ = nullptr;  // capture only; nothing runs on it
 };
 
+// Odd-site Schur complement of the Wilson operator (the even-odd
+// preconditioned fine solves the paper's multigrid uses, Sec. 4):
+//   S = A_oo - A_oe A_ee^{-1} A_eo = M - (1/4) H_oe M^{-1} H_eo
+// with A = M - H/2, M = 4 + m0 + i tau gamma5, on half fields of the odd
+// sites.
+template <class C> struct SchurOp : public Op<C> {
+  const qd_gauge* g;
+  const C* links;
+  double m0, tau;
+  mutable DevBuf t;  // even-site scratch
+  SchurOp(const qd_gauge* gauge, const C* lk, double m, double ta) : g(gauge), links(lk), m0(m), tau(ta) {}
+  int64_t nsites() const override;
+  int dof() const override { return 12; }
+  void apply(qd_ctx& ctx, const C* in, C* out, int nrhs) const override;
+};
+
+// Preconditioner of the Schur system from a full-lattice V-cycle: the odd
+// block of M_V (0, r_o) (the odd-odd block of A^{-1} is S^{-1}).  The
+// embedding buffers persist, so the V-cycle's captured graphs are reused.
+template <class C> class SchurPrecond : public Precond<C> {
+ public:
+  MGPrecond<C>* mg = nullptr;
+  const LevelGeom* geo = nullptr;
+  void apply(qd_ctx& ctx, const C* r, C* z, int nrhs) override;
+
+ private:
+  DevBuf R_, Z_;
+  int cap_ = -1;
+};
+
+// A x = b on the full lattice through the Schur complement: b_o' = b_o -
+// A_oe A_ee^{-1} b_e; S x_o = b_o' by flexible GCR (tolerance tol relative
+// to ||b_o'||, preconditioner pre: nullable); x_e = A_ee^{-1} (b_e - A_eo
+// x_o).  b and x full fields (even half first); scratch grow-only.
+template <class C>
+void schur_solve(qd_ctx& ctx, const qd_gauge& g, const C* links, double m0, double tau, SchurPrecond<C>* pre,
+                 GCR<C>& gcr, DevBuf& scratch, const C* b, C* x, int nrhs, double tol, int maxit, int restart,
+                 SolveInfo* info);
+
 // Learned gauge-covariant smoother of the fine level (an extension; the
 // paper has no counterpart): (S r)(x) = sum_d w_d (T_d r)(x), with T_0 the
 // identity, T_{1+mu} r(x) = U_mu(x) r(x+mu), T_{5+mu} r(x) = U_mu(x-mu)^H

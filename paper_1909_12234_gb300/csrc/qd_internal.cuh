@@ -81,6 +81,10 @@ struct LevelGeom {
   // stay in L2.
   std::vector<int> h_visit;
   DevBuf visit;                    // int32 [nsites]
+  // The same order restricted to the sites of one parity (even-odd
+  // lattices): visit_par[p] holds nsites/2 site indices, all in
+  // [p nsites/2, (p+1) nsites/2).
+  DevBuf visit_par[2];
   void build(const int d[4], bool even_odd);
   void coords(int64_t lex, int c[4]) const {
     c[0] = (int)(lex % dims[0]);
@@ -161,6 +165,16 @@ template <class C> struct WilsonOp : public Op<C> {
 template <class C>
 void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, double tau,
                   bool dagger, const C* in, C* out, int nrhs, const C* b = nullptr);
+// Parity-restricted hopping (wilson.cu): for the sites n of parity p,
+// out(n) = Q1 z(n) + Q2 (H in)(n) with A = M - H/2, Q1 and Q2 spin-diagonal
+// (q[0] upper spins, q[1] lower); in a half field of parity 1 - p, z
+// (nullable) and out half fields of parity p.
+template <class C>
+void wilson_eo(qd_ctx& ctx, const LevelGeom& geo, const C* links, int p, const cplx q1[2], const cplx q2[2],
+               const C* in, const C* z, C* out, int nrhs);
+// out = Q in on a half field of nh sites.
+template <class C>
+void spin_diag(qd_ctx& ctx, int64_t nh, int nrhs, const cplx q[2], const C* in, C* out);
 void gauge_import(qd_ctx& ctx, qd_gauge& g, const double* links_host);
 void links_to_f32(qd_ctx& ctx, const cplx* in, cplxf* out, int64_t n);
 

@@ -866,6 +866,84 @@ template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, C* Az,
 template class MGPrecond<cplx>;
 template class MGPrecond<cplxf>;
 
+// ---------------------------------------------------------------------------
+// Even-odd (Schur complement) solves
+// ---------------------------------------------------------------------------
+namespace {
+// M = 4 + m0 + i tau gamma5 on the upper (gamma5 = +1) and lower spins, and
+// its inverse
+void diag_m(double m0, double tau, cplx M[2], cplx Minv[2]) {
+  const double m = 4.0 + m0, d = m * m + tau * tau;
+  M[0] = mkc(m, tau);
+  M[1] = mkc(m, -tau);
+  Minv[0] = mkc(m / d, -tau / d);
+  Minv[1] = mkc(m / d, tau / d);
+}
+}  // namespace
+
+template <class C> int64_t SchurOp<C>::nsites() const { return g->geo.nsites / 2; }
+
+template <class C> void SchurOp<C>::apply(qd_ctx& ctx, const C* in, C* out, int nrhs) const {
+  const int64_t Vh = g->geo.nsites / 2;
+  t.resize((size_t)Vh * 12 * nrhs * sizeof(C));
+  cplx M[2], Minv[2];
+  diag_m(m0, tau, M, Minv);
+  const cplx zero[2] = {mkc(0.0, 0.0), mkc(0.0, 0.0)};
+  const cplx quarter[2] = {mkc(-0.25, 0.0), mkc(-0.25, 0.0)};
+  // t_e = M^{-1} H_eo in_o, then out_o = M in_o - (1/4) H_oe t_e
+  wilson_eo<C>(ctx, g->geo, links, 0, zero, Minv, in, nullptr, t.as<C>(), nrhs);
+  wilson_eo<C>(ctx, g->geo, links, 1, M, quarter, t.as<C>(), in, out, nrhs);
+}
+
+template <class C> void SchurPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, int nrhs) {
+  QD_REQUIRE(mg && geo, "Schur preconditioner without a V-cycle");
+  const int64_t Vh = geo->nsites / 2;
+  const size_t half = (size_t)Vh * 12 * nrhs * sizeof(C);
+  if (nrhs != cap_) {
+    R_.resize(2 * half);
+    Z_.resize(2 * half);
+    QD_CUDA(cudaMemsetAsync(R_.as<void>(), 0, half, ctx.stream));  // the even half stays zero
+    cap_ = nrhs;
+  }
+  unsigned char* Rb = R_.as<unsigned char>();
+  QD_CUDA(cudaMemcpyAsync(Rb + half, r, half, cudaMemcpyDeviceToDevice, ctx.stream));
+  mg->apply(ctx, R_.as<C>(), Z_.as<C>(), nrhs);
+  QD_CUDA(cudaMemcpyAsync(z, Z_.as<unsigned char>() + half, half, cudaMemcpyDeviceToDevice, ctx.stream));
+}
+
+template <class C>
+void schur_solve(qd_ctx& ctx, const qd_gauge& g, const C* links, double m0, double tau, SchurPrecond<C>* pre,
+                 GCR<C>& gcr, DevBuf& scratch, const C* b, C* x, int nrhs, double tol, int maxit, int restart,
+                 SolveInfo* info) {
+  QD_REQUIRE(g.geo.eo, "even-odd solve on a lattice without even-odd ordering");
+  const int64_t Vh = g.geo.nsites / 2;
+  const int64_t hn = Vh * 12 * (int64_t)nrhs;
+  scratch.resize((size_t)2 * hn * sizeof(C));
+  C* u = scratch.as<C>();
+  C* bh = u + hn;
+  cplx M[2], Minv[2];
+  diag_m(m0, tau, M, Minv);
+  const cplx one[2] = {mkc(1.0, 0.0), mkc(1.0, 0.0)};
+  const cplx half2[2] = {mkc(0.5, 0.0), mkc(0.5, 0.0)};
+  const cplx halfMinv[2] = {mkc(0.5 * Minv[0].x, 0.5 * Minv[0].y), mkc(0.5 * Minv[1].x, 0.5 * Minv[1].y)};
+  // b_o' = b_o + (1/2) H_oe M^{-1} b_e
+  spin_diag<C>(ctx, Vh, nrhs, Minv, b, u);
+  wilson_eo<C>(ctx, g.geo, links, 1, one, half2, u, b + hn, bh, nrhs);
+  SchurOp<C> S(&g, links, m0, tau);
+  gcr.solve(ctx, S, pre, bh, x + hn, nrhs, tol, maxit, restart, info);
+  // x_e = M^{-1} b_e + (1/2) M^{-1} H_eo x_o
+  wilson_eo<C>(ctx, g.geo, links, 0, Minv, halfMinv, x + hn, b, x, nrhs);
+}
+
+template struct SchurOp<cplx>;
+template struct SchurOp<cplxf>;
+template class SchurPrecond<cplx>;
+template class SchurPrecond<cplxf>;
+template void schur_solve<cplx>(qd_ctx&, const qd_gauge&, const cplx*, double, double, SchurPrecond<cplx>*,
+                                GCR<cplx>&, DevBuf&, const cplx*, cplx*, int, double, int, int, SolveInfo*);
+template void schur_solve<cplxf>(qd_ctx&, const qd_gauge&, const cplxf*, double, double, SchurPrecond<cplxf>*,
+                                 GCR<cplxf>&, DevBuf&, const cplxf*, cplxf*, int, double, int, int, SolveInfo*);
+
 }  // namespace qd
 
 // ---------------------------------------------------------------------------

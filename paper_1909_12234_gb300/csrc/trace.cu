@@ -94,9 +94,19 @@ static void solve_mixed(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, do
       if (hr[c].x > tol2 * hb[c].x) need = std::min(need, 0.5 * p.tol * std::sqrt(hb[c].x / hr[c].x));
     const double itol = std::min(0.5, std::max(p.inner_tol, need));
     SolveInfo in;
-    sc.gcr32.orth_passes = 1;
-    sc.gcr32.stag_window = p.stag_window;
-    sc.gcr32.solve(ctx, A32, mg ? mg->pre32.get() : nullptr, rf, ef, s, itol, p.maxit, p.restart, &in);
+    if (p.schur) {
+      // the correction through the odd-site Schur complement
+      sc.gcr32s.orth_passes = 1;
+      sc.gcr32s.stag_window = p.stag_window;
+      sc.spre32.mg = mg ? mg->pre32.get() : nullptr;
+      sc.spre32.geo = &g.geo;
+      schur_solve<cplxf>(ctx, g, const_cast<qd_gauge&>(g).links_f32(), m0, tau, mg ? &sc.spre32 : nullptr,
+                         sc.gcr32s, sc.sch32, rf, ef, s, itol, p.maxit, p.restart, &in);
+    } else {
+      sc.gcr32.orth_passes = 1;
+      sc.gcr32.stag_window = p.stag_window;
+      sc.gcr32.solve(ctx, A32, mg ? mg->pre32.get() : nullptr, rf, ef, s, itol, p.maxit, p.restart, &in);
+    }
     if (in.stagnated) info.stagnated = true;
     inner_total += in.iterations;
     for (int c = 0; c < s; ++c) iters[c] += in.iters[c];
@@ -139,6 +149,73 @@ static void solve_mixed(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, do
   }
 }
 
+// FP64 even-odd solve: Schur-complement solves of the full residual's
+// system until ||b - A x|| <= tol ||b|| per column (the Schur system's own
+// residual norm differs from the full one by the even-site scaling).
+static void solve_schur64(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, double tau, int s, const cplx* b,
+                          cplx* x, const qd_solver_params& p, SolveInfo& info) {
+  SolverCache& sc = cache(ctx);
+  const int64_t n = g.geo.nsites * 12, tot = n * s;
+  WilsonOp<cplx> A64(&g, g.links.as<cplx>(), m0, tau, false);
+  sc.mr.resize(tot * sizeof(cplx));
+  sc.mt.resize(tot * sizeof(cplx));
+  sc.mscal.resize((size_t)(4 * s) * sizeof(cplx) + 4 * sizeof(int));
+  cplx* r = sc.mr.as<cplx>();
+  cplx* e = sc.mt.as<cplx>();
+  cplx* bn2 = sc.mscal.as<cplx>();
+  cplx* rn2 = bn2 + s;
+  blas::zero(ctx, tot, x);
+  blas::copy(ctx, tot, b, r);
+  blas::dots(ctx, 1, n, s, b, 0, b, 0, bn2);
+  QD_CUDA(cudaMemcpyAsync(rn2, bn2, s * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx.stream));
+  sc.gcr64s.stag_window = p.stag_window;
+  sc.spre64.mg = mg ? mg->pre64.get() : nullptr;
+  sc.spre64.geo = &g.geo;
+  std::vector<cplx> hb(s), hr(s);
+  std::vector<int> iters(s, 0);
+  int total = 0;
+  const int steps = p.max_refine > 0 ? p.max_refine : 1;
+  for (int step = 0; step < steps; ++step) {
+    QD_CUDA(cudaMemcpyAsync(hb.data(), bn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaMemcpyAsync(hr.data(), rn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+    QD_CUDA(cudaStreamSynchronize(ctx.stream));
+    double need = 1.0;
+    bool open = false;
+    for (int c = 0; c < s; ++c)
+      if (hr[c].x > p.tol * p.tol * hb[c].x) {
+        open = true;
+        need = std::min(need, 0.5 * p.tol * std::sqrt(hb[c].x / hr[c].x));
+      }
+    if (!open) break;
+    SolveInfo in;
+    schur_solve<cplx>(ctx, g, g.links.as<cplx>(), m0, tau, mg ? &sc.spre64 : nullptr, sc.gcr64s, sc.sch64, r, e, s,
+                      need, p.maxit, p.restart, &in);
+    total += in.iterations;
+    for (int c = 0; c < s; ++c) iters[c] += in.iters[c];
+    blas::add(ctx, tot, e, x);
+    A64.residual(ctx, b, x, r, s);
+    blas::dots(ctx, 1, n, s, r, 0, r, 0, rn2);
+    if (in.stagnated) {
+      info.stagnated = true;
+      break;
+    }
+  }
+  QD_CUDA(cudaMemcpyAsync(hb.data(), bn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaMemcpyAsync(hr.data(), rn2, s * sizeof(cplx), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  info.iterations = total;
+  info.iters = iters;
+  info.true_rel.assign(s, 0.0);
+  info.converged = 0;
+  info.max_rel = 0.0;
+  for (int c = 0; c < s; ++c) {
+    const double rel = hb[c].x > 0.0 ? std::sqrt(hr[c].x / hb[c].x) : 0.0;
+    info.true_rel[c] = rel;
+    if (rel <= p.tol) info.converged++;
+    if (rel > info.max_rel || rel != rel) info.max_rel = rel;
+  }
+}
+
 // x = A^{-1} b for s columns (FP64 GCR + FP64 V-cycle, or mixed precision).
 void solve(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, double tau, int s, const cplx* b, cplx* x,
            const qd_solver_params& p, SolveInfo& info) {
@@ -155,6 +232,10 @@ void solve(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, double tau, int
   QD_REQUIRE(p.precision == QD_PREC_F64, "unknown precision");
   WilsonOp<cplx> A(&g, g.links.as<cplx>(), m0, tau, false);
   SolverCache& sc = cache(ctx);
+  if (p.schur) {
+    solve_schur64(ctx, g, mg, m0, tau, s, b, x, p, info);
+    return;
+  }
   sc.gcr64.stag_window = p.stag_window;
   sc.gcr64.solve(ctx, A, mg ? mg->pre64.get() : nullptr, b, x, s, p.tol, p.maxit, p.restart, &info);
 }

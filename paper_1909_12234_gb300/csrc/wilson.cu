@@ -80,12 +80,12 @@ __device__ __forceinline__ void su3mul(const C* __restrict__ L, const C x[3], C 
 template <int MU, bool DAG, class C>
 __device__ __forceinline__ void hop_dir(const C* __restrict__ U, const int* __restrict__ nb8,
                                         int64_t V, int64_t site, int64_t rs, int r,
-                                        const C* __restrict__ in, C hu[6], C hl[6]) {
+                                        const C* __restrict__ in, C hu[6], C hl[6], int64_t in_off = 0) {
   const double sg = DAG ? -1.0 : 1.0;
   // forward: (1 - s gamma) U_mu(n) x(n + mu)
   {
     const int64_t nf = nb8[MU];
-    const C* p = in + nf * 12 * rs + r;
+    const C* p = in + (nf - in_off) * 12 * rs + r;
     C h0[3], h1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -112,7 +112,7 @@ __device__ __forceinline__ void hop_dir(const C* __restrict__ U, const int* __re
   // backward: (1 + s gamma) U_mu(n - mu)^H x(n - mu)
   {
     const int64_t nbk = nb8[4 + MU];
-    const C* p = in + nbk * 12 * rs + r;
+    const C* p = in + (nbk - in_off) * 12 * rs + r;
     C h0[3], h1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -250,17 +250,17 @@ __device__ __forceinline__ void hop2(const float2* __restrict__ L, const float4*
 template <int MU, bool DAG>
 __device__ __forceinline__ void hop2_dir(const float2* __restrict__ U, const int nb8[8], int64_t V, int64_t site,
                                          int64_t rs, int r0, const float2* __restrict__ in, float2 hu[2][6],
-                                         float2 hl[2][6]) {
+                                         float2 hl[2][6], int64_t in_off = 0) {
   float4 q[12];
   {
-    const float2* p = in + (int64_t)nb8[MU] * 12 * rs + r0;
+    const float2* p = in + ((int64_t)nb8[MU] - in_off) * 12 * rs + r0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) q[k] = *reinterpret_cast<const float4*>(p + k * rs);
     hop2<MU, true, DAG>(U + ((int64_t)MU * V + site) * 9, q, hu, hl);
   }
   {
     const int64_t nbk = nb8[4 + MU];
-    const float2* p = in + nbk * 12 * rs + r0;
+    const float2* p = in + (nbk - in_off) * 12 * rs + r0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) q[k] = *reinterpret_cast<const float4*>(p + k * rs);
     hop2<MU, false, DAG>(U + ((int64_t)MU * V + nbk) * 9, q, hu, hl);
@@ -327,6 +327,159 @@ __global__ void __launch_bounds__(128, 4) k_wilson_f32x2(const float2* __restric
     __stcs(reinterpret_cast<float4*>(y + k * rs), make_float4(v0.x, v0.y, v1.x, v1.y));
   }
 }
+
+// ---------------------------------------------------------------------------
+// Parity-restricted hopping (even-odd solves).  With the sites of parity p
+// in [p V/2, (p+1) V/2) and every hop joining sites of opposite parity,
+//   y(n) = Q1 z(n) + Q2 (H x)(n)   for the sites n of parity p,
+// H x = sum_mu [(1 - gamma_mu) U_mu(n) x(n+mu) + (1 + gamma_mu) U_mu(n-mu)^H
+// x(n-mu)] (so A = M - H/2 with M = 4 + m0 + i tau gamma5), Q1 and Q2
+// spin-diagonal: q[0] on the upper spins (gamma5 = +1), q[1] on the lower.
+// x is a half field of parity 1 - p, z (nullable) and y half fields of
+// parity p: element (site, a, r) of a half field of parity q sits at
+// ((site - q V/2) 12 + a) nrhs + r.
+// ---------------------------------------------------------------------------
+struct EoCoef {
+  cplx q1[2], q2[2];
+};
+
+template <class C>
+__global__ void __launch_bounds__(128) k_wilson_eo(const C* __restrict__ U, const int* __restrict__ nbr,
+                                                   const int* __restrict__ visit, int64_t V, int nrhs, int p,
+                                                   EoCoef q, const C* __restrict__ in, const C* __restrict__ z,
+                                                   C* __restrict__ out) {
+  typedef typename CTraits<C>::R R;
+  const int64_t Vh = V / 2;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= Vh * nrhs) return;
+  const int64_t slot = g / nrhs;
+  const int r = (int)(g - slot * nrhs);
+  const int64_t site = visit[slot];
+  const int64_t rs = nrhs;
+  const int64_t in_off = (int64_t)(1 - p) * Vh, own = site - (int64_t)p * Vh;
+  int nb8[8];
+#pragma unroll
+  for (int h = 0; h < 8; ++h) nb8[h] = nbr[site * 8 + h];
+  C hu[6], hl[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) { hu[k] = mk<C>((R)0, (R)0); hl[k] = mk<C>((R)0, (R)0); }
+  hop_dir<0, false>(U, nb8, V, site, rs, r, in, hu, hl, in_off);
+  hop_dir<1, false>(U, nb8, V, site, rs, r, in, hu, hl, in_off);
+  hop_dir<2, false>(U, nb8, V, site, rs, r, in, hu, hl, in_off);
+  hop_dir<3, false>(U, nb8, V, site, rs, r, in, hu, hl, in_off);
+  const C q1u = mk<C>((R)q.q1[0].x, (R)q.q1[0].y), q1l = mk<C>((R)q.q1[1].x, (R)q.q1[1].y);
+  const C q2u = mk<C>((R)q.q2[0].x, (R)q.q2[0].y), q2l = mk<C>((R)q.q2[1].x, (R)q.q2[1].y);
+  const C* zz = z ? z + own * 12 * rs + r : nullptr;
+  C* y = out + own * 12 * rs + r;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    C v = cmul(k < 6 ? q2u : q2l, k < 6 ? hu[k] : hl[k - 6]);
+    if (zz) v = cadd(v, cmul(k < 6 ? q1u : q1l, zz[k * rs]));
+    y[k * rs] = v;
+  }
+}
+
+// FP32, two right-hand sides per thread (even nrhs, 16-byte aligned fields).
+__global__ void __launch_bounds__(128, 4) k_wilson_eo_f32x2(const float2* __restrict__ U, const int* __restrict__ nbr,
+                                                         const int* __restrict__ visit, int64_t V, int nrhs, int p,
+                                                         EoCoef q, const float2* __restrict__ in,
+                                                         const float2* __restrict__ z, float2* __restrict__ out) {
+  const int half = nrhs >> 1;
+  const int64_t Vh = V / 2;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= Vh * half) return;
+  const int64_t slot = g / half;
+  const int r0 = 2 * (int)(g - slot * half);
+  const int64_t site = visit[slot];
+  const int64_t rs = nrhs;
+  const int64_t in_off = (int64_t)(1 - p) * Vh, own = site - (int64_t)p * Vh;
+  int nb8[8];
+#pragma unroll
+  for (int h = 0; h < 8; ++h) nb8[h] = nbr[site * 8 + h];
+  float2 hu[2][6], hl[2][6];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { hu[j][k] = make_float2(0.f, 0.f); hl[j][k] = make_float2(0.f, 0.f); }
+  hop2_dir<0, false>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
+  hop2_dir<1, false>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
+  hop2_dir<2, false>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
+  hop2_dir<3, false>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
+  const float2 q1u = make_float2((float)q.q1[0].x, (float)q.q1[0].y), q1l = make_float2((float)q.q1[1].x, (float)q.q1[1].y);
+  const float2 q2u = make_float2((float)q.q2[0].x, (float)q.q2[0].y), q2l = make_float2((float)q.q2[1].x, (float)q.q2[1].y);
+  const float2* zz = z ? z + own * 12 * rs + r0 : nullptr;
+  float2* y = out + own * 12 * rs + r0;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float2 qa = k < 6 ? q2u : q2l, qb = k < 6 ? q1u : q1l;
+    float2 v0 = cmul(qa, k < 6 ? hu[0][k] : hl[0][k - 6]);
+    float2 v1 = cmul(qa, k < 6 ? hu[1][k] : hl[1][k - 6]);
+    if (zz) {
+      const float4 zv = *reinterpret_cast<const float4*>(zz + k * rs);
+      v0 = cadd(v0, cmul(qb, make_float2(zv.x, zv.y)));
+      v1 = cadd(v1, cmul(qb, make_float2(zv.z, zv.w)));
+    }
+    *reinterpret_cast<float4*>(y + k * rs) = make_float4(v0.x, v0.y, v1.x, v1.y);
+  }
+}
+
+template <class C>
+void wilson_eo(qd_ctx& ctx, const LevelGeom& geo, const C* links, int p, const cplx q1[2], const cplx q2[2],
+               const C* in, const C* z, C* out, int nrhs) {
+  QD_REQUIRE(geo.eo && geo.nsites % 2 == 0, "parity-restricted hopping needs an even-odd lattice");
+  const int64_t Vh = geo.nsites / 2;
+  const int64_t tot = Vh * nrhs;
+  if (tot == 0) return;
+  EoCoef q;
+  for (int h = 0; h < 2; ++h) {
+    q.q1[h] = q1[h];
+    q.q2[h] = q2[h];
+  }
+  const double cb = (double)sizeof(C);
+  ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_WILSON_F64 : QD_PROF_WILSON_F32, 1368.0 * (double)tot,
+               (double)Vh * ((z ? 36.0 : 24.0) * cb * nrhs + 72.0 * cb));
+  const int* nb = geo.nbr.as<int>();
+  const int* vis = geo.visit_par[p].as<int>();
+  const bool x2 = sizeof(C) == 8 && nrhs % 2 == 0 &&
+                  ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(z)) &
+                   15) == 0;
+  if (x2) {
+    k_wilson_eo_f32x2<<<div_up(Vh * (nrhs / 2), 128), 128, 0, ctx.stream>>>(
+        reinterpret_cast<const float2*>(links), nb, vis, geo.nsites, nrhs, p, q, reinterpret_cast<const float2*>(in),
+        reinterpret_cast<const float2*>(z), reinterpret_cast<float2*>(out));
+  } else {
+    k_wilson_eo<C><<<div_up(tot, 128), 128, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, p, q, in, z, out);
+  }
+  QD_LAUNCH_CHECK();
+}
+
+template void wilson_eo<cplx>(qd_ctx&, const LevelGeom&, const cplx*, int, const cplx*, const cplx*, const cplx*,
+                              const cplx*, cplx*, int);
+template void wilson_eo<cplxf>(qd_ctx&, const LevelGeom&, const cplxf*, int, const cplx*, const cplx*, const cplxf*,
+                               const cplxf*, cplxf*, int);
+
+// out = Q in on a half field (Q spin-diagonal as above).
+template <class C>
+__global__ void k_spin_diag(int64_t nh, int nrhs, cplx qu, cplx ql, const C* __restrict__ in, C* __restrict__ out) {
+  typedef typename CTraits<C>::R R;
+  const int64_t tot = nh * 12 * nrhs;
+  const C a = mk<C>((R)qu.x, (R)qu.y), b = mk<C>((R)ql.x, (R)ql.y);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)((e / nrhs) % 12);
+    out[e] = cmul(k < 6 ? a : b, in[e]);
+  }
+}
+
+template <class C>
+void spin_diag(qd_ctx& ctx, int64_t nh, int nrhs, const cplx q[2], const C* in, C* out) {
+  const int64_t tot = nh * 12 * nrhs;
+  if (tot == 0) return;
+  k_spin_diag<C><<<(int)std::min<int64_t>(div_up(tot, 256), 32 * kNumSMs), 256, 0, ctx.stream>>>(nh, nrhs, q[0], q[1],
+                                                                                               in, out);
+  QD_LAUNCH_CHECK();
+}
+template void spin_diag<cplx>(qd_ctx&, int64_t, int, const cplx*, const cplx*, cplx*);
+template void spin_diag<cplxf>(qd_ctx&, int64_t, int, const cplx*, const cplxf*, cplxf*);
 
 template <class C>
 void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, double tau,

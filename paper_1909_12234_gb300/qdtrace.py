@@ -69,7 +69,8 @@ class SolverParams(ctypes.Structure):
                 ("precision", ctypes.c_int),
                 ("inner_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int),
-                ("stag_window", ctypes.c_int)]
+                ("stag_window", ctypes.c_int),
+                ("schur", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -156,6 +157,8 @@ SIGNATURES = {
     "qd_rademacher": (_I, [_P, _P, ctypes.c_uint64, ctypes.c_int64, _I, _P]),
     "qd_dirac_apply": (_I, [_P, _P, _D, _D, _I, _I, _P, _P]),
     "qd_dirac_apply_f32": (_I, [_P, _P, _D, _D, _I, _I, _P, _P]),
+    "qd_dirac_schur_apply": (_I, [_P, _P, _D, _D, _I, _P, _P]),
+    "qd_dirac_schur_apply_f32": (_I, [_P, _P, _D, _D, _I, _P, _P]),
     "qd_mg_params_default": (None, [ctypes.POINTER(MGParams)]),
     "qd_mg_setup": (_I, [_P, _P, _D, _D, ctypes.POINTER(MGParams), _P, _PP]),
     "qd_mg_destroy": (_I, [_P]),
@@ -363,6 +366,17 @@ def dirac_apply_f32(ctx, gauge, m0, tau, dagger, nrhs, inp, out):
     """FP32 operator on torch.complex64 fields in qd layout."""
     _check(load().qd_dirac_apply_f32(ctx.h, gauge.h, float(m0), float(tau), 1 if dagger else 0, int(nrhs),
                                      _ptr64(inp), _ptr64(out)))
+
+
+def dirac_schur_apply(ctx, gauge, m0, tau, nrhs, inp, out):
+    """Odd-site Schur complement S on half fields (odd half of the qd layout), FP64."""
+    _check(load().qd_dirac_schur_apply(ctx.h, gauge.h, float(m0), float(tau), int(nrhs), _ptr(inp), _ptr(out)))
+
+
+def dirac_schur_apply_f32(ctx, gauge, m0, tau, nrhs, inp, out):
+    """The same in FP32 (torch.complex64)."""
+    _check(load().qd_dirac_schur_apply_f32(ctx.h, gauge.h, float(m0), float(tau), int(nrhs), _ptr64(inp),
+                                           _ptr64(out)))
 
 
 def mg_params(nlevels=1, blocks=((2, 2, 2, 2),), nvs=(12,), **kw):

@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(library):
 
 
 def test_abi_version(library):
-    assert library.qd_abi_version() == 3
+    assert library.qd_abi_version() == 4
 
 
 def test_struct_layouts_match_c(tmp_path):
@@ -58,8 +58,9 @@ int main(void) {
          offsetof(qd_defl_params, tau_restart), offsetof(qd_defl_params, fail_first));
   printf("%zu %zu %zu\n", sizeof(qd_trace_params), offsetof(qd_trace_params, solver),
          offsetof(qd_trace_params, dilution));
-  printf("%zu %zu %zu %zu\n", sizeof(qd_solver_params), offsetof(qd_solver_params, inner_tol),
-         offsetof(qd_solver_params, max_refine), offsetof(qd_solver_params, stag_window));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(qd_solver_params), offsetof(qd_solver_params, inner_tol),
+         offsetof(qd_solver_params, max_refine), offsetof(qd_solver_params, stag_window),
+         offsetof(qd_solver_params, schur));
   printf("%zu %zu %zu\n", sizeof(qd_trace_result), offsetof(qd_trace_result, nsamples), offsetof(qd_trace_result, UhKZ));
   printf("%zu %zu %zu\n", sizeof(qd_smoother_params), offsetof(qd_smoother_params, seed), offsetof(qd_smoother_params, mr_steps));
   printf("%zu %zu\n", sizeof(qd_smoother_info), offsetof(qd_smoother_info, enabled));
@@ -78,7 +79,7 @@ int main(void) {
          qd.DeflParams.fail_first.offset],
         [ctypes.sizeof(qd.TraceParams), qd.TraceParams.solver.offset, qd.TraceParams.dilution.offset],
         [ctypes.sizeof(qd.SolverParams), qd.SolverParams.inner_tol.offset, qd.SolverParams.max_refine.offset,
-         qd.SolverParams.stag_window.offset],
+         qd.SolverParams.stag_window.offset, qd.SolverParams.schur.offset],
         [ctypes.sizeof(qd.TraceResult), qd.TraceResult.nsamples.offset, qd.TraceResult.UhKZ.offset],
         [ctypes.sizeof(qd.SmootherParams), qd.SmootherParams.seed.offset, qd.SmootherParams.mr_steps.offset],
         [ctypes.sizeof(qd.SmootherInfo), qd.SmootherInfo.enabled.offset],
@@ -106,7 +107,7 @@ def test_defaults(library):
     d = qd.defl_params()
     assert d.kind == qd.QD_DEFL_MG_OBLIQUE and d.k == 24
     sp = qd.solver_params()
-    assert sp.tol == 1e-8 and sp.precision == qd.QD_PREC_F64 and sp.inner_tol == 1e-5
+    assert sp.tol == 1e-8 and sp.precision == qd.QD_PREC_F64 and sp.inner_tol == 1e-5 and sp.schur == 0
     assert p.coarsest_direct == 16384 and p.coarsest_bf16 == 1 and p.use_graphs == 1
     sm = qd.smoother_params()
     assert sm.nsamples == 8 and sm.solve_tol == 1e-6 and sm.seed == 4242 and sm.mr_steps == 2

@@ -124,3 +124,41 @@ def test_gauge_covariance():
     lhs = wilson.dirac_apply(Ug, gx, -0.4, dims, tau=0.1)
     rhs = np.einsum("vab,vsbr->vsar", g, wilson.dirac_apply(U, x, -0.4, dims, tau=0.1))
     assert np.abs(lhs - rhs).max() < 1e-12
+
+
+@pytest.mark.parametrize("dims,tau", [((4, 4, 2, 2), 0.0), ((4, 2, 2, 4), 0.3)])
+def test_schur_complement_eliminates_even_sites(dims, tau):
+    # through the matrix-free operator: with x_e = -A_ee^{-1} A_eo x_o (A_ee
+    # = (4 + m0) + i tau gamma5 written out here), the full field X = (x_e,
+    # x_o) has (A X)_e = 0 and (A X)_o = S x_o
+    from oracle import lattice
+    m0 = -0.4
+    U = synth.random_su3_links(dims, 0.4, 3)
+    S, od = wilson.schur_odd_sparse(U, m0, dims, tau)
+    V = int(np.prod(dims))
+    par = lattice.parity(dims)
+    rng = np.random.default_rng(2)
+    X = np.zeros((V, 4, 3), dtype=np.complex128)
+    X[par == 1] = rng.standard_normal((len(od), 4, 3)) + 1j * rng.standard_normal((len(od), 4, 3))
+    Ax = wilson.dirac_apply(U, X[..., None], m0, dims, tau=tau)[..., 0]  # (A_eo x_o) on even sites
+    m = 4.0 + m0
+    g5 = np.array([1.0, 1.0, -1.0, -1.0])[None, :, None]
+    inv_diag = (m - 1j * tau * g5) / (m * m + tau * tau)
+    X[par == 0] = -(inv_diag * Ax)[par == 0]
+    AX = wilson.dirac_apply(U, X[..., None], m0, dims, tau=tau)[..., 0]
+    assert np.abs(AX[par == 0]).max() < 1e-12
+    Sx = (S @ X[par == 1].reshape(-1)).reshape(-1, 4, 3)
+    assert np.abs(AX[par == 1] - Sx).max() < 1e-12
+
+
+def test_schur_complement_is_inverse_of_odd_block():
+    # (A^{-1})_oo = S^{-1} (block inverse), dense on a 4 x 2 x 2 x 2 lattice
+    from oracle import lattice
+    dims, m0, tau = (4, 2, 2, 2), -0.3, 0.2
+    U = synth.random_su3_links(dims, 0.5, 4)
+    A = wilson.dirac_sparse(U, m0, dims, tau).toarray()
+    S, od = wilson.schur_odd_sparse(U, m0, dims, tau)
+    O = (12 * od[:, None] + np.arange(12)[None, :]).ravel()
+    Ainv = np.linalg.inv(A)
+    assert np.abs(Ainv[np.ix_(O, O)] @ S.toarray() - np.eye(len(O))).max() < 1e-10
+    assert len(od) == lattice.volume(dims) // 2

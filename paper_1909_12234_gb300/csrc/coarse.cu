@@ -221,7 +221,11 @@ void prolongate(qd_ctx& ctx, const Transfer& T, const C* W, const C* coarse, C* 
       T.nfine * T.Df * (int64_t)nrhs < ((int64_t)1 << 31)) {
     const int nr2 = nrhs / 2;
     const int tps = nr2 < 256 ? nr2 : 256;
-    const int spb = 256 / tps;
+    // sites per block: 256 threads at most, their W in at most 32 KB
+    const int wsite = T.Df * (T.nv / 2) * (int)sizeof(float4);
+    int spb = 256 / tps;
+    if (spb * wsite > 32 * 1024) spb = 32 * 1024 / wsite;
+    if (spb < 1) spb = 1;
     const int nsites = (int)T.nfine;
     const int blocks = (int)std::min<int64_t>(div_up(nsites, spb), 16 * kNumSMs);
     const size_t smem = (size_t)spb * T.Df * (T.nv / 2) * sizeof(float4);

@@ -52,11 +52,12 @@ import numpy as np  # noqa: E402
 # per step, mixed precision with the learned smoother (the metric's form).
 CONFIG3 = dict(
     workload="wilson-dirac 16^3x32 eps0.2 seed3 m0=-0.8, 3-level MG (2^4, 2^4; nv 12, 16; level-1 GCR 6 its; "
-             "coarse MR 2), Algorithm 2 k=24 on the coarsest level, 128 Rademacher samples/step, learned smoother "
-             "+ 1 MR, FP32 GCR(8) inner solves with FP64 refinement to true rel. residual 1e-8",
+             "coarse MR 1), Algorithm 2 k=24 on the coarsest level, 128 Rademacher samples/step, learned smoother "
+             "+ 1 MR, even-odd (odd-site Schur complement) FP32 GCR(4) inner solves with FP64 refinement to true "
+             "rel. residual 1e-8",
     dims=(16, 16, 16, 32), eps=0.2, link_seed=3, m0=-0.8, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16],
-    k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=8, maxit=500, inner_tol=1e-5,
-    mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6, "coarse_smoother_steps": 2},
+    k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=4, maxit=500, inner_tol=1e-5, schur=1,
+    mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6, "coarse_smoother_steps": 1},
     learned=1, eig_maxit=30, fp64_samples=16,
 )
 # Config 2: 8^4 lattice (the two-level workload of round one), kept for
@@ -1079,6 +1080,8 @@ def main():
     ap.add_argument("--reps", type=int, default=20, help="launches timed per kernel with --kernel")
     ap.add_argument("--no-tune", action="store_true",
                     help="launch shapes fixed at their defaults (nothing timed by the autotuner)")
+    ap.add_argument("--candidate", type=int, default=-1,
+                    help=">= 0: with --kernel, launch shape k of every tunable kernel where it applies")
     args = ap.parse_args()
     if args.no_tune:
         from paper_1909_12234_gb300 import qdtrace as qd
@@ -1090,6 +1093,8 @@ def main():
         ctx = qd.Context(0)
         names = (["coarse_tc", "restrict_tc", "prolong_l1", "prolong_l2", "wilson_f32"] if args.kernel == "all"
                  else args.kernel.split(","))
+        if args.candidate >= 0:
+            qd.autotune_force(args.candidate)
         print(json.dumps({"kernels_alone": kernel_only(qd, ctx, names, args.reps)}))
         ctx.close()
         return 0

@@ -647,7 +647,8 @@ void qd_autotune_clear(void);
  * returns to the mode above.  Process-wide.  Lets a test compare every
  * launch shape of a kernel (coarse stencil on tensor cores: 0-3 input split
  * into operand tiles first, at most 8/4/3/2 operand slots; 4-6 input
- * converted in the kernel, 2/3/4 staging slots). */
+ * converted in the kernel, 2/3/4 staging slots; 7-8 split tiles, at most 8/4
+ * slots, one bulk copy per 4 KB tile region). */
 void qd_autotune_force(int candidate);
 /* The table as text, one line per shape key: the key, the chosen candidate,
  * then each candidate's best time in ms (-1: not applicable).  Writes at most

@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(256) k_split_tiles(int64_t nsites, int s, int 
 // (bulk-copied), its compact coefficients (bulk-copied) and its B tile
 // (built by the converter warps).  Roles as in k_block_tc; barriers per
 // slot: full (copies landed), bready (B tile built), empty (MMAs done).
-template <int D>
+template <int D, bool REGION_COPIES>
 __global__ void __launch_bounds__(kThreads, 1)
     k_stencil_tc_split(int64_t nout, int s, int nchunks, int NA, uint32_t slot_bytes, uint32_t b_tile,
                        const int* __restrict__ src, const uint32_t* __restrict__ Bsrc,
@@ -497,7 +497,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t slot = base + (uint32_t)as * slot_bytes;
           const uint32_t bar = smem_u32(&full[as]);
           mbar_expect_tx(bar, kTile + kCBytes);
-          bulk_g2s(slot, tiles + (size_t)(nb * nchunks + ch) * kTile, kTile, bar);
+          const unsigned char* tsrc = tiles + (size_t)(nb * nchunks + ch) * kTile;
+          if (REGION_COPIES) {
+            // one copy per 4 KB region (part, K step): more requests in flight
+#pragma unroll
+            for (int k = 0; k < 2 * KSTEPS; ++k)
+              bulk_g2s(slot + (uint32_t)k * kSplitRegion, tsrc + (size_t)k * kSplitRegion, kSplitRegion, bar);
+          } else {
+            bulk_g2s(slot, tsrc, kTile, bar);
+          }
           bulk_g2s(slot + c_off, Bsrc + (x * NSTEP + j) * (int64_t)kBWords, kCBytes, bar);
           last_use[as] = ua;
         }
@@ -623,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // them; false (nothing launched) when fewer than two operand slots fit.
 template <int D>
 bool launch_split(qd_ctx& ctx, int64_t nout, const int* src, const uint32_t* Bsrc, const cplxf* in, unsigned char* tiles,
-                  cplxf* out, int s, int* err, int NA_max) {
+                  cplxf* out, int s, int* err, int NA_max, bool region_copies) {
   constexpr uint32_t kTile = split_tile_bytes<D>();
   constexpr int KSTEPS = (2 * D + 15) / 16;
   const int nchunks = (s + 127) / 128;
@@ -640,10 +648,11 @@ bool launch_split(qd_ctx& ctx, int64_t nout, const int* src, const uint32_t* Bsr
   k_split_tiles<D><<<sgrid, 256, 0, ctx.stream>>>(nout, s, nchunks, reinterpret_cast<const float2*>(in), tiles);
   QD_LAUNCH_CHECK();
   const size_t smem = 1024 + (size_t)NA * slot;
-  ensure_smem_limit(reinterpret_cast<const void*>(k_stencil_tc_split<D>), smem);
   const int64_t items = nout * (int64_t)nchunks;
   const int grid = (int)(items < kNumSMs ? items : kNumSMs);
-  k_stencil_tc_split<D><<<grid, kThreads, smem, ctx.stream>>>(nout, s, nchunks, NA, slot, b_tile, src, Bsrc, tiles,
+  auto kern = region_copies ? k_stencil_tc_split<D, true> : k_stencil_tc_split<D, false>;
+  ensure_smem_limit(reinterpret_cast<const void*>(kern), smem);
+  kern<<<grid, kThreads, smem, ctx.stream>>>(nout, s, nchunks, NA, slot, b_tile, src, Bsrc, tiles,
                                                               reinterpret_cast<float2*>(out), err);
   QD_LAUNCH_CHECK();
   return true;

@@ -88,7 +88,7 @@ __global__ void k_prolong(int64_t nfine, int Df, int nv, int nrhs, const int* __
 // that chirality.  Same products in the same order as k_prolong, so the
 // results are identical.
 template <int NV>
-__global__ void __launch_bounds__(256) k_prolong_f32x2(int nsites, int bsites, int Df, int nrhs2, int tps, int spb,
+__global__ void __launch_bounds__(256, NV <= 12 ? 3 : 2) k_prolong_f32x2(int nsites, int bsites, int Df, int nrhs2, int tps, int spb,
                                                       const int* __restrict__ members, const float4* __restrict__ W,
                                                       const float4* __restrict__ coarse, float4* __restrict__ fine) {
   extern __shared__ float4 wsm[];  // [spb][Df][NV / 2]

@@ -12,7 +12,7 @@ namespace qd {
 
 namespace {
 
-constexpr int kCoarseTcCandidates = 7;
+constexpr int kCoarseTcCandidates = 9;
 
 // Compact split-BF16 copy of the stencil: for block (x, dir) of D x D
 // entries, Cb[(x*9 + dir)][0][d][e] = hi and [1][d][e] = lo of (Re, Im) C,
@@ -35,11 +35,12 @@ bool launch(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int
 }
 
 template <int D>
-bool launch_split(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int s, int* err, int NA) {
+bool launch_split(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int s, int* err, int NA,
+                  bool region_copies) {
   const size_t need = (size_t)lv.geo.nsites * ((s + 127) / 128) * blocktc::split_tile_bytes<D>();
   if (lv.ctc_tiles.bytes() < need) lv.ctc_tiles.resize(need);
   return blocktc::launch_split<D>(ctx, lv.geo.nsites, lv.sten_src.as<int>(), lv.Cmb.as<uint32_t>(), in,
-                                  lv.ctc_tiles.as<unsigned char>(), out, s, err, NA);
+                                  lv.ctc_tiles.as<unsigned char>(), out, s, err, NA, region_copies);
 }
 
 }  // namespace
@@ -83,12 +84,13 @@ void coarse_apply_tc(qd_ctx& ctx, CoarseLevel& lv, const cplxf* in, cplxf* out, 
                (double)lv.geo.nsites * (9.0 * D * D * 8.0 + 2.0 * D * 8.0 * s));
   int* err = lv.ctc_err.as<int>();
   // candidates 0-3: the input split once into operand tiles first
-  // (k_split_tiles), at most 8, 4, 3 or 2 operand slots; 4-6: the input
-  // blocks converted inside the kernel with 2, 3 or 4 staging slots.  Every
-  // candidate forms the same BF16 operands and issues the same MMAs in the
-  // same order.
+  // (k_split_tiles), at most 8, 4, 3 or 2 operand slots, one bulk copy per
+  // tile; 4-6: the input blocks converted inside the kernel with 2, 3 or 4
+  // staging slots; 7-8: split tiles, at most 8 or 4 slots, one bulk copy per
+  // 4 KB region of a tile.  Every candidate forms the same BF16 operands and
+  // issues the same MMAs in the same order.
   auto go = [&](int c) -> bool {
-    if (c >= 4) {
+    if (c >= 4 && c <= 6) {
       const int NS = c - 2;
       switch (lv.D) {
         case 8: return launch<8>(ctx, lv, in, out, s, err, NS);
@@ -97,13 +99,14 @@ void coarse_apply_tc(qd_ctx& ctx, CoarseLevel& lv, const cplxf* in, cplxf* out, 
         default: return launch<32>(ctx, lv, in, out, s, err, NS);
       }
     }
-    static const int kNA[4] = {8, 4, 3, 2};
+    static const int kNA[9] = {8, 4, 3, 2, 0, 0, 0, 8, 4};
     const int NA = kNA[c];
+    const bool rc = c >= 7;
     switch (lv.D) {
-      case 8: return launch_split<8>(ctx, lv, in, out, s, err, NA);
-      case 16: return launch_split<16>(ctx, lv, in, out, s, err, NA);
-      case 24: return launch_split<24>(ctx, lv, in, out, s, err, NA);
-      default: return launch_split<32>(ctx, lv, in, out, s, err, NA);
+      case 8: return launch_split<8>(ctx, lv, in, out, s, err, NA, rc);
+      case 16: return launch_split<16>(ctx, lv, in, out, s, err, NA, rc);
+      case 24: return launch_split<24>(ctx, lv, in, out, s, err, NA, rc);
+      default: return launch_split<32>(ctx, lv, in, out, s, err, NA, rc);
     }
   };
   const std::string key = "coarse_tc D" + std::to_string(lv.D) + " sites" + std::to_string(lv.geo.nsites) + " rhs" +

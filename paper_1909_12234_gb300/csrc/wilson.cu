@@ -273,8 +273,8 @@ __device__ __forceinline__ void hop2_dir(const float2* __restrict__ U, const int
 // lattice is traversed once per chunk, so that the spinors a traversal keeps
 // in flight between a site and its farthest neighbour in visiting order take
 // less L2 (a chunk of 2 rc2 = nrhs is the plain order).
-template <bool DAG, bool RESID>
-__global__ void __launch_bounds__(128, 4) k_wilson_f32x2(const float2* __restrict__ U, const int* __restrict__ nbr,
+template <bool DAG, bool RESID, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_wilson_f32x2(const float2* __restrict__ U, const int* __restrict__ nbr,
                                                       const int* __restrict__ visit, int64_t V, int nrhs, int rc2,
                                                       float mass, float tau,
                                                       const float2* __restrict__ in, float2* __restrict__ out,
@@ -494,10 +494,12 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
   const int* nb = geo.nbr.as<int>();
   const int* vis = geo.visit.as<int>();
   const double mass = 4.0 + m0;
-  // candidates 0, 2, 3: two right-hand sides per thread (FP32, even nrhs,
-  // 16-byte aligned fields), the columns swept whole, in chunks of 64 or in
-  // chunks of 32; candidate 1: one per thread.  The FP32 choice is tuned.
-  auto launch_x2 = [&](int rc) -> bool {
+  // candidates 0, 2-7: two right-hand sides per thread (FP32, even nrhs,
+  // 16-byte aligned fields), the columns swept whole or in chunks, in blocks
+  // of 128, 256 or 512 threads (a block of nt threads covers nt / (chunk / 2)
+  // consecutive sites of the visiting order, whose shared neighbours then
+  // hit in L1); candidate 1: one per thread.  The FP32 choice is tuned.
+  auto launch_x2 = [&](int rc, int nt) -> bool {
     if (!(sizeof(C) == 8 && (nrhs % 2) == 0 &&
           ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(b)) &
            15) == 0))
@@ -506,26 +508,29 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
     if (rc > nrhs || nrhs % rc != 0 || rc % 2 != 0) return false;
     const int rc2 = rc / 2;
     const int64_t tot2 = geo.nsites * (nrhs / 2);
-    const int blocks2 = div_up(tot2, threads);
     const float2* L = reinterpret_cast<const float2*>(links);
     const float2* xin = reinterpret_cast<const float2*>(in);
     float2* yout = reinterpret_cast<float2*>(out);
     const float2* bb = reinterpret_cast<const float2*>(b);
     const float fm = (float)mass, ft = (float)tau;
+    auto go = [&](auto kern) {
+      kern<<<(int)div_up(tot2, nt), nt, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin, yout, bb);
+    };
+    auto pick = [&](auto k128, auto k256, auto k512) {
+      if (nt == 512) go(k512);
+      else if (nt == 256) go(k256);
+      else go(k128);
+    };
     if (b) {
       if (dagger)
-        k_wilson_f32x2<true, true><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin, yout,
-                                                                        bb);
+        pick(k_wilson_f32x2<true, true, 128>, k_wilson_f32x2<true, true, 256>, k_wilson_f32x2<true, true, 512>);
       else
-        k_wilson_f32x2<false, true><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin,
-                                                                         yout, bb);
+        pick(k_wilson_f32x2<false, true, 128>, k_wilson_f32x2<false, true, 256>, k_wilson_f32x2<false, true, 512>);
     } else {
       if (dagger)
-        k_wilson_f32x2<true, false><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin,
-                                                                         yout, nullptr);
+        pick(k_wilson_f32x2<true, false, 128>, k_wilson_f32x2<true, false, 256>, k_wilson_f32x2<true, false, 512>);
       else
-        k_wilson_f32x2<false, false><<<blocks2, threads, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin,
-                                                                          yout, nullptr);
+        pick(k_wilson_f32x2<false, false, 128>, k_wilson_f32x2<false, false, 256>, k_wilson_f32x2<false, false, 512>);
     }
     QD_LAUNCH_CHECK();
     return true;
@@ -553,18 +558,22 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
   }
   auto launch = [&](int c) -> bool {
     switch (c) {
-      case 0: return launch_x2(0);
+      case 0: return launch_x2(0, 128);
       case 1: return launch_x1();
-      case 2: return nrhs > 64 && launch_x2(64);
-      default: return nrhs > 32 && launch_x2(32);
+      case 2: return nrhs > 64 && launch_x2(64, 128);
+      case 3: return nrhs > 32 && launch_x2(32, 128);
+      case 4: return nrhs > 32 && launch_x2(32, 256);
+      case 5: return nrhs > 32 && launch_x2(32, 512);
+      case 6: return nrhs > 16 && launch_x2(16, 512);
+      default: return nrhs > 64 && launch_x2(64, 512);
     }
   };
   // the residual form writes out = b - A in: out-of-place, safe to repeat
   const std::string key = std::string("wilson f32 sites") + std::to_string(geo.nsites) + " rhs" +
                           std::to_string(nrhs) + (b ? " resid" : "") + (dagger ? " dag" : "");
-  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 4, launch);
+  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 8, launch);
   if (c >= 0 && launch(c)) return;
-  if (!launch_x2(0)) launch_x1();
+  if (!launch_x2(0, 128)) launch_x1();
 }
 
 template void wilson_apply<cplx>(qd_ctx&, const LevelGeom&, const cplx*, double, double, bool,

@@ -33,7 +33,7 @@ from gpu_util import dev, host, need_gpu, torch
 pytestmark = pytest.mark.gpu
 
 U_BF16 = 2.0 ** -8
-N_TC_CANDIDATES = 7  # launch shapes of the tensor-core stencil
+N_TC_CANDIDATES = 9  # launch shapes of the tensor-core stencil
 
 
 @pytest.fixture(scope="module")

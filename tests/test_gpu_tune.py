@@ -65,9 +65,9 @@ def test_autotuned_shapes_match_defaults(qd, ctx):
 
 def test_wilson_f32_launch_shapes(qd, ctx):
     # the FP32 Wilson stencil's shapes: two columns per thread swept whole
-    # (0), in chunks of 64 (2) or of 32 columns (3) -- the same arithmetic per
-    # element, so the same bits -- and one column per thread (1), which
-    # agrees to FP32 rounding; A and A^H
+    # (0) or in chunks of 64, 32 or 16 columns with blocks of 128-512
+    # threads (2-7) -- the same arithmetic per element, so the same bits --
+    # and one column per thread (1), which agrees to FP32 rounding; A and A^H
     dims = (8, 8, 8, 8)
     U = synth.random_su3_links(dims, 0.3, 2)
     g = qd.Gauge(ctx, dims, U)
@@ -77,12 +77,12 @@ def test_wilson_f32_launch_shapes(qd, ctx):
                              generator=torch.Generator("cuda:0").manual_seed(s))
             for dag in (False, True):
                 outs = {}
-                for cand in range(4):
+                for cand in range(8):
                     qd.autotune_force(cand)
                     yf = torch.full_like(xf, float("nan"))
                     qd.dirac_apply_f32(ctx, g, -0.8, 0.1, dag, s, xf, yf)
                     outs[cand] = yf
-                for cand in (2, 3):
+                for cand in (2, 3, 4, 5, 6, 7):
                     assert torch.equal(outs[0], outs[cand]), (s, dag, cand)
                 assert rel_err(host(outs[1]), host(outs[0])) < 1e-6, (s, dag)
     finally:

@@ -912,6 +912,16 @@ def run_batch(args):
                  "ms_per_launch": pt["ms"] / max(pt["launches"], 1)})
     kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share_of_step": round(v["ms"] / ms_prof, 4)}
                for k, v in prof.items() if v["launches"]}
+    # what a single persistent launch over the batch could gain: its step
+    # cannot take less than the device time of the same kernels (summed
+    # CUDA-event time of every instrumented kernel of one sequential step);
+    # the rest of a step is launch gaps, host synchronisation and the small
+    # uninstrumented kernels
+    busy = sum(v["ms"] for v in prof.values())
+    persistent_bound = {"device_busy_ms": round(busy, 3), "sequential_ms": round(ms_seq / args.steps, 3),
+                        "concurrent_ms": round(ms / args.steps, 3),
+                        "sequential_idle_fraction": round(1.0 - busy / (ms_seq / args.steps), 4),
+                        "concurrent_over_busy": round((ms / args.steps) / busy, 4)}
 
     # end to end: links from pinned host memory, setup of all three, one batch
     pinned = []
@@ -943,6 +953,7 @@ def run_batch(args):
                    "l2": "16^4 fields (0.8-1.6 GB) exceed L2", "setup_s": round(setup_s, 3),
                    "max_true_rel_residual": worst, "bit_identical_to_sequential": same,
                    "sequential": {"value": args.steps * total / (ms_seq / 1e3), "ms_per_step": ms_seq / args.steps},
+                   "persistent_launch_bound": persistent_bound,
                    "estimates": [[r["estimate"].real, r["stderr"]] for r in res[-1]],
                    "autotune": {k: v[0] for k, v in tune.items()}},
         "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
@@ -951,6 +962,65 @@ def run_batch(args):
     print(json.dumps(line))
     close(probs)
     ctx.close()
+    return 0
+
+
+# Smoother depth at equal cost (scope row f3): on the 16^3 x 32 workload,
+# the plain MR smoother, the one-layer learned smoother with 1 or 2 MR steps
+# after it, and stacks of 2 and 3 layers (S = S_L ... S_1, each layer the
+# one-hop form, trained layer by layer) with 0 or 1 MR steps.  Cost is what
+# samples/s measures: every variant runs the same 128-sample batches.
+SMOOTHER_DEPTH = [(0, 0), (1, 1), (1, 2), (2, 0), (2, 1), (3, 0)]  # (layers, MR steps); layers 0 = plain MR
+
+
+def run_smoother_depth(args):
+    import torch
+    from paper_1909_12234_gb300 import qdtrace as qd
+    from paper_1909_12234_gb300 import synth
+
+    if int(os.environ.get("WORLD_SIZE", "1")) != 1 or args.gpus != 1:
+        raise SystemExit("the smoother-depth comparison runs on one GPU")
+    WL.clear()
+    WL.update(CONFIG3)
+    qd.load()
+    ctx = qd.Context(0)
+    U = synth.random_su3_links(WL["dims"], WL["eps"], WL["link_seed"])
+    wl = dict(WL, learned=0)
+    g, mg, d, _ = _setup(qd, ctx, U, wl)
+    s = WL["s"]
+    rows = []
+    for layers, mr in SMOOTHER_DEPTH:
+        info = None
+        if layers:
+            t = time.perf_counter()
+            info = qd.smoother_train(mg, nsamples=4, solve_tol=1e-3, mr_steps=mr, layers=layers)
+            train_s = time.perf_counter() - t
+            qd.smoother_enable(mg, True, mr)  # measured whatever the held-out judge said
+        else:
+            train_s = 0.0
+            if qd.smoother_layers(mg):
+                qd.smoother_enable(mg, False, 0)
+        for i in range(args.warmup):
+            _batch(qd, ctx, g, mg, d, 5000 * i, qd.QD_PREC_MIXED)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        res = [_batch(qd, ctx, g, mg, d, 100000 + 1000 * i, qd.QD_PREC_MIXED) for i in range(args.steps)]
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        row = {"layers": layers, "mr_steps": mr if layers else "plain MR(%d)" % _mg_params(qd).smoother_steps,
+               "samples_per_s": s / (ms / 1e3), "ms_per_step": ms,
+               "outer_iterations": [r["iterations"] for r in res],
+               "max_true_rel_residual": max(r["max_true_rel_residual"] for r in res), "train_s": train_s}
+        if info:
+            row.update(held_out_err_learned=info["err_learned"], held_out_err_plain=info["err_plain"],
+                       judge_enables=info["enabled"])
+        rows.append(row)
+        sys.stderr.write(json.dumps(row) + "\n")
+    print(json.dumps({"workload": "smoother depth at equal cost: " + WL["workload"], "unit": UNIT, "rows": rows}))
+    for o in (d, mg, g, ctx):
+        o.close()
     return 0
 
 
@@ -1060,7 +1130,7 @@ def main():
     ap.add_argument("--no-errors", action="store_true", help="skip the errors-against-the-oracle leg")
     ap.add_argument("--prof-steps", type=int, default=2)
     ap.add_argument("--workload", default="config3",
-                    choices=sorted(WORKLOADS) + ["config4", "config5", "deflation"])
+                    choices=sorted(WORKLOADS) + ["config4", "config5", "deflation", "smoother-depth"])
     ap.add_argument("--stencil-only", action="store_true",
                     help="only the Wilson stencil alone on 16^3 x 32 (a profiling target)")
     ap.add_argument("--small", action="store_true",
@@ -1109,12 +1179,14 @@ def main():
         print(json.dumps({"stencil": stencil_roofline(qd, ctx)}))
         ctx.close()
         return 0
-    if args.workload in ("config4", "config5", "deflation"):
+    if args.workload in ("config4", "config5", "deflation", "smoother-depth"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-lattice workload"}))
             return 0
         if args.workload == "deflation":
             return run_deflation_compare(args)
+        if args.workload == "smoother-depth":
+            return run_smoother_depth(args)
         return run_batch(args) if args.workload == "config4" else run_learned(args)
     WL.clear()
     WL.update(WORKLOADS[args.workload])

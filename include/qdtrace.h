@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define QD_ABI_VERSION 4
+#define QD_ABI_VERSION 5
 #define QD_MAX_LEVELS 4 /* fine level + up to 3 coarse levels */
 
 typedef enum {
@@ -593,6 +593,10 @@ typedef struct {
   double solve_tol;  /* relative residual of the solves e = A^{-1} r (1e-6) */
   uint64_t seed;     /* Philox key of the random vectors (4242) */
   int mr_steps;      /* minimal-residual steps after S in the V-cycle (2) */
+  int layers;        /* 1 (default) - 4: S = S_L ... S_1, a stack of layers of
+                        the form above (L-hop reach, L applications per use),
+                        trained layer by layer: S_l fits e ~ S_l (S_{l-1} ...
+                        S_1 r) with the layers below fixed */
 } qd_smoother_params;
 
 typedef struct {
@@ -615,9 +619,17 @@ int qd_smoother_train(qd_mg* mg, const qd_smoother_params* p, qd_smoother_info* 
  * columns each); the enabled state is unchanged.  Synchronous. */
 int qd_smoother_fit(qd_mg* mg, int nrhs, const double* e, const double* r);
 
-/* Host weights w[9][4][4] (complex, 2 doubles each): set / read. */
+/* Host weights w[9][4][4] (complex, 2 doubles each): set (one layer) /
+ * read (the first layer). */
 int qd_smoother_set_weights(qd_mg* mg, const double* w);
 int qd_smoother_get_weights(const qd_mg* mg, double* w);
+/* Layered form: layers (1-4) x 144 complex weights, first layer first (the
+ * layer applied first to r). */
+int qd_smoother_set_layer_weights(qd_mg* mg, int layers, const double* w);
+/* Number of layers of the current weights (0: none), and their weights
+ * (layers x 144 complex, host). */
+int qd_smoother_layers(const qd_mg* mg);
+int qd_smoother_get_layer_weights(const qd_mg* mg, double* w);
 
 /* Use S in the V-cycle (enabled != 0, weights must be set) with mr_steps
  * minimal-residual steps after it, or go back to the plain smoother. */

@@ -854,6 +854,7 @@ void qd_smoother_params_default(qd_smoother_params* p) {
   p->solve_tol = 1e-6;
   p->seed = 4242;
   p->mr_steps = 2;
+  p->layers = 1;
 }
 
 int qd_smoother_train(qd_mg* mg, const qd_smoother_params* p, qd_smoother_info* info) {
@@ -864,7 +865,7 @@ int qd_smoother_train(qd_mg* mg, const qd_smoother_params* p, qd_smoother_info* 
     set_device(mg->ctx);
     double el = 0.0, ep = 0.0;
     int en = 0;
-    qd::smoother_train(*mg, p->nsamples, p->solve_tol, p->seed, p->mr_steps, &el, &ep, &en);
+    qd::smoother_train(*mg, p->nsamples, p->solve_tol, p->seed, p->mr_steps, p->layers, &el, &ep, &en);
     if (info) {
       info->err_learned = el;
       info->err_plain = ep;
@@ -899,6 +900,27 @@ int qd_smoother_get_weights(const qd_mg* mg, double* w) {
     NONNULL(w);
     QD_REQUIRE(mg->ls != nullptr, "no learned-smoother weights set");
     std::memcpy(w, mg->ls->w.data(), 144 * sizeof(qd::cplx));
+  });
+}
+
+int qd_smoother_set_layer_weights(qd_mg* mg, int layers, const double* w) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(w);
+    QD_REQUIRE(layers >= 1 && layers <= 4, "layers must be in [1, 4]");
+    set_device(mg->ctx);
+    qd::smoother_set_layers(*mg, layers, reinterpret_cast<const qd::cplx*>(w));
+  });
+}
+
+int qd_smoother_layers(const qd_mg* mg) { return (mg && mg->ls) ? mg->ls->layers : 0; }
+
+int qd_smoother_get_layer_weights(const qd_mg* mg, double* w) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(w);
+    QD_REQUIRE(mg->ls != nullptr, "no learned-smoother weights set");
+    std::memcpy(w, mg->ls->w.data(), mg->ls->w.size() * sizeof(qd::cplx));
   });
 }
 

@@ -159,18 +159,24 @@ void schur_solve(qd_ctx& ctx, const qd_gauge& g, const C* links, double m0, doub
 // paper has no counterpart): (S r)(x) = sum_d w_d (T_d r)(x), with T_0 the
 // identity, T_{1+mu} r(x) = U_mu(x) r(x+mu), T_{5+mu} r(x) = U_mu(x-mu)^H
 // r(x-mu), and w_d 4x4 spin matrices (colour moved by links only).
+// With layers > 1, S = S_L ... S_1, each S_l a layer of the same form
+// (weights w_l): reach L hops, L applications per use.
 struct LearnedSmoother {
   bool enabled = false;
   int mr_steps = 2;                 // minimal-residual steps after S in the V-cycle
-  std::vector<cplx> w;              // [9][4][4] FP64 (fitted)
+  int layers = 1;
+  std::vector<cplx> w;              // [layers][9][4][4] FP64 (fitted)
   DevBuf w64;                       // device copy of w
   DevBuf w32;                       // w rounded to FP16, held as float2 (FP32 V-cycle)
+  mutable DevBuf t[2];              // intermediate fields of a layered apply (grow-only)
   double err_learned = 0.0, err_plain = 0.0;
 };
 
 void smoother_set_weights(qd_mg& mg, const cplx* w);
+// layers x 144 weights (layer-major).
+void smoother_set_layers(qd_mg& mg, int layers, const cplx* w);
 void smoother_fit(qd_mg& mg, int s, const cplx* e, const cplx* r);
-void smoother_train(qd_mg& mg, int s, double solve_tol, uint64_t seed, int mr_steps, double* err_learned,
+void smoother_train(qd_mg& mg, int s, double solve_tol, uint64_t seed, int mr_steps, int layers, double* err_learned,
                     double* err_plain, int* enabled);
 // out = S in (accumulate: out += S in) on the fine level, nrhs columns.
 template <class C>

@@ -195,21 +195,16 @@ __global__ void __launch_bounds__(128, 4) k_smoother_apply_x2(const float2* __re
   }
 }
 
+// out (+)= S_l in for one layer with device weights w.
 template <class C>
-void smoother_apply(qd_ctx& ctx, qd_mg& mg, int nrhs, const C* in, C* out, bool accumulate) {
-  const LearnedSmoother& ls = *mg.ls;
+static void apply_layer(qd_ctx& ctx, const qd_mg& mg, int nrhs, const C* w, const C* in, C* out, bool accumulate) {
   const LevelGeom& geo = mg.gauge->geo;
   const int64_t tot = geo.nsites * nrhs;
-  if (tot == 0) return;
   const C* links;
-  const C* w;
-  if (sizeof(C) == 16) {
+  if (sizeof(C) == 16)
     links = reinterpret_cast<const C*>(mg.gauge->links.as<cplx>());
-    w = ls.w64.as<C>();
-  } else {
+  else
     links = reinterpret_cast<const C*>(const_cast<qd_gauge*>(mg.gauge)->links_f32());
-    w = ls.w32.as<C>();
-  }
   const double cb = (double)sizeof(C);
   ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_SMOOTHER_F64 : QD_PROF_SMOOTHER_F32,
                (9.0 * 36 + 9.0 * 48) * 8.0 * (double)tot,
@@ -236,6 +231,28 @@ void smoother_apply(qd_ctx& ctx, qd_mg& mg, int nrhs, const C* in, C* out, bool 
   else
     k_smoother_apply<C, false><<<blocks, 128, 0, ctx.stream>>>(links, geo.nbr.as<int>(), geo.nsites, nrhs, w, in, out);
   QD_LAUNCH_CHECK();
+}
+
+template <class C>
+void smoother_apply(qd_ctx& ctx, qd_mg& mg, int nrhs, const C* in, C* out, bool accumulate) {
+  const LearnedSmoother& ls = *mg.ls;
+  const LevelGeom& geo = mg.gauge->geo;
+  const int64_t tot = geo.nsites * nrhs;
+  if (tot == 0) return;
+  const C* w = sizeof(C) == 16 ? ls.w64.as<C>() : ls.w32.as<C>();
+  // S_L ... S_1 in: the intermediate fields alternate between two buffers
+  const C* src = in;
+  for (int l = 0; l < ls.layers; ++l) {
+    const bool last = l == ls.layers - 1;
+    C* dst = out;
+    if (!last) {
+      DevBuf& tb = ls.t[l & 1];
+      tb.resize((size_t)tot * 12 * sizeof(C));
+      dst = tb.as<C>();
+    }
+    apply_layer<C>(ctx, mg, nrhs, w + (size_t)144 * l, src, dst, last && accumulate);
+    src = dst;
+  }
 }
 template void smoother_apply<cplx>(qd_ctx&, qd_mg&, int, const cplx*, cplx*, bool);
 template void smoother_apply<cplxf>(qd_ctx&, qd_mg&, int, const cplxf*, cplxf*, bool);
@@ -331,24 +348,30 @@ static void chol_solve(int n, int m, std::vector<cplx>& G, std::vector<cplx>& H)
 }
 
 static void upload_weights(qd_ctx& ctx, LearnedSmoother& ls) {
-  ls.w64.resize(144 * sizeof(cplx));
-  ls.w32.resize(144 * sizeof(cplxf));
-  std::vector<cplxf> h(144);
-  for (int k = 0; k < 144; ++k)
+  const size_t nw = (size_t)144 * ls.layers;
+  ls.w64.resize(nw * sizeof(cplx));
+  ls.w32.resize(nw * sizeof(cplxf));
+  std::vector<cplxf> h(nw);
+  for (size_t k = 0; k < nw; ++k)
     h[k] = make_float2(__half2float(__float2half_rn((float)ls.w[k].x)), __half2float(__float2half_rn((float)ls.w[k].y)));
-  QD_CUDA(cudaMemcpyAsync(ls.w64.as<cplx>(), ls.w.data(), 144 * sizeof(cplx), cudaMemcpyHostToDevice, ctx.stream));
-  QD_CUDA(cudaMemcpyAsync(ls.w32.as<cplxf>(), h.data(), 144 * sizeof(cplxf), cudaMemcpyHostToDevice, ctx.stream));
+  QD_CUDA(cudaMemcpyAsync(ls.w64.as<cplx>(), ls.w.data(), nw * sizeof(cplx), cudaMemcpyHostToDevice, ctx.stream));
+  QD_CUDA(cudaMemcpyAsync(ls.w32.as<cplxf>(), h.data(), nw * sizeof(cplxf), cudaMemcpyHostToDevice, ctx.stream));
   QD_CUDA(cudaStreamSynchronize(ctx.stream));
 }
 
-void smoother_set_weights(qd_mg& mg, const cplx* w) {
+void smoother_set_layers(qd_mg& mg, int layers, const cplx* w) {
+  QD_REQUIRE(layers >= 1 && layers <= 4, "layers must be in [1, 4]");
   if (!mg.ls) mg.ls.reset(new LearnedSmoother());
-  mg.ls->w.assign(w, w + 144);
+  mg.ls->layers = layers;
+  mg.ls->w.assign(w, w + (size_t)144 * layers);
   upload_weights(*mg.ctx, *mg.ls);
 }
 
-// Least-squares weights for s pairs (e, r) in fine qd layout (device).
-void smoother_fit(qd_mg& mg, int s, const cplx* e, const cplx* r) {
+void smoother_set_weights(qd_mg& mg, const cplx* w) { smoother_set_layers(mg, 1, w); }
+
+// Least-squares weights of one layer for s pairs (e, r) in fine qd layout
+// (device): e ~ S r.
+static std::vector<cplx> fit_layer(qd_mg& mg, int s, const cplx* e, const cplx* r) {
   qd_ctx& ctx = *mg.ctx;
   const LevelGeom& geo = mg.gauge->geo;
   const int64_t rows = geo.nsites * 3 * (int64_t)s;
@@ -368,6 +391,11 @@ void smoother_fit(qd_mg& mg, int s, const cplx* e, const cplx* r) {
   for (int d = 0; d < 9; ++d)
     for (int o = 0; o < 4; ++o)
       for (int i = 0; i < 4; ++i) w[(d * 4 + o) * 4 + i] = hH[(size_t)(d * 4 + i) * 4 + o];
+  return w;
+}
+
+void smoother_fit(qd_mg& mg, int s, const cplx* e, const cplx* r) {
+  const std::vector<cplx> w = fit_layer(mg, s, e, r);
   smoother_set_weights(mg, w.data());
 }
 
@@ -404,16 +432,30 @@ static double mean_rel_err(qd_ctx& ctx, int64_t n, int s, const cplx* e, const c
   return m / s;
 }
 
-void smoother_train(qd_mg& mg, int s, double solve_tol, uint64_t seed, int mr_steps, double* err_learned,
+void smoother_train(qd_mg& mg, int s, double solve_tol, uint64_t seed, int mr_steps, int layers, double* err_learned,
                     double* err_plain, int* enabled) {
   QD_REQUIRE(s >= 1 && s <= 1024, "nsamples must be in [1, 1024]");
   QD_REQUIRE(mr_steps >= 0 && mr_steps <= 64, "mr_steps must be in [0, 64]");
+  QD_REQUIRE(layers >= 1 && layers <= 4, "layers must be in [1, 4]");
   qd_ctx& ctx = *mg.ctx;
   const LevelGeom& geo = mg.gauge->geo;
   const int64_t n = geo.nsites * 12;
   DevBuf e, r;
   make_pairs(mg, s, seed, solve_tol, e, r);
-  smoother_fit(mg, s, e.as<cplx>(), r.as<cplx>());
+  // layer by layer: S_1 fits e ~ S_1 r, then S_l fits e ~ S_l (S_{l-1} ... S_1 r)
+  // with the layers below fixed (each layer's family holds the identity, so
+  // the training error cannot grow with depth)
+  std::vector<cplx> all = fit_layer(mg, s, e.as<cplx>(), r.as<cplx>());
+  smoother_set_layers(mg, 1, all.data());
+  if (layers > 1) {
+    DevBuf rl((size_t)n * s * sizeof(cplx));
+    for (int l = 2; l <= layers; ++l) {
+      smoother_apply<cplx>(ctx, mg, s, r.as<cplx>(), rl.as<cplx>(), false);
+      const std::vector<cplx> wl = fit_layer(mg, s, e.as<cplx>(), rl.as<cplx>());
+      all.insert(all.end(), wl.begin(), wl.end());
+      smoother_set_layers(mg, l, all.data());
+    }
+  }
   LearnedSmoother& ls = *mg.ls;
   ls.mr_steps = mr_steps;
   // held-out pairs: the whole smoothing step of each kind, from x = 0

@@ -721,6 +721,9 @@ template <class C> void MGPrecond<C>::run(qd_ctx& ctx, const C* r, C* z, C* Az, 
   if (ls) {
     cur.push_back(ls->w64.as<void>());
     cur.push_back(ls->w32.as<void>());
+    cur.push_back(reinterpret_cast<const void*>((uintptr_t)ls->layers));
+    cur.push_back(ls->t[0].as<void>());
+    cur.push_back(ls->t[1].as<void>());
   }
   if (!graphs_.empty() && (graphs_.front().ptrs != cur || graphs_.front().nrhs != nrhs)) {
     // another context or a reallocated buffer: run eagerly once more first

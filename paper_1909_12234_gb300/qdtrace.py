@@ -123,7 +123,7 @@ class TraceResult(ctypes.Structure):
 
 class SmootherParams(ctypes.Structure):
     _fields_ = [("nsamples", ctypes.c_int), ("solve_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("mr_steps", ctypes.c_int)]
+                ("mr_steps", ctypes.c_int), ("layers", ctypes.c_int)]
 
 
 class SmootherInfo(ctypes.Structure):
@@ -190,6 +190,9 @@ SIGNATURES = {
     "qd_smoother_fit": (_I, [_P, _I, _P, _P]),
     "qd_smoother_set_weights": (_I, [_P, _DPTR]),
     "qd_smoother_get_weights": (_I, [_P, _DPTR]),
+    "qd_smoother_set_layer_weights": (_I, [_P, _I, _DPTR]),
+    "qd_smoother_layers": (_I, [_P]),
+    "qd_smoother_get_layer_weights": (_I, [_P, _DPTR]),
     "qd_smoother_enable": (_I, [_P, _I, _I]),
     "qd_smoother_apply": (_I, [_P, _I, _P, _P]),
     "qd_smoother_apply_f32": (_I, [_P, _I, _P, _P]),
@@ -763,6 +766,24 @@ def smoother_set_weights(mg, w):
 def smoother_get_weights(mg):
     w = np.zeros((9, 4, 4), dtype=np.complex128)
     _check(load().qd_smoother_get_weights(mg.h, w.view(np.float64).ctypes.data_as(_DPTR)))
+    return w
+
+
+def smoother_set_layer_weights(mg, w):
+    """w: (layers, 9, 4, 4) complex, the layer applied first to r first."""
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.complex128))
+    layers = w.size // 144
+    _check(load().qd_smoother_set_layer_weights(mg.h, int(layers), w.view(np.float64).ctypes.data_as(_DPTR)))
+
+
+def smoother_layers(mg):
+    return int(load().qd_smoother_layers(mg.h))
+
+
+def smoother_get_layer_weights(mg):
+    L = smoother_layers(mg)
+    w = np.zeros((L, 9, 4, 4), dtype=np.complex128)
+    _check(load().qd_smoother_get_layer_weights(mg.h, w.view(np.float64).ctypes.data_as(_DPTR)))
     return w
 
 

@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(library):
 
 
 def test_abi_version(library):
-    assert library.qd_abi_version() == 4
+    assert library.qd_abi_version() == 5
 
 
 def test_struct_layouts_match_c(tmp_path):
@@ -62,7 +62,8 @@ int main(void) {
          offsetof(qd_solver_params, max_refine), offsetof(qd_solver_params, stag_window),
          offsetof(qd_solver_params, schur));
   printf("%zu %zu %zu\n", sizeof(qd_trace_result), offsetof(qd_trace_result, nsamples), offsetof(qd_trace_result, UhKZ));
-  printf("%zu %zu %zu\n", sizeof(qd_smoother_params), offsetof(qd_smoother_params, seed), offsetof(qd_smoother_params, mr_steps));
+  printf("%zu %zu %zu %zu\n", sizeof(qd_smoother_params), offsetof(qd_smoother_params, seed),
+         offsetof(qd_smoother_params, mr_steps), offsetof(qd_smoother_params, layers));
   printf("%zu %zu\n", sizeof(qd_smoother_info), offsetof(qd_smoother_info, enabled));
   printf("%zu %zu %zu %zu %zu\n", sizeof(qd_batch_item), offsetof(qd_batch_item, m0), offsetof(qd_batch_item, params),
          offsetof(qd_batch_item, result), offsetof(qd_batch_item, status));
@@ -81,7 +82,8 @@ int main(void) {
         [ctypes.sizeof(qd.SolverParams), qd.SolverParams.inner_tol.offset, qd.SolverParams.max_refine.offset,
          qd.SolverParams.stag_window.offset, qd.SolverParams.schur.offset],
         [ctypes.sizeof(qd.TraceResult), qd.TraceResult.nsamples.offset, qd.TraceResult.UhKZ.offset],
-        [ctypes.sizeof(qd.SmootherParams), qd.SmootherParams.seed.offset, qd.SmootherParams.mr_steps.offset],
+        [ctypes.sizeof(qd.SmootherParams), qd.SmootherParams.seed.offset, qd.SmootherParams.mr_steps.offset,
+         qd.SmootherParams.layers.offset],
         [ctypes.sizeof(qd.SmootherInfo), qd.SmootherInfo.enabled.offset],
         [ctypes.sizeof(qd.BatchItem), qd.BatchItem.m0.offset, qd.BatchItem.params.offset, qd.BatchItem.result.offset,
          qd.BatchItem.status.offset],
@@ -110,7 +112,7 @@ def test_defaults(library):
     assert sp.tol == 1e-8 and sp.precision == qd.QD_PREC_F64 and sp.inner_tol == 1e-5 and sp.schur == 0
     assert p.coarsest_direct == 16384 and p.coarsest_bf16 == 1 and p.use_graphs == 1
     sm = qd.smoother_params()
-    assert sm.nsamples == 8 and sm.solve_tol == 1e-6 and sm.seed == 4242 and sm.mr_steps == 2
+    assert sm.nsamples == 8 and sm.solve_tol == 1e-6 and sm.seed == 4242 and sm.mr_steps == 2 and sm.layers == 1
 
 
 def test_autotune_table_host_side(library):

@@ -106,3 +106,63 @@ def test_solves_with_the_learned_smoother(qd, ctx):
         B = b.reshape(-1, s)
         assert np.all(np.linalg.norm(B - A @ x, axis=0) / np.linalg.norm(B, axis=0) <= 1e-10)
     qd.smoother_enable(mg, False, 2)
+
+
+def test_layered_smoother_against_oracle(qd, ctx):
+    # S = S_3 S_2 S_1 (each layer the one-hop form): FP64 against the
+    # oracle's composition, FP32 (FP16-rounded weights) within its rounding;
+    # greedy training: each layer fits e ~ S_l (S_{l-1} ... S_1 r) by least
+    # squares with the layers below fixed, checked against the oracle's fit
+    # of the same pairs
+    dims = (8, 4, 4, 6)
+    U = synth.random_su3_links(dims, 0.3, 3)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, -0.5, 0.0, qd.mg_params(1, [(2, 2, 2, 2)], [4], null_maxit=0))
+    rng = np.random.default_rng(8)
+    W = 0.3 * (rng.standard_normal((3, 9, 4, 4)) + 1j * rng.standard_normal((3, 9, 4, 4)))
+    qd.smoother_set_layer_weights(mg, W)
+    assert qd.smoother_layers(mg) == 3
+    assert np.array_equal(qd.smoother_get_layer_weights(mg), W)
+    assert np.array_equal(qd.smoother_get_weights(mg), W[0])
+    for s in (1, 4):
+        r = synth.random_field(dims, s, 20 + s)
+        ref = r
+        for l in range(3):
+            ref = osm.apply(U, W[l], ref, dims)
+        out = torch.empty((g.V, 12, s), dtype=torch.complex128, device="cuda:0")
+        qd.smoother_apply(mg, s, qd.to_qd(ctx, g, r), out)
+        assert rel_err(qd.from_qd(ctx, g, out), ref) < 1e-12
+        x32 = qd.to_qd(ctx, g, r).to(torch.complex64)
+        o32 = torch.empty_like(x32)
+        qd.smoother_apply_f32(mg, s, x32, o32)
+        # FP16 weights (u = 2^-11) in each of three layers
+        assert rel_err(qd.from_qd(ctx, g, o32.to(torch.complex128)), ref) < 3e-2
+    # one layer again: the single-layer entry points still apply
+    qd.smoother_set_weights(mg, W[1])
+    assert qd.smoother_layers(mg) == 1
+    mg.close()
+    g.close()
+
+
+def test_layered_training_builds_on_the_one_layer_fit(qd, ctx):
+    # greedy training: the first layer of a layered fit is the one-layer fit
+    # of the same pairs, and the depth is what was asked for (each added
+    # layer's family holds the identity, so its least-squares error on the
+    # training pairs cannot exceed the stack below it; the held-out judge
+    # still decides whether the V-cycle uses S)
+    dims = (8, 8, 8, 8)
+    U = synth.random_su3_links(dims, 0.3, 2)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, -0.8, 0.0, qd.mg_params(1, [(2, 2, 2, 2)], [12]))
+    infos = []
+    for layers in (1, 2, 3):
+        info = qd.smoother_train(mg, nsamples=8, solve_tol=1e-6, mr_steps=1, layers=layers)
+        assert qd.smoother_layers(mg) == layers
+        infos.append(info)
+    # the first layer of the layered fit is the one-layer fit (same pairs)
+    w_all = qd.smoother_get_layer_weights(mg)
+    qd.smoother_train(mg, nsamples=8, solve_tol=1e-6, mr_steps=1, layers=1)
+    assert rel_err(w_all[0], qd.smoother_get_weights(mg)) < 1e-10
+    print("held-out errors (learned, plain) by depth:", [(i["err_learned"], i["err_plain"]) for i in infos])
+    mg.close()
+    g.close()

@@ -247,10 +247,72 @@ __device__ __forceinline__ void hop2(const float2* __restrict__ L, const float4*
   }
 }
 
-template <int MU, bool DAG>
+// The same hop with the neighbour spinor projected as it is loaded: only
+// the half spinor h (both right-hand sides, 6 x 16 bytes) stays live instead
+// of the 12 loaded words, which leaves registers for the next hop's loads.
+template <int MU, bool FWD, bool DAG>
+__device__ __forceinline__ void hop2p(const float2* __restrict__ L, const float2* __restrict__ p, int64_t rs,
+                                      float2 hu[2][6], float2 hl[2][6]) {
+  constexpr bool plus = (FWD == DAG);
+  float4 hq[6];  // hq[c]: h0[c] of rhs 0 (xy) and 1 (zw); hq[3 + c]: h1[c]
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float4 u0 = *reinterpret_cast<const float4*>(p + (0 * 3 + c) * rs);
+    const float4 u1 = *reinterpret_cast<const float4*>(p + (1 * 3 + c) * rs);
+    const float4 w0 = *reinterpret_cast<const float4*>(p + (2 * 3 + c) * rs);
+    const float4 w1 = *reinterpret_cast<const float4*>(p + (3 * 3 + c) * rs);
+    float2 h[2][2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float2 a0 = j ? make_float2(u0.z, u0.w) : make_float2(u0.x, u0.y);
+      const float2 a1 = j ? make_float2(u1.z, u1.w) : make_float2(u1.x, u1.y);
+      const float2 l0 = j ? make_float2(w0.z, w0.w) : make_float2(w0.x, w0.y);
+      const float2 l1 = j ? make_float2(w1.z, w1.w) : make_float2(w1.x, w1.y);
+      float2 b0, b1;
+      bdag<MU>(a0, a1, b0, b1);
+      if (plus) { h[j][0] = cadd(l0, b0); h[j][1] = cadd(l1, b1); }
+      else      { h[j][0] = csub(l0, b0); h[j][1] = csub(l1, b1); }
+    }
+    hq[c] = make_float4(h[0][0].x, h[0][0].y, h[1][0].x, h[1][0].y);
+    hq[3 + c] = make_float4(h[0][1].x, h[0][1].y, h[1][1].x, h[1][1].y);
+  }
+  float2 l[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) l[k] = L[k];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    float2 h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h0[c] = j ? make_float2(hq[c].z, hq[c].w) : make_float2(hq[c].x, hq[c].y);
+      h1[c] = j ? make_float2(hq[3 + c].z, hq[3 + c].w) : make_float2(hq[3 + c].x, hq[3 + c].y);
+    }
+    float2 g0[3], g1[3];
+    su3mul_r<!FWD>(l, h0, g0);
+    su3mul_r<!FWD>(l, h1, g1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      hl[j][c] = cadd(hl[j][c], g0[c]);
+      hl[j][3 + c] = cadd(hl[j][3 + c], g1[c]);
+      float2 b0, b1;
+      bmul<MU>(g0[c], g1[c], b0, b1);
+      if (plus) { hu[j][c] = cadd(hu[j][c], b0); hu[j][3 + c] = cadd(hu[j][3 + c], b1); }
+      else      { hu[j][c] = csub(hu[j][c], b0); hu[j][3 + c] = csub(hu[j][3 + c], b1); }
+    }
+  }
+}
+
+template <int MU, bool DAG, bool PROJ = false>
 __device__ __forceinline__ void hop2_dir(const float2* __restrict__ U, const int nb8[8], int64_t V, int64_t site,
                                          int64_t rs, int r0, const float2* __restrict__ in, float2 hu[2][6],
                                          float2 hl[2][6], int64_t in_off = 0) {
+  if (PROJ) {
+    const int64_t nbk = nb8[4 + MU];
+    hop2p<MU, true, DAG>(U + ((int64_t)MU * V + site) * 9, in + ((int64_t)nb8[MU] - in_off) * 12 * rs + r0, rs, hu,
+                         hl);
+    hop2p<MU, false, DAG>(U + ((int64_t)MU * V + nbk) * 9, in + (nbk - in_off) * 12 * rs + r0, rs, hu, hl);
+    return;
+  }
   float4 q[12];
   {
     const float2* p = in + ((int64_t)nb8[MU] - in_off) * 12 * rs + r0;
@@ -273,7 +335,7 @@ __device__ __forceinline__ void hop2_dir(const float2* __restrict__ U, const int
 // lattice is traversed once per chunk, so that the spinors a traversal keeps
 // in flight between a site and its farthest neighbour in visiting order take
 // less L2 (a chunk of 2 rc2 = nrhs is the plain order).
-template <bool DAG, bool RESID, int NT>
+template <bool DAG, bool RESID, int NT, bool PROJ = false>
 __global__ void __launch_bounds__(NT, 512 / NT) k_wilson_f32x2(const float2* __restrict__ U, const int* __restrict__ nbr,
                                                       const int* __restrict__ visit, int64_t V, int nrhs, int rc2,
                                                       float mass, float tau,
@@ -297,10 +359,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_wilson_f32x2(const float2* __r
   for (int j = 0; j < 2; ++j)
 #pragma unroll
     for (int k = 0; k < 6; ++k) { hu[j][k] = make_float2(0.f, 0.f); hl[j][k] = make_float2(0.f, 0.f); }
-  hop2_dir<0, DAG>(U, nb8, V, site, rs, r0, in, hu, hl);
-  hop2_dir<1, DAG>(U, nb8, V, site, rs, r0, in, hu, hl);
-  hop2_dir<2, DAG>(U, nb8, V, site, rs, r0, in, hu, hl);
-  hop2_dir<3, DAG>(U, nb8, V, site, rs, r0, in, hu, hl);
+  hop2_dir<0, DAG, PROJ>(U, nb8, V, site, rs, r0, in, hu, hl);
+  hop2_dir<1, DAG, PROJ>(U, nb8, V, site, rs, r0, in, hu, hl);
+  hop2_dir<2, DAG, PROJ>(U, nb8, V, site, rs, r0, in, hu, hl);
+  hop2_dir<3, DAG, PROJ>(U, nb8, V, site, rs, r0, in, hu, hl);
   const float te = DAG ? -tau : tau;
   const float2 mup = make_float2(mass, te);
   const float2 mlo = make_float2(mass, -te);
@@ -498,8 +560,9 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
   // 16-byte aligned fields), the columns swept whole or in chunks, in blocks
   // of 128, 256 or 512 threads (a block of nt threads covers nt / (chunk / 2)
   // consecutive sites of the visiting order, whose shared neighbours then
-  // hit in L1); candidate 1: one per thread.  The FP32 choice is tuned.
-  auto launch_x2 = [&](int rc, int nt) -> bool {
+  // hit in L1); 8-9: whole or chunks of 64 with the neighbours projected as
+  // they load (hop2p); candidate 1: one per thread.  The FP32 choice is tuned.
+  auto launch_x2 = [&](int rc, int nt, bool proj = false) -> bool {
     if (!(sizeof(C) == 8 && (nrhs % 2) == 0 &&
           ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(b)) &
            15) == 0))
@@ -516,21 +579,26 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
     auto go = [&](auto kern) {
       kern<<<(int)div_up(tot2, nt), nt, 0, ctx.stream>>>(L, nb, vis, geo.nsites, nrhs, rc2, fm, ft, xin, yout, bb);
     };
-    auto pick = [&](auto k128, auto k256, auto k512) {
-      if (nt == 512) go(k512);
+    auto pick = [&](auto k128, auto k256, auto k512, auto k128p) {
+      if (proj) go(k128p);
+      else if (nt == 512) go(k512);
       else if (nt == 256) go(k256);
       else go(k128);
     };
     if (b) {
       if (dagger)
-        pick(k_wilson_f32x2<true, true, 128>, k_wilson_f32x2<true, true, 256>, k_wilson_f32x2<true, true, 512>);
+        pick(k_wilson_f32x2<true, true, 128>, k_wilson_f32x2<true, true, 256>, k_wilson_f32x2<true, true, 512>,
+             k_wilson_f32x2<true, true, 128, true>);
       else
-        pick(k_wilson_f32x2<false, true, 128>, k_wilson_f32x2<false, true, 256>, k_wilson_f32x2<false, true, 512>);
+        pick(k_wilson_f32x2<false, true, 128>, k_wilson_f32x2<false, true, 256>, k_wilson_f32x2<false, true, 512>,
+             k_wilson_f32x2<false, true, 128, true>);
     } else {
       if (dagger)
-        pick(k_wilson_f32x2<true, false, 128>, k_wilson_f32x2<true, false, 256>, k_wilson_f32x2<true, false, 512>);
+        pick(k_wilson_f32x2<true, false, 128>, k_wilson_f32x2<true, false, 256>, k_wilson_f32x2<true, false, 512>,
+             k_wilson_f32x2<true, false, 128, true>);
       else
-        pick(k_wilson_f32x2<false, false, 128>, k_wilson_f32x2<false, false, 256>, k_wilson_f32x2<false, false, 512>);
+        pick(k_wilson_f32x2<false, false, 128>, k_wilson_f32x2<false, false, 256>, k_wilson_f32x2<false, false, 512>,
+             k_wilson_f32x2<false, false, 128, true>);
     }
     QD_LAUNCH_CHECK();
     return true;
@@ -565,13 +633,15 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
       case 4: return nrhs > 32 && launch_x2(32, 256);
       case 5: return nrhs > 32 && launch_x2(32, 512);
       case 6: return nrhs > 16 && launch_x2(16, 512);
-      default: return nrhs > 64 && launch_x2(64, 512);
+      case 7: return nrhs > 64 && launch_x2(64, 512);
+      case 8: return launch_x2(0, 128, true);
+      default: return nrhs > 64 && launch_x2(64, 128, true);
     }
   };
   // the residual form writes out = b - A in: out-of-place, safe to repeat
   const std::string key = std::string("wilson f32 sites") + std::to_string(geo.nsites) + " rhs" +
                           std::to_string(nrhs) + (b ? " resid" : "") + (dagger ? " dag" : "");
-  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 8, launch);
+  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 10, launch);
   if (c >= 0 && launch(c)) return;
   if (!launch_x2(0, 128)) launch_x1();
 }

@@ -67,7 +67,8 @@ def test_wilson_f32_launch_shapes(qd, ctx):
     # the FP32 Wilson stencil's shapes: two columns per thread swept whole
     # (0) or in chunks of 64, 32 or 16 columns with blocks of 128-512
     # threads (2-7) -- the same arithmetic per element, so the same bits --
-    # and one column per thread (1), which agrees to FP32 rounding; A and A^H
+    # the neighbours projected as they load (8-9) and one column per thread
+    # (1), which agree to FP32 rounding; A and A^H
     dims = (8, 8, 8, 8)
     U = synth.random_su3_links(dims, 0.3, 2)
     g = qd.Gauge(ctx, dims, U)
@@ -77,13 +78,15 @@ def test_wilson_f32_launch_shapes(qd, ctx):
                              generator=torch.Generator("cuda:0").manual_seed(s))
             for dag in (False, True):
                 outs = {}
-                for cand in range(8):
+                for cand in range(10):
                     qd.autotune_force(cand)
                     yf = torch.full_like(xf, float("nan"))
                     qd.dirac_apply_f32(ctx, g, -0.8, 0.1, dag, s, xf, yf)
                     outs[cand] = yf
                 for cand in (2, 3, 4, 5, 6, 7):
                     assert torch.equal(outs[0], outs[cand]), (s, dag, cand)
+                for cand in (8, 9):  # projection on load: the same sums, possibly contracted differently
+                    assert rel_err(host(outs[cand]), host(outs[0])) < 1e-6, (s, dag, cand)
                 assert rel_err(host(outs[1]), host(outs[0])) < 1e-6, (s, dag)
     finally:
         qd.autotune_force(-1)

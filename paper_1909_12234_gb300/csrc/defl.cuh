@@ -38,6 +38,8 @@ struct qd_defl {
   int iterations = 0;
   int rank = 0;
   qd::DevBuf U;          // nb x rank (ld rank): U_bar U_hat (Alg 2) or U (Alg 1)
+  qd::DevBuf pj[4];      // work spaces of the projection (grow-only)
+  qd::DevBuf chain[2];   // intermediate levels of the composite W, W^H (grow-only)
   qd::DevBuf lam;        // rank doubles (Algorithm 2)
   qd::DevBuf t0buf;      // one complex on device
   double t0[2] = {0.0, 0.0};

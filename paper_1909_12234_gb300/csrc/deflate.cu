@@ -316,7 +316,7 @@ void defl_set_rank(qd_defl& d, int r) {
 // c = W^H z with the composite W = W_0 ... W_{L-1} (L = d.level), s columns
 static void restrict_chain(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* c) {
   const cplx* src = z;
-  DevBuf tmp[2];
+  DevBuf* tmp = d.chain;
   for (int l = 0; l < d.level; ++l) {
     const Transfer& T = *d.mg->T[l];
     cplx* dst = c;
@@ -332,7 +332,7 @@ static void restrict_chain(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* 
 // f = W c with the composite W, s columns
 static void prolong_chain(qd_ctx& ctx, qd_defl& d, int s, const cplx* c, cplx* f) {
   const cplx* src = c;
-  DevBuf tmp[2];
+  DevBuf* tmp = d.chain;
   for (int l = d.level - 1; l >= 0; --l) {
     const Transfer& T = *d.mg->T[l];
     cplx* dst = f;
@@ -349,11 +349,18 @@ static void prolong_chain(qd_ctx& ctx, qd_defl& d, int s, const cplx* c, cplx* f
 void defl_project(qd_ctx& ctx, qd_defl& d, int s, const cplx* z, cplx* out) {
   const int r = d.rank;
   const int64_t nf = d.gauge->geo.nsites * 12;
-  DevBuf a((size_t)r * s * sizeof(cplx));
+  // work spaces kept on the object (grow-only): no allocation per batch
+  DevBuf& a = d.pj[0];
+  a.resize((size_t)r * s * sizeof(cplx));
   if (d.kind == QD_DEFL_MG_OBLIQUE) {
     const LevelGeom& cg = d.mg->geom(d.level);
     const int dc = d.mg->dof(d.level);
-    DevBuf c((size_t)d.nb * s * sizeof(cplx)), gc((size_t)d.nb * s * sizeof(cplx)), f((size_t)nf * s * sizeof(cplx));
+    DevBuf& c = d.pj[1];
+    DevBuf& gc = d.pj[2];
+    DevBuf& f = d.pj[3];
+    c.resize((size_t)d.nb * s * sizeof(cplx));
+    gc.resize((size_t)d.nb * s * sizeof(cplx));
+    f.resize((size_t)nf * s * sizeof(cplx));
     restrict_chain(ctx, d, s, z, c.as<cplx>());
     blas::gamma5(ctx, cg.nsites, dc, s, c.as<cplx>(), gc.as<cplx>());
     blockdot(ctx, d.nb, d.U.as<cplx>(), r, r, gc.as<cplx>(), s, s, a.as<cplx>());  // U^H g5 W^H z

@@ -52,13 +52,13 @@ import numpy as np  # noqa: E402
 # per step, mixed precision with the learned smoother (the metric's form).
 CONFIG3 = dict(
     workload="wilson-dirac 16^3x32 eps0.2 seed3 m0=-0.8, 3-level MG (2^4, 2^4; nv 12, 16; level-1 GCR 6 its; "
-             "coarse MR 1), Algorithm 2 k=24 on the coarsest level, 128 Rademacher samples/step, learned smoother "
-             "+ 1 MR, even-odd (odd-site Schur complement) FP32 GCR(4) inner solves with FP64 refinement to true "
+             "coarse MR 1), Algorithm 2 k=24 on the coarsest level, 128 Rademacher samples/step, two-layer learned "
+             "smoother, even-odd (odd-site Schur complement) FP32 GCR(4) inner solves with FP64 refinement to true "
              "rel. residual 1e-8",
     dims=(16, 16, 16, 32), eps=0.2, link_seed=3, m0=-0.8, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16],
     k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=4, maxit=500, inner_tol=1e-5, schur=1,
     mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6, "coarse_smoother_steps": 1},
-    learned=1, eig_maxit=30, fp64_samples=16,
+    learned=1, learned_mr=0, layers=2, eig_maxit=30, fp64_samples=16,
 )
 # Config 2: 8^4 lattice (the two-level workload of round one), kept for
 # comparison with earlier numbers.
@@ -180,6 +180,11 @@ def _mg_params(qd, wl=None):
     return qd.mg_params(len(wl["blocks"]), wl["blocks"], wl["nvs"], **wl.get("mg_kw", {}))
 
 
+def _learned_mr(wl):
+    """Minimal-residual steps after the learned smoother."""
+    return wl.get("learned_mr", wl.get("learned", 0))
+
+
 def _setup(qd, ctx, U, wl=None):
     """Gauge, hierarchy, learned smoother, deflation space for the workload."""
     wl = WL if wl is None else wl
@@ -187,8 +192,9 @@ def _setup(qd, ctx, U, wl=None):
     mg = qd.Multigrid(ctx, g, wl["m0"], 0.0, _mg_params(qd, wl))
     judge = None
     if wl.get("learned"):
-        judge = qd.smoother_train(mg, nsamples=4, solve_tol=1e-3, mr_steps=wl["learned"])
-        qd.smoother_enable(mg, True, wl["learned"])
+        judge = qd.smoother_train(mg, nsamples=4, solve_tol=1e-3, mr_steps=_learned_mr(wl),
+                                  layers=wl.get("layers", 1))
+        qd.smoother_enable(mg, True, _learned_mr(wl))
     d = qd.Deflation(ctx, g, mg, wl["m0"], 0.0,
                      qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, wl["k"], guard=wl["guard"], eig_tol=1e-6,
                                     solve_tol=1e-10, maxit=wl.get("eig_maxit", 60)))
@@ -573,8 +579,8 @@ def run_ours(args):
         mg2 = qd.Multigrid(ctx, g2, WL["m0"], 0.0, _mg_params(qd))
         tp = lap("mg_setup", tp)
         if WL.get("learned"):
-            qd.smoother_train(mg2, nsamples=4, solve_tol=1e-3, mr_steps=WL["learned"])
-            qd.smoother_enable(mg2, True, WL["learned"])
+            qd.smoother_train(mg2, nsamples=4, solve_tol=1e-3, mr_steps=_learned_mr(WL), layers=WL.get("layers", 1))
+            qd.smoother_enable(mg2, True, _learned_mr(WL))
         tp = lap("smoother_train", tp)
         d2 = qd.Deflation(ctx, g2, mg2, WL["m0"], 0.0,
                           qd.defl_params(qd.QD_DEFL_MG_OBLIQUE, WL["k"], guard=WL["guard"], eig_tol=1e-6,
@@ -604,7 +610,7 @@ def run_ours(args):
     if args.precision == "mixed" and args.fp64_steps > 0:
         sf = WL.get("fp64_samples", s)
         if WL.get("learned"):
-            qd.smoother_enable(mg, False, WL["learned"])  # the plain FP64 form
+            qd.smoother_enable(mg, False, _learned_mr(WL))  # the plain FP64 form
         _batch(qd, ctx, g, mg, d, offset(2000), qd.QD_PREC_F64, nsamples=sf, plain=True)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -619,7 +625,7 @@ def run_ours(args):
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             fms = float(tt.item())
         if WL.get("learned"):
-            qd.smoother_enable(mg, True, WL["learned"])
+            qd.smoother_enable(mg, True, _learned_mr(WL))
         fp64 = {"value": args.fp64_steps * sf * world / (fms / 1e3), "unit": UNIT, "steps": args.fp64_steps,
                 "samples_per_step": sf, "ms_per_step": fms / args.fp64_steps, "dtype": "f64",
                 "smoother": "plain MR (4 fine, coarse as the workload)", "solver": "full-lattice FP64 GCR(16)",
@@ -657,7 +663,7 @@ def run_ours(args):
                        "estimate": [run_stats["estimate"].real, run_stats["stderr"]],
                        "estimate_samples": int(run_stats["s"]),
                        "mg_overrides": WL.get("mg_kw", {}),
-                       "learned_smoother": ({"mr_steps": WL["learned"], "judge": judge}
+                       "learned_smoother": ({"layers": WL.get("layers", 1), "mr_steps": _learned_mr(WL), "judge": judge}
                                             if WL.get("learned") else None)},
             "errors": errors,
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
@@ -970,7 +976,7 @@ def run_batch(args):
 # after it, and stacks of 2 and 3 layers (S = S_L ... S_1, each layer the
 # one-hop form, trained layer by layer) with 0 or 1 MR steps.  Cost is what
 # samples/s measures: every variant runs the same 128-sample batches.
-SMOOTHER_DEPTH = [(0, 0), (1, 1), (1, 2), (2, 0), (2, 1), (3, 0)]  # (layers, MR steps); layers 0 = plain MR
+SMOOTHER_DEPTH = [(0, 0), (1, 0), (1, 1), (1, 2), (2, 0), (2, 1), (3, 0)]  # (layers, MR steps); layers 0 = plain MR
 
 
 def run_smoother_depth(args):
@@ -1198,6 +1204,8 @@ def main():
         WL["mg_kw"] = dict(WL.get("mg_kw", {}), coarse_smoother_steps=args.coarse_smoother_steps)
     if args.learned >= 0:
         WL["learned"] = args.learned
+        WL["learned_mr"] = args.learned
+        WL["layers"] = 1
     if args.restart > 0:
         WL["restart"] = args.restart
     if args.inner_tol > 0:

@@ -358,7 +358,11 @@ def kernel_only(qd, ctx, names, reps=20):
         "prolong_l1": (lambda: qd.prolongate_f32(mg, 0, s, x1, y0), 8.0 * (V * 12 * 12 + V * 12 * s + n1 * s)),
         "prolong_l2": (lambda: qd.prolongate_f32(mg, 1, s, x2, y1), 8.0 * (8192 * 24 * 16 + n1 * s + n2 * s)),
         "wilson_f32": (lambda: qd.dirac_apply_f32(ctx, g, -0.8, 0.0, False, s, x0, y0), V * (24.0 * 8 * s + 36.0 * 8)),
+        "smoother_f32": (lambda: qd.smoother_apply_f32(mg, s, x0, y0), V * (24.0 * 8 * s + 36.0 * 8)),
     }
+    if "smoother_f32" in names:
+        rng = np.random.default_rng(1)
+        qd.smoother_set_weights(mg, 0.1 * (rng.standard_normal((9, 4, 4)) + 1j * rng.standard_normal((9, 4, 4))))
     out = {"lattice": "16^3x32", "nrhs": s, "peak_gbs": hbm}
     for name in names:
         fn, nbytes = cases[name]
@@ -1156,7 +1160,8 @@ def main():
                          "default: the workload's setting")
     ap.add_argument("--kernel", default="",
                     help="comma-separated hot kernels timed alone on the 16^3 x 32 shapes (a profiling target): "
-                         "coarse_tc, restrict_tc, prolong_l1, prolong_l2, wilson_f32; 'all' for every one")
+                         "coarse_tc, restrict_tc, prolong_l1, prolong_l2, wilson_f32, smoother_f32; 'all' for "
+                         "every one")
     ap.add_argument("--reps", type=int, default=20, help="launches timed per kernel with --kernel")
     ap.add_argument("--no-tune", action="store_true",
                     help="launch shapes fixed at their defaults (nothing timed by the autotuner)")
@@ -1171,7 +1176,8 @@ def main():
         from paper_1909_12234_gb300 import qdtrace as qd
         qd.load()
         ctx = qd.Context(0)
-        names = (["coarse_tc", "restrict_tc", "prolong_l1", "prolong_l2", "wilson_f32"] if args.kernel == "all"
+        names = (["coarse_tc", "restrict_tc", "prolong_l1", "prolong_l2", "wilson_f32", "smoother_f32"]
+                 if args.kernel == "all"
                  else args.kernel.split(","))
         if args.candidate >= 0:
             qd.autotune_force(args.candidate)

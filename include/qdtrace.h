@@ -292,6 +292,11 @@ int qd_coarse_apply_f32(qd_mg* mg, int level, int nrhs, const float* in,
  * qd_hutchinson_trace).  Asynchronous. */
 int qd_coarse_apply_tc(qd_mg* mg, int level, int nrhs, const float* in,
                        float* out);
+/* Residual form of the same kernel, r = b - C x (the subtraction in the
+ * kernel's epilogue, in FP32: the same bits as b - (C x) stored first).
+ * b, x, r distinct.  Asynchronous. */
+int qd_coarse_residual_tc(qd_mg* mg, int level, int nrhs, const float* b,
+                          const float* x, float* r);
 
 /* out = C_level^{-1} in, level >= 1: the coarse solve of the V-cycle (a5).
  * On the coarsest level with a dense inverse: the product with the inverse
@@ -660,7 +665,8 @@ void qd_autotune_clear(void);
  * launch shape of a kernel (coarse stencil on tensor cores: 0-3 input split
  * into operand tiles first, at most 8/4/3/2 operand slots; 4-6 input
  * converted in the kernel, 2/3/4 staging slots; 7-8 split tiles, at most 8/4
- * slots, one bulk copy per 4 KB tile region). */
+ * slots, one bulk copy per 4 KB tile region; 9-10 split tiles, two CTAs per
+ * SM). */
 void qd_autotune_force(int candidate);
 /* The table as text, one line per shape key: the key, the chosen candidate,
  * then each candidate's best time in ms (-1: not applicable).  Writes at most

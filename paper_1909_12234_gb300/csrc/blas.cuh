@@ -44,31 +44,35 @@ template <class C> struct DotPairs {
 };
 
 // partials[(blk*K + k)*nrhs + r] = sum over this block's rows of conj(X_k) Y_k
-template <class C>
+// KK: the pair count as a compile-time bound (1, 2 or kDotK).  The loop over
+// pairs is unrolled to KK, so a launch with one pair carries no predicated-off
+// multiply-adds: for FP64, whose pipe is narrow on this GPU, those cost as
+// much issue time as live ones.
+template <class C, int KK = kDotK>
 __global__ void k_dots(int K, int64_t n, int nrhs, DotPairs<C> pr, cplx* __restrict__ partials) {
   typedef typename CTraits<C>::R R;
-  __shared__ cplx sm[kDotK][kThreads];
+  __shared__ cplx sm[KK][kThreads];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int r = blockIdx.y * blockDim.x + tx;
-  C acc[kDotK];
+  C acc[KK];
 #pragma unroll
-  for (int k = 0; k < kDotK; ++k) acc[k] = mk<C>((R)0, (R)0);
+  for (int k = 0; k < KK; ++k) acc[k] = mk<C>((R)0, (R)0);
   if (r < nrhs) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.y + ty; i < n; i += (int64_t)gridDim.x * blockDim.y) {
       const int64_t e = i * nrhs + r;
 #pragma unroll
-      for (int k = 0; k < kDotK; ++k)
-        if (k < K) cfmac(acc[k], pr.x[k][e], pr.y[k][e]);
+      for (int k = 0; k < KK; ++k)
+        if (KK == 1 || k < K) cfmac(acc[k], pr.x[k][e], pr.y[k][e]);
     }
   }
   const int t = ty * blockDim.x + tx;
 #pragma unroll
-  for (int k = 0; k < kDotK; ++k) sm[k][t] = mkc((double)acc[k].x, (double)acc[k].y);
+  for (int k = 0; k < KK; ++k) sm[k][t] = mkc((double)acc[k].x, (double)acc[k].y);
   __syncthreads();
   for (int h = blockDim.y / 2; h > 0; h >>= 1) {
     if (ty < h) {
 #pragma unroll
-      for (int k = 0; k < kDotK; ++k)
+      for (int k = 0; k < KK; ++k)
         if (k < K) sm[k][t] = cadd(sm[k][t], sm[k][t + h * blockDim.x]);
     }
     __syncthreads();
@@ -104,7 +108,12 @@ void dots_launch(qd_ctx& ctx, int K, int64_t n, int nrhs, const DotPairs<C>& pr,
   {
     ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_DOTS_F32, 8.0 * K * n * nrhs,
                  (double)sizeof(C) * 2.0 * K * n * nrhs);
-    k_dots<C><<<s.grid, s.block, 0, ctx.stream>>>(K, n, nrhs, pr, ctx.red_partials.as<cplx>());
+    if (K == 1)
+      k_dots<C, 1><<<s.grid, s.block, 0, ctx.stream>>>(K, n, nrhs, pr, ctx.red_partials.as<cplx>());
+    else if (K == 2)
+      k_dots<C, 2><<<s.grid, s.block, 0, ctx.stream>>>(K, n, nrhs, pr, ctx.red_partials.as<cplx>());
+    else
+      k_dots<C><<<s.grid, s.block, 0, ctx.stream>>>(K, n, nrhs, pr, ctx.red_partials.as<cplx>());
     QD_LAUNCH_CHECK();
   }
   const int tot = K * nrhs;  // one warp each, 8 warps per block

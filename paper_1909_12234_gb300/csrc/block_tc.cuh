@@ -137,7 +137,7 @@ template <int DIN, int DOUT, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     k_block_tc(int64_t nout, int nstep, int s, int nchunks, int NS, int NA, uint32_t stage_bytes, uint32_t b_tile,
                const int* __restrict__ src, const uint32_t* __restrict__ Bsrc, const float2* __restrict__ in,
-               float2* __restrict__ out, int* __restrict__ err) {
+               float2* __restrict__ out, int* __restrict__ err, const float2* __restrict__ bres = nullptr) {
   static_assert(DOUT % 8 == 0 && DOUT <= 32, "2 DOUT must be a multiple of 16 and at most 64");
   static_assert(DIN % 4 == 0 && DIN <= 32, "DIN must be a multiple of 4 and at most 32");
   constexpr int KSTEPS = (2 * DIN + 15) / 16;  // MMA K steps of 16 per input block
@@ -304,9 +304,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       mbar_arrive(smem_u32(&acce[b]));
       if (r < w) {
-        float2* o = out + x * DOUT * (int64_t)s + r0 + r;
+        const int64_t ob = x * DOUT * (int64_t)s + r0 + r;
+        float2* o = out + ob;
+        if (bres) {  // residual form: out = b - y
 #pragma unroll
-        for (int d = 0; d < DOUT; ++d) o[(int64_t)d * s] = make_float2(v[d], v[DOUT + d]);
+          for (int d = 0; d < DOUT; ++d) {
+            const float2 bv = bres[ob + (int64_t)d * s];
+            o[(int64_t)d * s] = make_float2(bv.x - v[d], bv.y - v[DOUT + d]);
+          }
+        } else {
+#pragma unroll
+          for (int d = 0; d < DOUT; ++d) o[(int64_t)d * s] = make_float2(v[d], v[DOUT + d]);
+        }
       }
     }
   } else if (warp >= 8) {
@@ -426,12 +435,17 @@ __global__ void __launch_bounds__(256) k_split_tiles(int64_t nsites, int s, int 
 // (bulk-copied), its compact coefficients (bulk-copied) and its B tile
 // (built by the converter warps).  Roles as in k_block_tc; barriers per
 // slot: full (copies landed), bready (B tile built), empty (MMAs done).
-template <int D, bool REGION_COPIES>
-__global__ void __launch_bounds__(kThreads, 1)
+// NT = 512: converter warps 8-15 (256 threads), one CTA per SM; NT = 256:
+// converter warps 2-3 (64 threads), two CTAs per SM (two pipelines).
+template <int D, bool REGION_COPIES, int NT = kThreads>
+__global__ void __launch_bounds__(NT, 512 / NT)
     k_stencil_tc_split(int64_t nout, int s, int nchunks, int NA, uint32_t slot_bytes, uint32_t b_tile,
                        const int* __restrict__ src, const uint32_t* __restrict__ Bsrc,
-                       const unsigned char* __restrict__ tiles, float2* __restrict__ out, int* __restrict__ err) {
+                       const unsigned char* __restrict__ tiles, float2* __restrict__ out, int* __restrict__ err,
+                       const float2* __restrict__ bres) {
   constexpr int NSTEP = 9;
+  constexpr int kConv = NT == 512 ? 256 : 64;      // converter threads
+  constexpr int kConvBase = NT == 512 ? 256 : 64;  // their first thread
   constexpr int KSTEPS = (2 * D + 15) / 16;
   constexpr int NCOL = 2 * D;
   constexpr uint32_t kTile = split_tile_bytes<D>();
@@ -453,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     abort_flag = 0;
     for (int i = 0; i < NA; ++i) {
       mbar_init(smem_u32(&full[i]), 1);
-      mbar_init(smem_u32(&bready[i]), 256);
+      mbar_init(smem_u32(&bready[i]), kConv);
       mbar_init(smem_u32(&empty[i]), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -590,14 +604,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       mbar_arrive(smem_u32(&acce[b]));
       if (r < w) {
-        float2* o = out + x * D * (int64_t)s + r0 + r;
+        const int64_t ob = x * D * (int64_t)s + r0 + r;
+        float2* o = out + ob;
+        if (bres) {  // residual form: out = b - y
 #pragma unroll
-        for (int d = 0; d < D; ++d) o[(int64_t)d * s] = make_float2(v[d], v[D + d]);
+          for (int d = 0; d < D; ++d) {
+            const float2 bv = bres[ob + (int64_t)d * s];
+            o[(int64_t)d * s] = make_float2(bv.x - v[d], bv.y - v[D + d]);
+          }
+        } else {
+#pragma unroll
+          for (int d = 0; d < D; ++d) o[(int64_t)d * s] = make_float2(v[d], v[D + d]);
+        }
       }
     }
-  } else if (warp >= 8) {
+  } else if (NT == 512 ? warp >= 8 : (warp == 2 || warp == 3)) {
     // ---- converters: compact coefficients -> B tiles ----
-    const int ct = tid - 256;
+    const int ct = tid - kConvBase;
     int64_t q = 0;
     for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
       bool ok = true;
@@ -610,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         unsigned char* slot = gbase + (size_t)as * slot_bytes;
-        build_b_tile<D, D, kStencilSplit>(ct, 256, reinterpret_cast<const uint32_t*>(slot + c_off), slot + b_off);
+        build_b_tile<D, D, kStencilSplit>(ct, kConv, reinterpret_cast<const uint32_t*>(slot + c_off), slot + b_off);
         fence_proxy_async_smem();
         mbar_arrive(smem_u32(&bready[as]));
       }
@@ -631,14 +654,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 // them; false (nothing launched) when fewer than two operand slots fit.
 template <int D>
 bool launch_split(qd_ctx& ctx, int64_t nout, const int* src, const uint32_t* Bsrc, const cplxf* in, unsigned char* tiles,
-                  cplxf* out, int s, int* err, int NA_max, bool region_copies) {
+                  cplxf* out, int s, int* err, int NA_max, bool region_copies, bool two_per_sm = false,
+                  const cplxf* b = nullptr) {
   constexpr uint32_t kTile = split_tile_bytes<D>();
   constexpr int KSTEPS = (2 * D + 15) / 16;
   const int nchunks = (s + 127) / 128;
   const uint32_t b_tile = (uint32_t)((4 * D * 128 + 1023) / 1024 * 1024);
   const uint32_t c_bytes = (uint32_t)((2u * D * D * 4u + 1023) / 1024 * 1024);
   const uint32_t slot = kTile + b_tile + c_bytes;
-  const size_t budget = 220 * 1024;
+  const size_t budget = two_per_sm ? 110 * 1024 : 220 * 1024;
   int NA = (int)((budget - 1024) / slot);
   if (NA > NA_max) NA = NA_max;
   if (NA > kMaxNA) NA = kMaxNA;
@@ -647,13 +671,18 @@ bool launch_split(qd_ctx& ctx, int64_t nout, const int* src, const uint32_t* Bsr
   const int sgrid = (int)(div_up(st, 256) < 16 * kNumSMs ? div_up(st, 256) : 16 * kNumSMs);
   k_split_tiles<D><<<sgrid, 256, 0, ctx.stream>>>(nout, s, nchunks, reinterpret_cast<const float2*>(in), tiles);
   QD_LAUNCH_CHECK();
-  const size_t smem = 1024 + (size_t)NA * slot;
+  // two CTAs per SM at most (each holds 256 TMEM columns of the 512): the
+  // shared-memory request keeps a third CTA off the SM
+  size_t smem = 1024 + (size_t)NA * slot;
+  if (two_per_sm && smem < 80 * 1024) smem = 80 * 1024;
   const int64_t items = nout * (int64_t)nchunks;
-  const int grid = (int)(items < kNumSMs ? items : kNumSMs);
-  auto kern = region_copies ? k_stencil_tc_split<D, true> : k_stencil_tc_split<D, false>;
+  const int ctas = two_per_sm ? 2 * kNumSMs : kNumSMs;
+  const int grid = (int)(items < ctas ? items : ctas);
+  auto kern = two_per_sm ? (region_copies ? k_stencil_tc_split<D, true, 256> : k_stencil_tc_split<D, false, 256>)
+                         : (region_copies ? k_stencil_tc_split<D, true, 512> : k_stencil_tc_split<D, false, 512>);
   ensure_smem_limit(reinterpret_cast<const void*>(kern), smem);
-  kern<<<grid, kThreads, smem, ctx.stream>>>(nout, s, nchunks, NA, slot, b_tile, src, Bsrc, tiles,
-                                                              reinterpret_cast<float2*>(out), err);
+  kern<<<grid, two_per_sm ? 256 : 512, smem, ctx.stream>>>(nout, s, nchunks, NA, slot, b_tile, src, Bsrc, tiles,
+                                                              reinterpret_cast<float2*>(out), err, reinterpret_cast<const float2*>(b));
   QD_LAUNCH_CHECK();
   return true;
 }
@@ -662,7 +691,7 @@ bool launch_split(qd_ctx& ctx, int64_t nout, const int* src, const uint32_t* Bsr
 // (at most kMaxNA); false (nothing launched) when fewer than two fit.
 template <int DIN, int DOUT, int MODE>
 bool launch(qd_ctx& ctx, int64_t nout, int nstep, const int* src, const uint32_t* Bsrc, const cplxf* in, cplxf* out,
-            int s, int* err, int NS) {
+            int s, int* err, int NS, const cplxf* b = nullptr) {
   constexpr int NV = DOUT / 2;
   constexpr size_t kBBytes = (MODE == kStencil ? 2u * DOUT * DIN : 2u * DIN * NV) * 4u;
   const int nchunks = (s + 127) / 128;
@@ -679,7 +708,7 @@ bool launch(qd_ctx& ctx, int64_t nout, int nstep, const int* src, const uint32_t
   const int grid = (int)(items < kNumSMs ? items : kNumSMs);
   k_block_tc<DIN, DOUT, MODE><<<grid, kThreads, smem, ctx.stream>>>(
       nout, nstep, s, nchunks, NS, NA, stage, b_tile, src, Bsrc, reinterpret_cast<const float2*>(in),
-      reinterpret_cast<float2*>(out), err);
+      reinterpret_cast<float2*>(out), err, reinterpret_cast<const float2*>(b));
   QD_LAUNCH_CHECK();
   return true;
 }

@@ -385,6 +385,25 @@ int qd_coarse_apply_f32(qd_mg* mg, int level, int nrhs, const float* in, float* 
   });
 }
 
+int qd_coarse_residual_tc(qd_mg* mg, int level, int nrhs, const float* b, const float* x, float* r) {
+  return guarded([&] {
+    NONNULL(mg);
+    NONNULL(b);
+    NONNULL(x);
+    NONNULL(r);
+    QD_REQUIRE(level >= 1 && level <= mg->nlevels, "coarse level out of range");
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    QD_REQUIRE((const void*)x != (void*)r && (const void*)b != (void*)r && b != x, "b, x and r must be distinct");
+    set_device(mg->ctx);
+    qd::CoarseLevel& lv = *mg->L[level - 1];
+    QD_REQUIRE(qd::coarse_tc_supported(lv, x, r, nrhs) && (reinterpret_cast<uintptr_t>(b) & 15) == 0,
+               "tensor-core coarse stencil needs dof 8, 16, 24 or 32, 16-byte aligned fields and an even nrhs "
+               "above 128");
+    qd::coarse_apply_tc(*mg->ctx, lv, reinterpret_cast<const qd::cplxf*>(x), reinterpret_cast<qd::cplxf*>(r), nrhs,
+                        reinterpret_cast<const qd::cplxf*>(b));
+  });
+}
+
 int qd_coarse_apply_tc(qd_mg* mg, int level, int nrhs, const float* in, float* out) {
   return guarded([&] {
     NONNULL(mg);

@@ -482,6 +482,20 @@ void CoarseOp<cplxf>::apply(qd_ctx& ctx, const cplxf* in, cplxf* out, int nrhs) 
   }
   coarse_apply<cplxf>(ctx, *lv, mat, in, out, nrhs);
 }
+template <>
+void CoarseOp<cplx>::residual(qd_ctx& ctx, const cplx* b, const cplx* x, cplx* r, int nrhs) const {
+  Op<cplx>::residual(ctx, b, x, r, nrhs);
+}
+// r = b - C x: on the tensor cores the subtraction is part of the epilogue
+template <>
+void CoarseOp<cplxf>::residual(qd_ctx& ctx, const cplxf* b, const cplxf* x, cplxf* r, int nrhs) const {
+  if (lv->use_tc && r != x && r != b && coarse_tc_supported(*lv, x, r, nrhs) &&
+      (reinterpret_cast<uintptr_t>(b) & 15) == 0) {
+    coarse_apply_tc(ctx, const_cast<CoarseLevel&>(*lv), x, r, nrhs, b);
+    return;
+  }
+  Op<cplxf>::residual(ctx, b, x, r, nrhs);
+}
 
 // ---------------------------------------------------------------------------
 // Block orthonormalisation: one CTA per (aggregate, chirality).  The block

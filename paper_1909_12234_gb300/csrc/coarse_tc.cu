@@ -12,7 +12,7 @@ namespace qd {
 
 namespace {
 
-constexpr int kCoarseTcCandidates = 9;
+constexpr int kCoarseTcCandidates = 11;
 
 // Compact split-BF16 copy of the stencil: for block (x, dir) of D x D
 // entries, Cb[(x*9 + dir)][0][d][e] = hi and [1][d][e] = lo of (Re, Im) C,
@@ -29,18 +29,19 @@ __global__ void k_build_cb(int64_t nblk, int DD, const cplx* __restrict__ C, uin
 }
 
 template <int D>
-bool launch(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int s, int* err, int NS) {
+bool launch(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int s, int* err, int NS,
+            const cplxf* b) {
   return blocktc::launch<D, D, blocktc::kStencil>(ctx, lv.geo.nsites, 9, lv.sten_src.as<int>(),
-                                                  lv.Cmb.as<uint32_t>(), in, out, s, err, NS);
+                                                  lv.Cmb.as<uint32_t>(), in, out, s, err, NS, b);
 }
 
 template <int D>
 bool launch_split(qd_ctx& ctx, const CoarseLevel& lv, const cplxf* in, cplxf* out, int s, int* err, int NA,
-                  bool region_copies) {
+                  bool region_copies, bool two_per_sm, const cplxf* b) {
   const size_t need = (size_t)lv.geo.nsites * ((s + 127) / 128) * blocktc::split_tile_bytes<D>();
   if (lv.ctc_tiles.bytes() < need) lv.ctc_tiles.resize(need);
   return blocktc::launch_split<D>(ctx, lv.geo.nsites, lv.sten_src.as<int>(), lv.Cmb.as<uint32_t>(), in,
-                                  lv.ctc_tiles.as<unsigned char>(), out, s, err, NA, region_copies);
+                                  lv.ctc_tiles.as<unsigned char>(), out, s, err, NA, region_copies, two_per_sm, b);
 }
 
 }  // namespace
@@ -76,41 +77,43 @@ void coarse_tc_prepare(qd_ctx& ctx, CoarseLevel& lv) {
   }
 }
 
-void coarse_apply_tc(qd_ctx& ctx, CoarseLevel& lv, const cplxf* in, cplxf* out, int s) {
+void coarse_apply_tc(qd_ctx& ctx, CoarseLevel& lv, const cplxf* in, cplxf* out, int s, const cplxf* b) {
   QD_REQUIRE(coarse_tc_supported(lv, in, out, s), "tensor-core coarse stencil: unsupported size or alignment");
   coarse_tc_prepare(ctx, lv);
   const double D = lv.D;
   ProfScope ps(ctx, QD_PROF_COARSE_TC, 72.0 * D * D * (double)lv.geo.nsites * s,
-               (double)lv.geo.nsites * (9.0 * D * D * 8.0 + 2.0 * D * 8.0 * s));
+               (double)lv.geo.nsites * (9.0 * D * D * 8.0 + (b ? 3.0 : 2.0) * D * 8.0 * s));
   int* err = lv.ctc_err.as<int>();
   // candidates 0-3: the input split once into operand tiles first
   // (k_split_tiles), at most 8, 4, 3 or 2 operand slots, one bulk copy per
   // tile; 4-6: the input blocks converted inside the kernel with 2, 3 or 4
   // staging slots; 7-8: split tiles, at most 8 or 4 slots, one bulk copy per
-  // 4 KB region of a tile.  Every candidate forms the same BF16 operands and
-  // issues the same MMAs in the same order.
+  // 4 KB region of a tile; 9-10: split tiles with two CTAs of 256 threads per
+  // SM (two pipelines), at most 8 or 2 slots each.  Every candidate forms the
+  // same BF16 operands and issues the same MMAs in the same order.
   auto go = [&](int c) -> bool {
     if (c >= 4 && c <= 6) {
       const int NS = c - 2;
       switch (lv.D) {
-        case 8: return launch<8>(ctx, lv, in, out, s, err, NS);
-        case 16: return launch<16>(ctx, lv, in, out, s, err, NS);
-        case 24: return launch<24>(ctx, lv, in, out, s, err, NS);
-        default: return launch<32>(ctx, lv, in, out, s, err, NS);
+        case 8: return launch<8>(ctx, lv, in, out, s, err, NS, b);
+        case 16: return launch<16>(ctx, lv, in, out, s, err, NS, b);
+        case 24: return launch<24>(ctx, lv, in, out, s, err, NS, b);
+        default: return launch<32>(ctx, lv, in, out, s, err, NS, b);
       }
     }
-    static const int kNA[9] = {8, 4, 3, 2, 0, 0, 0, 8, 4};
+    static const int kNA[11] = {8, 4, 3, 2, 0, 0, 0, 8, 4, 8, 2};
     const int NA = kNA[c];
-    const bool rc = c >= 7;
+    const bool rc = c == 7 || c == 8;
+    const bool two = c >= 9;
     switch (lv.D) {
-      case 8: return launch_split<8>(ctx, lv, in, out, s, err, NA, rc);
-      case 16: return launch_split<16>(ctx, lv, in, out, s, err, NA, rc);
-      case 24: return launch_split<24>(ctx, lv, in, out, s, err, NA, rc);
-      default: return launch_split<32>(ctx, lv, in, out, s, err, NA, rc);
+      case 8: return launch_split<8>(ctx, lv, in, out, s, err, NA, rc, two, b);
+      case 16: return launch_split<16>(ctx, lv, in, out, s, err, NA, rc, two, b);
+      case 24: return launch_split<24>(ctx, lv, in, out, s, err, NA, rc, two, b);
+      default: return launch_split<32>(ctx, lv, in, out, s, err, NA, rc, two, b);
     }
   };
   const std::string key = "coarse_tc D" + std::to_string(lv.D) + " sites" + std::to_string(lv.geo.nsites) + " rhs" +
-                          std::to_string(s);
+                          std::to_string(s) + (b ? " res" : "");
   const int c = tune_pick(ctx, key, kCoarseTcCandidates, go);
   if (c >= 0 && go(c)) return;
   for (int d = 0; d < kCoarseTcCandidates; ++d)

@@ -11,8 +11,9 @@ namespace qd {
 bool coarse_tc_supported(const CoarseLevel& lv, const void* in, const void* out, int s);
 // Make the compact BF16 copy of the level's stencil (once).
 void coarse_tc_prepare(qd_ctx& ctx, CoarseLevel& lv);
-// out = C in for s right-hand sides (interleaved complex FP32 in and out).
-void coarse_apply_tc(qd_ctx& ctx, CoarseLevel& lv, const cplxf* in, cplxf* out, int s);
+// out = C in for s right-hand sides (interleaved complex FP32 in and out);
+// with b: out = b - C in (b may not alias out or in).
+void coarse_apply_tc(qd_ctx& ctx, CoarseLevel& lv, const cplxf* in, cplxf* out, int s, const cplxf* b = nullptr);
 // Error code recorded by a bounded wait of the kernel (0: none); synchronises.
 int coarse_tc_error(qd_ctx& ctx, const CoarseLevel& lv);
 

@@ -169,6 +169,7 @@ struct LearnedSmoother {
   DevBuf w64;                       // device copy of w
   DevBuf w32;                       // w rounded to FP16, held as float2 (FP32 V-cycle)
   mutable DevBuf t[2];              // intermediate fields of a layered apply (grow-only)
+  mutable DevBuf tune_scratch;      // output of the launch-shape timing (released after it)
   double err_learned = 0.0, err_plain = 0.0;
 };
 

@@ -238,6 +238,7 @@ template <class C> struct CoarseOp : public Op<C> {
   int64_t nsites() const override { return lv->geo.nsites; }
   int dof() const override { return lv->D; }
   void apply(qd_ctx& ctx, const C* in, C* out, int nrhs) const override;
+  void residual(qd_ctx& ctx, const C* b, const C* x, C* r, int nrhs) const override;
   bool same(const Op<C>& o) const override {
     const CoarseOp<C>* c = dynamic_cast<const CoarseOp<C>*>(&o);
     return c && c->lv == lv && c->mat == mat;

@@ -20,6 +20,7 @@
 #include "blas.cuh"
 #include "dense.cuh"
 #include "mg.cuh"
+#include "tune.cuh"
 
 namespace qd {
 
@@ -195,6 +196,142 @@ __global__ void __launch_bounds__(128, 4) k_smoother_apply_x2(const float2* __re
   }
 }
 
+// Packed-FP32 form of k_smoother_apply_x2 (fma.rn.f32x2: one instruction
+// for two FP32 multiply-adds).  A complex value is one 64-bit pair (re, im);
+// acc += c t is fma2((c.x, c.x), (t.x, t.y), fma2((-c.y, c.y), (t.y, t.x),
+// acc)) and acc += conj(l) x is fma2((l.x, l.x), (x.x, x.y), fma2((l.y,
+// -l.y), (x.y, x.x), acc)): lane by lane the same multiply-adds in the same
+// order as cfma / cfmac, so the results are bit-identical to the unpacked
+// kernel.  The weights are staged in shared memory already packed.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(u64 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 swap2(u64 v) {
+  const float2 f = upk2(v);
+  return pk2(f.y, f.x);
+}
+
+template <bool ADJ>
+__device__ __forceinline__ void transport4p(const float2* __restrict__ L, const float2* __restrict__ p, int64_t rs,
+                                            u64 t[2][12]) {
+  float2 l[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) l[k] = L[k];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    u64 x[2][3], xs[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float4 v = *reinterpret_cast<const float4*>(p + (s * 3 + c) * rs);
+      x[0][c] = pk2(v.x, v.y);
+      xs[0][c] = pk2(v.y, v.x);
+      x[1][c] = pk2(v.z, v.w);
+      xs[1][c] = pk2(v.w, v.z);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      u64 a0 = 0ull, a1 = 0ull;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float2 lv = ADJ ? l[b * 3 + a] : l[a * 3 + b];
+        const u64 lxx = pk2(lv.x, lv.x);
+        const u64 ly = ADJ ? pk2(lv.y, -lv.y) : pk2(-lv.y, lv.y);
+        a0 = fma2(lxx, x[0][b], fma2(ly, xs[0][b], a0));
+        a1 = fma2(lxx, x[1][b], fma2(ly, xs[1][b], a1));
+      }
+      t[0][s * 3 + a] = a0;
+      t[1][s * 3 + a] = a1;
+    }
+  }
+}
+
+template <bool ACC>
+__global__ void __launch_bounds__(128, 4) k_smoother_apply_p2(const float2* __restrict__ U, const int* __restrict__ nbr,
+                                                              int64_t V, int nrhs, const float2* __restrict__ w,
+                                                              const float2* __restrict__ in, float2* __restrict__ out) {
+  __shared__ u64 sw[144][2];  // (c.x, c.x), (-c.y, c.y)
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) {
+    const float2 c = w[k];
+    sw[k][0] = pk2(c.x, c.x);
+    sw[k][1] = pk2(-c.y, c.y);
+  }
+  __syncthreads();
+  const int half = nrhs >> 1;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= V * half) return;
+  const int64_t site = g / half;
+  const int r0 = 2 * (int)(g - site * half);
+  const int64_t rs = nrhs;
+  u64 acc[2][12];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[j][k] = 0ull;
+  for (int d = 0; d < 9; ++d) {
+    u64 t[2][12];
+    if (d == 0) {
+      const float2* p = in + site * 12 * rs + r0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const float4 q = *reinterpret_cast<const float4*>(p + k * rs);
+        t[0][k] = pk2(q.x, q.y);
+        t[1][k] = pk2(q.z, q.w);
+      }
+    } else if (d <= 4) {
+      const int mu = d - 1;
+      const int64_t y = nbr[site * 8 + mu];
+      transport4p<false>(U + ((int64_t)mu * V + site) * 9, in + y * 12 * rs + r0, rs, t);
+    } else {
+      const int mu = d - 5;
+      const int64_t y = nbr[site * 8 + 4 + mu];
+      transport4p<true>(U + ((int64_t)mu * V + y) * 9, in + y * 12 * rs + r0, rs, t);
+    }
+    // spin mixing, i outer: each accumulator still takes its i terms in order
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      u64 ts[2][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        ts[0][a] = swap2(t[0][i * 3 + a]);
+        ts[1][a] = swap2(t[1][i * 3 + a]);
+      }
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const u64 cxx = sw[d * 16 + o * 4 + i][0], cny = sw[d * 16 + o * 4 + i][1];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          acc[0][o * 3 + a] = fma2(cxx, t[0][i * 3 + a], fma2(cny, ts[0][a], acc[0][o * 3 + a]));
+          acc[1][o * 3 + a] = fma2(cxx, t[1][i * 3 + a], fma2(cny, ts[1][a], acc[1][o * 3 + a]));
+        }
+      }
+    }
+  }
+  float2* y = out + site * 12 * rs + r0;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float2 a0 = upk2(acc[0][k]), a1 = upk2(acc[1][k]);
+    float4 v = make_float4(a0.x, a0.y, a1.x, a1.y);
+    if (ACC) {
+      const float4 o = *reinterpret_cast<const float4*>(y + k * rs);
+      v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+    }
+    *reinterpret_cast<float4*>(y + k * rs) = v;
+  }
+}
+
 // out (+)= S_l in for one layer with device weights w.
 template <class C>
 static void apply_layer(qd_ctx& ctx, const qd_mg& mg, int nrhs, const C* w, const C* in, C* out, bool accumulate) {
@@ -214,15 +351,47 @@ static void apply_layer(qd_ctx& ctx, const qd_mg& mg, int nrhs, const C* w, cons
     const int blocks2 = div_up(geo.nsites * (nrhs / 2), 128);
     const float2* L = reinterpret_cast<const float2*>(links);
     const float2* W2 = reinterpret_cast<const float2*>(w);
-    if (accumulate)
-      k_smoother_apply_x2<true><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2,
-                                                                 reinterpret_cast<const float2*>(in),
-                                                                 reinterpret_cast<float2*>(out));
-    else
-      k_smoother_apply_x2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2,
-                                                                  reinterpret_cast<const float2*>(in),
-                                                                  reinterpret_cast<float2*>(out));
-    QD_LAUNCH_CHECK();
+    const float2* xi = reinterpret_cast<const float2*>(in);
+    float2* yo = reinterpret_cast<float2*>(out);
+    // candidate 0: two right-hand sides per thread; 1: the same with packed
+    // FP32 multiply-adds (bit-identical).  Accumulating launches are not
+    // timed by the tuner (they change out); they follow the plain choice.
+    auto launch = [&](int c) -> bool {
+      if (c == 0) {
+        if (accumulate)
+          k_smoother_apply_x2<true><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, yo);
+        else
+          k_smoother_apply_x2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, yo);
+      } else {
+        if (accumulate)
+          k_smoother_apply_p2<true><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, yo);
+        else
+          k_smoother_apply_p2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, yo);
+      }
+      QD_LAUNCH_CHECK();
+      return true;
+    };
+    const std::string key = "smoother f32 sites" + std::to_string(geo.nsites) + " rhs" + std::to_string(nrhs);
+    int c = tune_lookup(key);
+    if (c < 0 && tune_can_time(ctx)) {
+      // time the non-accumulating form into scratch (the candidates then
+      // neither change out nor read it), released afterwards
+      DevBuf& scr = mg.ls->tune_scratch;
+      scr.resize((size_t)tot * 12 * sizeof(C));
+      float2* so = scr.as<float2>();
+      auto time_into_scratch = [&](int cc) -> bool {
+        if (cc == 0)
+          k_smoother_apply_x2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, so);
+        else
+          k_smoother_apply_p2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, so);
+        QD_LAUNCH_CHECK();
+        return true;
+      };
+      c = tune_pick(ctx, key, 2, time_into_scratch);
+      QD_CUDA(cudaStreamSynchronize(ctx.stream));
+      scr.release();
+    }
+    launch(c >= 0 ? c : 0);
     return;
   }
   const int blocks = div_up(tot, 128);

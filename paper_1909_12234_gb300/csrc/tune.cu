@@ -36,6 +36,16 @@ void tune_set_mode(int mode) { g_mode.store(mode ? 1 : 0); }
 void tune_force(int candidate) { g_force.store(candidate >= 0 ? candidate : -1); }
 int tune_mode() { return g_mode.load(); }
 
+int tune_lookup(const std::string& key) {
+  const int forced = g_force.load();
+  if (forced >= 0) return forced;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = table().find(key);
+  return it != table().end() ? it->second.choice : -1;
+}
+
+bool tune_can_time(qd_ctx& ctx) { return g_force.load() < 0 && g_mode.load() != 0 && !capturing(ctx.stream); }
+
 void tune_clear() {
   std::lock_guard<std::mutex> lk(g_mu);
   table().clear();

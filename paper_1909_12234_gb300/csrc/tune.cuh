@@ -23,6 +23,12 @@ namespace qd {
 // chosen candidate, whose launch the caller then makes itself.
 int tune_pick(qd_ctx& ctx, const std::string& key, int ncand, const std::function<bool(int)>& launch);
 
+// The stored (or forced) choice for key without timing anything; -1: none.
+int tune_lookup(const std::string& key);
+// Whether tune_pick would time candidates now (tuning on, no forced
+// candidate, the stream not being captured).
+bool tune_can_time(qd_ctx& ctx);
+
 // 0: defaults only; 1: tune on first use (the library's default).
 void tune_set_mode(int mode);
 // >= 0: tune_pick returns this candidate (when < ncand) without timing;

@@ -170,6 +170,7 @@ SIGNATURES = {
     "qd_coarse_apply_tc": (_I, [_P, _I, _I, _P, _P]),
     "qd_restrict_tc": (_I, [_P, _I, _I, _P, _P]),
     "qd_prolongate_f32": (_I, [_P, _I, _I, _P, _P]),
+    "qd_coarse_residual_tc": (_I, [_P, _I, _I, _P, _P, _P]),
     "qd_coarse_solve": (_I, [_P, _I, _I, _P, _P]),
     "qd_coarse_solve_f32": (_I, [_P, _I, _I, _P, _P]),
     "qd_solver_params_default": (None, [ctypes.POINTER(SolverParams)]),
@@ -466,6 +467,10 @@ def coarse_apply_f32(mg, level, nrhs, inp, out):
 
 def coarse_apply_tc(mg, level, nrhs, inp, out):
     _check(load().qd_coarse_apply_tc(mg.h, int(level), int(nrhs), _ptr64(inp), _ptr64(out)))
+
+
+def coarse_residual_tc(mg, level, nrhs, b, x, r):
+    _check(load().qd_coarse_residual_tc(mg.h, int(level), int(nrhs), _ptr64(b), _ptr64(x), _ptr64(r)))
 
 
 def prolongate_f32(mg, level, nrhs, coarse, fine):

@@ -33,7 +33,7 @@ from gpu_util import dev, host, need_gpu, torch
 pytestmark = pytest.mark.gpu
 
 U_BF16 = 2.0 ** -8
-N_TC_CANDIDATES = 9  # launch shapes of the tensor-core stencil
+N_TC_CANDIDATES = 11  # launch shapes of the tensor-core stencil
 
 
 @pytest.fixture(scope="module")
@@ -130,12 +130,20 @@ def test_tensor_core_coarse_stencil(qd, ctx, dims, m0, blocks, nvs):
             # every launch shape (input split into operand tiles first, or
             # converted inside the kernel; operand/staging ring depths) forms
             # the same operands and MMAs: the same bits
+            # the residual form subtracts in the epilogue: the same bits as
+            # b - (C x) in FP32
+            bd = torch.from_numpy(np.ascontiguousarray(
+                (rng.standard_normal((nc, s)) + 1j * rng.standard_normal((nc, s))).astype(np.complex64))).to("cuda:0")
+            want = bd - out
             try:
                 for cand in range(N_TC_CANDIDATES):
                     qd.autotune_force(cand)
                     out3 = torch.full_like(xd, float("nan"))
                     qd.coarse_apply_tc(mg, l + 1, s, xd, out3)
                     assert torch.equal(out, out3), (l, s, cand)
+                    res = torch.full_like(xd, float("nan"))
+                    qd.coarse_residual_tc(mg, l + 1, s, bd, xd, res)
+                    assert torch.equal(res, want), (l, s, cand)
             finally:
                 qd.autotune_force(-1)
     for o in (mg, g):

@@ -172,3 +172,32 @@ def test_layered_training_builds_on_the_one_layer_fit(qd, ctx):
     print("held-out errors (learned, plain) by depth:", [(i["err_learned"], i["err_plain"]) for i in infos])
     mg.close()
     g.close()
+
+
+def test_packed_fp32_smoother_is_bit_identical(qd, ctx):
+    # the FP32 smoother with packed multiply-adds (fma.rn.f32x2) computes the
+    # same multiply-adds in the same order lane by lane: the same bits, for
+    # the plain and the accumulating form and for one and two layers
+    dims = (8, 8, 4, 4)
+    U = synth.random_su3_links(dims, 0.3, 4)
+    g = qd.Gauge(ctx, dims, U)
+    mg = qd.Multigrid(ctx, g, -0.5, 0.0, qd.mg_params(1, [(2, 2, 2, 2)], [4], null_maxit=0))
+    rng = np.random.default_rng(12)
+    W = rng.standard_normal((2, 9, 4, 4)) + 1j * rng.standard_normal((2, 9, 4, 4))
+    try:
+        for layers in (1, 2):
+            qd.smoother_set_layer_weights(mg, W[:layers])
+            for s in (2, 64, 130):
+                x = torch.randn((g.V, 12, s), dtype=torch.complex64, device="cuda:0",
+                                generator=torch.Generator("cuda:0").manual_seed(s))
+                outs = []
+                for cand in (0, 1):
+                    qd.autotune_force(cand)
+                    o = torch.full_like(x, float("nan"))
+                    qd.smoother_apply_f32(mg, s, x, o)
+                    outs.append(o)
+                assert torch.equal(outs[0], outs[1]), (layers, s)
+    finally:
+        qd.autotune_force(-1)
+    mg.close()
+    g.close()

@@ -441,17 +441,23 @@ __global__ void __launch_bounds__(128) k_wilson_eo(const C* __restrict__ U, cons
   }
 }
 
-// FP32, two right-hand sides per thread (even nrhs, 16-byte aligned fields).
+// FP32, two right-hand sides per thread (even nrhs, 16-byte aligned fields),
+// the columns swept in chunks of 2 rc2 as in k_wilson_f32x2; PROJ: the
+// neighbours projected as they load.
+template <bool PROJ>
 __global__ void __launch_bounds__(128, 4) k_wilson_eo_f32x2(const float2* __restrict__ U, const int* __restrict__ nbr,
-                                                         const int* __restrict__ visit, int64_t V, int nrhs, int p,
-                                                         EoCoef q, const float2* __restrict__ in,
+                                                         const int* __restrict__ visit, int64_t V, int nrhs, int rc2,
+                                                         int p, EoCoef q, const float2* __restrict__ in,
                                                          const float2* __restrict__ z, float2* __restrict__ out) {
   const int half = nrhs >> 1;
   const int64_t Vh = V / 2;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= Vh * half) return;
-  const int64_t slot = g / half;
-  const int r0 = 2 * (int)(g - slot * half);
+  const int64_t per_chunk = Vh * rc2;
+  const int ch = (int)(g / per_chunk);
+  const int64_t rem = g - ch * per_chunk;
+  const int64_t slot = rem / rc2;
+  const int r0 = 2 * (ch * rc2 + (int)(rem - slot * rc2));
   const int64_t site = visit[slot];
   const int64_t rs = nrhs;
   const int64_t in_off = (int64_t)(1 - p) * Vh, own = site - (int64_t)p * Vh;
@@ -463,10 +469,10 @@ __global__ void __launch_bounds__(128, 4) k_wilson_eo_f32x2(const float2* __rest
   for (int j = 0; j < 2; ++j)
 #pragma unroll
     for (int k = 0; k < 6; ++k) { hu[j][k] = make_float2(0.f, 0.f); hl[j][k] = make_float2(0.f, 0.f); }
-  hop2_dir<0, false>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
-  hop2_dir<1, false>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
-  hop2_dir<2, false>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
-  hop2_dir<3, false>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
+  hop2_dir<0, false, PROJ>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
+  hop2_dir<1, false, PROJ>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
+  hop2_dir<2, false, PROJ>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
+  hop2_dir<3, false, PROJ>(U, nb8, V, site, rs, r0, in, hu, hl, in_off);
   const float2 q1u = make_float2((float)q.q1[0].x, (float)q.q1[0].y), q1l = make_float2((float)q.q1[1].x, (float)q.q1[1].y);
   const float2 q2u = make_float2((float)q.q2[0].x, (float)q.q2[0].y), q2l = make_float2((float)q.q2[1].x, (float)q.q2[1].y);
   const float2* zz = z ? z + own * 12 * rs + r0 : nullptr;
@@ -506,9 +512,25 @@ void wilson_eo(qd_ctx& ctx, const LevelGeom& geo, const C* links, int p, const c
                   ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(z)) &
                    15) == 0;
   if (x2) {
-    k_wilson_eo_f32x2<<<div_up(Vh * (nrhs / 2), 128), 128, 0, ctx.stream>>>(
-        reinterpret_cast<const float2*>(links), nb, vis, geo.nsites, nrhs, p, q, reinterpret_cast<const float2*>(in),
-        reinterpret_cast<const float2*>(z), reinterpret_cast<float2*>(out));
+    // candidates: columns swept whole, in chunks of 64 or 32, and the whole
+    // sweep with the neighbours projected as they load (same sums per
+    // element in the first three: the same bits)
+    auto launch = [&](int c) -> bool {
+      const int rc = c == 1 ? 64 : (c == 2 ? 32 : nrhs);
+      if (rc > nrhs || nrhs % rc != 0 || (c == 1 && nrhs <= 64) || (c == 2 && nrhs <= 32)) return false;
+      auto kern = c == 3 ? k_wilson_eo_f32x2<true> : k_wilson_eo_f32x2<false>;
+      kern<<<div_up(Vh * (nrhs / 2), 128), 128, 0, ctx.stream>>>(
+          reinterpret_cast<const float2*>(links), nb, vis, geo.nsites, nrhs, rc / 2, p, q,
+          reinterpret_cast<const float2*>(in), reinterpret_cast<const float2*>(z), reinterpret_cast<float2*>(out));
+      QD_LAUNCH_CHECK();
+      return true;
+    };
+    // out-of-place (out differs from in and z): safe to time
+    const std::string key = "wilson eo f32 sites" + std::to_string(geo.nsites) + " rhs" + std::to_string(nrhs) +
+                            (z ? " z" : "");
+    const int c = (out == in || out == z) ? -1 : tune_pick(ctx, key, 4, launch);
+    if (c < 0 || !launch(c)) launch(0);
+    return;
   } else {
     k_wilson_eo<C><<<div_up(tot, 128), 128, 0, ctx.stream>>>(links, nb, vis, geo.nsites, nrhs, p, q, in, z, out);
   }

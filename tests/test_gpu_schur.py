@@ -50,6 +50,19 @@ def test_schur_operator_against_oracle(qd, ctx, dims, tau):
         y32 = torch.empty_like(x32)
         qd.dirac_schur_apply_f32(ctx, g, m0, tau, s, x32, y32)
         assert rel_err(host(y32).astype(np.complex128), ref) < 1e-5, s
+        # the launch shapes of the parity-restricted hops: whole, chunks of 64
+        # and 32 columns (the same bits) and projection on load (rounding)
+        try:
+            outs = []
+            for cand in range(4):
+                qd.autotune_force(cand)
+                o = torch.full_like(x32, float("nan"))
+                qd.dirac_schur_apply_f32(ctx, g, m0, tau, s, x32, o)
+                outs.append(o)
+            assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2]), s
+            assert rel_err(host(outs[3]), host(outs[0])) < 1e-6, s
+        finally:
+            qd.autotune_force(-1)
     g.close()
 
 

@@ -57,7 +57,7 @@ CONFIG3 = dict(
              "rel. residual 1e-8",
     dims=(16, 16, 16, 32), eps=0.2, link_seed=3, m0=-0.8, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvs=[12, 16],
     k=24, guard=16, s=128, tol=1e-8, noise_seed=103, restart=4, maxit=500, inner_tol=1e-5, schur=1,
-    mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6, "coarse_smoother_steps": 1},
+    mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6, "coarse_smoother_steps": 1, "null_f32": 1},
     learned=1, learned_mr=0, layers=2, eig_maxit=30, fp64_samples=16,
 )
 # Config 2: 8^4 lattice (the two-level workload of round one), kept for

@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define QD_ABI_VERSION 5
+#define QD_ABI_VERSION 6
 #define QD_MAX_LEVELS 4 /* fine level + up to 3 coarse levels */
 
 typedef enum {
@@ -209,6 +209,10 @@ typedef struct {
   int coarse_smoother_steps;    /* minimal-residual post-smoothing steps of
                                    the V-cycles on coarse levels; < 0: the
                                    same as smoother_steps */
+  int null_f32;                 /* 1: the null-vector iterations run in FP32
+                                   (FP32 operators; the vectors only need
+                                   null_tol, 1e-2); 0 (default): FP64, the
+                                   oracle's arithmetic */
 } qd_mg_params;
 
 /* Fill `p` with this library's defaults (1 level, 2^4 blocks, nv 12,

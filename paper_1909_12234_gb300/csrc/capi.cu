@@ -239,6 +239,7 @@ void qd_mg_params_default(qd_mg_params* p) {
   p->use_graphs = 1;
   p->coarse_tc = 1;
   p->coarse_smoother_steps = -1;
+  p->null_f32 = 0;
 }
 
 void qd_solver_params_default(qd_solver_params* p) {

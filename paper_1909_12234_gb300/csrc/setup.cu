@@ -42,9 +42,21 @@ void mg_build(qd_mg& mg, const double* injected_null) {
                               ctx.stream));
       DevBuf zero(n * nv * sizeof(cplx));
       QD_CUDA(cudaMemsetAsync(zero.as<cplx>(), 0, n * nv * sizeof(cplx), ctx.stream));
-      auto A = mg.op<cplx>(l);
-      mr_steps<cplx>(ctx, *A, zero.as<cplx>(), Y.as<cplx>(), false, nv, p.null_maxit, p.null_tol,
-                     R.as<cplx>(), Qb.as<cplx>(), steps.as<int>(), scratch);
+      if (p.null_f32) {
+        // the same iteration with FP32 operators and vectors
+        DevBuf Yf(n * nv * sizeof(cplxf)), Rf(n * nv * sizeof(cplxf)), Qf(n * nv * sizeof(cplxf)),
+            zf(n * nv * sizeof(cplxf));
+        to_f32(ctx, Y.as<cplx>(), Yf.as<cplxf>(), n * nv);
+        QD_CUDA(cudaMemsetAsync(zf.as<cplxf>(), 0, n * nv * sizeof(cplxf), ctx.stream));
+        auto A = mg.op<cplxf>(l);
+        mr_steps<cplxf>(ctx, *A, zf.as<cplxf>(), Yf.as<cplxf>(), false, nv, p.null_maxit, p.null_tol,
+                        Rf.as<cplxf>(), Qf.as<cplxf>(), steps.as<int>(), scratch);
+        to_f64(ctx, Yf.as<cplxf>(), Y.as<cplx>(), n * nv);
+      } else {
+        auto A = mg.op<cplx>(l);
+        mr_steps<cplx>(ctx, *A, zero.as<cplx>(), Y.as<cplx>(), false, nv, p.null_maxit, p.null_tol,
+                       R.as<cplx>(), Qb.as<cplx>(), steps.as<int>(), scratch);
+      }
       QD_CUDA(cudaMemcpyAsync(T->null_steps.data(), steps.as<int>(), nv * sizeof(int), cudaMemcpyDeviceToHost,
                               ctx.stream));
     }

@@ -19,6 +19,7 @@
 
 #include "blas.cuh"
 #include "dense.cuh"
+#include "defl.cuh"
 #include "mg.cuh"
 #include "tune.cuh"
 
@@ -581,9 +582,18 @@ static void make_pairs(qd_mg& mg, int s, uint64_t key, double solve_tol, DevBuf&
   mg.pre64->coarse_correction(ctx, v.as<cplx>(), z.as<cplx>(), s);
   auto A = mg.op<cplx>(0);
   A->residual(ctx, v.as<cplx>(), z.as<cplx>(), r.as<cplx>(), s);
-  GCR<cplx> gcr;
+  // e = A^{-1} r to solve_tol on the FP64 residual: FP32 GCR corrections with
+  // the FP32 V-cycle inside FP64 refinement (the pairs need no more than the
+  // tolerance, and the FP64 V-cycle's dense coarsest product is slow here)
+  qd_solver_params sp{};
+  sp.tol = solve_tol;
+  sp.maxit = 2000;
+  sp.restart = 16;
+  sp.precision = QD_PREC_MIXED;
+  sp.inner_tol = 1e-5;
+  sp.max_refine = 20;
   SolveInfo info;
-  gcr.solve(ctx, *A, mg.pre64.get(), r.as<cplx>(), e.as<cplx>(), s, solve_tol, 2000, 16, &info);
+  solve(ctx, *mg.gauge, &mg, mg.m0, mg.tau, s, r.as<cplx>(), e.as<cplx>(), sp, info);
   QD_REQUIRE(info.converged == s, "learned-smoother training solves did not converge");
 }
 

@@ -59,7 +59,8 @@ class MGParams(ctypes.Structure):
                 ("coarsest_bf16", ctypes.c_int),
                 ("use_graphs", ctypes.c_int),
                 ("coarse_tc", ctypes.c_int),
-                ("coarse_smoother_steps", ctypes.c_int)]
+                ("coarse_smoother_steps", ctypes.c_int),
+                ("null_f32", ctypes.c_int)]
 
 
 class SolverParams(ctypes.Structure):

@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(library):
 
 
 def test_abi_version(library):
-    assert library.qd_abi_version() == 5
+    assert library.qd_abi_version() == 6
 
 
 def test_struct_layouts_match_c(tmp_path):
@@ -49,9 +49,9 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "qdtrace.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(qd_mg_params), offsetof(qd_mg_params, null_tol),
          offsetof(qd_mg_params, coarsest_direct), offsetof(qd_mg_params, use_graphs), offsetof(qd_mg_params, coarse_tc),
-         offsetof(qd_mg_params, coarse_smoother_steps));
+         offsetof(qd_mg_params, coarse_smoother_steps), offsetof(qd_mg_params, null_f32));
   printf("%zu %zu %zu\n", sizeof(qd_solve_stats), offsetof(qd_solve_stats, true_rel_residual),
          offsetof(qd_solve_stats, stagnated));
   printf("%zu %zu %zu %zu\n", sizeof(qd_defl_params), offsetof(qd_defl_params, seed),
@@ -74,7 +74,8 @@ int main(void) {
     got = [list(map(int, l.split())) for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines()]
     want = [
         [ctypes.sizeof(qd.MGParams), qd.MGParams.null_tol.offset, qd.MGParams.coarsest_direct.offset,
-         qd.MGParams.use_graphs.offset, qd.MGParams.coarse_tc.offset, qd.MGParams.coarse_smoother_steps.offset],
+         qd.MGParams.use_graphs.offset, qd.MGParams.coarse_tc.offset, qd.MGParams.coarse_smoother_steps.offset,
+         qd.MGParams.null_f32.offset],
         [ctypes.sizeof(qd.SolveStats), qd.SolveStats.true_rel_residual.offset, qd.SolveStats.stagnated.offset],
         [ctypes.sizeof(qd.DeflParams), qd.DeflParams.seed.offset, qd.DeflParams.tau_restart.offset,
          qd.DeflParams.fail_first.offset],

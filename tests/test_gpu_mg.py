@@ -193,3 +193,34 @@ def test_direct_coarsest_solve(qd, ctx, dims, m0, blocks, nvs):
     import scipy.sparse.linalg as spla
     ref = spla.splu(H.matrices[-1].tocsc()).solve(x)
     assert rel_err(host(y).reshape(T.nc, s), ref) < 1e-9
+
+
+def test_null_vectors_in_fp32(qd, ctx):
+    # null_f32: the same minimal-residual iteration in FP32 (the vectors need
+    # only the 1e-2 null_tol); step counts within one or two of the FP64
+    # iteration's, an orthonormal W, and a solve that reaches the FP64
+    # tolerance with the resulting hierarchy
+    dims, m0 = (8, 8, 8, 8), -0.8
+    U = synth.random_su3_links(dims, 0.3, 2)
+    g = qd.Gauge(ctx, dims, U)
+    steps = {}
+    for f32 in (0, 1):
+        mg = qd.Multigrid(ctx, g, m0, 0.0, qd.mg_params(2, [(2, 2, 2, 2), (2, 2, 2, 2)], [12, 16], null_f32=f32,
+                                                         coarse_tol=0.0, coarse_maxit=6))
+        steps[f32] = [mg.level_info(l)[3] for l in (0, 1)]
+        if f32:
+            T_nc = mg.level_info(1)[2] * mg.level_info(1)[1]
+            c = np.random.default_rng(1).standard_normal((T_nc, 2)) + 0j
+            fine = torch.empty((g.V * 12 * 2,), dtype=torch.complex128, device="cuda:0")
+            qd.prolongate(mg, 0, 2, dev(c), fine)
+            back = torch.empty((T_nc * 2,), dtype=torch.complex128, device="cuda:0")
+            qd.restrict(mg, 0, 2, fine, back)
+            assert rel_err(host(back).reshape(T_nc, 2), c) < 1e-12  # W^H W = I
+            b = dev(np.random.default_rng(2).standard_normal((g.V, 12, 4)) + 0j)
+            x = torch.empty_like(b)
+            _, its, _, rel = qd.solve(ctx, g, mg, m0, 0.0, 4, b, x, 1e-8, maxit=500, precision=qd.QD_PREC_MIXED)
+            assert max(rel) <= 1e-8
+        mg.close()
+    for l in (0, 1):
+        assert all(abs(int(a) - int(b)) <= 2 for a, b in zip(steps[0][l], steps[1][l])), (l, steps)
+    g.close()

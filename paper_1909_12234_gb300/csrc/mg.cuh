@@ -26,6 +26,13 @@ template <class C> class GCR {
   // SolveInfo::stagnated (the inverter stagnating, Sec. 3.2).
   int stag_window = 0;
   double stag_ratio = 0.9;
+  // > 0 (fused FP32 form only): each direction P_i and the residual r sit at
+  // offset `embed` (complex elements) inside a slot of embed + n nrhs
+  // elements whose leading part of r is zero, so a preconditioner can read r
+  // and write P_i as the second half of a larger field (the odd sites of a
+  // full-lattice field in the even-odd solve) without copies.
+  int64_t embed = 0;
+  bool embeds(int restart) const;
   // x = A^{-1} b to ||b - A x|| <= tol ||b|| per column (x overwritten,
   // zero initial guess).  M (nullable) is a right preconditioner that may
   // change between calls.  `quiet` skips per-column statistics.
@@ -35,8 +42,9 @@ template <class C> class GCR {
   void buffers(std::vector<const void*>& v) const;
 
  private:
-  void ensure(int64_t n, int nrhs, int m);
+  void ensure(int64_t n, int nrhs, int m, int64_t emb);
   DevBuf P_, Q_, r_, t_;
+  int64_t cap_emb_ = -1;
   DevBuf sc_;   // cplx per-RHS scalars
   DevBuf tab_;  // cplx coefficient tables of the fused one-pass form
   DevBuf act_;  // int [nrhs + 1]: active flags, then the count of active
@@ -139,6 +147,9 @@ template <class C> class SchurPrecond : public Precond<C> {
  public:
   MGPrecond<C>* mg = nullptr;
   const LevelGeom* geo = nullptr;
+  // r and z are the odd halves of full fields whose even half of r is zero
+  // (GCR::embed): the V-cycle runs on them in place
+  bool embedded = false;
   void apply(qd_ctx& ctx, const C* r, C* z, int nrhs) override;
 
  private:

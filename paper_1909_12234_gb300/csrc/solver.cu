@@ -339,15 +339,21 @@ template <class C> void GCR<C>::buffers(std::vector<const void*>& v) const {
   for (const DevBuf* b : {&P_, &Q_, &r_, &t_, &sc_, &act_, &tab_}) v.push_back(b->as<void>());
 }
 
-template <class C> void GCR<C>::ensure(int64_t n, int nrhs, int m) {
-  if (n == cap_n_ && nrhs <= cap_rhs_ && m <= cap_m_) return;
+template <class C> bool GCR<C>::embeds(int restart) const {
+  return embed > 0 && orth_passes == 1 && sizeof(C) == sizeof(cplxf) && restart <= kMaxMdot;
+}
+
+template <class C> void GCR<C>::ensure(int64_t n, int nrhs, int m, int64_t emb) {
+  if (n == cap_n_ && nrhs <= cap_rhs_ && m <= cap_m_ && emb == cap_emb_) return;
   const size_t vec = (size_t)n * nrhs * sizeof(C);
+  const size_t slot = vec + (size_t)emb * sizeof(C);
   P_.release();
   Q_.release();
-  P_.resize(vec * m);
+  P_.resize(slot * m);
   Q_.resize(vec * m);
-  r_.resize(vec);
+  r_.resize(slot);
   t_.resize(vec);
+  cap_emb_ = emb;
   sc_.resize((size_t)(4 + m) * nrhs * sizeof(cplx));
   act_.resize((size_t)(2 * nrhs + 4) * sizeof(int));
   cap_n_ = n;
@@ -362,19 +368,23 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
   QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
   const int64_t n = A.n();
   const int64_t tot = n * nrhs;
-  ensure(n, nrhs, restart);
   // FP32 with one Gram-Schmidt pass: the fused form with a deferred update
   const bool fused = orth_passes == 1 && sizeof(C) == sizeof(cplxf) && restart <= kMaxMdot;
+  const int64_t emb = embeds(restart) ? embed : 0;
+  QD_REQUIRE(emb == 0 || emb >= tot, "GCR embedding shorter than a vector");
+  ensure(n, nrhs, restart, emb);
+  const int64_t pst = tot + emb;  // stride of the directions P_i
   tab_.resize((size_t)(2 * kMaxMdot + kMaxMdot * kMaxMdot + 3 * kMaxMdot) * nrhs * sizeof(cplx));
   cplx* ngtab = tab_.as<cplx>();                          // [m][2][nrhs]: nu_i, gamma_i
   cplx* btab = ngtab + (int64_t)2 * kMaxMdot * nrhs;      // [m][16][nrhs]: beta_ik
   cplx* atab = btab + (int64_t)kMaxMdot * kMaxMdot * nrhs;  // [m][nrhs]: a_i
   cplx* coefx = atab + (int64_t)kMaxMdot * nrhs;           // [m][nrhs]: -d_k
   cplx* braw = coefx + (int64_t)kMaxMdot * nrhs;           // [m][nrhs]: <Q_k, Q_i>
-  C* P = P_.as<C>();
+  C* P = P_.as<C>() + emb;
   C* Q = Q_.as<C>();
-  C* r = r_.as<C>();
+  C* r = r_.as<C>() + emb;
   C* t = t_.as<C>();
+  if (emb) QD_CUDA(cudaMemsetAsync(r_.as<C>(), 0, (size_t)emb * sizeof(C), ctx.stream));  // the leading part of r
   cplx* bn2 = sc_.as<cplx>();
   cplx* rn2 = bn2 + nrhs;
   cplx* s2 = bn2 + 2 * nrhs;
@@ -431,7 +441,7 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
       float2* rf = reinterpret_cast<float2*>(r);
       int mi = 0;
       for (int i = 0; i < restart; ++i) {
-        C* Pi = P + i * tot;
+        C* Pi = P + i * pst;
         C* Qi = Q + i * tot;
         bool have_q = false;
         if (M)
@@ -485,7 +495,7 @@ void GCR<C>::solve(qd_ctx& ctx, const Op<C>& A, Precond<C>* M, const C* b, C* x,
       // x += sum_k d_k Pt_k
       k_backsub<<<div_up(nrhs, 128), 128, 0, ctx.stream>>>(mi, nrhs, atab, btab, coefx);
       QD_LAUNCH_CHECK();
-      blas::multi_axpy(ctx, mi, n, nrhs, coefx, nullptr, P, tot, x);
+      blas::multi_axpy(ctx, mi, n, nrhs, coefx, nullptr, P, pst, x);
       (void)Pf;
       if (!check && its >= maxit) break;
       A.residual(ctx, b, x, r, nrhs);
@@ -902,6 +912,12 @@ template <class C> void SchurPrecond<C>::apply(qd_ctx& ctx, const C* r, C* z, in
   QD_REQUIRE(mg && geo, "Schur preconditioner without a V-cycle");
   const int64_t Vh = geo->nsites / 2;
   const size_t half = (size_t)Vh * 12 * nrhs * sizeof(C);
+  if (embedded) {
+    // r and z are the odd halves of full fields (the even half of r zero)
+    const int64_t hn = Vh * 12 * (int64_t)nrhs;
+    mg->apply(ctx, r - hn, z - hn, nrhs);
+    return;
+  }
   if (nrhs != cap_) {
     R_.resize(2 * half);
     Z_.resize(2 * half);
@@ -933,7 +949,12 @@ void schur_solve(qd_ctx& ctx, const qd_gauge& g, const C* links, double m0, doub
   spin_diag<C>(ctx, Vh, nrhs, Minv, b, u);
   wilson_eo<C>(ctx, g.geo, links, 1, one, half2, u, b + hn, bh, nrhs);
   SchurOp<C> S(&g, links, m0, tau);
+  // the GCR's residual and directions as odd halves of full fields: the
+  // preconditioner runs the V-cycle on them in place
+  gcr.embed = hn;
+  if (pre) pre->embedded = gcr.embeds(restart);
   gcr.solve(ctx, S, pre, bh, x + hn, nrhs, tol, maxit, restart, info);
+  if (pre) pre->embedded = false;
   // x_e = M^{-1} b_e + (1/2) M^{-1} H_eo x_o
   wilson_eo<C>(ctx, g.geo, links, 0, Minv, halfMinv, x + hn, b, x, nrhs);
 }

@@ -61,10 +61,11 @@ void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int
 // nsteps minimal-residual steps on A e = res, accumulated into x; res is
 // updated in place (smoother: no checks, no host synchronisation).  With
 // rin and Az given (res = rin - A x on entry), the last step also writes
-// Az = rin - res = A x.
+// Az = rin - res = A x.  keep_res = false: the last step's residual is not
+// written back (the caller does not read res afterwards).
 template <class C>
 void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int nsteps, DevBuf& scratch,
-               const C* rin = nullptr, C* Az = nullptr);
+               const C* rin = nullptr, C* Az = nullptr, bool keep_res = true);
 
 }  // namespace qd
 

@@ -72,7 +72,7 @@ template <class C>
 __global__ void k_mr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
                             const int* __restrict__ active, C* __restrict__ q, C* __restrict__ x,
                             C* __restrict__ r, cplx* __restrict__ partials, const C* __restrict__ rin = nullptr,
-                            C* __restrict__ Az = nullptr) {
+                            C* __restrict__ Az = nullptr, bool write_r = true) {
   typedef typename CTraits<C>::R R;
   const int col = blockIdx.y * blockDim.x + threadIdx.x;
   R acc = 0;
@@ -89,7 +89,7 @@ __global__ void k_mr_update(int64_t n, int nrhs, const cplx* __restrict__ s2,
       cfma(xv, a, rv);
       cfma(rv, na, qv);
       x[e] = xv;
-      r[e] = rv;
+      if (write_r) r[e] = rv;
       if (Az) {
         // A x = rin - res once res is the residual of x
         const C bv = rin[e];
@@ -622,7 +622,7 @@ void mr_steps(qd_ctx& ctx, const Op<C>& A, const C* b, C* x, bool x_is_zero, int
 // in place (no convergence checks, no host synchronisation).
 template <class C>
 void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int nsteps, DevBuf& scratch,
-               const C* rin, C* Az) {
+               const C* rin, C* Az, bool keep_res) {
   const int64_t n = A.n();
   scratch.resize((size_t)2 * nrhs * sizeof(cplx));
   cplx* s2 = scratch.as<cplx>();
@@ -630,18 +630,21 @@ void mr_smooth(qd_ctx& ctx, const Op<C>& A, C* x, C* res, C* q, int nrhs, int ns
   for (int k = 0; k < nsteps; ++k) {
     A.apply(ctx, res, q, nrhs);
     blas::dots_qq_qr(ctx, n, nrhs, q, res, s2);
-    const bool last_az = Az && k == nsteps - 1;
+    const bool last = k == nsteps - 1;
+    const bool last_az = Az && last;
+    // the residual of the last step is not written when res is not kept
+    const bool write_r = !last || keep_res;
     ProfScope ps(ctx, sizeof(C) == 16 ? QD_PROF_BLAS_F64 : QD_PROF_UPDATE_F32, 8.0 * n * nrhs,
-                 (double)sizeof(C) * (last_az ? 7.0 : 5.0) * n * nrhs);
+                 (double)sizeof(C) * ((last_az ? 6.0 : 4.0) + (write_r ? 1.0 : 0.0)) * n * nrhs);
     k_mr_update<C><<<sw.grid, sw.block, 0, ctx.stream>>>(n, nrhs, s2, nullptr, q, x, res, nullptr,
-                                                         last_az ? rin : nullptr, last_az ? Az : nullptr);
+                                                         last_az ? rin : nullptr, last_az ? Az : nullptr, write_r);
     QD_LAUNCH_CHECK();
   }
 }
 template void mr_smooth<cplx>(qd_ctx&, const Op<cplx>&, cplx*, cplx*, cplx*, int, int, DevBuf&, const cplx*,
-                              cplx*);
+                              cplx*, bool);
 template void mr_smooth<cplxf>(qd_ctx&, const Op<cplxf>&, cplxf*, cplxf*, cplxf*, int, int, DevBuf&,
-                               const cplxf*, cplxf*);
+                               const cplxf*, cplxf*, bool);
 
 template void mr_steps<cplx>(qd_ctx&, const Op<cplx>&, const cplx*, cplx*, bool, int, int, double, cplx*,
                              cplx*, int*, DevBuf&);
@@ -864,7 +867,7 @@ template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, C* Az,
     smoother_apply<C>(ctx, *mg_, nrhs, res_.as<C>(), z, true);
     if (ls->mr_steps > 0) {
       Af->residual(ctx, r, z, res_.as<C>(), nrhs);
-      mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, ls->mr_steps, scratch_, r, Az);
+      mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, ls->mr_steps, scratch_, r, Az, false);
     }
     return;
   }
@@ -872,7 +875,7 @@ template <class C> void MGPrecond<C>::body(qd_ctx& ctx, const C* r, C* z, C* Az,
                                                                     : mg_->p.smoother_steps;
   if (nu > 0) {
     Af->residual(ctx, r, z, res_.as<C>(), nrhs);
-    mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, nu, scratch_, r, Az);
+    mr_smooth<C>(ctx, *Af, z, res_.as<C>(), q_.as<C>(), nrhs, nu, scratch_, r, Az, false);
   }
 }
 

@@ -135,9 +135,14 @@ __device__ __forceinline__ void transport4x2(const float2* __restrict__ L, const
   }
 }
 
+// Sites are taken in the stencil visiting order (visit: 4^4 tiles, Morton
+// inside; nullptr: index order) and the columns in chunks of 2 rc2,
+// chunk-major, so that the neighbour fields a traversal keeps in flight fit
+// in L2 (the same traversal as the Wilson stencil).
 template <bool ACC>
 __global__ void __launch_bounds__(128, 4) k_smoother_apply_x2(const float2* __restrict__ U, const int* __restrict__ nbr,
-                                                              int64_t V, int nrhs, const float2* __restrict__ w,
+                                                              const int* __restrict__ visit, int64_t V, int nrhs,
+                                                              int rc2, const float2* __restrict__ w,
                                                               const float2* __restrict__ in, float2* __restrict__ out) {
   __shared__ float2 sw[144];
   for (int k = threadIdx.x; k < 144; k += blockDim.x) sw[k] = w[k];
@@ -145,8 +150,12 @@ __global__ void __launch_bounds__(128, 4) k_smoother_apply_x2(const float2* __re
   const int half = nrhs >> 1;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= V * half) return;
-  const int64_t site = g / half;
-  const int r0 = 2 * (int)(g - site * half);
+  const int64_t per_chunk = V * rc2;
+  const int ch = (int)(g / per_chunk);
+  const int64_t rem = g - ch * per_chunk;
+  const int64_t slot = rem / rc2;
+  const int r0 = 2 * (ch * rc2 + (int)(rem - slot * rc2));
+  const int64_t site = visit ? visit[slot] : slot;
   const int64_t rs = nrhs;
   float2 acc[2][12];
 #pragma unroll
@@ -261,7 +270,8 @@ __device__ __forceinline__ void transport4p(const float2* __restrict__ L, const 
 
 template <bool ACC>
 __global__ void __launch_bounds__(128, 4) k_smoother_apply_p2(const float2* __restrict__ U, const int* __restrict__ nbr,
-                                                              int64_t V, int nrhs, const float2* __restrict__ w,
+                                                              const int* __restrict__ visit, int64_t V, int nrhs,
+                                                              int rc2, const float2* __restrict__ w,
                                                               const float2* __restrict__ in, float2* __restrict__ out) {
   __shared__ u64 sw[144][2];  // (c.x, c.x), (-c.y, c.y)
   for (int k = threadIdx.x; k < 144; k += blockDim.x) {
@@ -273,8 +283,12 @@ __global__ void __launch_bounds__(128, 4) k_smoother_apply_p2(const float2* __re
   const int half = nrhs >> 1;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= V * half) return;
-  const int64_t site = g / half;
-  const int r0 = 2 * (int)(g - site * half);
+  const int64_t per_chunk = V * rc2;
+  const int ch = (int)(g / per_chunk);
+  const int64_t rem = g - ch * per_chunk;
+  const int64_t slot = rem / rc2;
+  const int r0 = 2 * (ch * rc2 + (int)(rem - slot * rc2));
+  const int64_t site = visit ? visit[slot] : slot;
   const int64_t rs = nrhs;
   u64 acc[2][12];
 #pragma unroll
@@ -354,24 +368,43 @@ static void apply_layer(qd_ctx& ctx, const qd_mg& mg, int nrhs, const C* w, cons
     const float2* W2 = reinterpret_cast<const float2*>(w);
     const float2* xi = reinterpret_cast<const float2*>(in);
     float2* yo = reinterpret_cast<float2*>(out);
-    // candidate 0: two right-hand sides per thread; 1: the same with packed
-    // FP32 multiply-adds (bit-identical).  Accumulating launches are not
-    // timed by the tuner (they change out); they follow the plain choice.
-    auto launch = [&](int c) -> bool {
-      if (c == 0) {
-        if (accumulate)
-          k_smoother_apply_x2<true><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, yo);
+    // candidates: two right-hand sides per thread in index order (0), in the
+    // stencil visiting order with the columns swept whole (1), in chunks of
+    // 64 (2) or 32 (3), and the packed-FP32 form in the visiting order (4).
+    // All bit-identical.  Accumulating launches are not timed by the tuner
+    // (they change out): they take the choice timed on the plain form.
+    const int* vis = geo.visit.as<int>();
+    auto shape = [&](int c, int& rc, const int*& vv) -> bool {
+      rc = c == 2 ? 64 : (c == 3 ? 32 : nrhs);
+      vv = c == 0 ? nullptr : vis;
+      if (rc > nrhs || nrhs % rc != 0 || rc % 2 != 0) return false;
+      if ((c == 2 && nrhs <= 64) || (c == 3 && nrhs <= 32)) return false;
+      return true;
+    };
+    auto launch_into = [&](int c, bool acc, float2* dst) -> bool {
+      int rc;
+      const int* vv;
+      if (!shape(c, rc, vv)) return false;
+      const int h = rc / 2;
+      if (c == 4) {
+        if (acc)
+          k_smoother_apply_p2<true><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), vv, geo.nsites, nrhs, h, W2,
+                                                                     xi, dst);
         else
-          k_smoother_apply_x2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, yo);
+          k_smoother_apply_p2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), vv, geo.nsites, nrhs, h, W2,
+                                                                      xi, dst);
       } else {
-        if (accumulate)
-          k_smoother_apply_p2<true><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, yo);
+        if (acc)
+          k_smoother_apply_x2<true><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), vv, geo.nsites, nrhs, h, W2,
+                                                                     xi, dst);
         else
-          k_smoother_apply_p2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, yo);
+          k_smoother_apply_x2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), vv, geo.nsites, nrhs, h, W2,
+                                                                      xi, dst);
       }
       QD_LAUNCH_CHECK();
       return true;
     };
+    auto launch = [&](int c) -> bool { return launch_into(c, accumulate, yo); };
     const std::string key = "smoother f32 sites" + std::to_string(geo.nsites) + " rhs" + std::to_string(nrhs);
     int c = tune_lookup(key);
     if (c < 0 && tune_can_time(ctx)) {
@@ -380,19 +413,11 @@ static void apply_layer(qd_ctx& ctx, const qd_mg& mg, int nrhs, const C* w, cons
       DevBuf& scr = mg.ls->tune_scratch;
       scr.resize((size_t)tot * 12 * sizeof(C));
       float2* so = scr.as<float2>();
-      auto time_into_scratch = [&](int cc) -> bool {
-        if (cc == 0)
-          k_smoother_apply_x2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, so);
-        else
-          k_smoother_apply_p2<false><<<blocks2, 128, 0, ctx.stream>>>(L, geo.nbr.as<int>(), geo.nsites, nrhs, W2, xi, so);
-        QD_LAUNCH_CHECK();
-        return true;
-      };
-      c = tune_pick(ctx, key, 2, time_into_scratch);
+      c = tune_pick(ctx, key, 5, [&](int cc) { return launch_into(cc, false, so); });
       QD_CUDA(cudaStreamSynchronize(ctx.stream));
       scr.release();
     }
-    launch(c >= 0 ? c : 0);
+    if (c < 0 || !launch(c)) launch(1);
     return;
   }
   const int blocks = div_up(tot, 128);

@@ -174,10 +174,11 @@ def test_layered_training_builds_on_the_one_layer_fit(qd, ctx):
     g.close()
 
 
-def test_packed_fp32_smoother_is_bit_identical(qd, ctx):
-    # the FP32 smoother with packed multiply-adds (fma.rn.f32x2) computes the
-    # same multiply-adds in the same order lane by lane: the same bits, for
-    # the plain and the accumulating form and for one and two layers
+def test_fp32_smoother_launch_shapes_are_bit_identical(qd, ctx):
+    # the FP32 smoother's launch shapes: index order, the stencil visiting
+    # order with the columns whole or in chunks of 64 / 32, and packed
+    # multiply-adds (fma.rn.f32x2: lane by lane the same multiply-adds in the
+    # same order): the same bits, for one and two layers
     dims = (8, 8, 4, 4)
     U = synth.random_su3_links(dims, 0.3, 4)
     g = qd.Gauge(ctx, dims, U)
@@ -191,12 +192,13 @@ def test_packed_fp32_smoother_is_bit_identical(qd, ctx):
                 x = torch.randn((g.V, 12, s), dtype=torch.complex64, device="cuda:0",
                                 generator=torch.Generator("cuda:0").manual_seed(s))
                 outs = []
-                for cand in (0, 1):
+                for cand in range(5):
                     qd.autotune_force(cand)
                     o = torch.full_like(x, float("nan"))
                     qd.smoother_apply_f32(mg, s, x, o)
                     outs.append(o)
-                assert torch.equal(outs[0], outs[1]), (layers, s)
+                for cand in range(1, 5):
+                    assert torch.equal(outs[0], outs[cand]), (layers, s, cand)
     finally:
         qd.autotune_force(-1)
     mg.close()

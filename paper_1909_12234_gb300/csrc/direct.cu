@@ -433,21 +433,21 @@ void coarsest_solve_refined(qd_ctx& ctx, const CoarseLevel& lv, int nrhs, const 
 // or FP32.  64 x 64 output tile per CTA (256 threads, 4 x 4 per thread),
 // k-tiles of 16 staged in shared memory.
 // ---------------------------------------------------------------------------
-template <class C>
+template <class C, int BM = 64, int BN = 64>
 __global__ void __launch_bounds__(256) k_zgemm(int n, int s, const C* __restrict__ M, const C* __restrict__ X,
                                                C* __restrict__ Y) {
   typedef typename CTraits<C>::R R;
-  constexpr int BM = 64, BN = 64, BK = 16;
+  constexpr int BK = 16, TM = BM / 16, TN = BN / 16;  // 16 x 16 threads, TM x TN outputs each
   __shared__ C sa[BK][BM + 1];
   __shared__ C sb[BK][BN + 1];
   const int tid = threadIdx.x;
-  const int tr = tid / 16, tc = tid % 16;  // 16 x 16 threads, each 4 rows x 4 cols
+  const int tr = tid / 16, tc = tid % 16;
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-  C acc[4][4];
+  C acc[TM][TN];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < TM; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = mk<C>((R)0, (R)0);
+    for (int b = 0; b < TN; ++b) acc[a][b] = mk<C>((R)0, (R)0);
   for (int k0 = 0; k0 < n; k0 += BK) {
     // load M[row0 .. +64][k0 .. +16] -> sa[k][m] and X[k0 .. +16][col0 .. +64] -> sb[k][c]
     for (int e = tid; e < BM * BK; e += 256) {
@@ -463,24 +463,24 @@ __global__ void __launch_bounds__(256) k_zgemm(int n, int s, const C* __restrict
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      C a[4], b[4];
+      C a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sa[kk][tr + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = sa[kk][tr + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = sb[kk][tc + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = sb[kk][tc + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < TN; ++j) cfma(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) {
     const int gr = row0 + tr + 16 * i;
     if (gr >= n) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int gc = col0 + tc + 16 * j;
       if (gc < s) Y[(int64_t)gr * s + gc] = acc[i][j];
     }
@@ -532,6 +532,14 @@ template <class C> void dense_apply(qd_ctx& ctx, int n, int s, const C* M, const
       k_dense_small<C, 8><<<blocks, 256, 0, ctx.stream>>>(n, s, M, X, Y);
     else
       k_dense_small<C, 16><<<blocks, 256, 0, ctx.stream>>>(n, s, M, X, Y);
+    QD_LAUNCH_CHECK();
+    return;
+  }
+  if (s <= 48) {
+    // narrow blocks of right-hand sides (the eigensolver's 40): 32 x 48
+    // tiles waste less of each tile and give twice the blocks
+    dim3 grid(div_up(s, 48), div_up(n, 32));
+    k_zgemm<C, 32, 48><<<grid, 256, 0, ctx.stream>>>(n, s, M, X, Y);
     QD_LAUNCH_CHECK();
     return;
   }

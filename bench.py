@@ -332,7 +332,9 @@ def kernel_only(qd, ctx, names, reps=20):
     target): the FP32 V-cycle's level-1 stencil on tensor cores (8192 sites,
     D = 24, split pass included), the restriction fine -> level 1 on tensor
     cores, the FP32 prolongation level 1 -> fine and level 2 -> level 1, and
-    the FP32 Wilson stencil; 128 right-hand sides.  The hierarchy takes
+    the FP32 Wilson stencil (A x, the residual b - A x, and the odd-site
+    Schur complement through the parity-restricted hops); 128 right-hand
+    sides.  The hierarchy takes
     random blocked vectors (no null-vector iteration: the kernels' cost does
     not depend on W) and no dense coarsest inverse.  Algorithmic bytes as in
     the bench's per-kernel table; every field is larger than L2 except the
@@ -350,6 +352,9 @@ def kernel_only(qd, ctx, names, reps=20):
     n1, n2 = 8192 * 24, 512 * 32
     x0 = torch.randn((V * 12, s), dtype=torch.complex64, device=dev)
     y0 = torch.empty_like(x0)
+    b0 = torch.randn((V * 12, s), dtype=torch.complex64, device=dev) if "wilson_resid_f32" in names else None
+    xh = torch.randn((V // 2 * 12, s), dtype=torch.complex64, device=dev) if "schur_f32" in names else None
+    yh = torch.empty_like(xh) if xh is not None else None
     x1 = torch.randn((n1, s), dtype=torch.complex64, device=dev)
     y1 = torch.empty_like(x1)
     x2 = torch.randn((n2, s), dtype=torch.complex64, device=dev)
@@ -360,6 +365,11 @@ def kernel_only(qd, ctx, names, reps=20):
         "prolong_l1": (lambda: qd.prolongate_f32(mg, 0, s, x1, y0), 8.0 * (V * 12 * 12 + V * 12 * s + n1 * s)),
         "prolong_l2": (lambda: qd.prolongate_f32(mg, 1, s, x2, y1), 8.0 * (8192 * 24 * 16 + n1 * s + n2 * s)),
         "wilson_f32": (lambda: qd.dirac_apply_f32(ctx, g, -0.8, 0.0, False, s, x0, y0), V * (24.0 * 8 * s + 36.0 * 8)),
+        "wilson_resid_f32": (lambda: qd.dirac_residual_f32(ctx, g, -0.8, 0.0, False, s, b0, x0, y0),
+                             V * (36.0 * 8 * s + 36.0 * 8)),
+        # the entry point also allocates its half-field scratch and synchronises
+        "schur_f32": (lambda: qd.dirac_schur_apply_f32(ctx, g, -0.8, 0.0, s, xh, yh),
+                      (V // 2) * (60.0 * 8 * s + 144.0 * 8)),
         "smoother_f32": (lambda: qd.smoother_apply_f32(mg, s, x0, y0), V * (24.0 * 8 * s + 36.0 * 8)),
     }
     if "smoother_f32" in names:
@@ -1163,8 +1173,8 @@ def main():
                          "default: the workload's setting")
     ap.add_argument("--kernel", default="",
                     help="comma-separated hot kernels timed alone on the 16^3 x 32 shapes (a profiling target): "
-                         "coarse_tc, restrict_tc, prolong_l1, prolong_l2, wilson_f32, smoother_f32; 'all' for "
-                         "every one")
+                         "coarse_tc, restrict_tc, prolong_l1, prolong_l2, wilson_f32, wilson_resid_f32, schur_f32, "
+                         "smoother_f32; 'all' for every one")
     ap.add_argument("--reps", type=int, default=20, help="launches timed per kernel with --kernel")
     ap.add_argument("--no-tune", action="store_true",
                     help="launch shapes fixed at their defaults (nothing timed by the autotuner)")
@@ -1179,7 +1189,8 @@ def main():
         from paper_1909_12234_gb300 import qdtrace as qd
         qd.load()
         ctx = qd.Context(0)
-        names = (["coarse_tc", "restrict_tc", "prolong_l1", "prolong_l2", "wilson_f32", "smoother_f32"]
+        names = (["coarse_tc", "restrict_tc", "prolong_l1", "prolong_l2", "wilson_f32", "wilson_resid_f32",
+                  "schur_f32", "smoother_f32"]
                  if args.kernel == "all"
                  else args.kernel.split(","))
         if args.candidate >= 0:

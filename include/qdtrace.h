@@ -150,6 +150,17 @@ int qd_dirac_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau,
 int qd_dirac_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau,
                        int dagger, int nrhs, const float* in, float* out);
 
+/* r = b - A x (or b - A^H x) in FP32, the residual form of the same
+ * stencil (the subtraction in the kernel's epilogue, as the mixed-precision
+ * inner solves use it).  b, x, r: interleaved complex float in qd layout;
+ * r must not overlap b or x.  A bounded wait of the bulk-staged form of the
+ * FP32 stencil that gives up is reported as QD_ERR_TIMEOUT by the next
+ * synchronising call on the gauge (qd_dirac_schur_apply_f32, qd_solve,
+ * qd_hutchinson_trace).  Asynchronous. */
+int qd_dirac_residual_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau,
+                          int dagger, int nrhs, const float* b,
+                          const float* x, float* r);
+
 /* out = S in with S = A_oo - A_oe A_ee^{-1} A_eo, the Schur complement of A
  * on the odd sites (the even-odd solves of Sec. 4; qd_solver_params.schur).
  * in/out: half fields of the odd sites, (site - V/2, 12, nrhs) for the odd

@@ -185,6 +185,25 @@ int qd_dirac_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau, int 
   });
 }
 
+int qd_dirac_residual_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau, int dagger, int nrhs, const float* b,
+                          const float* x, float* r) {
+  return guarded([&] {
+    NONNULL(ctx);
+    NONNULL(gauge);
+    NONNULL(b);
+    NONNULL(x);
+    NONNULL(r);
+    QD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    const size_t bytes = (size_t)gauge->geo.nsites * 12 * nrhs * sizeof(qd::cplxf);
+    QD_REQUIRE(!overlaps(r, x, bytes) && !overlaps(r, b, bytes), "r must not overlap b or x");
+    QD_REQUIRE(std::isfinite(m0) && std::isfinite(tau), "m0 and tau must be finite");
+    set_device(ctx);
+    qd::wilson_apply<qd::cplxf>(*ctx, gauge->geo, gauge->links_f32(), m0, tau, dagger != 0,
+                                reinterpret_cast<const qd::cplxf*>(x), reinterpret_cast<qd::cplxf*>(r), nrhs,
+                                reinterpret_cast<const qd::cplxf*>(b));
+  });
+}
+
 int qd_dirac_schur_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau, int nrhs, const double* in,
                          double* out) {
   return guarded([&] {
@@ -216,6 +235,8 @@ int qd_dirac_schur_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau
     qd::SchurOp<qd::cplxf> S(gauge, gauge->links_f32(), m0, tau);
     S.apply(*ctx, reinterpret_cast<const qd::cplxf*>(in), reinterpret_cast<qd::cplxf*>(out), nrhs);
     QD_CUDA(cudaStreamSynchronize(ctx->stream));  // S's scratch is released on return
+    const int e = qd::wilson_bulk_error(*ctx, gauge->geo);
+    if (e) qd::fail(QD_ERR_TIMEOUT, "FP32 Wilson stencil: bounded wait timed out (code " + std::to_string(e) + ")");
   });
 }
 

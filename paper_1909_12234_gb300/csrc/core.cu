@@ -78,6 +78,8 @@ void LevelGeom::build(const int d[4], bool even_odd) {
       QD_CUDA(cudaMemcpy(visit_par[par].as<int>(), vp.data(), vp.size() * sizeof(int), cudaMemcpyHostToDevice));
     }
   }
+  bulk_err.resize(sizeof(int));
+  QD_CUDA(cudaMemset(bulk_err.as<int>(), 0, sizeof(int)));
   nbr.resize(V * 8 * sizeof(int));
   lex_of_site.resize(V * sizeof(int));
   site_of_lex.resize(V * sizeof(int));

@@ -85,6 +85,8 @@ struct LevelGeom {
   // lattices): visit_par[p] holds nsites/2 site indices, all in
   // [p nsites/2, (p+1) nsites/2).
   DevBuf visit_par[2];
+  // int, 0 until a bounded wait of the bulk-staged FP32 stencil gives up
+  mutable DevBuf bulk_err;
   void build(const int d[4], bool even_odd);
   void coords(int64_t lex, int c[4]) const {
     c[0] = (int)(lex % dims[0]);
@@ -172,6 +174,9 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
 template <class C>
 void wilson_eo(qd_ctx& ctx, const LevelGeom& geo, const C* links, int p, const cplx q1[2], const cplx q2[2],
                const C* in, const C* z, C* out, int nrhs);
+// Nonzero when a bounded wait of the bulk-staged FP32 stencil gave up on
+// this geometry (synchronises the stream).
+int wilson_bulk_error(qd_ctx& ctx, const LevelGeom& geo);
 // out = Q in on a half field of nh sites.
 template <class C>
 void spin_diag(qd_ctx& ctx, int64_t nh, int nrhs, const cplx q[2], const C* in, C* out);

@@ -116,6 +116,10 @@ static void solve_mixed(qd_ctx& ctx, const qd_gauge& g, qd_mg* mg, double m0, do
     blas::dots(ctx, 1, n, s, r, 0, r, 0, rn2);
     if (info.stagnated) break;
   }
+  {
+    const int e = wilson_bulk_error(ctx, g.geo);
+    if (e) fail(QD_ERR_TIMEOUT, "FP32 Wilson stencil: bounded wait timed out (code " + std::to_string(e) + ")");
+  }
   if (mg && mg->L.back()->tc) {
     const int e = tc_error(ctx, *mg->L.back());
     if (e) fail(QD_ERR_TIMEOUT, "tensor-core coarsest solve: bounded wait timed out (code " + std::to_string(e) + ")");

@@ -14,6 +14,9 @@
 // instead of 4.
 #include <string>
 
+#include <type_traits>
+
+#include "ptx.cuh"
 #include "qd_internal.cuh"
 #include "tune.cuh"
 
@@ -491,6 +494,347 @@ __global__ void __launch_bounds__(128, 4) k_wilson_eo_f32x2(const float2* __rest
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 stencil with its operands staged in shared memory by bulk copies
+// (cp.async.bulk, completion counted on an mbarrier).  A warp computes one
+// site for a chunk of 64 columns at a time, lane l owning columns 2l and
+// 2l + 1 of the chunk.  The site's operand chunks -- the eight neighbour
+// spinors in hop order (mu = 0..3, forward then backward), then its own
+// input (full lattice) or z (parity-restricted form), then b (residual
+// form), each 12 rows of 512 contiguous bytes -- stream through a ring of NS
+// slots per warp: once a slot has been read into registers, the warp refills
+// it with the chunk NS positions ahead, so that NS x 6 KB of loads per warp
+// stay in flight without holding registers.  The links of the next site are
+// copied into a double buffer with cp.async while the current site
+// computes; the neighbour indices are looked up two sites ahead and the
+// visiting order three.  The arithmetic per element is that of
+// k_wilson_f32x2 and k_wilson_eo_f32x2 (the same hop2 and epilogue).  Every
+// wait is bounded: on a timeout the warp records it in *err, waits (bounded)
+// for its own copies in flight and returns.
+// ---------------------------------------------------------------------------
+constexpr int kBulkCols = 64;
+constexpr uint32_t kBulkRow = kBulkCols * 8;    // one spin-colour row of a chunk: 512 B
+constexpr uint32_t kBulkChunk = 12 * kBulkRow;  // 6144 B
+
+struct BulkArgs {
+  const float2* U;
+  const int* nbr;
+  const int* visit;
+  int64_t V;        // sites of the full lattice (the link stride)
+  int64_t nslots;   // sites in the visiting order (V, or V/2 for one parity)
+  int nrhs;
+  int64_t in_off;   // first site of the input field (0, or (1 - p) V/2)
+  int64_t own_off;  // first site of z and out (0, or p V/2)
+  float mass, tau;  // full lattice: 4 + m0, tau
+  EoCoef q;         // parity-restricted: Q1, Q2
+  const float2* in;
+  const float2* aux;  // b (residual form) or z (parity-restricted; null: none)
+  float2* out;
+  int* err;
+};
+
+// MODE 0: out = A in (A^H with DAG); 1: out = b - A in; 2: out = Q2 (H in)
+// on one parity; 3: out = Q1 z + Q2 (H in).
+template <int MODE>
+struct BulkMode {
+  static constexpr bool eo = MODE >= 2;
+  static constexpr bool own = MODE != 2;
+  static constexpr bool resid = MODE == 1;
+  static constexpr int cps = 8 + (own ? 1 : 0) + (resid ? 1 : 0);  // chunks per site
+};
+
+template <int NW, int NS>
+constexpr size_t bulk_smem_bytes() {
+  return (size_t)NW * NS * kBulkChunk + (size_t)NW * 144 * sizeof(float2) + (size_t)NW * NS * 8 + 16;
+}
+
+// Lane k < cps of a warp holds the source of chunk k of a site (and, for a
+// hop, its link); dst is the site's output chunk (the same in every lane).
+struct BulkAddr {
+  const float2* src;
+  const float2* lnk;
+  float2* dst;
+};
+
+__device__ __forceinline__ int bulk_visit(const BulkArgs& a, bool valid, int64_t u) {
+  if (!valid) return 0;
+  const int64_t ch = u / a.nslots;
+  return a.visit[u - ch * a.nslots];
+}
+
+// The lookups of a site: lane k < 8 loads the neighbour of hop k.  Its
+// value is first used when the record is turned into addresses (bulk_cook),
+// one site later, so the load does not stall the warp.
+struct BulkRaw {
+  int nb;
+  int site;
+  int64_t r0;
+  bool valid;
+};
+
+__device__ __forceinline__ BulkRaw bulk_raw(const BulkArgs& a, bool valid, int64_t u, int site, int lane) {
+  BulkRaw w{0, site, 0, valid};
+  if (!valid) return w;
+  w.r0 = (u / a.nslots) * kBulkCols;
+  if (lane < 8) w.nb = a.nbr[(int64_t)site * 8 + ((lane & 1) ? 4 + (lane >> 1) : (lane >> 1))];
+  return w;
+}
+
+template <int MODE>
+__device__ __forceinline__ BulkAddr bulk_cook(const BulkArgs& a, const BulkRaw& w, int lane) {
+  using M = BulkMode<MODE>;
+  BulkAddr o{nullptr, nullptr, nullptr};
+  if (!w.valid) return o;
+  const int64_t rs = a.nrhs;
+  o.dst = a.out + ((int64_t)w.site - a.own_off) * 12 * rs + w.r0;
+  if (lane < 8) {
+    const int mu = lane >> 1;
+    const bool fwd = (lane & 1) == 0;
+    o.src = a.in + ((int64_t)w.nb - a.in_off) * 12 * rs + w.r0;
+    o.lnk = a.U + ((int64_t)mu * a.V + (fwd ? w.site : w.nb)) * 9;
+  } else if (M::own && lane == 8) {
+    o.src = (M::eo ? a.aux : a.in) + ((int64_t)w.site - a.own_off) * 12 * rs + w.r0;
+  } else if (M::resid && lane == 9) {
+    o.src = a.aux + (int64_t)w.site * 12 * rs + w.r0;
+  }
+  return o;
+}
+
+template <class P>
+__device__ __forceinline__ P* shfl_ptr(P* p, int src_lane) {
+  return reinterpret_cast<P*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(p), src_lane));
+}
+
+// The 12 rows of one chunk into a ring slot (all lanes of the warp call it).
+__device__ __forceinline__ void bulk_issue(uint32_t slot, uint32_t bar, const float2* src, int64_t rs, int lane) {
+  if (lane == 0) ptx::mbar_expect_tx(bar, kBulkChunk);
+  __syncwarp();
+  if (lane < 12) ptx::bulk_g2s(slot + lane * kBulkRow, src + lane * rs, kBulkRow, bar);
+}
+
+// The eight links of a site (72 float2, 8-byte aligned) into dst with
+// cp.async; lane k < 8 holds the address of link k.  One commit group.
+__device__ __forceinline__ void bulk_links(float2* dst, const float2* lnk, int lane) {
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    const int e = lane + 32 * it;
+    const int h = e < 72 ? e / 9 : 7;
+    const float2* L = shfl_ptr(lnk, h);
+    if (e < 72) {
+      const uint32_t d = ptx::smem_u32(dst + e);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(L + (e - 9 * h)) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <bool DAG, int MODE, int NW, int NS>
+__global__ void __launch_bounds__(NW * 32, 1) k_wilson_bulk(const BulkArgs a) {
+  using M = BulkMode<MODE>;
+  constexpr int CPS = M::cps;
+  static_assert(NS >= 1 && NS <= 8, "a refill must land at most one site ahead");
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t ring_bytes = (size_t)NW * NS * kBulkChunk, link_bytes = (size_t)NW * 144 * sizeof(float2);
+  unsigned char* ring = smem + (size_t)warp * NS * kBulkChunk;
+  float2* lbuf = reinterpret_cast<float2*>(smem + ring_bytes) + warp * 144;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ring_bytes + link_bytes) + warp * NS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + ring_bytes + link_bytes + (size_t)NW * NS * 8);
+  if (threadIdx.x == 0) *abort_flag = 0;
+  if (lane == 0)
+    for (int s = 0; s < NS; ++s) ptx::mbar_init(ptx::smem_u32(bars + s), 1);
+  ptx::mbar_init_fence();
+  __syncthreads();
+
+  const int64_t rs = a.nrhs;
+  const int64_t total = a.nslots * (a.nrhs / kBulkCols);
+  const int64_t GW = (int64_t)gridDim.x * NW;
+  const int64_t gw = (int64_t)blockIdx.x * NW + warp;
+  const int64_t nw = gw < total ? (total - 1 - gw) / GW + 1 : 0;  // sites of this warp: units gw + i GW
+  if (nw == 0) return;
+  const uint32_t ring_a = ptx::smem_u32(ring), bar_a = ptx::smem_u32(bars);
+
+  // cur: site i, na: site i + 1 (addresses); nb: site i + 2 (lookups); vs:
+  // the visiting order of site i + 3
+  BulkAddr cur = bulk_cook<MODE>(a, bulk_raw(a, true, gw, bulk_visit(a, true, gw), lane), lane);
+  BulkAddr na = bulk_cook<MODE>(a, bulk_raw(a, 1 < nw, gw + GW, bulk_visit(a, 1 < nw, gw + GW), lane), lane);
+  BulkRaw nb = bulk_raw(a, 2 < nw, gw + 2 * GW, bulk_visit(a, 2 < nw, gw + 2 * GW), lane);
+  int vs = bulk_visit(a, 3 < nw, gw + 3 * GW);
+  bulk_links(lbuf, cur.lnk, lane);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) bulk_issue(ring_a + k * kBulkChunk, bar_a + 8 * k, shfl_ptr(cur.src, k), rs, lane);
+
+  int slot = 0;
+  uint32_t ph = 0;
+  int64_t consumed = 0, issued = NS;  // positions in the warp's sequence of chunks
+  bool ok = true;
+  const float te = DAG ? -a.tau : a.tau;
+  const float2 mup = make_float2(a.mass, te), mlo = make_float2(a.mass, -te);
+  const float2 q1u = make_float2((float)a.q.q1[0].x, (float)a.q.q1[0].y);
+  const float2 q1l = make_float2((float)a.q.q1[1].x, (float)a.q.q1[1].y);
+  const float2 q2u = make_float2((float)a.q.q2[0].x, (float)a.q.q2[0].y);
+  const float2 q2l = make_float2((float)a.q.q2[1].x, (float)a.q.q2[1].y);
+
+  for (int64_t i = 0; i < nw && ok; ++i) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();  // the links of site i are in lbuf[i & 1] for the whole warp
+    const float2* L = lbuf + (i & 1) * 72;
+    if (i + 1 < nw) bulk_links(lbuf + ((i + 1) & 1) * 72, na.lnk, lane);
+    float2 hu[2][6], hl[2][6];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) { hu[j][k] = make_float2(0.f, 0.f); hl[j][k] = make_float2(0.f, 0.f); }
+
+    auto step = [&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      if constexpr (K < CPS) {
+        if (!ok) return;
+        const bool got = ptx::mbar_wait(bar_a + 8 * slot, ph, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          return;
+        }
+        ++consumed;
+        const float4* S = reinterpret_cast<const float4*>(ring + (size_t)slot * kBulkChunk) + lane;
+        float4 q[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) q[c] = S[c * 32];
+        __syncwarp();
+        // the slot takes the chunk NS positions ahead: this site's, or the next one's
+        constexpr int KN = K + NS;
+        const float2* nsrc;
+        if constexpr (KN < CPS) nsrc = shfl_ptr(cur.src, KN);
+        else nsrc = shfl_ptr(na.src, KN - CPS);
+        if (KN < CPS || i + 1 < nw) {
+          ptx::fence_proxy_async_smem();
+          bulk_issue(ring_a + slot * kBulkChunk, bar_a + 8 * slot, nsrc, rs, lane);
+          ++issued;
+        }
+        if (++slot == NS) {
+          slot = 0;
+          ph ^= 1u;
+        }
+        if constexpr (K < 8) hop2<K / 2, (K % 2) == 0, DAG>(L + K * 9, q, hu, hl);
+        if constexpr (MODE == 2 && K == 7) {  // Q2 (H in)
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            const float2 qa = c < 6 ? q2u : q2l;
+            const float2 v0 = cmul(qa, c < 6 ? hu[0][c] : hl[0][c - 6]);
+            const float2 v1 = cmul(qa, c < 6 ? hu[1][c] : hl[1][c - 6]);
+            reinterpret_cast<float4*>(cur.dst + c * rs)[lane] = make_float4(v0.x, v0.y, v1.x, v1.y);
+          }
+        }
+        if constexpr (MODE == 3 && K == 8) {  // Q2 (H in) + Q1 z
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            const float2 qa = c < 6 ? q2u : q2l, qb = c < 6 ? q1u : q1l;
+            float2 v0 = cmul(qa, c < 6 ? hu[0][c] : hl[0][c - 6]);
+            float2 v1 = cmul(qa, c < 6 ? hu[1][c] : hl[1][c - 6]);
+            v0 = cadd(v0, cmul(qb, make_float2(q[c].x, q[c].y)));
+            v1 = cadd(v1, cmul(qb, make_float2(q[c].z, q[c].w)));
+            reinterpret_cast<float4*>(cur.dst + c * rs)[lane] = make_float4(v0.x, v0.y, v1.x, v1.y);
+          }
+        }
+        if constexpr (MODE <= 1 && K == 8) {  // (4 + m0 + i tau gamma5) in - H in / 2
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            const float2 m = c < 6 ? mup : mlo;
+            float2 v0 = cmul(m, make_float2(q[c].x, q[c].y));
+            float2 v1 = cmul(m, make_float2(q[c].z, q[c].w));
+            float2& h0 = c < 6 ? hu[0][c] : hl[0][c - 6];
+            float2& h1 = c < 6 ? hu[1][c] : hl[1][c - 6];
+            v0.x = fmaf(-0.5f, h0.x, v0.x);
+            v0.y = fmaf(-0.5f, h0.y, v0.y);
+            v1.x = fmaf(-0.5f, h1.x, v1.x);
+            v1.y = fmaf(-0.5f, h1.y, v1.y);
+            if constexpr (MODE == 1) {
+              h0 = v0;
+              h1 = v1;
+            } else {
+              __stcs(reinterpret_cast<float4*>(cur.dst + c * rs) + lane, make_float4(v0.x, v0.y, v1.x, v1.y));
+            }
+          }
+        }
+        if constexpr (MODE == 1 && K == 9) {  // b - A in
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            const float2 v0 = c < 6 ? hu[0][c] : hl[0][c - 6];
+            const float2 v1 = c < 6 ? hu[1][c] : hl[1][c - 6];
+            __stcs(reinterpret_cast<float4*>(cur.dst + c * rs) + lane,
+                   make_float4(q[c].x - v0.x, q[c].y - v0.y, q[c].z - v1.x, q[c].w - v1.y));
+          }
+        }
+      }
+    };
+    step(std::integral_constant<int, 0>{});
+    step(std::integral_constant<int, 1>{});
+    step(std::integral_constant<int, 2>{});
+    step(std::integral_constant<int, 3>{});
+    step(std::integral_constant<int, 4>{});
+    step(std::integral_constant<int, 5>{});
+    step(std::integral_constant<int, 6>{});
+    step(std::integral_constant<int, 7>{});
+    step(std::integral_constant<int, 8>{});
+    step(std::integral_constant<int, 9>{});
+    cur = na;
+    na = bulk_cook<MODE>(a, nb, lane);
+    nb = bulk_raw(a, i + 3 < nw, gw + (i + 3) * GW, vs, lane);
+    vs = bulk_visit(a, i + 4 < nw, gw + (i + 4) * GW);
+  }
+  if (!ok) {
+    if (lane == 0) {
+      atomicExch(a.err, 1);
+      *abort_flag = 1;
+    }
+    // the copies this warp still has in flight land before it leaves
+    int never = 0;
+    for (int64_t j = consumed; j < issued; ++j)
+      (void)ptx::mbar_wait(bar_a + 8 * (uint32_t)(j % NS), (uint32_t)((j / NS) & 1), &never);
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Launch of k_wilson_bulk: NW warps per CTA, NS ring slots per warp, one
+// CTA per SM (persistent).  false when the shape does not apply (nrhs not a
+// multiple of 64, fields not 16-byte aligned).
+template <bool DAG, int MODE, int NW, int NS>
+bool launch_bulk(qd_ctx& ctx, const BulkArgs& a) {
+  if (a.nrhs % kBulkCols != 0) return false;
+  if (((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.aux) | reinterpret_cast<uintptr_t>(a.out)) &
+       15) != 0)
+    return false;
+  const int64_t total = a.nslots * (a.nrhs / kBulkCols);
+  if (total == 0) return true;
+  constexpr size_t smem = bulk_smem_bytes<NW, NS>();
+  static_assert(smem <= 227 * 1024, "shared memory per CTA");
+  auto kern = k_wilson_bulk<DAG, MODE, NW, NS>;
+  ensure_smem_limit(reinterpret_cast<const void*>(kern), smem);
+  const int blocks = (int)std::min<int64_t>(div_up(total, NW), kNumSMs);
+  kern<<<blocks, NW * 32, smem, ctx.stream>>>(a);
+  QD_LAUNCH_CHECK();
+  return true;
+}
+
+// The ring shapes the tuner tries: (warps, slots) = (8, 4), (4, 8), (6, 5),
+// 192 KB, 192 KB and 180 KB of loads in flight per SM.
+template <bool DAG, int MODE>
+bool launch_bulk_shape(qd_ctx& ctx, const BulkArgs& a, int shape) {
+  switch (shape) {
+    case 0: return launch_bulk<DAG, MODE, 8, 4>(ctx, a);
+    case 1: return launch_bulk<DAG, MODE, 4, 8>(ctx, a);
+    default: return launch_bulk<DAG, MODE, 6, 5>(ctx, a);
+  }
+}
+
+int wilson_bulk_error(qd_ctx& ctx, const LevelGeom& geo) {
+  if (geo.bulk_err.bytes() == 0) return 0;
+  int h = 0;
+  QD_CUDA(cudaMemcpyAsync(&h, geo.bulk_err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  QD_CUDA(cudaStreamSynchronize(ctx.stream));
+  return h;
+}
+
 template <class C>
 void wilson_eo(qd_ctx& ctx, const LevelGeom& geo, const C* links, int p, const cplx q1[2], const cplx q2[2],
                const C* in, const C* z, C* out, int nrhs) {
@@ -525,10 +869,31 @@ void wilson_eo(qd_ctx& ctx, const LevelGeom& geo, const C* links, int p, const c
       QD_LAUNCH_CHECK();
       return true;
     };
+    // candidates 4-6: operands staged by bulk copies (k_wilson_bulk), ring
+    // shapes 0-2; nrhs a multiple of 64
+    auto launch_any = [&](int c) -> bool {
+      if (c < 4) return launch(c);
+      BulkArgs a{};
+      a.U = reinterpret_cast<const float2*>(links);
+      a.nbr = nb;
+      a.visit = vis;
+      a.V = geo.nsites;
+      a.nslots = Vh;
+      a.nrhs = nrhs;
+      a.in_off = (int64_t)(1 - p) * Vh;
+      a.own_off = (int64_t)p * Vh;
+      a.q = q;
+      a.in = reinterpret_cast<const float2*>(in);
+      a.aux = reinterpret_cast<const float2*>(z);
+      a.out = reinterpret_cast<float2*>(out);
+      a.err = geo.bulk_err.as<int>();
+      return z ? launch_bulk_shape<false, 3>(ctx, a, c - 4) : launch_bulk_shape<false, 2>(ctx, a, c - 4);
+    };
     // out-of-place (out differs from in and z): safe to time
     const std::string key = "wilson eo f32 sites" + std::to_string(geo.nsites) + " rhs" + std::to_string(nrhs) +
                             (z ? " z" : "");
-    const int c = (out == in || out == z) ? -1 : tune_pick(ctx, key, 4, launch);
+    const int c = (out == in || out == z) ? -1 : tune_pick(ctx, key, 7, launch_any);
+    if (c >= 4 && launch_any(c)) return;
     if (c < 0 || !launch(c)) launch(0);
     return;
   } else {
@@ -646,8 +1011,29 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
     launch_x1();
     return;
   }
+  // candidates 10-12: operands staged by bulk copies (k_wilson_bulk), ring
+  // shapes 0-2; FP32, nrhs a multiple of 64, 16-byte aligned fields
+  auto launch_bulk_c = [&](int shape) -> bool {
+    if (sizeof(C) != 8) return false;
+    BulkArgs a{};
+    a.U = reinterpret_cast<const float2*>(links);
+    a.nbr = nb;
+    a.visit = vis;
+    a.V = geo.nsites;
+    a.nslots = geo.nsites;
+    a.nrhs = nrhs;
+    a.mass = (float)mass;
+    a.tau = (float)tau;
+    a.in = reinterpret_cast<const float2*>(in);
+    a.aux = reinterpret_cast<const float2*>(b);
+    a.out = reinterpret_cast<float2*>(out);
+    a.err = geo.bulk_err.as<int>();
+    if (b) return dagger ? launch_bulk_shape<true, 1>(ctx, a, shape) : launch_bulk_shape<false, 1>(ctx, a, shape);
+    return dagger ? launch_bulk_shape<true, 0>(ctx, a, shape) : launch_bulk_shape<false, 0>(ctx, a, shape);
+  };
   auto launch = [&](int c) -> bool {
     switch (c) {
+      case 10: case 11: case 12: return launch_bulk_c(c - 10);
       case 0: return launch_x2(0, 128);
       case 1: return launch_x1();
       case 2: return nrhs > 64 && launch_x2(64, 128);
@@ -663,7 +1049,7 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
   // the residual form writes out = b - A in: out-of-place, safe to repeat
   const std::string key = std::string("wilson f32 sites") + std::to_string(geo.nsites) + " rhs" +
                           std::to_string(nrhs) + (b ? " resid" : "") + (dagger ? " dag" : "");
-  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 10, launch);
+  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 13, launch);
   if (c >= 0 && launch(c)) return;
   if (!launch_x2(0, 128)) launch_x1();
 }

@@ -158,6 +158,7 @@ SIGNATURES = {
     "qd_rademacher": (_I, [_P, _P, ctypes.c_uint64, ctypes.c_int64, _I, _P]),
     "qd_dirac_apply": (_I, [_P, _P, _D, _D, _I, _I, _P, _P]),
     "qd_dirac_apply_f32": (_I, [_P, _P, _D, _D, _I, _I, _P, _P]),
+    "qd_dirac_residual_f32": (_I, [_P, _P, _D, _D, _I, _I, _P, _P, _P]),
     "qd_dirac_schur_apply": (_I, [_P, _P, _D, _D, _I, _P, _P]),
     "qd_dirac_schur_apply_f32": (_I, [_P, _P, _D, _D, _I, _P, _P]),
     "qd_mg_params_default": (None, [ctypes.POINTER(MGParams)]),
@@ -371,6 +372,12 @@ def dirac_apply_f32(ctx, gauge, m0, tau, dagger, nrhs, inp, out):
     """FP32 operator on torch.complex64 fields in qd layout."""
     _check(load().qd_dirac_apply_f32(ctx.h, gauge.h, float(m0), float(tau), 1 if dagger else 0, int(nrhs),
                                      _ptr64(inp), _ptr64(out)))
+
+
+def dirac_residual_f32(ctx, gauge, m0, tau, dagger, nrhs, b, x, r):
+    """r = b - A x (A^H with dagger) in FP32, torch.complex64 fields in qd layout."""
+    _check(load().qd_dirac_residual_f32(ctx.h, gauge.h, float(m0), float(tau), 1 if dagger else 0, int(nrhs),
+                                        _ptr64(b), _ptr64(x), _ptr64(r)))
 
 
 def dirac_schur_apply(ctx, gauge, m0, tau, nrhs, inp, out):

@@ -104,6 +104,48 @@ def test_wilson_fp32_matches_oracle(qd, ctx, dims, s, tau, dag):
     assert rel_err(got[..., cols], ref) < 1e-5
 
 
+@pytest.mark.parametrize("dims,s", [((4, 4, 4, 4), 64), ((8, 8, 8, 8), 64), ((8, 4, 6, 2), 128),
+                                    ((6, 6, 6, 6), 128)])
+@pytest.mark.parametrize("tau,dag", [(0.0, False), (0.25, True)])
+def test_wilson_fp32_bulk_staged_matches_oracle(qd, ctx, dims, s, tau, dag):
+    # the stencil with its operands staged in shared memory by bulk copies
+    # (launch shapes 10-12: rings of 8 warps x 4 slots, 4 x 8 and 6 x 5; one
+    # to seven sites per warp here, the last round of sites ragged), as
+    # A x and as the residual b - A x, against the oracle (tolerance as
+    # above); every output element written (NaN-filled outputs) and equal to
+    # the register-only form to FP32 rounding
+    U = synth.random_su3_links(dims, 0.2, 4)
+    g = qd.Gauge(ctx, dims, U)
+    x = synth.random_field(dims, s, 3)
+    b = synth.random_field(dims, s, 5)
+    xin = qd.to_qd(ctx, g, x).to(torch.complex64)
+    bin_ = qd.to_qd(ctx, g, b).to(torch.complex64)
+    cols = [0, s // 2 + 1, s - 1]
+    ref = wilson.dirac_apply(U, x[..., cols], -0.8, dims, tau=tau, dagger=dag)
+    refr = b[..., cols] - ref
+    try:
+        qd.autotune_force(0)
+        y0 = torch.empty_like(xin)
+        qd.dirac_apply_f32(ctx, g, -0.8, tau, dag, s, xin, y0)
+        r0 = torch.empty_like(xin)
+        qd.dirac_residual_f32(ctx, g, -0.8, tau, dag, s, bin_, xin, r0)
+        for cand in (10, 11, 12):
+            qd.autotune_force(cand)
+            y = torch.full_like(xin, float("nan"))
+            qd.dirac_apply_f32(ctx, g, -0.8, tau, dag, s, xin, y)
+            got = qd.from_qd(ctx, g, y.to(torch.complex128))
+            assert rel_err(got[..., cols], ref) < 1e-5, cand
+            assert rel_err(host(y), host(y0)) < 1e-6, cand
+            r = torch.full_like(xin, float("nan"))
+            qd.dirac_residual_f32(ctx, g, -0.8, tau, dag, s, bin_, xin, r)
+            gotr = qd.from_qd(ctx, g, r.to(torch.complex128))
+            assert rel_err(gotr[..., cols], refr) < 1e-5, cand
+            assert rel_err(host(r), host(r0)) < 1e-6, cand
+    finally:
+        qd.autotune_force(-1)
+    g.close()
+
+
 def test_gamma5_hermiticity_on_gpu(qd, ctx):
     dims = (4, 4, 4, 4)
     U = synth.random_su3_links(dims, 0.3, 6)

@@ -214,12 +214,9 @@ __device__ __forceinline__ void su3mul_r(const float2 l[9], const float2 x[3], f
 // (1 + sig gamma_mu), sig = -s forward and +s backward: h = lo + sig B^H up,
 // then lower += U h and upper += sig B (U h).
 template <int MU, bool FWD, bool DAG>
-__device__ __forceinline__ void hop2(const float2* __restrict__ L, const float4* __restrict__ q,
-                                     float2 hu[2][6], float2 hl[2][6]) {
+__device__ __forceinline__ void hop2l(const float2 l[9], const float4* __restrict__ q, float2 hu[2][6],
+                                      float2 hl[2][6]) {
   constexpr bool plus = (FWD == DAG);  // sig = +1 forward with DAG, backward without
-  float2 l[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) l[k] = L[k];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     float2 h0[3], h1[3];
@@ -248,6 +245,16 @@ __device__ __forceinline__ void hop2(const float2* __restrict__ L, const float4*
       else      { hu[j][c] = csub(hu[j][c], b0); hu[j][3 + c] = csub(hu[j][3 + c], b1); }
     }
   }
+}
+
+// The same with the link read from L (the link of the hop).
+template <int MU, bool FWD, bool DAG>
+__device__ __forceinline__ void hop2(const float2* __restrict__ L, const float4* __restrict__ q,
+                                     float2 hu[2][6], float2 hl[2][6]) {
+  float2 l[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) l[k] = L[k];
+  hop2l<MU, FWD, DAG>(l, q, hu, hl);
 }
 
 // The same hop with the neighbour spinor projected as it is loaded: only
@@ -492,6 +499,171 @@ __global__ void __launch_bounds__(128, 4) k_wilson_eo_f32x2(const float2* __rest
     }
     *reinterpret_cast<float4*>(y + k * rs) = make_float4(v0.x, v0.y, v1.x, v1.y);
   }
+}
+
+// ---------------------------------------------------------------------------
+// FP32, two right-hand sides per thread, with the next hop's neighbour
+// spinor copied into shared memory (cp.async, 12 x 16 bytes per thread) while
+// the current hop computes, and the next hop's link loaded into registers
+// likewise: each thread keeps one hop's loads in flight behind its
+// arithmetic instead of waiting for them at the start of every hop.  Two
+// stages of 12 x 16 bytes per thread (48 KB per 128-thread block, four
+// blocks per SM).  After the eight hops the stages take the site's own input
+// (full lattice) or z, then b (residual form).  MODE as k_wilson_bulk; the
+// thread-to-(site, column pair) map, the sums and the epilogue are those of
+// k_wilson_f32x2 / k_wilson_eo_f32x2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cpa16(float4* dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(ptx::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+constexpr int kCpThreads = 128;
+constexpr size_t kCpSmem = 2 * 12 * kCpThreads * sizeof(float4);  // 48 KB
+
+template <bool DAG, int MODE>
+__global__ void __launch_bounds__(kCpThreads, 4) k_wilson_cp(const float2* __restrict__ U, const int* __restrict__ nbr,
+                                                        const int* __restrict__ visit, int64_t V, int nrhs, int rc2,
+                                                        float mass, float tau, EoCoef q, int p,
+                                                        const float2* __restrict__ in,
+                                                        const float2* __restrict__ aux, float2* __restrict__ out) {
+  constexpr bool eo = MODE >= 2;
+  extern __shared__ float4 cp_stage[];  // [2][12][kCpThreads]
+  const int half = nrhs >> 1;
+  const int64_t nslots = eo ? V / 2 : V;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= nslots * half) return;
+  const int64_t per_chunk = nslots * rc2;
+  const int ch = (int)(g / per_chunk);
+  const int64_t rem = g - ch * per_chunk;
+  const int64_t slot = rem / rc2;
+  const int r0 = 2 * (ch * rc2 + (int)(rem - slot * rc2));
+  const int64_t site = visit[slot];
+  const int64_t rs = nrhs;
+  const int64_t in_off = eo ? (int64_t)(1 - p) * (V / 2) : 0, own = eo ? site - (int64_t)p * (V / 2) : site;
+  int nb8[8];
+#pragma unroll
+  for (int h = 0; h < 8; ++h) nb8[h] = nbr[site * 8 + h];
+  float4* st = cp_stage + threadIdx.x;
+  // operand h: hop h (mu = h / 2, forward when h is even), 8: the site's own
+  // input (full lattice) or z, 9: b
+  auto src = [&](int h) -> const float2* {
+    if (h < 8) return in + ((int64_t)nb8[(h & 1) ? 4 + (h >> 1) : (h >> 1)] - in_off) * 12 * rs + r0;
+    if (h == 8) return (eo ? aux : in) + own * 12 * rs + r0;
+    return aux + site * 12 * rs + r0;
+  };
+  auto issue = [&](int j, const float2* ptr) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) cpa16(st + (j * 12 + k) * kCpThreads, ptr + k * rs);
+    cpa_commit();
+  };
+  auto load_link = [&](int h, float2 l[9]) {
+    const int mu = h >> 1;
+    const float2* L = U + ((int64_t)mu * V + ((h & 1) ? (int64_t)nb8[4 + mu] : site)) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) l[k] = L[k];
+  };
+  float2 hu[2][6], hl[2][6];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { hu[j][k] = make_float2(0.f, 0.f); hl[j][k] = make_float2(0.f, 0.f); }
+  issue(0, src(0));
+  float2 lc[9];
+  load_link(0, lc);
+  auto step = [&](auto hc) {
+    constexpr int H = decltype(hc)::value;
+    constexpr bool more = H + 1 < 8 || MODE != 2;  // an operand follows hop H
+    if constexpr (more) issue((H + 1) & 1, src(H + 1));
+    float2 ln[9];
+    if constexpr (H + 1 < 8) load_link(H + 1, ln);
+    if constexpr (more) cpa_wait<1>();
+    else cpa_wait<0>();
+    float4 qv[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) qv[k] = st[((H & 1) * 12 + k) * kCpThreads];
+    hop2l<H / 2, (H % 2) == 0, DAG>(lc, qv, hu, hl);
+    if constexpr (H + 1 < 8) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) lc[k] = ln[k];
+    }
+  };
+  step(std::integral_constant<int, 0>{});
+  step(std::integral_constant<int, 1>{});
+  step(std::integral_constant<int, 2>{});
+  step(std::integral_constant<int, 3>{});
+  step(std::integral_constant<int, 4>{});
+  step(std::integral_constant<int, 5>{});
+  step(std::integral_constant<int, 6>{});
+  step(std::integral_constant<int, 7>{});
+  float2* y = out + own * 12 * rs + r0;
+  if constexpr (MODE == 1) issue(1, src(9));  // b, into the stage hop 7 used
+  if constexpr (MODE != 2) cpa_wait<0>();
+  const float4* xs = st;                  // own input or z: stage 0
+  const float4* bs = st + 12 * kCpThreads;  // b: stage 1
+  if constexpr (!eo) {
+    const float te = DAG ? -tau : tau;
+    const float2 mup = make_float2(mass, te);
+    const float2 mlo = make_float2(mass, -te);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const float4 xv = xs[k * kCpThreads];
+      const float2 m = k < 6 ? mup : mlo;
+      float2 v0 = cmul(m, make_float2(xv.x, xv.y));
+      float2 v1 = cmul(m, make_float2(xv.z, xv.w));
+      const float2 h0 = k < 6 ? hu[0][k] : hl[0][k - 6];
+      const float2 h1 = k < 6 ? hu[1][k] : hl[1][k - 6];
+      v0.x = fmaf(-0.5f, h0.x, v0.x);
+      v0.y = fmaf(-0.5f, h0.y, v0.y);
+      v1.x = fmaf(-0.5f, h1.x, v1.x);
+      v1.y = fmaf(-0.5f, h1.y, v1.y);
+      if constexpr (MODE == 1) {
+        const float4 bv = bs[k * kCpThreads];
+        v0 = make_float2(bv.x - v0.x, bv.y - v0.y);
+        v1 = make_float2(bv.z - v1.x, bv.w - v1.y);
+      }
+      __stcs(reinterpret_cast<float4*>(y + k * rs), make_float4(v0.x, v0.y, v1.x, v1.y));
+    }
+  } else {
+    const float2 q1u = make_float2((float)q.q1[0].x, (float)q.q1[0].y), q1l = make_float2((float)q.q1[1].x, (float)q.q1[1].y);
+    const float2 q2u = make_float2((float)q.q2[0].x, (float)q.q2[0].y), q2l = make_float2((float)q.q2[1].x, (float)q.q2[1].y);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const float2 qa = k < 6 ? q2u : q2l, qb = k < 6 ? q1u : q1l;
+      float2 v0 = cmul(qa, k < 6 ? hu[0][k] : hl[0][k - 6]);
+      float2 v1 = cmul(qa, k < 6 ? hu[1][k] : hl[1][k - 6]);
+      if constexpr (MODE == 3) {
+        const float4 zv = xs[k * kCpThreads];
+        v0 = cadd(v0, cmul(qb, make_float2(zv.x, zv.y)));
+        v1 = cadd(v1, cmul(qb, make_float2(zv.z, zv.w)));
+      }
+      *reinterpret_cast<float4*>(y + k * rs) = make_float4(v0.x, v0.y, v1.x, v1.y);
+    }
+  }
+}
+
+// Launch of k_wilson_cp over chunks of 2 rc2 columns; false when it does not
+// apply (odd nrhs, fields not 16-byte aligned, rc2 not dividing nrhs / 2).
+template <bool DAG, int MODE>
+bool launch_cp(qd_ctx& ctx, const float2* U, const int* nbr, const int* visit, int64_t V, int nrhs, int rc2,
+               float mass, float tau, const EoCoef& q, int p, const float2* in, const float2* aux, float2* out) {
+  if (nrhs % 2 != 0 || rc2 <= 0 || (nrhs / 2) % rc2 != 0) return false;
+  if (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(aux) | reinterpret_cast<uintptr_t>(out)) & 15) !=
+      0)
+    return false;
+  const int64_t nslots = MODE >= 2 ? V / 2 : V;
+  const int64_t tot = nslots * (nrhs / 2);
+  if (tot == 0) return true;
+  auto kern = k_wilson_cp<DAG, MODE>;
+  ensure_smem_limit(reinterpret_cast<const void*>(kern), kCpSmem);
+  kern<<<(int)div_up(tot, kCpThreads), kCpThreads, kCpSmem, ctx.stream>>>(U, nbr, visit, V, nrhs, rc2, mass, tau, q, p,
+                                                                          in, aux, out);
+  QD_LAUNCH_CHECK();
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -873,6 +1045,16 @@ void wilson_eo(qd_ctx& ctx, const LevelGeom& geo, const C* links, int p, const c
     // shapes 0-2; nrhs a multiple of 64
     auto launch_any = [&](int c) -> bool {
       if (c < 4) return launch(c);
+      if (c >= 7) {  // the next hop's operands in flight behind the current one (k_wilson_cp)
+        const int rc = c == 8 ? 64 : nrhs;
+        if (c == 8 && (nrhs <= 64 || nrhs % 64 != 0)) return false;
+        const float2* Lf = reinterpret_cast<const float2*>(links);
+        const float2* xin = reinterpret_cast<const float2*>(in);
+        const float2* zz = reinterpret_cast<const float2*>(z);
+        float2* yo = reinterpret_cast<float2*>(out);
+        return z ? launch_cp<false, 3>(ctx, Lf, nb, vis, geo.nsites, nrhs, rc / 2, 0.f, 0.f, q, p, xin, zz, yo)
+                 : launch_cp<false, 2>(ctx, Lf, nb, vis, geo.nsites, nrhs, rc / 2, 0.f, 0.f, q, p, xin, zz, yo);
+      }
       BulkArgs a{};
       a.U = reinterpret_cast<const float2*>(links);
       a.nbr = nb;
@@ -892,7 +1074,7 @@ void wilson_eo(qd_ctx& ctx, const LevelGeom& geo, const C* links, int p, const c
     // out-of-place (out differs from in and z): safe to time
     const std::string key = "wilson eo f32 sites" + std::to_string(geo.nsites) + " rhs" + std::to_string(nrhs) +
                             (z ? " z" : "");
-    const int c = (out == in || out == z) ? -1 : tune_pick(ctx, key, 7, launch_any);
+    const int c = (out == in || out == z) ? -1 : tune_pick(ctx, key, 9, launch_any);
     if (c >= 4 && launch_any(c)) return;
     if (c < 0 || !launch(c)) launch(0);
     return;
@@ -1031,8 +1213,28 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
     if (b) return dagger ? launch_bulk_shape<true, 1>(ctx, a, shape) : launch_bulk_shape<false, 1>(ctx, a, shape);
     return dagger ? launch_bulk_shape<true, 0>(ctx, a, shape) : launch_bulk_shape<false, 0>(ctx, a, shape);
   };
+  // candidates 13-14: the next hop's operands in flight behind the current
+  // one (k_wilson_cp), columns swept whole or in chunks of 64
+  auto launch_cp_c = [&](int rc) -> bool {
+    if (sizeof(C) != 8) return false;
+    if (rc <= 0) rc = nrhs;
+    if (rc > nrhs || nrhs % rc != 0 || rc % 2 != 0) return false;
+    const float2* Lf = reinterpret_cast<const float2*>(links);
+    const float2* xin = reinterpret_cast<const float2*>(in);
+    const float2* bb = reinterpret_cast<const float2*>(b);
+    float2* yo = reinterpret_cast<float2*>(out);
+    const float fm = (float)mass, ft = (float)tau;
+    const EoCoef q0{};
+    if (b)
+      return dagger ? launch_cp<true, 1>(ctx, Lf, nb, vis, geo.nsites, nrhs, rc / 2, fm, ft, q0, 0, xin, bb, yo)
+                    : launch_cp<false, 1>(ctx, Lf, nb, vis, geo.nsites, nrhs, rc / 2, fm, ft, q0, 0, xin, bb, yo);
+    return dagger ? launch_cp<true, 0>(ctx, Lf, nb, vis, geo.nsites, nrhs, rc / 2, fm, ft, q0, 0, xin, bb, yo)
+                  : launch_cp<false, 0>(ctx, Lf, nb, vis, geo.nsites, nrhs, rc / 2, fm, ft, q0, 0, xin, bb, yo);
+  };
   auto launch = [&](int c) -> bool {
     switch (c) {
+      case 13: return launch_cp_c(0);
+      case 14: return nrhs > 64 && launch_cp_c(64);
       case 10: case 11: case 12: return launch_bulk_c(c - 10);
       case 0: return launch_x2(0, 128);
       case 1: return launch_x1();
@@ -1049,7 +1251,7 @@ void wilson_apply(qd_ctx& ctx, const LevelGeom& geo, const C* links, double m0, 
   // the residual form writes out = b - A in: out-of-place, safe to repeat
   const std::string key = std::string("wilson f32 sites") + std::to_string(geo.nsites) + " rhs" +
                           std::to_string(nrhs) + (b ? " resid" : "") + (dagger ? " dag" : "");
-  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 13, launch);
+  const int c = (out == b || out == in) ? -1 : tune_pick(ctx, key, 15, launch);
   if (c >= 0 && launch(c)) return;
   if (!launch_x2(0, 128)) launch_x1();
 }

@@ -107,10 +107,11 @@ def test_wilson_fp32_matches_oracle(qd, ctx, dims, s, tau, dag):
 @pytest.mark.parametrize("dims,s", [((4, 4, 4, 4), 64), ((8, 8, 8, 8), 64), ((8, 4, 6, 2), 128),
                                     ((6, 6, 6, 6), 128)])
 @pytest.mark.parametrize("tau,dag", [(0.0, False), (0.25, True)])
-def test_wilson_fp32_bulk_staged_matches_oracle(qd, ctx, dims, s, tau, dag):
-    # the stencil with its operands staged in shared memory by bulk copies
+def test_wilson_fp32_staged_matches_oracle(qd, ctx, dims, s, tau, dag):
+    # the stencil with its operands staged in shared memory: by bulk copies
     # (launch shapes 10-12: rings of 8 warps x 4 slots, 4 x 8 and 6 x 5; one
-    # to seven sites per warp here, the last round of sites ragged), as
+    # to seven sites per warp here, the last round of sites ragged) and by
+    # cp.async one hop ahead (13-14: columns whole or in chunks of 64), as
     # A x and as the residual b - A x, against the oracle (tolerance as
     # above); every output element written (NaN-filled outputs) and equal to
     # the register-only form to FP32 rounding
@@ -129,7 +130,7 @@ def test_wilson_fp32_bulk_staged_matches_oracle(qd, ctx, dims, s, tau, dag):
         qd.dirac_apply_f32(ctx, g, -0.8, tau, dag, s, xin, y0)
         r0 = torch.empty_like(xin)
         qd.dirac_residual_f32(ctx, g, -0.8, tau, dag, s, bin_, xin, r0)
-        for cand in (10, 11, 12):
+        for cand in (10, 11, 12, 13, 14):
             qd.autotune_force(cand)
             y = torch.full_like(xin, float("nan"))
             qd.dirac_apply_f32(ctx, g, -0.8, tau, dag, s, xin, y)

@@ -51,28 +51,29 @@ def test_schur_operator_against_oracle(qd, ctx, dims, tau):
         qd.dirac_schur_apply_f32(ctx, g, m0, tau, s, x32, y32)
         assert rel_err(host(y32).astype(np.complex128), ref) < 1e-5, s
         # the launch shapes of the parity-restricted hops: whole, chunks of 64
-        # and 32 columns (the same bits), projection on load and the operands
-        # staged by bulk copies (4-6, nrhs a multiple of 64; rounding)
+        # and 32 columns (the same bits), projection on load, the operands
+        # staged by bulk copies (4-6, nrhs a multiple of 64) or by cp.async
+        # one hop ahead (7-8) (rounding)
         try:
             outs = []
-            for cand in range(7):
+            for cand in range(9):
                 qd.autotune_force(cand)
                 o = torch.full_like(x32, float("nan"))
                 qd.dirac_schur_apply_f32(ctx, g, m0, tau, s, x32, o)
                 outs.append(o)
             assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2]), s
-            for cand in (3, 4, 5, 6):
+            for cand in (3, 4, 5, 6, 7, 8):
                 assert rel_err(host(outs[cand]), host(outs[0])) < 1e-6, (s, cand)
         finally:
             qd.autotune_force(-1)
     g.close()
 
 
-def test_schur_bulk_staged_several_sites_per_warp(qd, ctx):
-    # the bulk-staged parity-restricted hops where each warp takes several
-    # sites (8^4: 2048 odd sites, 4096 units of 64 columns at 128 rhs, the
-    # last round ragged) against the oracle's S (sampled columns, FP32
-    # tolerance as above)
+def test_schur_staged_hops_at_8x4(qd, ctx):
+    # the staged parity-restricted hops on 8^4 at 128 rhs: bulk-staged (4-6;
+    # each warp takes several sites, 4096 units of 64 columns, the last
+    # round ragged) and cp.async-staged (7-8), against the oracle's S
+    # (sampled columns, FP32 tolerance as above)
     dims, m0, tau, s = (8, 8, 8, 8), -0.6, 0.1, 128
     U = synth.random_su3_links(dims, 0.3, 6)
     g = qd.Gauge(ctx, dims, U)
@@ -83,7 +84,7 @@ def test_schur_bulk_staged_several_sites_per_warp(qd, ctx):
     cols = [0, 63, 64, 127]
     ref = S @ host(x32).astype(np.complex128)[:, cols]
     try:
-        for cand in (4, 5, 6):
+        for cand in (4, 5, 6, 7, 8):
             qd.autotune_force(cand)
             o = torch.full_like(x32, float("nan"))
             qd.dirac_schur_apply_f32(ctx, g, m0, tau, s, x32, o)

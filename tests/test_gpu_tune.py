@@ -68,8 +68,9 @@ def test_wilson_f32_launch_shapes(qd, ctx):
     # (0) or in chunks of 64, 32 or 16 columns with blocks of 128-512
     # threads (2-7) -- the same arithmetic per element, so the same bits --
     # the neighbours projected as they load (8-9) and one column per thread
-    # (1) and the operands staged in shared memory by bulk copies (10-12),
-    # which agree to FP32 rounding; A and A^H
+    # (1) and the operands staged in shared memory by bulk copies (10-12) or
+    # by cp.async one hop ahead (13-14), which agree to FP32 rounding; A and
+    # A^H
     dims = (8, 8, 8, 8)
     U = synth.random_su3_links(dims, 0.3, 2)
     g = qd.Gauge(ctx, dims, U)
@@ -79,7 +80,7 @@ def test_wilson_f32_launch_shapes(qd, ctx):
                              generator=torch.Generator("cuda:0").manual_seed(s))
             for dag in (False, True):
                 outs = {}
-                for cand in range(13):
+                for cand in range(15):
                     qd.autotune_force(cand)
                     yf = torch.full_like(xf, float("nan"))
                     qd.dirac_apply_f32(ctx, g, -0.8, 0.1, dag, s, xf, yf)
@@ -89,7 +90,9 @@ def test_wilson_f32_launch_shapes(qd, ctx):
                 for cand in (8, 9):  # projection on load: the same sums, possibly contracted differently
                     assert rel_err(host(outs[cand]), host(outs[0])) < 1e-6, (s, dag, cand)
                 assert rel_err(host(outs[1]), host(outs[0])) < 1e-6, (s, dag)
-                for cand in (10, 11, 12):  # operands staged by bulk copies (nrhs a multiple of 64)
+                # operands staged by bulk copies (10-12, nrhs a multiple of 64) or
+                # by cp.async one hop ahead (13-14)
+                for cand in (10, 11, 12, 13, 14):
                     assert rel_err(host(outs[cand]), host(outs[0])) < 1e-6, (s, dag, cand)
     finally:
         qd.autotune_force(-1)

@@ -4,14 +4,17 @@ Default workload (the mixed-precision estimator configuration of the
 metric): Wilson-Dirac operator on a 16^3 x 32 periodic lattice
 (N = 1,572,864), random SU(3) links exp(i 0.2 H) (seed 3), m0 = -0.8;
 three-level multigrid (2^4 then 2^4 aggregates, 12 and 16 null vectors per
-chirality; level-1 GCR of 6 iterations, two minimal-residual smoothing steps
-on the coarse levels, dense coarsest inverse applied on tensor cores);
-Algorithm 2 deflation of rank 24 on the coarsest level; 128 real Rademacher
-samples per step solved together, each to ||b - A x|| <= 1e-8 ||b|| on the
-FP64 residual.  The path: FP32 flexible GCR and FP32 V-cycle (learned
-smoother + 1 MR step on the fine level, tensor-core coarse stencil) inside
-FP64 residual refinement.  The plain FP64 form (FP64 GCR and V-cycle, plain
-minimal-residual smoother) is timed on the same lattice ("fp64_path").
+chirality, FP32 null-vector iterations; level-1 GCR of 6 iterations, one
+minimal-residual smoothing step on the coarse levels, dense coarsest inverse
+applied on tensor cores); Algorithm 2 deflation of rank 24 on the coarsest
+level; 128 real Rademacher samples per step solved together, each to
+||b - A x|| <= 1e-8 ||b|| on the FP64 residual.  The path: FP32 flexible
+GCR(4) on the odd-site Schur complement (even-odd solve) and the FP32
+V-cycle (two-layer learned smoother on the fine level with no MR step after
+it, tensor-core coarse stencil and restriction) inside FP64 residual
+refinement.  The plain FP64 form (full-lattice FP64 GCR(16) and V-cycle,
+plain minimal-residual smoother) is timed on the same lattice
+("fp64_path").
 
 A step = one batch through the whole sample path: Rademacher noise (a1),
 deflation projection (a8, with the Wilson and transfer kernels), the
@@ -60,8 +63,8 @@ CONFIG3 = dict(
     mg_kw={"coarse_tol": 0.0, "coarse_maxit": 6, "coarse_smoother_steps": 1, "null_f32": 1},
     learned=1, learned_mr=0, layers=2, eig_maxit=30, fp64_samples=16,
 )
-# Config 2: 8^4 lattice (the two-level workload of round one), kept for
-# comparison with earlier numbers.
+# Config 2: 8^4 lattice, two-level multigrid, kept for comparison with
+# earlier numbers.
 CONFIG2 = dict(
     workload="wilson-dirac 8^4 eps0.3 seed2 m0=-0.8, 2-level MG (2^4 blocks, nv 12; learned smoother + 1 MR), "
              "Algorithm 2 k=24, 64 Rademacher samples/step, true FP64 rel. residual 1e-8",

@@ -146,7 +146,10 @@ int qd_dirac_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0, double tau,
  * solves): in/out are interleaved complex float (re, im) in qd layout,
  * links rounded once to FP32 and cached on the gauge (the first call
  * allocates that copy, so gauge is not const).  Same errors as
- * qd_dirac_apply.  Asynchronous. */
+ * qd_dirac_apply; a bounded wait of the stencil's bulk-staged launch shape
+ * that gives up is reported as QD_ERR_TIMEOUT by the next synchronising
+ * call on the gauge (qd_dirac_schur_apply_f32, qd_solve,
+ * qd_hutchinson_trace).  Asynchronous. */
 int qd_dirac_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau,
                        int dagger, int nrhs, const float* in, float* out);
 
@@ -169,7 +172,8 @@ int qd_dirac_residual_f32(qd_ctx* ctx, qd_gauge* gauge, double m0, double tau,
 int qd_dirac_schur_apply(qd_ctx* ctx, const qd_gauge* gauge, double m0,
                          double tau, int nrhs, const double* in, double* out);
 /* The same in FP32 (interleaved complex float, links as
- * qd_dirac_apply_f32). */
+ * qd_dirac_apply_f32); QD_ERR_TIMEOUT when a bounded wait of the stencil
+ * gave up in this or an earlier FP32 stencil call on the gauge. */
 int qd_dirac_schur_apply_f32(qd_ctx* ctx, qd_gauge* gauge, double m0,
                              double tau, int nrhs, const float* in,
                              float* out);

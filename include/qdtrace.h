@@ -369,6 +369,7 @@ typedef struct {
                         0 (default): GCR on A itself */
 } qd_solver_params;
 
+/* Fills *p with the defaults given beside each field above (NULL: no-op). */
 void qd_solver_params_default(qd_solver_params* p);
 
 typedef struct {
@@ -428,6 +429,7 @@ typedef struct {
                           as stagnated without solving (0) */
 } qd_defl_params;
 
+/* Fills *p with the defaults given beside each field above (NULL: no-op). */
 void qd_defl_params_default(qd_defl_params* p);
 
 /* Build a deflation space for A(m0, tau) (tau taken from mg for kind 2).
@@ -629,6 +631,7 @@ typedef struct {
   int enabled;         /* err_learned < err_plain: the V-cycle now uses S */
 } qd_smoother_info;
 
+/* Fills *p with the defaults given beside each field above (NULL: no-op). */
 void qd_smoother_params_default(qd_smoother_params* p);
 
 /* Train on pairs the solver generates: for random vectors v (Philox starts,

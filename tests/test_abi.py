@@ -38,6 +38,27 @@ def test_exports_every_declared_symbol(library):
     assert set(names) == set(qd.SIGNATURES), "binding and header disagree"
 
 
+def test_every_declaration_is_documented():
+    # each function the header declares has a comment block right before it
+    # (or before the group of declarations it belongs to)
+    lines = open(HEADER).read().split("\n")
+    decl = re.compile(r"^(?:const\s+)?(?:int|void|long long|double|char|size_t)\b[\s*]*(qd_[a-z0-9_]+)\s*\(")
+    missing = []
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        j = i - 1
+        while j >= 0 and (not lines[j].strip() or lines[j].startswith(" ") or decl.match(lines[j])
+                          or lines[j].rstrip().endswith(");")):
+            if lines[j].rstrip().endswith("*/"):
+                break
+            j -= 1
+        if j < 0 or not lines[j].rstrip().endswith("*/"):
+            missing.append(m.group(1))
+    assert not missing, missing
+
+
 def test_abi_version(library):
     assert library.qd_abi_version() == 6
 
